@@ -1,0 +1,264 @@
+"""Damped parallel EP with the l1-TV prior, and its EM update (oracle, FP64).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+State (Sec. III-A): five Gaussian sites per pixel, q_{x,0} for the likelihood
+and q_{x,k}, k = 1..4, one per matching V_k.  All covariances are diagonal, so
+a site is a pair of per-pixel natural parameters: precision tau = 1/Sigma and
+precision-times-mean nu = mu / Sigma.  Arrays ``tau`` and ``nu`` have shape
+(5, N), row s holding site s.
+
+The global approximation (Eq. Q_x_final) is tau_x = sum_s tau_s,
+nu_x = sum_s nu_s, mu_x = nu_x / tau_x, Sigma_x = 1 / tau_x.  The cavity of
+site s (Sec. III-B) is the product of the other four sites, i.e. the sums over
+s' != s; the oracle recomputes it from the sites every time it needs it.
+
+One sweep (Algorithm 1) updates q_{x,0} and the four q_{x,k}; all edges of one
+V_k are updated together ("in parallel").  The readings of the points the
+paper leaves open are:
+
+* order: ``"prior_first"`` (default) runs the four V_k updates and then the
+  q_{x,0} update, so that the initial q_{x,0} of Algorithm 1 is used;
+  ``"q0_first"`` follows the listing literally.  For denoising the two agree
+  because the q_{x,0} update returns the site unchanged.
+* k order: 1, 2, 3, 4 unless an explicit order is passed per sweep.
+* variance cap (Sec. III-C): a new site precision below 1/var_cap (negative or
+  larger-than-cap variance) is set to 1/var_cap before the mean is formed.
+* damping: natural parameters are mixed, new = a * updated + (1 - a) * old,
+  with a the weight on the updated value; applied to every site.
+* EM (Sec. IV, Algorithm 2, Option 3, Eq. 3rd_alternative_a0): the statistic
+  a_u is the sum over the four V_k of E_{P_k}|u_n| over all edges, taken at the
+  tilted distributions of the last sweep, and lam = N / a_u with N the number
+  of pixels.
+* initialisation (Algorithm 1): mu_{x,0} = y, Sigma_{x,0} = xi I, the other
+  sites have zero mean and variance var_cap.  For compressive sensing y has
+  length M < N; the oracle uses mu_{x,0} = H^T y.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+import scipy.linalg
+
+from . import operators
+from .partition import edges
+from .tilted import laplace_tilted
+
+
+class EPOracle:
+    """Algorithm 1 / Algorithm 2 in FP64.
+
+    Parameters
+    ----------
+    kind : "denoise", "deconv" or "cs"
+    y : observation, (H, W) for denoise/deconv, (M,) for cs
+    xi : noise variance (Eq. likelihood)
+    lam : TV parameter lambda (Eq. L1_TV)
+    height, width : image size
+    kernel : blur kernel for "deconv"
+    A : M x N sensing matrix for "cs"
+    site0 : how the tilted moments of P_0 (Eq. tilted_P_1) are formed.
+        "exact": dense inverse of Cov_P0^{-1} (small N only).
+        "woodbury": Woodbury identity (cs; H^T H low rank).
+        "rbmc": mean by a dense solve, variance by the Rao-Blackwellised
+        Monte Carlo estimator with the given fixed probes (deconv).
+    probes : (eps1 (S, M), eps2 (S, N)) standard normals for "rbmc".
+    """
+
+    def __init__(self, kind: str, y: np.ndarray, xi: float, lam: float,
+                 height: int, width: int, kernel: Optional[np.ndarray] = None,
+                 A: Optional[np.ndarray] = None, damping: float = 0.5,
+                 var_cap: float = 1e8, periodic: bool = True,
+                 order: str = "prior_first", site0: str = "exact",
+                 probes=None):
+        if kind not in ("denoise", "deconv", "cs"):
+            raise ValueError(kind)
+        self.kind = kind
+        self.height, self.width = int(height), int(width)
+        self.n = self.height * self.width
+        self.y = np.asarray(y, dtype=np.float64).reshape(-1)
+        self.xi = float(xi)
+        self.lam = float(lam)
+        self.kernel = None if kernel is None else np.asarray(kernel, np.float64)
+        self.A = None if A is None else np.asarray(A, np.float64)
+        self.damping = float(damping)
+        self.var_cap = float(var_cap)
+        self.periodic = bool(periodic)
+        self.order = order
+        self.site0 = site0
+        self.probes = probes
+        self.edge_lists = [edges(self.height, self.width, k, self.periodic) for k in (1, 2, 3, 4)]
+        self.abar = 0.0          # sum of E|u| over the edges of the last sweep
+        self.n_sweeps = 0
+        self.init()
+
+    # ------------------------------------------------------------------ state
+    def init(self):
+        """Initialisation of Algorithm 1 in natural parameters."""
+        n = self.n
+        self.tau = np.zeros((5, n))
+        self.nu = np.zeros((5, n))
+        if self.kind == "cs":
+            mu0 = self.A.T @ self.y
+        else:
+            mu0 = self.y.copy()
+        self.tau[0] = 1.0 / self.xi
+        self.nu[0] = mu0 / self.xi
+        self.tau[1:] = 1.0 / self.var_cap
+        self.nu[1:] = 0.0
+
+    def cavity(self, s: int):
+        """Cavity of site s (product of the other sites): (c, m) = variance, mean."""
+        others = [t for t in range(5) if t != s]
+        tau_c = self.tau[others].sum(axis=0)
+        nu_c = self.nu[others].sum(axis=0)
+        return 1.0 / tau_c, nu_c / tau_c
+
+    def posterior(self):
+        """Eq. Q_x_final: mean and marginal variance of Q(x)."""
+        tau_x = self.tau.sum(axis=0)
+        nu_x = self.nu.sum(axis=0)
+        sigma = 1.0 / tau_x
+        mu = sigma * nu_x
+        return mu.reshape(self.height, self.width), sigma.reshape(self.height, self.width)
+
+    # ---------------------------------------------------------- site updates
+    def _new_site(self, E, Var, c, m):
+        """Eq. update_qk_x / Eq. update_q0_x with the variance cap, natural form."""
+        tau_new = 1.0 / Var - 1.0 / c
+        capped = tau_new < 1.0 / self.var_cap
+        tau_new = np.where(capped, 1.0 / self.var_cap, tau_new)
+        sigma_site = 1.0 / tau_new
+        # mu_site = Sigma_site [(Sigma_site^-1 + Sigma_cav^-1) E - Sigma_cav^-1 m]
+        mu_site = sigma_site * ((tau_new + 1.0 / c) * E - m / c)
+        return tau_new, mu_site * tau_new
+
+    def _damp(self, s: int, idx, tau_new, nu_new):
+        a = self.damping
+        self.tau[s, idx] = a * tau_new + (1.0 - a) * self.tau[s, idx]
+        self.nu[s, idx] = a * nu_new + (1.0 - a) * self.nu[s, idx]
+
+    def prior_update(self, k: int) -> float:
+        """Update q_{x,k} and Q(u_k) for all edges of V_k at once; return sum E|u|."""
+        first, second = self.edge_lists[k - 1]
+        if first.size == 0:
+            return 0.0
+        c, m = self.cavity(k)
+        ci, cj = c[first], c[second]
+        mi, mj = m[first], m[second]
+        # Eq. marginal_tilted_un
+        mu_u = mi - mj
+        s2 = ci + cj
+        m_bar, S_bar, eabs = laplace_tilted(mu_u, s2, self.lam)
+        # projection of the edge moments onto (x_i, x_j) (Sec. III-C)
+        Ei = mi + (m_bar - mu_u) / s2 * ci
+        Ej = mj - (m_bar - mu_u) / s2 * cj
+        Vi = ci + (S_bar - s2) / s2 ** 2 * ci ** 2
+        Vj = cj + (S_bar - s2) / s2 ** 2 * cj ** 2
+        tau_i, nu_i = self._new_site(Ei, Vi, ci, mi)
+        tau_j, nu_j = self._new_site(Ej, Vj, cj, mj)
+        self._damp(k, first, tau_i, nu_i)
+        self._damp(k, second, tau_j, nu_j)
+        return float(np.sum(eabs))
+
+    def tilted_p0(self, c: np.ndarray, m: np.ndarray):
+        """Mean and marginal variances of P_0 (Eq. tilted_P_1) for cavity (c, m)."""
+        if self.kind == "denoise":
+            var = 1.0 / (1.0 / self.xi + 1.0 / c)
+            return var * (self.y / self.xi + m / c), var
+        H, Hty = self._operator()
+        if self.site0 == "woodbury":
+            return self._woodbury(H, c, m)
+        Q = H.T @ H / self.xi + np.diag(1.0 / c)
+        b = Hty / self.xi + m / c
+        cho = scipy.linalg.cho_factor(Q, lower=True)
+        E = scipy.linalg.cho_solve(cho, b)
+        if self.site0 == "exact":
+            cov = scipy.linalg.cho_solve(cho, np.eye(self.n))
+            return E, np.diag(cov).copy()
+        if self.site0 == "rbmc":
+            return E, self._rbmc_var(H, Q, cho, c)
+        raise ValueError(self.site0)
+
+    def _operator(self):
+        """Dense H and H^T y (built once; the convolution from its definition)."""
+        if getattr(self, "_H", None) is None:
+            if self.kind == "deconv":
+                self._H = operators.conv_matrix(self.height, self.width, self.kernel)
+                self._Hty = operators.conv_periodic_t(
+                    self.y.reshape(self.height, self.width), self.kernel).reshape(-1)
+            else:
+                self._H = self.A
+                self._Hty = self.A.T @ self.y
+        return self._H, self._Hty
+
+    def _rbmc_var(self, H, Q, cho, c):
+        """Rao-Blackwellised Monte Carlo estimate of diag(Q^{-1}).
+
+        Samples z_s ~ N(0, Q^{-1}) are drawn by perturbation: z_s solves
+        Q z_s = H^T eps1_s / sqrt(xi) + eps2_s / sqrt(c), whose right-hand side has
+        covariance H^T H / xi + diag(1/c) = Q.  For each pixel, x_i given the
+        other pixels is Gaussian with variance 1/Q_ii and mean
+        -(1/Q_ii) sum_{j != i} Q_ij z_j, so
+        Var_i = 1/Q_ii + (1/S) sum_s ((sum_{j != i} Q_ij z_{s,j}) / Q_ii)^2.
+        """
+        eps1, eps2 = self.probes
+        S = eps1.shape[0]
+        qdiag = np.diag(Q).copy()
+        acc = np.zeros(self.n)
+        for s in range(S):
+            w = H.T @ eps1[s] / math.sqrt(self.xi) + eps2[s] / np.sqrt(c)
+            z = scipy.linalg.cho_solve(cho, w)
+            off = Q @ z - qdiag * z
+            acc += (off / qdiag) ** 2
+        return 1.0 / qdiag + acc / S
+
+    def _woodbury(self, H, c, m):
+        """Cov_P0 = C - C H^T (xi I + H C H^T)^{-1} H C with C = diag(c)."""
+        K = self.xi * np.eye(H.shape[0]) + (H * c[None, :]) @ H.T
+        cho = scipy.linalg.cho_factor(K, lower=True)
+        KinvH = scipy.linalg.cho_solve(cho, H)
+        var = c - c * c * np.einsum("mi,mi->i", H, KinvH)
+        E = m + c * (H.T @ scipy.linalg.cho_solve(cho, self.y - H @ m))
+        return E, var
+
+    def site0_update(self):
+        """Update q_{x,0} (Eq. tilted_P_1 then Eq. update_q0_x)."""
+        c, m = self.cavity(0)
+        E, Var = self.tilted_p0(c, m)
+        tau_new, nu_new = self._new_site(E, Var, c, m)
+        self._damp(0, slice(None), tau_new, nu_new)
+
+    # ------------------------------------------------------------ algorithms
+    def sweep(self, k_order: Optional[Sequence[int]] = None) -> float:
+        """One iteration of Algorithm 1; returns a_u of this sweep."""
+        order = list(k_order) if k_order is not None else [1, 2, 3, 4]
+        if sorted(order) != [1, 2, 3, 4]:
+            raise ValueError("k_order must be a permutation of 1..4")
+        abar = 0.0
+        if self.order == "q0_first":
+            self.site0_update()
+        for k in order:
+            abar += self.prior_update(k)
+        if self.order == "prior_first":
+            self.site0_update()
+        self.abar = abar
+        self.n_sweeps += 1
+        return abar
+
+    def em_update(self) -> float:
+        """M-step of Algorithm 2 with Option 3: lam = N / a_u of the last sweep."""
+        self.lam = self.n / self.abar
+        return self.lam
+
+    def run(self, n_sweeps: int, em_every: int = 0, k_orders=None):
+        """n_sweeps sweeps; with em_every > 0, lam is updated after every
+        em_every-th sweep.  Returns the list of lam values after each update."""
+        lams = []
+        for t in range(n_sweeps):
+            self.sweep(None if k_orders is None else k_orders[t])
+            if em_every and (t + 1) % em_every == 0:
+                lams.append(self.em_update())
+        return lams

@@ -1,0 +1,340 @@
+"""Pins that tie the FP64 oracle to the paper and to mathematics, not to itself.
+
+Each test checks the oracle against something it does not compute itself:
+high-precision quadrature, textbook closed forms, an exact special case of the
+method, brute-force enumeration, FFT closed forms or a symmetry of the model.
+"""
+import math
+
+import mpmath as mp
+import numpy as np
+import pytest
+from scipy.stats import norm
+
+from oracle import operators
+from oracle.ep import EPOracle
+from oracle.partition import edges
+from oracle.tilted import laplace_tilted
+from paper_2110_01585_gb300 import synthetic as syn
+
+
+# ---------------------------------------------------------------- tilted moments
+def _quad_tilted(mu, s2, lam, dps=30):
+    """Mean, variance and E|u| of N(u; mu, s2) exp(-lam|u|) by mpmath quadrature
+    of the raw integrand on a grid refined around the kink and the modes."""
+    mp.mp.dps = dps
+    mu, s2, lam = mp.mpf(mu), mp.mpf(s2), mp.mpf(lam)
+    s = mp.sqrt(s2)
+
+    def f(u):
+        return mp.exp(-(u - mu) ** 2 / (2 * s2) - lam * abs(u))
+
+    pts = set()
+    for md in (max(mp.mpf(0), mu - lam * s2), min(mp.mpf(0), mu + lam * s2), mp.mpf(0)):
+        for k in range(-30, 31):
+            pts.add(md + k * s / 2)
+    a_plus, a_minus = lam * s - mu / s, lam * s + mu / s
+    for a, sign in ((a_plus, 1), (a_minus, -1)):
+        if a > 1:
+            for k in range(0, 61):
+                pts.add(sign * k * s / a / 2)
+    pts = sorted(pts)
+    grid = [pts[0] - 20 * s] + pts + [pts[-1] + 20 * s]
+    z = mp.quad(f, grid)
+    m1 = mp.quad(lambda u: u * f(u), grid) / z
+    var = mp.quad(lambda u: (u - m1) ** 2 * f(u), grid) / z
+    eabs = mp.quad(lambda u: abs(u) * f(u), grid) / z
+    return float(m1), float(var), float(eabs)
+
+
+QUAD_CASES = [(m, l) for m in (-50.0, -7.0, -0.3, 0.0, 3.0, 12.0, 50.0)
+              for l in (1e-4, 0.3, 4.0, 50.0)]
+
+
+@pytest.mark.parametrize("mu_over_s,lam_s", QUAD_CASES)
+def test_tilted_moments_match_quadrature(mu_over_s, lam_s):
+    """P1: the closed forms (erfcx and continued fraction) agree with quadrature to 1e-10."""
+    s2 = 0.04
+    s = math.sqrt(s2)
+    mu, lam = mu_over_s * s, lam_s / s
+    ref = _quad_tilted(mu, s2, lam)
+    got = [float(v[0]) for v in laplace_tilted(np.array([mu]), np.array([s2]), lam)]
+    assert abs(got[0] - ref[0]) <= 1e-10 * max(abs(ref[0]), 1e-3 * s)
+    assert abs(got[1] - ref[1]) <= 1e-10 * ref[1]
+    assert abs(got[2] - ref[2]) <= 1e-10 * ref[2]
+
+
+def test_tilted_lambda_zero_is_gaussian_and_folded_normal():
+    """lam = 0: the tilted law is N(mu, s2); E|u| is the folded-normal mean."""
+    rng = np.random.default_rng(3)
+    mu = rng.normal(size=200) * 3
+    s2 = rng.uniform(0.01, 4, size=200)
+    m, v, ea = laplace_tilted(mu, s2, 0.0)
+    s = np.sqrt(s2)
+    folded = s * math.sqrt(2 / math.pi) * np.exp(-mu ** 2 / (2 * s2)) + mu * (1 - 2 * norm.cdf(-mu / s))
+    np.testing.assert_allclose(m, mu, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(v, s2, rtol=1e-12)
+    np.testing.assert_allclose(ea, folded, rtol=1e-12)
+
+
+def test_tilted_log_concavity_and_symmetry():
+    """P6: for a log-concave factor the tilted variance never exceeds s2; the
+    moments are odd/even in mu because exp(-lam|u|) is even."""
+    rng = np.random.default_rng(4)
+    mu = rng.normal(size=2000) * 5
+    s2 = np.exp(rng.uniform(-8, 3, size=2000))
+    for lam in (0.01, 1.0, 30.0, 400.0):
+        m, v, ea = laplace_tilted(mu, s2, lam)
+        assert np.all(v <= s2 * (1 + 1e-13))
+        assert np.all(v > 0) and np.all(ea > 0)
+        m2, v2, ea2 = laplace_tilted(-mu, s2, lam)
+        np.testing.assert_allclose(m2, -m, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(v2, v, rtol=1e-12)
+        np.testing.assert_allclose(ea2, ea, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- partition
+@pytest.mark.parametrize("hw", [(2, 2), (4, 6), (6, 4), (8, 8)])
+def test_partition_is_four_matchings_covering_the_torus(hw):
+    h, w = hw
+    n = h * w
+    # brute-force list of the 2N torus edges (a multigraph when a side is 2)
+    torus = []
+    for r in range(h):
+        for c in range(w):
+            torus.append(tuple(sorted((r * w + c, r * w + (c + 1) % w))))
+            torus.append(tuple(sorted((r * w + c, ((r + 1) % h) * w + c))))
+    got = []
+    for k in (1, 2, 3, 4):
+        f, s = edges(h, w, k)
+        assert f.size == n // 2
+        # a matching: no pixel twice; every pixel exactly once
+        assert sorted(np.concatenate([f, s]).tolist()) == list(range(n))
+        got += [tuple(sorted(p)) for p in zip(f.tolist(), s.tolist())]
+    assert sorted(got) == sorted(torus)
+
+
+def test_partition_free_boundary_drops_wrap_edges():
+    h, w = 5, 7
+    total = 0
+    for k in (1, 2, 3, 4):
+        f, s = edges(h, w, k, periodic=False)
+        for a, b in zip(f.tolist(), s.tolist()):
+            ra, ca = divmod(a, w)
+            rb, cb = divmod(b, w)
+            assert abs(ra - rb) + abs(ca - cb) == 1
+        total += f.size
+    assert total == h * (w - 1) + (h - 1) * w
+
+
+# ---------------------------------------------------------------- operators
+def test_convolution_matches_fft_and_adjoint():
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(12, 10))
+    k = rng.random((5, 3))
+    np.testing.assert_allclose(operators.conv_periodic(x, k), syn.circular_blur(x, k), atol=1e-13)
+    z = rng.normal(size=(12, 10))
+    lhs = np.sum(z * operators.conv_periodic(x, k))
+    rhs = np.sum(x * operators.conv_periodic_t(z, k))
+    assert abs(lhs - rhs) < 1e-12
+
+
+# ---------------------------------------------------------------- exact 1x2 case
+def _exact_pair_moments(y, xi, lam, empty_tau):
+    """Moments of p(x1, x2) ~ N(y1; x1, xi) N(y2; x2, xi) exp(-lam|x1 - x2|)
+    exp(-empty_tau (x1^2 + x2^2) / 2) by 2-D Gauss-Legendre quadrature on the
+    two half-planes x1 > x2 and x1 < x2 (coordinates u = x1 - x2, v = x1 + x2)."""
+    sd = math.sqrt(xi)
+    nodes, weights = np.polynomial.legendre.leggauss(600)
+    v_lo, v_hi = y[0] + y[1] - 16 * sd, y[0] + y[1] + 16 * sd
+    u_span = abs(y[0] - y[1]) + 16 * sd
+    acc = np.zeros(6)
+    for u_lo, u_hi in ((-u_span, 0.0), (0.0, u_span)):
+        u = 0.5 * (u_hi - u_lo) * nodes + 0.5 * (u_hi + u_lo)
+        wu = 0.5 * (u_hi - u_lo) * weights
+        v = 0.5 * (v_hi - v_lo) * nodes + 0.5 * (v_hi + v_lo)
+        wv = 0.5 * (v_hi - v_lo) * weights
+        U, V = np.meshgrid(u, v, indexing="ij")
+        W = np.outer(wu, wv)
+        x1, x2 = (V + U) / 2, (V - U) / 2
+        logp = (-(y[0] - x1) ** 2 / (2 * xi) - (y[1] - x2) ** 2 / (2 * xi)
+                - lam * np.abs(x1 - x2) - empty_tau * (x1 ** 2 + x2 ** 2) / 2)
+        p = np.exp(logp) * W
+        acc += [p.sum(), (p * x1).sum(), (p * x2).sum(), (p * x1 ** 2).sum(),
+                (p * x2 ** 2).sum(), (p * np.abs(x1 - x2)).sum()]
+    z = acc[0]
+    m1, m2 = acc[1] / z, acc[2] / z
+    return m1, m2, acc[3] / z - m1 ** 2, acc[4] / z - m2 ** 2, acc[5] / z
+
+
+@pytest.mark.parametrize("y,xi,lam", [((0.3, 0.7), 0.01, 20.0), ((0.9, -0.2), 0.04, 3.0),
+                                      ((0.5, 0.52), 0.01, 80.0)])
+def test_one_by_two_image_is_exact(y, xi, lam):
+    """P2: with a single edge the tilted distribution is the exact posterior and
+    the projection is exact, so the EP fixed point has the exact marginals."""
+    o = EPOracle("denoise", np.array([y]), xi, lam, 1, 2, periodic=False)
+    o.run(80)
+    mu, var = o.posterior()
+    # sites 2, 3, 4 have no edge here and keep precision 1/var_cap each
+    m1, m2, v1, v2, eabs = _exact_pair_moments(y, xi, lam, 3.0 / o.var_cap)
+    np.testing.assert_allclose(mu.ravel(), [m1, m2], rtol=1e-8)
+    np.testing.assert_allclose(var.ravel(), [v1, v2], rtol=1e-8)
+    # EM (Algorithm 2, Option 3): a_u = E|x1 - x2| under the exact posterior
+    lam_new = o.em_update()
+    assert abs(lam_new - 2.0 / eabs) <= 1e-8 * lam_new
+
+
+# ---------------------------------------------------------------- lam -> 0
+def test_lambda_zero_denoise_closed_form():
+    """P3: with lam = 0 every prior site sits at the cap, mu = y and
+    sigma^2 = 1 / (1/xi + 4/var_cap)."""
+    p = syn.denoise_problem(16, 12, seed=2)
+    o = EPOracle("denoise", p.y, p.xi, 0.0, 16, 12)
+    o.run(30)
+    mu, var = o.posterior()
+    np.testing.assert_allclose(var, 1.0 / (1.0 / p.xi + 4e-8), rtol=1e-13)
+    np.testing.assert_allclose(mu, p.y, rtol=1e-9, atol=1e-12)
+
+
+def test_lambda_zero_deconv_matches_fft_posterior():
+    """P3: with lam = 0 and a periodic blur the q0 update gives the exact
+    marginal variances of N(x; ., (H^T H / xi + 4e-8 I)^{-1}), which are the same
+    at every pixel: (1/N) sum_f 1 / (|h_f|^2 / xi + 4e-8); the mean tends to the
+    least-squares deconvolution."""
+    h, w = 8, 10
+    k = np.array([[0.02, 0.05, 0.01], [0.04, 0.7, 0.08], [0.03, 0.06, 0.01]])
+    rng = np.random.default_rng(11)
+    x = rng.random((h, w))
+    xi = 1e-3
+    y = syn.circular_blur(x, k) + math.sqrt(xi) * rng.normal(size=(h, w))
+    o = EPOracle("deconv", y, xi, 0.0, h, w, kernel=k, site0="exact")
+    o.run(40)
+    mu, var = o.posterior()
+    pad = np.zeros((h, w))
+    pad[:3, :3] = k
+    hf = np.fft.fft2(np.roll(pad, (-1, -1), axis=(0, 1)))
+    var_ref = np.mean(1.0 / (np.abs(hf) ** 2 / xi + 4e-8))
+    np.testing.assert_allclose(var, var_ref, rtol=1e-10)
+    mu_ls = np.real(np.fft.ifft2(np.conj(hf) * np.fft.fft2(y) / np.abs(hf) ** 2))
+    np.testing.assert_allclose(mu, mu_ls, rtol=0, atol=1e-6)
+
+
+# ---------------------------------------------------------------- likelihood site
+def test_denoise_site0_is_a_fixed_point():
+    """C6: for H = I the q0 update returns (1/xi, y/xi) whatever the cavity."""
+    p = syn.denoise_problem(10, 8, seed=5)
+    o = EPOracle("denoise", p.y, p.xi, 15.0, 10, 8)
+    for _ in range(3):
+        for k in (1, 2, 3, 4):
+            o.prior_update(k)
+        before = (o.tau[0].copy(), o.nu[0].copy())
+        o.site0_update()
+        np.testing.assert_allclose(o.tau[0], before[0], rtol=1e-13)
+        np.testing.assert_allclose(o.nu[0], before[1], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(o.tau[0], 1.0 / p.xi, rtol=1e-13)
+        np.testing.assert_allclose(o.nu[0], p.y.ravel() / p.xi, rtol=1e-11, atol=1e-11)
+
+
+def test_woodbury_equals_dense_inverse():
+    """P4: the Woodbury form of Cov_P0 for compressive sensing equals the dense inverse."""
+    p = syn.cs_problem(16, 16, m=77, seed=3)
+    a = EPOracle("cs", p.y, p.xi, 2.0, 16, 16, A=p.A, site0="exact")
+    rng = np.random.default_rng(15)
+    c = rng.uniform(0.01, 1.0, size=256)
+    m = rng.normal(size=256)
+    e_dense, v_dense = a.tilted_p0(c, m)
+    a.site0 = "woodbury"
+    e_wood, v_wood = a.tilted_p0(c, m)
+    np.testing.assert_allclose(e_wood, e_dense, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(v_wood, v_dense, rtol=1e-9)
+    # whole runs agree up to the conditioning of the dense N x N solve
+    a = EPOracle("cs", p.y, p.xi, 2.0, 16, 16, A=p.A, site0="exact")
+    b = EPOracle("cs", p.y, p.xi, 2.0, 16, 16, A=p.A, site0="woodbury")
+    a.run(4)
+    b.run(4)
+    for u, v in zip(a.posterior(), b.posterior()):
+        np.testing.assert_allclose(u, v, rtol=1e-4, atol=1e-5)
+
+
+def test_rbmc_is_exact_for_a_diagonal_precision():
+    """With H = I the precision is diagonal, the conditional mean of each pixel
+    is zero and the Rao-Blackwellised estimator returns 1/Q_ii exactly; the
+    deconvolution route with a 1x1 unit kernel then equals denoising."""
+    p = syn.denoise_problem(8, 6, seed=6)
+    pr = syn.rbmc_probes(3, 48, 48, seed=1)
+    a = EPOracle("deconv", p.y, p.xi, 9.0, 8, 6, kernel=np.ones((1, 1)), site0="rbmc", probes=pr)
+    b = EPOracle("denoise", p.y, p.xi, 9.0, 8, 6)
+    a.run(6)
+    b.run(6)
+    for u, v in zip(a.posterior(), b.posterior()):
+        np.testing.assert_allclose(u, v, rtol=1e-11)
+
+
+def test_rbmc_is_unbiased():
+    """The RB estimate averaged over many probes approaches diag(Q^{-1})."""
+    h, w = 6, 6
+    n = h * w
+    rng = np.random.default_rng(8)
+    k = rng.random((3, 3)) ** 3       # asymmetric, so H^T differs from H
+    k /= k.sum()
+    y = rng.random((h, w))
+    S = 4000
+    pr = syn.rbmc_probes(S, n, n, seed=9)
+    o = EPOracle("deconv", y, 1e-2, 1.0, h, w, kernel=k, site0="rbmc", probes=pr)
+    c = rng.uniform(0.02, 0.5, size=n)
+    m = rng.normal(size=n)
+    _, v_rb = o.tilted_p0(c, m)
+    o.site0 = "exact"
+    _, v_ex = o.tilted_p0(c, m)
+    # the estimator's spread is at most the spread of 1/Q_ii + (.)^2 terms; use 6 sigma
+    rel = np.abs(v_rb / v_ex - 1)
+    assert rel.max() < 6.0 / math.sqrt(S) * 2.0
+    assert np.all(v_rb >= 1.0 / np.diag(o._operator()[0].T @ o._operator()[0] / 1e-2 + np.diag(1 / c)))
+
+
+# ---------------------------------------------------------------- symmetry
+def _run(y, lam, order=None, kind="denoise", kernel=None, xi=0.01, sweeps=8):
+    h, w = y.shape
+    o = EPOracle(kind, y, xi, lam, h, w, kernel=kernel)
+    for _ in range(sweeps):
+        o.sweep(order)
+    return o.posterior()
+
+
+def test_flip_and_transpose_symmetry():
+    """P5: flips map each V_k to itself; the transpose swaps V1<->V3 and V2<->V4."""
+    rng = np.random.default_rng(12)
+    y = rng.random((8, 6))
+    base = _run(y, 12.0)
+    for f in (lambda a: a[:, ::-1], lambda a: a[::-1, :]):
+        got = _run(f(y).copy(), 12.0)
+        for u, v in zip(got, base):
+            np.testing.assert_allclose(u, f(v), rtol=1e-12)
+    got = _run(y.T.copy(), 12.0, order=[3, 4, 1, 2])
+    for u, v in zip(got, base):
+        np.testing.assert_allclose(u, v.T, rtol=1e-12)
+
+
+def test_flip_symmetry_deconv_with_mirrored_kernel():
+    rng = np.random.default_rng(13)
+    y = rng.random((6, 8))
+    k = rng.random((3, 3))
+    k /= k.sum()
+    base = _run(y, 5.0, kind="deconv", kernel=k, xi=1e-3, sweeps=4)
+    got = _run(y[:, ::-1].copy(), 5.0, kind="deconv", kernel=k[:, ::-1].copy(), xi=1e-3, sweeps=4)
+    for u, v in zip(got, base):
+        np.testing.assert_allclose(u, v[:, ::-1], rtol=1e-10)
+
+
+# ---------------------------------------------------------------- invariants
+def test_site_invariants_after_sweeps():
+    """P6: every site precision stays >= 1/var_cap; cavities stay proper; a_u > 0."""
+    p = syn.denoise_problem(16, 16, seed=14)
+    o = EPOracle("denoise", p.y, p.xi, 25.0, 16, 16)
+    for _ in range(10):
+        abar = o.sweep()
+        assert abar > 0
+        assert np.all(o.tau[1:] >= 1e-8 * (1 - 1e-15))
+        for s in range(5):
+            c, _ = o.cavity(s)
+            assert np.all(c > 0)
