@@ -1,0 +1,320 @@
+"""Throughput benchmark of the EP sweep (Mpixel-EP-sweeps/s).
+
+Workloads (synthetic, seeded; the paper's images are not available):
+  deconv512   512x512, rectangles + discs + Gaussian random field (length 32 px),
+              9x9 uniform periodic blur, BSNR 40 dB, beta by EM every 5 sweeps from 1,
+              32 RBMC probes, FP32 sweeps.              (default)
+  denoise4096 4096x4096, 40 rectangles, sigma 0.1, beta 20, damping 0.5.
+A step is one EP sweep: the four prior-site updates, the likelihood-site update
+and, every fifth sweep, the EM update of beta.  Inputs are resident on the GPU
+when the timed region starts; L2 is flushed (256 MB write) before every timed
+step and the flush is not timed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload deconv512|denoise4096]
+
+With --gpus N > 1 (one process per GPU, launched by torch.distributed.run) every
+rank solves its own independent problem ("replicas", weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "deconv512": dict(kind="deconv", h=512, w=512, kernel=("uniform", 9), bsnr_db=40.0, beta0=1.0,
+                      em_every=5, S=32, seed=0),
+    "denoise4096": dict(kind="denoise", h=4096, w=4096, sigma=0.1, beta0=20.0, em_every=0,
+                        seed=0, n_rect=40),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _problem(cfg, rank=0):
+    from paper_2110_01585_gb300 import synthetic as syn
+    seed = cfg["seed"] + 1000 * rank
+    if cfg["kind"] == "deconv":
+        k = syn.uniform_kernel(cfg["kernel"][1])
+        return syn.deconv_problem(cfg["h"], cfg["w"], kernel=k, bsnr_db=cfg["bsnr_db"],
+                                  beta0=cfg["beta0"], seed=seed)
+    return syn.denoise_problem(cfg["h"], cfg["w"], sigma=cfg["sigma"], beta=cfg["beta0"],
+                               seed=seed, n_rect=cfg.get("n_rect", 8))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                parts = [x.strip() for x in out.split(",")]
+                if len(parts) == 6:
+                    self.samples.append(parts)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(s[0]) for s in self.samples)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[2 + i]})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(self.samples[0][1]),
+                "reasons": reasons, "samples": len(sm)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2110_01585_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_name):
+    """DRAM bytes per unit from the committed ncu summary, if taken on this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(kernel_name)
+        if e and e.get("source_hash") == _kernel_source_hash():
+            return e["dram_bytes_per_unit"]
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC, OP_IDENTITY, solve_host
+
+    cfg = WORKLOADS[args.workload]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prob = _problem(cfg, rank)
+    n_px = prob.n_pixels
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    kw = {}
+    if cfg["kind"] == "deconv":
+        kw = dict(op=OP_CONV_PERIODIC, kernel=prob.kernel, rbmc_samples=cfg["S"])
+    with torch.cuda.stream(stream):
+        yt = torch.as_tensor(prob.y.astype(np.float32), device=dev)
+        ep = EPTV(yt, prob.xi, prob.beta, stream=stream, **kw)
+    em_every = cfg["em_every"]
+    sweep_idx = [0]
+
+    def step():
+        ep.sweep(1)
+        sweep_idx[0] += 1
+        if em_every and sweep_idx[0] % em_every == 0:
+            ep.em_beta(sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ep.trace(True)
+    cs = ClockSampler(dev.index)
+    with cs:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[i][0].record(stream)
+            step()
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    trace = ep.trace_read()
+    ep.trace(False)
+    st = ep.stats()
+    status = ep.status()
+    ms_total = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = n_px * world * args.steps / (ms_total / 1e3) / 1e6
+    launches = sum(v[1] for v in trace.values())
+    dom = max(trace.items(), key=lambda kv: kv[1][0])
+    name, (kms, kl, units, bpu) = dom
+    peak, peak_src = _peaks()
+    achieved = units * bpu / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    traffic = _ncu_traffic(name)
+    traffic_per_launch = traffic * units / kl if (traffic is not None and kl) else None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic_per_launch,
+                "algorithmic_bytes_per_launch": units * bpu / kl if kl else None,
+                "avg_launch_us": kms / kl * 1e3 if kl else None,
+                "share_of_step": round(kms / ms_total, 4) if ms_total else None}
+    ep.close()
+
+    # end to end through the host-buffer API: copies in, all sweeps, posterior out
+    e2e = None
+    if rank == 0:
+        y32 = prob.y.astype(np.float32)
+        n_e2e = max(args.steps, em_every or 1)
+        t0 = time.perf_counter()
+        extra = {}
+        if cfg["kind"] == "deconv":
+            extra = dict(op=OP_CONV_PERIODIC, kernel=prob.kernel, rbmc_samples=cfg["S"])
+        solve_host(y32, prob.xi, prob.beta, n_e2e, em_every=em_every, **extra)
+        t1 = time.perf_counter()
+        e2e = {"value": round(n_px * n_e2e / (t1 - t0) / 1e6, 3), "unit": "Mpixel-EP-sweeps/s",
+               "h2d_bytes_per_step": 4 * y32.size / n_e2e, "d2h_bytes_per_step": 8 * n_px / n_e2e,
+               "sweeps_per_call": n_e2e,
+               "what": "ep_tv_solve_host: y host->device, init, sweeps with EM, posterior "
+                       "mean/var device->host, wall clock"}
+    return dict(value=value, ms_per_step=ms_per_step, roofline=roofline, clocks=cs.summary(),
+                launches=launches, trace=trace, stats=st, status=status, e2e=e2e, n_px=n_px)
+
+
+def run_oracle_sample(cfg, budget_s=20.0):
+    """The FP64 oracle on a bounded sample of the workload: same generator,
+    operator and parameters at a reduced size, sweeps until the time budget."""
+    from oracle.ep import EPOracle
+    from paper_2110_01585_gb300 import synthetic as syn
+    if cfg["kind"] == "deconv":
+        side = 128
+        p = syn.deconv_problem(side, side, kernel=syn.uniform_kernel(cfg["kernel"][1]),
+                               bsnr_db=cfg["bsnr_db"], beta0=cfg["beta0"], seed=cfg["seed"],
+                               grf_length=cfg.get("grf", 32.0) * side / cfg["h"])
+        pr = syn.rbmc_probes(cfg["S"], side * side, side * side, seed=1)
+        o = EPOracle("deconv", p.y, p.xi, p.beta, side, side, kernel=p.kernel, site0="rbmc_cg",
+                     probes=pr)
+        sample = f"{side}x{side} crop-size instance of the same generator/blur/BSNR, CG mode"
+    else:
+        side = 512
+        p = syn.denoise_problem(side, side, sigma=cfg["sigma"], beta=cfg["beta0"], seed=cfg["seed"])
+        o = EPOracle("denoise", p.y, p.xi, p.beta, side, side)
+        sample = f"{side}x{side} instance of the same generator"
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.sweep()
+        n += 1
+        if cfg["em_every"] and n % cfg["em_every"] == 0:
+            o.em_update()
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(side * side * n / dt / 1e6, 5), "unit": "Mpixel-EP-sweeps/s", "cores": 1,
+            "kind": "oracle", "sample": f"{sample}, {n} sweeps in {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="deconv512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    cfg = WORKLOADS[args.workload]
+    config = {"workload": args.workload, "height": cfg["h"], "width": cfg["w"],
+              "l2": "flushed before every timed step (256 MB write, untimed)"}
+    if cfg["kind"] == "deconv":
+        config.update(kernel="uniform 9x9 periodic", bsnr_db=cfg["bsnr_db"], beta0=cfg["beta0"],
+                      em_every=cfg["em_every"], rbmc_probes=cfg["S"])
+    else:
+        config.update(sigma=cfg["sigma"], beta=cfg["beta0"])
+    config["parallelism"] = f"replicas{world}" if world > 1 else "single"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(args.steps):
+            steps.append(run_oracle_sample(cfg, budget_s=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))["value"])
+        v = sum(steps) / len(steps)
+        cpu = run_oracle_sample(cfg, budget_s=2.0)
+        line = {"impl": "reference", "metric": "Mpixel-EP-sweeps/s", "value": v,
+                "unit": "Mpixel-EP-sweeps/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "Mpixel-EP-sweeps/s", "cores": 1, "kind": "oracle",
+                                 "sample": cpu["sample"]},
+                "e2e": {"value": v, "unit": "Mpixel-EP-sweeps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle_sample(cfg, budget_s=20.0)
+    line = {"metric": "Mpixel-EP-sweeps/s", "value": round(res["value"], 3), "unit": "Mpixel-EP-sweeps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["ms_per_step"], 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "solver": {"cg_iters_last_sweep": res["stats"]["cg_iters"],
+                       "fp64_edges": res["stats"]["n_fp64"], "status": res["status"]},
+            "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in res["trace"].items() if v[1]}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ep_tv.h - C ABI of the GB300 expectation-propagation library for image
+ * restoration with an anisotropic l1 total-variation prior.
+ *
+ * Method: Yao, McLaughlin and Altmann, "Fast Scalable Image Restoration using
+ * Total Variation Priors and Expectation Propagation" (arXiv:2110.01585).
+ *
+ *   Observation model (Sec. II-A, Eq. likelihood): y = H x + n, n ~ N(0, xi I),
+ *     x an H x W image (N = H W pixels, row-major, p = r W + c), y of length M.
+ *   Prior (Sec. II-B, Eq. prior1, Eq. L1_TV): prod over the four matchings V_k of
+ *     the 4-neighbour graph of exp(-beta |x_i - x_j|)  (beta is the paper's lambda).
+ *   Approximation (Sec. III): Q(x) = N(mu, diag sigma^2) built from five diagonal
+ *     Gaussian sites: q_{x,0} for the likelihood and q_{x,k}, k = 1..4, one per V_k.
+ *   One sweep (Algorithm 1) updates the four prior sites (all edges of a V_k in
+ *     parallel) and the likelihood site, with the variance cap and damping of
+ *     Sec. III-C; the EM step (Sec. IV, Algorithm 2, Eq. 3rd_alternative_a0) sets
+ *     beta = N / a_u, a_u the sum over all edges of the tilted E|x_i - x_j|.
+ *
+ * Conventions for every call:
+ *   - Pointers documented as "device" must be CUDA device pointers valid on the
+ *     context's device; "host" pointers are ordinary CPU memory.
+ *   - Floating-point data are float32 unless stated.  Images are row-major,
+ *     contiguous, H rows of W elements.
+ *   - All work is enqueued on the stream given to ep_tv_init (0 = legacy default
+ *     stream).  Calls return once the work is enqueued, except where stated.
+ *   - The library owns all site state and scratch memory it allocates; the
+ *     caller owns every buffer it passes in.  Input buffers are copied during the
+ *     call that receives them, except the dense sensing matrix (see below).
+ *   - Argument errors are returned synchronously and change nothing.  Errors found
+ *     on the device (non-finite site values, solver failure) are latched in a
+ *     device status word and returned by the next call that synchronises
+ *     (ep_tv_em_beta with an output pointer, ep_tv_posterior_host, ep_tv_status_check,
+ *     ep_tv_state_export); after that the context refuses further sweeps with
+ *     EP_TV_ERR_STATE until ep_tv_reset.  No call aborts the process.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef EP_TV_H
+#define EP_TV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ep_tv_ctx ep_tv_ctx;
+
+typedef enum {
+  EP_TV_OK = 0,
+  EP_TV_ERR_ARG = 1,          /* invalid argument (returned before any work) */
+  EP_TV_ERR_NOMEM = 2,        /* device allocation failed */
+  EP_TV_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  EP_TV_ERR_NONFINITE = 4,    /* a site value became NaN or infinite */
+  EP_TV_ERR_CG_NOCONV = 5,    /* the likelihood-site solver hit its iteration cap */
+  EP_TV_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  EP_TV_ERR_STATE = 7,        /* context unusable after a latched device error */
+  EP_TV_ERR_UNSUPPORTED = 8   /* valid request this build does not implement */
+} ep_tv_status;
+
+/* Degradation operators (Sec. II-A): (i) identity, (ii) convolution, (iii) dense. */
+typedef enum {
+  EP_TV_OP_IDENTITY = 0,        /* denoising, M = N */
+  EP_TV_OP_CONV_PERIODIC = 1,   /* periodic convolution with a centred odd kernel, M = N */
+  EP_TV_OP_DENSE = 2            /* compressive sensing, dense M x N matrix */
+} ep_tv_op;
+
+typedef struct {
+  int32_t op;            /* ep_tv_op */
+  int32_t height;        /* image rows H >= 1 */
+  int32_t width;         /* image columns W >= 1 */
+  int32_t m;             /* length of y: N for IDENTITY and CONV_PERIODIC, M for DENSE */
+  const float* kernel;   /* CONV_PERIODIC: HOST pointer, kh x kw row-major, copied at init.
+                            (H x)[r,c] = sum_{a,b} k[a,b] x[(r-a+kh/2) mod H, (c-b+kw/2) mod W] */
+  int32_t kh, kw;        /* odd kernel sizes, kh <= H, kw <= W */
+  const float* dense;    /* DENSE: DEVICE pointer, M x N row-major.  Borrowed: it must stay
+                            valid and unchanged for the life of the context. */
+} ep_tv_operator;
+
+typedef struct {
+  double xi;             /* noise variance xi > 0 (Eq. likelihood) */
+  double beta;           /* TV parameter (the paper's lambda) >= 0; EM start value */
+  double damping;        /* weight in (0, 1] on the freshly updated site when mixing
+                            natural parameters: new = d * updated + (1 - d) * old */
+  double var_cap;        /* site variances are capped at var_cap (the paper suggests
+                            1e8, Sec. III-C): a new site precision below 1/var_cap
+                            (negative or tiny) is set to 1/var_cap */
+  int32_t periodic;      /* 1: torus, every pixel in one edge of each V_k; needs even
+                            H and W.  0: free boundary, wrap-around edges dropped. */
+  int32_t order_mode;    /* 0: the four prior-site updates, then the likelihood site
+                            (uses the initial likelihood site).  1: likelihood site
+                            first, as Algorithm 1 lists it. */
+  int32_t rbmc_samples;  /* CONV_PERIODIC: S probes of the Rao-Blackwellised Monte Carlo
+                            variance estimator (default 32) */
+  int32_t cg_max_iter;   /* CONV_PERIODIC: iteration cap of the conjugate-gradient solves */
+  double cg_rtol;        /* CONV_PERIODIC: relative residual target of those solves */
+  int32_t precision;     /* 0: FP32 with FP64 for edges whose tilted moments lose
+                            FP32 accuracy; 1: FP32 only */
+  uint64_t seed;         /* seed of the library's own probe generator */
+} ep_tv_params;
+
+/* Fills *p with defaults: damping 0.5, var_cap 1e8, periodic 1, order_mode 0,
+   rbmc_samples 32, cg_max_iter 1000, cg_rtol 1e-6, precision 0, seed 1234.
+   xi and beta are set to 0 and must be provided. */
+ep_tv_status ep_tv_default_params(ep_tv_params* p);
+
+/* Creates a context and initialises the sites as Algorithm 1 does:
+   q_{x,0} has mean y (H^T y for DENSE) and variance xi; q_{x,1..4} have mean 0
+   and variance var_cap.  y: DEVICE pointer of length op->m, copied.
+   cuda_stream: a cudaStream_t (or NULL) on the current device; all later work of
+   this context is enqueued on it.  *out receives the context. */
+ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
+                        void* cuda_stream, ep_tv_ctx** out);
+
+/* Replaces the library-drawn probe vectors of the RBMC estimator (CONV_PERIODIC)
+   by caller-drawn standard normals.  eps1: DEVICE, S x M; eps2: DEVICE, S x N;
+   both copied.  The probes stay fixed across sweeps (common random numbers). */
+ep_tv_status ep_tv_set_probes(ep_tv_ctx* ctx, const float* eps1, const float* eps2,
+                              int32_t n_samples);
+
+/* Runs n_sweeps sweeps of Algorithm 1.  k_order: HOST array of 4 * n_sweeps values,
+   each group of four a permutation of {1,2,3,4} giving the order of the prior-site
+   updates in that sweep; NULL means 1,2,3,4 every sweep.  em_every > 0 applies the
+   EM update of beta after every em_every-th sweep of this call, on the device.
+   Each sweep also records a_u for ep_tv_em_beta. */
+ep_tv_status ep_tv_sweep(ep_tv_ctx* ctx, int32_t n_sweeps, const int8_t* k_order,
+                         int32_t em_every);
+
+/* EM M-step (Algorithm 2, Option 3): beta <- N / a_u, with a_u the sum over all
+   edges of E_{P_k}|u_n| taken during the last sweep, reduced in FP64 in a fixed
+   order.  Enqueued on the stream.  If beta_out or abar_out is non-NULL the call
+   synchronises the stream and writes the new beta / a_u there (HOST doubles). */
+ep_tv_status ep_tv_em_beta(ep_tv_ctx* ctx, double* beta_out, double* abar_out);
+
+/* Sets beta (no EM). */
+ep_tv_status ep_tv_set_beta(ep_tv_ctx* ctx, double beta);
+
+/* Posterior of Eq. Q_x_final: mean = nu_x / tau_x and var = 1 / tau_x, with
+   tau_x, nu_x the sums of the five sites.  mean, var: DEVICE, N floats each. */
+ep_tv_status ep_tv_posterior(ep_tv_ctx* ctx, float* mean, float* var);
+
+/* Site natural parameters, for inspection: tau, nu DEVICE, 5 x N floats each,
+   row s = site s (0 likelihood, 1..4 prior sites of V_1..V_4). */
+ep_tv_status ep_tv_get_sites(ep_tv_ctx* ctx, float* tau, float* nu);
+
+/* Synchronises the stream and returns the latched device status. */
+ep_tv_status ep_tv_status_check(ep_tv_ctx* ctx);
+
+/* Statistics of the last sweep call (HOST out-pointers may be NULL):
+   cg_iters   conjugate-gradient iterations of the last likelihood-site update,
+   n_fp64     number of edges whose moments were recomputed in FP64,
+   n_capped   number of site updates that hit the variance cap.  Synchronises. */
+ep_tv_status ep_tv_stats(ep_tv_ctx* ctx, int32_t* cg_iters, uint64_t* n_fp64,
+                         uint64_t* n_capped);
+
+/* Checkpoint: the full EP state (sites, beta, a_u, solver warm starts, counters).
+   With host_buf == NULL, *bytes receives the size.  Otherwise host_buf (HOST,
+   *bytes long) receives the state; synchronises.  A run resumed with
+   ep_tv_state_import continues bit-identically. */
+ep_tv_status ep_tv_state_export(ep_tv_ctx* ctx, void* host_buf, size_t* bytes);
+ep_tv_status ep_tv_state_import(ep_tv_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Re-initialises the sites (as ep_tv_init) and clears a latched error. */
+ep_tv_status ep_tv_reset(ep_tv_ctx* ctx);
+
+/* One complete restoration from HOST memory: copies y (HOST, op->m floats) to the
+   device, runs n_sweeps sweeps with EM every em_every sweeps (0 = never), and
+   copies the posterior mean and variance (HOST, N floats each) and the final beta
+   (HOST, may be NULL) back.  op->kernel is HOST as in ep_tv_init; op->dense must
+   be a DEVICE pointer.  Synchronous; allocates and frees its own context. */
+ep_tv_status ep_tv_solve_host(const ep_tv_operator* op, const float* y_host,
+                              const ep_tv_params* p, int32_t n_sweeps, int32_t em_every,
+                              float* mean_host, float* var_host, double* beta_out);
+
+/* Kernel classes reported by the tracer. */
+typedef enum {
+  EP_TV_K_PRIOR_SWEEP = 0,   /* fused V_1..V_4 prior-site pass, unit = pixel */
+  EP_TV_K_CG_DIRECTION = 1,  /* CG direction + H^T H stencil, unit = pixel of one active system */
+  EP_TV_K_CG_UPDATE = 2,     /* CG x / r update, unit = pixel of one active system */
+  EP_TV_K_CG_RESIDUAL = 3,   /* initial CG residual, unit = pixel of one system */
+  EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
+  EP_TV_K_COUNT = 5
+} ep_tv_kernel;
+
+/* Tracing: with on != 0, every launch of the kernel classes above is bracketed
+   by CUDA events on the context's stream.  ep_tv_trace_read synchronises and
+   returns, for one class since tracing was enabled: total device milliseconds,
+   number of launches, units processed, and the algorithmic DRAM bytes per unit
+   (what the kernel must read and write at least once).  HOST out-pointers may
+   be NULL.  Enabling resets the totals. */
+ep_tv_status ep_tv_trace_enable(ep_tv_ctx* ctx, int32_t on);
+ep_tv_status ep_tv_trace_read(ep_tv_ctx* ctx, int32_t kernel, double* ms, int64_t* launches,
+                              double* units, double* bytes_per_unit);
+
+/* Frees the context (synchronises its stream first).  NULL is accepted. */
+void ep_tv_destroy(ep_tv_ctx* ctx);
+
+/* Static English description of a status code. */
+const char* ep_tv_status_str(ep_tv_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EP_TV_H */

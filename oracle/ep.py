@@ -64,6 +64,10 @@ class EPOracle:
         "woodbury": Woodbury identity (cs; H^T H low rank).
         "rbmc": mean by a dense solve, variance by the Rao-Blackwellised
         Monte Carlo estimator with the given fixed probes (deconv).
+        "rbmc_cg": the same estimator with every solve done by conjugate
+        gradients to a relative residual of 1e-11 and H applied through the FFT
+        (periodic convolution is diagonal in the Fourier basis); for images too
+        large for dense factorisation (deconv).
     probes : (eps1 (S, M), eps2 (S, N)) standard normals for "rbmc".
     """
 
@@ -168,6 +172,8 @@ class EPOracle:
         if self.kind == "denoise":
             var = 1.0 / (1.0 / self.xi + 1.0 / c)
             return var * (self.y / self.xi + m / c), var
+        if self.site0 == "rbmc_cg":
+            return self._rbmc_cg(c, m)
         H, Hty = self._operator()
         if self.site0 == "woodbury":
             return self._woodbury(H, c, m)
@@ -214,6 +220,44 @@ class EPOracle:
             off = Q @ z - qdiag * z
             acc += (off / qdiag) ** 2
         return 1.0 / qdiag + acc / S
+
+    def _rbmc_cg(self, c, m):
+        """Site-0 moments with CG solves; same estimator as :meth:`_rbmc_var`."""
+        from scipy.sparse.linalg import LinearOperator, cg
+        h, w = self.height, self.width
+        kh, kw = self.kernel.shape
+        pad = np.zeros((h, w))
+        pad[:kh, :kw] = self.kernel
+        hf = np.fft.fft2(np.roll(pad, (-(kh // 2), -(kw // 2)), axis=(0, 1)))
+        hth = np.abs(hf) ** 2
+        inv_c = 1.0 / c
+
+        def qmul(v):
+            v2 = np.asarray(v).reshape(h, w)
+            return (np.real(np.fft.ifft2(hth * np.fft.fft2(v2))).reshape(-1) / self.xi + inv_c * v2.reshape(-1))
+
+        Q = LinearOperator((self.n, self.n), matvec=qmul, dtype=np.float64)
+
+        def solve(b):
+            x, info = cg(Q, b, rtol=1e-11, atol=0.0, maxiter=20000)
+            if info != 0:
+                raise RuntimeError("oracle CG did not converge")
+            return x
+
+        def ht(v):
+            return np.real(np.fft.ifft2(np.conj(hf) * np.fft.fft2(v.reshape(h, w)))).reshape(-1)
+
+        E = solve(ht(self.y) / self.xi + m / c)
+        eps1, eps2 = self.probes
+        S = eps1.shape[0]
+        qdiag = np.sum(self.kernel ** 2) / self.xi + inv_c
+        acc = np.zeros(self.n)
+        for s in range(S):
+            wv = ht(eps1[s]) / math.sqrt(self.xi) + eps2[s] / np.sqrt(c)
+            z = solve(wv)
+            off = qmul(z) - qdiag * z
+            acc += (off / qdiag) ** 2
+        return E, 1.0 / qdiag + acc / S
 
     def _woodbury(self, H, c, m):
         """Cov_P0 = C - C H^T (xi I + H C H^T)^{-1} H C with C = diag(c)."""

@@ -1,0 +1,504 @@
+// C ABI of libeptv: context management, argument checking, the sweep driver
+// (Algorithm 1) and the EM step (Algorithm 2).  Compute runs in the kernels of
+// the other translation units; this file only orders their launches.
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "likelihood.cuh"
+
+using namespace eptv;
+
+struct ep_tv_ctx {
+  ep_tv_operator op;
+  ep_tv_params p;
+  int height = 0, width = 0;
+  long long n = 0;
+  int m = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  float* tau = nullptr;       // [5][N]
+  float* nu = nullptr;        // [5][N]
+  float* y = nullptr;         // [M]
+  float* mu0 = nullptr;       // initial mean of site 0 (y, or H^T y for DENSE)
+  double* dscal = nullptr;    // DS_*
+  double* abar_partial = nullptr;
+  int n_partial = 0;
+  unsigned* status = nullptr;
+  unsigned long long* counters = nullptr;
+  LikelihoodState* lik = nullptr;  // CONV_PERIODIC / DENSE
+  Tracer tracer;
+  unsigned long long cnt_base[DC_COUNT] = {};  // counters when tracing was enabled
+  bool failed = false;
+  long long sweeps = 0;
+};
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return EP_TV_ERR_CUDA;  \
+  } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+ep_tv_status check_params(const ep_tv_operator* op, const ep_tv_params* p) {
+  if (!op || !p) return EP_TV_ERR_ARG;
+  if (op->height < 1 || op->width < 1) return EP_TV_ERR_ARG;
+  if ((long long)op->height * op->width > (1ll << 31)) return EP_TV_ERR_ARG;
+  if (!finite_pos(p->xi)) return EP_TV_ERR_ARG;
+  if (!(std::isfinite(p->beta) && p->beta >= 0.0)) return EP_TV_ERR_ARG;
+  if (!(p->damping > 0.0 && p->damping <= 1.0)) return EP_TV_ERR_ARG;
+  if (!finite_pos(p->var_cap)) return EP_TV_ERR_ARG;
+  if (p->periodic != 0 && p->periodic != 1) return EP_TV_ERR_ARG;
+  if (p->periodic && ((op->height % 2) || (op->width % 2))) return EP_TV_ERR_ARG;
+  if (p->order_mode != 0 && p->order_mode != 1) return EP_TV_ERR_ARG;
+  if (p->precision != 0 && p->precision != 1) return EP_TV_ERR_ARG;
+  const long long n = (long long)op->height * op->width;
+  switch (op->op) {
+    case EP_TV_OP_IDENTITY:
+      if (op->m != n) return EP_TV_ERR_ARG;
+      break;
+    case EP_TV_OP_CONV_PERIODIC:
+      if (op->m != n || !op->kernel) return EP_TV_ERR_ARG;
+      if (op->kh < 1 || op->kw < 1 || !(op->kh % 2) || !(op->kw % 2)) return EP_TV_ERR_ARG;
+      if (op->kh > op->height || op->kw > op->width) return EP_TV_ERR_ARG;
+      if (p->rbmc_samples < 1 || p->cg_max_iter < 1 || !finite_pos(p->cg_rtol)) return EP_TV_ERR_ARG;
+      break;
+    case EP_TV_OP_DENSE:
+      if (op->m < 1 || !op->dense) return EP_TV_ERR_ARG;
+      break;
+    default:
+      return EP_TV_ERR_ARG;
+  }
+  return EP_TV_OK;
+}
+
+void free_ctx(ep_tv_ctx* c) {
+  if (!c) return;
+  if (c->lik) likelihood_destroy(c->lik);
+  cudaFree(c->tau);
+  cudaFree(c->nu);
+  cudaFree(c->y);
+  cudaFree(c->mu0);
+  cudaFree(c->dscal);
+  cudaFree(c->abar_partial);
+  cudaFree(c->status);
+  cudaFree(c->counters);
+  delete c;
+}
+
+ep_tv_status init_state(ep_tv_ctx* c) {
+  const float inv_xi = (float)(1.0 / c->p.xi);
+  const float min_tau = (float)(1.0 / c->p.var_cap);
+  launch_init_sites(c->tau, c->nu, c->mu0, c->n, inv_xi, min_tau, c->stream);
+  double ds[DS_COUNT] = {c->p.beta, 0.0, 0.0, 0.0};
+  CK(cudaMemcpyAsync(c->dscal, ds, sizeof(ds), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * DC_COUNT, c->stream));
+  CK(cudaMemsetAsync(c->abar_partial, 0, sizeof(double) * c->n_partial, c->stream));
+  if (c->lik) {
+    ep_tv_status st = likelihood_reset(c->lik, c->stream);
+    if (st != EP_TV_OK) return st;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->failed = false;
+  c->sweeps = 0;
+  return EP_TV_OK;
+}
+
+ep_tv_status latched(ep_tv_ctx* c) {
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) c->failed = true;
+  if (st & ST_NONFINITE) return EP_TV_ERR_NONFINITE;
+  if (st & ST_TIMEOUT) return EP_TV_ERR_TIMEOUT;
+  if (st & ST_CG_NOCONV) return EP_TV_ERR_CG_NOCONV;
+  return EP_TV_OK;
+}
+
+SweepArgs sweep_args(ep_tv_ctx* c, int order) {
+  SweepArgs a;
+  a.tau = c->tau;
+  a.nu = c->nu;
+  a.y = c->y;
+  a.inv_xi = (float)(1.0 / c->p.xi);
+  a.height = c->height;
+  a.width = c->width;
+  a.n = c->n;
+  a.periodic = c->p.periodic;
+  a.damping = (float)c->p.damping;
+  a.min_tau = (float)(1.0 / c->p.var_cap);
+  a.beta = c->dscal + DS_BETA;
+  a.order = order;
+  a.fp64_tail = c->p.precision == 0;
+  a.abar_partial = c->abar_partial;
+  a.status = c->status;
+  a.counters = c->counters;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+ep_tv_status ep_tv_default_params(ep_tv_params* p) {
+  if (!p) return EP_TV_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->damping = 0.5;
+  p->var_cap = 1e8;
+  p->periodic = 1;
+  p->order_mode = 0;
+  p->rbmc_samples = 32;
+  p->cg_max_iter = 1000;
+  p->cg_rtol = 1e-6;
+  p->precision = 0;
+  p->seed = 1234;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
+                        void* cuda_stream, ep_tv_ctx** out) {
+  if (!out) return EP_TV_ERR_ARG;
+  *out = nullptr;
+  ep_tv_status st = check_params(op, p);
+  if (st != EP_TV_OK) return st;
+  if (!y) return EP_TV_ERR_ARG;
+  ep_tv_ctx* c = new (std::nothrow) ep_tv_ctx();
+  if (!c) return EP_TV_ERR_NOMEM;
+  c->op = *op;
+  c->p = *p;
+  c->height = op->height;
+  c->width = op->width;
+  c->n = (long long)op->height * op->width;
+  c->m = op->m;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return EP_TV_ERR_CUDA; }
+  c->n_partial = prior_sweep_blocks(c->height, c->width);
+  bool ok = cudaMalloc(&c->tau, sizeof(float) * 5 * c->n) == cudaSuccess &&
+            cudaMalloc(&c->nu, sizeof(float) * 5 * c->n) == cudaSuccess &&
+            cudaMalloc(&c->y, sizeof(float) * c->m) == cudaSuccess &&
+            cudaMalloc(&c->mu0, sizeof(float) * c->n) == cudaSuccess &&
+            cudaMalloc(&c->dscal, sizeof(double) * DS_COUNT) == cudaSuccess &&
+            cudaMalloc(&c->abar_partial, sizeof(double) * c->n_partial) == cudaSuccess &&
+            cudaMalloc(&c->status, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&c->counters, sizeof(unsigned long long) * DC_COUNT) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_ctx(c);
+    return EP_TV_ERR_NOMEM;
+  }
+  if (cudaMemcpyAsync(c->y, y, sizeof(float) * c->m, cudaMemcpyDeviceToDevice, c->stream) !=
+      cudaSuccess) {
+    free_ctx(c);
+    return EP_TV_ERR_CUDA;
+  }
+  if (op->op == EP_TV_OP_IDENTITY) {
+    if (cudaMemcpyAsync(c->mu0, c->y, sizeof(float) * c->n, cudaMemcpyDeviceToDevice, c->stream) !=
+        cudaSuccess) {
+      free_ctx(c);
+      return EP_TV_ERR_CUDA;
+    }
+  } else {
+    LikelihoodConfig lc;
+    lc.op = op;
+    lc.p = p;
+    lc.height = c->height;
+    lc.width = c->width;
+    lc.n = c->n;
+    lc.m = c->m;
+    lc.y = c->y;
+    st = likelihood_create(lc, c->stream, &c->lik, c->mu0);
+    if (st != EP_TV_OK) {
+      free_ctx(c);
+      return st;
+    }
+  }
+  st = init_state(c);
+  if (st != EP_TV_OK) {
+    free_ctx(c);
+    return st;
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    free_ctx(c);
+    return EP_TV_ERR_CUDA;
+  }
+  *out = c;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_set_probes(ep_tv_ctx* c, const float* eps1, const float* eps2,
+                              int32_t n_samples) {
+  if (!c || !eps1 || !eps2 || n_samples < 1) return EP_TV_ERR_ARG;
+  if (!c->lik) return EP_TV_ERR_ARG;
+  return likelihood_set_probes(c->lik, eps1, eps2, n_samples, c->stream);
+}
+
+ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
+                         int32_t em_every) {
+  if (!c || n_sweeps < 0 || em_every < 0) return EP_TV_ERR_ARG;
+  if (c->failed) return EP_TV_ERR_STATE;
+  if (k_order) {
+    for (int t = 0; t < n_sweeps; ++t) {
+      int seen = 0;
+      for (int u = 0; u < 4; ++u) {
+        int k = k_order[4 * t + u];
+        if (k < 1 || k > 4 || (seen & (1 << k))) return EP_TV_ERR_ARG;
+        seen |= 1 << k;
+      }
+    }
+  }
+  for (int t = 0; t < n_sweeps; ++t) {
+    int order = 0;
+    for (int u = 0; u < 4; ++u) {
+      int k = k_order ? k_order[4 * t + u] : u + 1;
+      order |= k << (4 * u);
+    }
+    if (c->lik && c->p.order_mode == 1) {
+      ep_tv_status st = likelihood_update(c->lik, c->tau, c->nu, c->status, c->counters,
+                                          &c->tracer, c->stream);
+      if (st != EP_TV_OK) return st;
+    }
+    c->tracer.begin(EP_TV_K_PRIOR_SWEEP, c->stream);
+    launch_prior_sweep(sweep_args(c, order), c->op.op == EP_TV_OP_IDENTITY, c->stream);
+    c->tracer.end(c->stream, (double)c->n);
+    if (c->lik && c->p.order_mode == 0) {
+      ep_tv_status st = likelihood_update(c->lik, c->tau, c->nu, c->status, c->counters,
+                                          &c->tracer, c->stream);
+      if (st != EP_TV_OK) return st;
+    }
+    ++c->sweeps;
+    if (em_every > 0 && (t + 1) % em_every == 0) {
+      launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_em_beta(ep_tv_ctx* c, double* beta_out, double* abar_out) {
+  if (!c) return EP_TV_ERR_ARG;
+  if (c->failed) return EP_TV_ERR_STATE;
+  if (c->sweeps == 0) return EP_TV_ERR_ARG;
+  launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
+  if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
+  if (beta_out || abar_out) {
+    double ds[DS_COUNT];
+    CK(cudaMemcpyAsync(ds, c->dscal, sizeof(ds), cudaMemcpyDeviceToHost, c->stream));
+    ep_tv_status st = latched(c);
+    if (st != EP_TV_OK) return st;
+    if (beta_out) *beta_out = ds[DS_BETA];
+    if (abar_out) *abar_out = ds[DS_ABAR];
+  }
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_set_beta(ep_tv_ctx* c, double beta) {
+  if (!c || !(std::isfinite(beta) && beta >= 0.0)) return EP_TV_ERR_ARG;
+  CK(cudaMemcpyAsync(c->dscal + DS_BETA, &beta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_posterior(ep_tv_ctx* c, float* mean, float* var) {
+  if (!c || (!mean && !var)) return EP_TV_ERR_ARG;
+  launch_posterior(c->tau, c->nu, c->n, mean, var, c->stream);
+  if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_get_sites(ep_tv_ctx* c, float* tau, float* nu) {
+  if (!c || !tau || !nu) return EP_TV_ERR_ARG;
+  CK(cudaMemcpyAsync(tau, c->tau, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(nu, c->nu, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_status_check(ep_tv_ctx* c) {
+  if (!c) return EP_TV_ERR_ARG;
+  return latched(c);
+}
+
+ep_tv_status ep_tv_stats(ep_tv_ctx* c, int32_t* cg_iters, uint64_t* n_fp64, uint64_t* n_capped) {
+  if (!c) return EP_TV_ERR_ARG;
+  unsigned long long cnt[DC_COUNT];
+  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (cg_iters) *cg_iters = c->lik ? likelihood_last_iters(c->lik) : 0;
+  if (n_fp64) *n_fp64 = cnt[DC_FP64];
+  if (n_capped) *n_capped = cnt[DC_CAPPED];
+  return EP_TV_OK;
+}
+
+// State layout: header (magic, n, m, sweeps), dscal, tau, nu, likelihood blob.
+ep_tv_status ep_tv_state_export(ep_tv_ctx* c, void* host_buf, size_t* bytes) {
+  if (!c || !bytes) return EP_TV_ERR_ARG;
+  const size_t lik_bytes = c->lik ? likelihood_state_bytes(c->lik) : 0;
+  const size_t need = 4 * sizeof(long long) + sizeof(double) * DS_COUNT +
+                      2 * sizeof(float) * 5 * (size_t)c->n + lik_bytes;
+  if (!host_buf) {
+    *bytes = need;
+    return EP_TV_OK;
+  }
+  if (*bytes < need) return EP_TV_ERR_ARG;
+  char* b = (char*)host_buf;
+  long long hdr[4] = {0x45505456ll, c->n, c->m, c->sweeps};
+  memcpy(b, hdr, sizeof(hdr));
+  b += sizeof(hdr);
+  CK(cudaMemcpyAsync(b, c->dscal, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost, c->stream));
+  b += sizeof(double) * DS_COUNT;
+  CK(cudaMemcpyAsync(b, c->tau, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToHost, c->stream));
+  b += sizeof(float) * 5 * c->n;
+  CK(cudaMemcpyAsync(b, c->nu, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToHost, c->stream));
+  b += sizeof(float) * 5 * c->n;
+  if (c->lik) {
+    ep_tv_status st = likelihood_state_export(c->lik, b, c->stream);
+    if (st != EP_TV_OK) return st;
+  }
+  *bytes = need;
+  return latched(c);
+}
+
+ep_tv_status ep_tv_state_import(ep_tv_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return EP_TV_ERR_ARG;
+  const size_t lik_bytes = c->lik ? likelihood_state_bytes(c->lik) : 0;
+  const size_t need = 4 * sizeof(long long) + sizeof(double) * DS_COUNT +
+                      2 * sizeof(float) * 5 * (size_t)c->n + lik_bytes;
+  if (bytes != need) return EP_TV_ERR_ARG;
+  const char* b = (const char*)host_buf;
+  long long hdr[4];
+  memcpy(hdr, b, sizeof(hdr));
+  if (hdr[0] != 0x45505456ll || hdr[1] != c->n || hdr[2] != c->m) return EP_TV_ERR_ARG;
+  b += sizeof(hdr);
+  CK(cudaMemcpyAsync(c->dscal, b, sizeof(double) * DS_COUNT, cudaMemcpyHostToDevice, c->stream));
+  b += sizeof(double) * DS_COUNT;
+  CK(cudaMemcpyAsync(c->tau, b, sizeof(float) * 5 * c->n, cudaMemcpyHostToDevice, c->stream));
+  b += sizeof(float) * 5 * c->n;
+  CK(cudaMemcpyAsync(c->nu, b, sizeof(float) * 5 * c->n, cudaMemcpyHostToDevice, c->stream));
+  b += sizeof(float) * 5 * c->n;
+  if (c->lik) {
+    ep_tv_status st = likelihood_state_import(c->lik, b, c->stream);
+    if (st != EP_TV_OK) return st;
+  }
+  CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->sweeps = hdr[3];
+  c->failed = false;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_reset(ep_tv_ctx* c) {
+  if (!c) return EP_TV_ERR_ARG;
+  return init_state(c);
+}
+
+ep_tv_status ep_tv_solve_host(const ep_tv_operator* op, const float* y_host,
+                              const ep_tv_params* p, int32_t n_sweeps, int32_t em_every,
+                              float* mean_host, float* var_host, double* beta_out) {
+  if (!op || !y_host || !p || !mean_host || !var_host || n_sweeps < 0) return EP_TV_ERR_ARG;
+  ep_tv_status st = check_params(op, p);
+  if (st != EP_TV_OK) return st;
+  const long long n = (long long)op->height * op->width;
+  float* d_y = nullptr;
+  float* d_out = nullptr;
+  cudaStream_t s;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  if (cudaMalloc(&d_y, sizeof(float) * op->m) != cudaSuccess ||
+      cudaMalloc(&d_out, sizeof(float) * 2 * n) != cudaSuccess) {
+    cudaFree(d_y);
+    cudaStreamDestroy(s);
+    return EP_TV_ERR_NOMEM;
+  }
+  ep_tv_ctx* c = nullptr;
+  st = EP_TV_OK;
+  if (cudaMemcpyAsync(d_y, y_host, sizeof(float) * op->m, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    st = EP_TV_ERR_CUDA;
+  if (st == EP_TV_OK) st = ep_tv_init(op, d_y, p, s, &c);
+  if (st == EP_TV_OK) st = ep_tv_sweep(c, n_sweeps, nullptr, em_every);
+  if (st == EP_TV_OK) st = ep_tv_posterior(c, d_out, d_out + n);
+  if (st == EP_TV_OK) {
+    if (cudaMemcpyAsync(mean_host, d_out, sizeof(float) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(var_host, d_out + n, sizeof(float) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = EP_TV_ERR_CUDA;
+  }
+  if (st == EP_TV_OK && beta_out) {
+    if (cudaMemcpyAsync(beta_out, c->dscal + DS_BETA, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      st = EP_TV_ERR_CUDA;
+  }
+  if (st == EP_TV_OK) st = latched(c);
+  ep_tv_destroy(c);
+  cudaFree(d_y);
+  cudaFree(d_out);
+  cudaStreamDestroy(s);
+  return st;
+}
+
+ep_tv_status ep_tv_trace_enable(ep_tv_ctx* c, int32_t on) {
+  if (!c) return EP_TV_ERR_ARG;
+  if (on) {
+    if (!c->tracer.ensure()) return EP_TV_ERR_CUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    c->tracer.reset();
+    CK(cudaMemcpy(c->cnt_base, c->counters, sizeof(c->cnt_base), cudaMemcpyDeviceToHost));
+  } else if (c->tracer.on) {
+    c->tracer.harvest();
+  }
+  c->tracer.on = on != 0;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_trace_read(ep_tv_ctx* c, int32_t kernel, double* ms, int64_t* launches,
+                              double* units, double* bytes_per_unit) {
+  if (!c || kernel < 0 || kernel >= EP_TV_K_COUNT) return EP_TV_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  c->tracer.harvest();
+  unsigned long long cnt[DC_COUNT];
+  CK(cudaMemcpy(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  double u = c->tracer.host_units[kernel];
+  if (kernel == EP_TV_K_CG_DIRECTION)
+    u = (double)(cnt[DC_CG_DIR_UNITS] - c->cnt_base[DC_CG_DIR_UNITS]) * (double)c->n;
+  if (kernel == EP_TV_K_CG_UPDATE)
+    u = (double)(cnt[DC_CG_UPD_UNITS] - c->cnt_base[DC_CG_UPD_UNITS]) * (double)c->n;
+  double bpu = 0.0;
+  if (kernel == EP_TV_K_PRIOR_SWEEP)
+    bpu = prior_sweep_bytes_per_pixel(c->op.op == EP_TV_OP_IDENTITY);
+  else if (c->lik)
+    bpu = likelihood_bytes_per_unit(c->lik, kernel);
+  if (ms) *ms = c->tracer.ms[kernel];
+  if (launches) *launches = c->tracer.launches[kernel];
+  if (units) *units = u;
+  if (bytes_per_unit) *bytes_per_unit = bpu;
+  return EP_TV_OK;
+}
+
+void ep_tv_destroy(ep_tv_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+const char* ep_tv_status_str(ep_tv_status s) {
+  switch (s) {
+    case EP_TV_OK: return "ok";
+    case EP_TV_ERR_ARG: return "invalid argument";
+    case EP_TV_ERR_NOMEM: return "device allocation failed";
+    case EP_TV_ERR_CUDA: return "CUDA runtime error";
+    case EP_TV_ERR_NONFINITE: return "a site value became NaN or infinite";
+    case EP_TV_ERR_CG_NOCONV: return "likelihood-site solver hit its iteration cap";
+    case EP_TV_ERR_TIMEOUT: return "bounded device-side wait gave up";
+    case EP_TV_ERR_STATE: return "context unusable after a device error; call ep_tv_reset";
+    case EP_TV_ERR_UNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

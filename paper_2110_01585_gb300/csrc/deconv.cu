@@ -1,0 +1,811 @@
+// Likelihood site q_{x,0} for a periodic convolution H (deconvolution).
+//
+// Eq. tilted_P_1: the tilted P_0 is Gaussian with precision
+//   Q = H^T H / xi + diag(d),  d = cavity precision of site 0 = sum_{k=1..4} tau_k,
+// mean E = Q^{-1} (H^T y / xi + n), n = sum_{k=1..4} nu_k (cavity natural mean).
+// Only diag(Q^{-1}) is needed (Sec. III-C).  The paper names Rao-Blackwellised
+// Monte Carlo for it; the estimator here (fixed probes, so the EP map stays
+// deterministic across sweeps) is
+//   z_s = Q^{-1} w_s,  w_s = H^T eps1_s / sqrt(xi) + sqrt(d) eps2_s   (cov w_s = Q)
+//   Var_i = 1/Q_ii + (1/S) sum_s ((w_s)_i - Q_ii z_{s,i})^2 / Q_ii^2,
+// where (w_s)_i - Q_ii z_{s,i} = sum_{j != i} Q_ij z_{s,j} at the solution.
+// The 1 + S systems share Q and are solved together by Jacobi-preconditioned
+// conjugate gradients in FP32 with FP64 dot products, warm-started from the
+// previous sweep's solutions.  Then Eq. update_q0_x with cap and damping.
+//
+// Q p is a periodic stencil: H^T H is the autocorrelation of the kernel,
+// G(a, b) = sum_{u,v} k[u,v] k[u+a, v+b], |a| <= kh-1, |b| <= kw-1.  A separable
+// kernel k = u v^T gives G = autocorr(u) x autocorr(v), applied as two 1-D passes;
+// otherwise H then H^T are applied in shared memory.
+//
+// Layout: every vector is one FP32 plane of N = H*W pixels, row-major; the
+// 1 + S right-hand sides are consecutive planes ([0] = mean system).
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "likelihood.cuh"
+
+namespace eptv {
+
+namespace {
+
+constexpr int kTile = 32;        // stencil and update tile, kTile x kTile pixels
+constexpr int kThreads = 256;
+constexpr int kMaxHalf = 14;     // H^T H half-width, kernels up to 15 x 15
+constexpr int kChunk = 4;        // CG iterations between convergence polls
+
+struct ConvDesc {
+  int H, W;
+  long long N;
+  int kh, kw;
+  int hr, hc;            // H^T H half-widths: kh - 1, kw - 1
+  int separable;
+  const float* k;        // kh x kw
+  const float* gr;       // 2 hr + 1 (separable)
+  const float* gc;       // 2 hc + 1 (separable)
+  float inv_xi;
+  float g0_xi;           // diag of H^T H / xi = sum k^2 / xi
+  int tiles_x, tiles_y;
+};
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+struct StencilSmem {
+  float* v;    // region (kTile + 2 hr) x (kTile + 2 hc)
+  float* tmp;  // separable: (kTile + 2 hr) x kTile; otherwise (kTile + hr) x (kTile + hc)
+  float* taps; // kernel taps staged in shared memory
+};
+
+// out[tr * kTile + tc] = (H^T H v)(tile pixel) for the region staged in sm.v.
+// All threads of the block participate; ends with __syncthreads().
+__device__ void hth_tile(const ConvDesc& c, StencilSmem& sm, float* out) {
+  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
+  const int tid = threadIdx.x;
+  if (c.separable) {
+    const float* gr = sm.taps;
+    const float* gc = sm.taps + (2 * c.hr + 1);
+    // pass 1: along rows, all region rows, tile columns
+    for (int idx = tid; idx < RH * kTile; idx += kThreads) {
+      const int rr = idx / kTile, tc = idx - rr * kTile;
+      const float* row = sm.v + rr * RW + tc;
+      float acc = 0.f;
+      for (int b = 0; b <= 2 * c.hc; ++b) acc = fmaf(gc[b], row[b], acc);
+      sm.tmp[idx] = acc;
+    }
+    __syncthreads();
+    // pass 2: along columns
+    for (int idx = tid; idx < kTile * kTile; idx += kThreads) {
+      const int tr = idx / kTile, tc = idx - tr * kTile;
+      const float* col = sm.tmp + tr * kTile + tc;
+      float acc = 0.f;
+      for (int a = 0; a <= 2 * c.hr; ++a) acc = fmaf(gr[a], col[a * kTile], acc);
+      out[idx] = acc;
+    }
+    __syncthreads();
+  } else {
+    const float* k = sm.taps;
+    const int hh = c.kh / 2, hw = c.kw / 2;
+    const int UH = kTile + 2 * hh, UW = kTile + 2 * hw;
+    // u = H v on the tile plus a (kh/2, kw/2) halo: u(r,c) = sum k[a,b] v(r-a+hh, c-b+hw)
+    for (int idx = tid; idx < UH * UW; idx += kThreads) {
+      const int ur = idx / UW, uc = idx - ur * UW;
+      float acc = 0.f;
+      for (int a = 0; a < c.kh; ++a) {
+        const float* vrow = sm.v + (ur - a + c.hr) * RW + uc + c.hc;
+        const float* krow = k + a * c.kw;
+        for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], vrow[-b], acc);
+      }
+      sm.tmp[idx] = acc;
+    }
+    __syncthreads();
+    // out = H^T u: out(r,c) = sum k[a,b] u(r+a-hh, c+b-hw)
+    for (int idx = tid; idx < kTile * kTile; idx += kThreads) {
+      const int tr = idx / kTile, tc = idx - tr * kTile;
+      float acc = 0.f;
+      for (int a = 0; a < c.kh; ++a) {
+        const float* urow = sm.tmp + (tr + a) * UW + tc;
+        const float* krow = k + a * c.kw;
+        for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], urow[b], acc);
+      }
+      out[idx] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void stage_taps(const ConvDesc& c, float* taps) {
+  if (c.separable) {
+    const int nr = 2 * c.hr + 1, nc = 2 * c.hc + 1;
+    for (int i = threadIdx.x; i < nr + nc; i += kThreads) taps[i] = i < nr ? c.gr[i] : c.gc[i - nr];
+  } else {
+    for (int i = threadIdx.x; i < c.kh * c.kw; i += kThreads) taps[i] = c.k[i];
+  }
+}
+
+__device__ __forceinline__ StencilSmem carve(const ConvDesc& c, float* base) {
+  StencilSmem sm;
+  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
+  sm.taps = base;
+  sm.v = base + 512;
+  sm.tmp = sm.v + RH * RW;
+  return sm;
+}
+
+// FP64 block sum of up to three per-thread values, written by thread 0.
+__device__ __forceinline__ void block_sum3(double a, double b, double c3, double* out_a,
+                                           double* out_b, double* out_c) {
+  __shared__ double red[3][kThreads / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+    c3 += __shfl_down_sync(0xffffffffu, c3, off);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+    red[2][w] = c3;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0, sc = 0;
+    for (int i = 0; i < kThreads / 32; ++i) {
+      sa += red[0][i];
+      sb += red[1][i];
+      sc += red[2][i];
+    }
+    if (out_a) *out_a = sa;
+    if (out_b) *out_b = sb;
+    if (out_c) *out_c = sc;
+  }
+  __syncthreads();
+}
+
+// Sum of one RHS's block partials, fixed order (warp 0), broadcast to the block.
+__device__ __forceinline__ double sum_partials(const double* part, int nb) {
+  __shared__ double bc;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) s += part[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) bc = s;
+  }
+  __syncthreads();
+  const double r = bc;
+  __syncthreads();
+  return r;
+}
+
+struct CgArgs {
+  ConvDesc c;
+  int R;                 // right-hand sides (1 + S)
+  int S;
+  float* X;              // R planes
+  float* Rr;             // R planes
+  float* P;              // R planes
+  float* Qp;             // R planes
+  const float* D;        // cavity precision
+  const float* Ncav;     // cavity natural mean
+  const float* Minv;     // 1 / diag(Q)
+  const float* Hty;      // H^T y / xi
+  const float* E1;       // S planes, H^T eps1 / sqrt(xi)
+  const float* E2;       // S planes, eps2
+  double* part_pq;       // [R][nb]
+  double* part_rz;       // [2][R][nb]
+  double* part_rr;       // [2][R][nb]
+  double* part_bb;       // [R][nb]
+  double rtol2;
+  int nb;
+  unsigned long long* counters;
+};
+
+__device__ __forceinline__ float rhs_value(const CgArgs& a, int j, long long p) {
+  if (j == 0) return a.Hty[p] + a.Ncav[p];
+  return a.E1[(long long)(j - 1) * a.c.N + p] + sqrtf(a.D[p]) * a.E2[(long long)(j - 1) * a.c.N + p];
+}
+
+// d = sum tau_k, n = sum nu_k (k = 1..4), Minv = 1 / (sum k^2 / xi + d)
+__global__ void prep_kernel(const float* __restrict__ tau, const float* __restrict__ nu,
+                            long long N, float g0_xi, float* D, float* Ncav, float* Minv) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    const float d = tau[N + p] + tau[2 * N + p] + tau[3 * N + p] + tau[4 * N + p];
+    const float n = nu[N + p] + nu[2 * N + p] + nu[3 * N + p] + nu[4 * N + p];
+    D[p] = d;
+    Ncav[p] = n;
+    Minv[p] = 1.0f / (g0_xi + d);
+  }
+}
+
+// r = b - Q x for every RHS (blockIdx.z), with partials r.Minv.r, r.r, b.b.
+__global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
+  extern __shared__ float smem[];
+  const ConvDesc& c = a.c;
+  const int j = blockIdx.z;
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  StencilSmem sm = carve(c, smem);
+  __shared__ float outb[kTile * kTile];
+  stage_taps(c, sm.taps);
+  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
+  const float* x = a.X + (long long)j * c.N;
+  for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
+    const int rr = idx / RW, cc = idx - rr * RW;
+    const int gr = wrapi(r0 - c.hr + rr, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
+    sm.v[idx] = x[(long long)gr * c.W + gcol];
+  }
+  __syncthreads();
+  hth_tile(c, sm, outb);
+  double rz = 0, rr2 = 0, bb = 0;
+  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+    const int tr = idx / kTile, tc = idx - tr * kTile;
+    const int gr = r0 + tr, gcol = c0 + tc;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    const float xv = sm.v[(tr + c.hr) * RW + tc + c.hc];
+    const float qx = outb[idx] * c.inv_xi + a.D[p] * xv;
+    const float b = rhs_value(a, j, p);
+    const float r = b - qx;
+    a.Rr[(long long)j * c.N + p] = r;
+    rz += (double)(r * r * a.Minv[p]);
+    rr2 += (double)(r * r);
+    bb += (double)(b * b);
+  }
+  const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
+  block_sum3(rz, rr2, bb, a.part_rz + o, a.part_rr + o, a.part_bb + o);
+}
+
+// Direction and product: p = Minv r + beta p, q = Q p, partial p.q.
+__global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
+  extern __shared__ float smem[];
+  const ConvDesc& c = a.c;
+  const int j = blockIdx.z;
+  const int buf = it & 1;
+  const double* rr_cur = a.part_rr + ((long long)buf * a.R + j) * a.nb;
+  const double rr = sum_partials(rr_cur, a.nb);
+  const double bb = sum_partials(a.part_bb + (long long)j * a.nb, a.nb);
+  if (rr <= a.rtol2 * bb) return;  // this system has converged
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(&a.counters[DC_CG_DIR_UNITS], 1ull);
+  float beta = 0.f;
+  if (it > 0) {
+    const double rz_new = sum_partials(a.part_rz + ((long long)buf * a.R + j) * a.nb, a.nb);
+    const double rz_old = sum_partials(a.part_rz + ((long long)(buf ^ 1) * a.R + j) * a.nb, a.nb);
+    beta = (float)(rz_new / rz_old);
+  }
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  StencilSmem sm = carve(c, smem);
+  __shared__ float outb[kTile * kTile];
+  stage_taps(c, sm.taps);
+  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
+  const float* r = a.Rr + (long long)j * c.N;
+  float* P = a.P + (long long)j * c.N;
+  for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
+    const int rr_ = idx / RW, cc = idx - rr_ * RW;
+    const int gr = wrapi(r0 - c.hr + rr_, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
+    const long long p = (long long)gr * c.W + gcol;
+    float v = r[p] * a.Minv[p];
+    if (it > 0) v = fmaf(beta, P[p], v);
+    sm.v[idx] = v;
+  }
+  __syncthreads();  // all reads of the old P are done before any write below
+  hth_tile(c, sm, outb);
+  double pq = 0;
+  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+    const int tr = idx / kTile, tc = idx - tr * kTile;
+    const int gr = r0 + tr, gcol = c0 + tc;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    const float pv = sm.v[(tr + c.hr) * RW + tc + c.hc];
+    const float q = outb[idx] * c.inv_xi + a.D[p] * pv;
+    P[p] = pv;
+    a.Qp[(long long)j * c.N + p] = q;
+    pq += (double)(pv * q);
+  }
+  block_sum3(pq, 0.0, 0.0, a.part_pq + (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x,
+             nullptr, nullptr);
+}
+
+// x += alpha p, r -= alpha q, partials of the new r.Minv.r and r.r.
+__global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
+  const ConvDesc& c = a.c;
+  const int j = blockIdx.z;
+  const int buf = it & 1, nbuf = buf ^ 1;
+  const long long o_cur = ((long long)buf * a.R + j) * a.nb;
+  const long long o_nxt = ((long long)nbuf * a.R + j) * a.nb;
+  const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
+  const double rr = sum_partials(a.part_rr + o_cur, a.nb);
+  const double bb = sum_partials(a.part_bb + (long long)j * a.nb, a.nb);
+  if (rr <= a.rtol2 * bb) {
+    // converged: carry this block's partials forward so the state stays converged
+    if (threadIdx.x == 0) {
+      a.part_rr[o_nxt + blk] = a.part_rr[o_cur + blk];
+      a.part_rz[o_nxt + blk] = a.part_rz[o_cur + blk];
+    }
+    return;
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(&a.counters[DC_CG_UPD_UNITS], 1ull);
+  const double rz = sum_partials(a.part_rz + o_cur, a.nb);
+  const double pq = sum_partials(a.part_pq + (long long)j * a.nb, a.nb);
+  const float alpha = (float)(rz / pq);
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  float* X = a.X + (long long)j * c.N;
+  float* Rr = a.Rr + (long long)j * c.N;
+  const float* P = a.P + (long long)j * c.N;
+  const float* Q = a.Qp + (long long)j * c.N;
+  double rz2 = 0, rr2 = 0;
+  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+    const int tr = idx / kTile, tc = idx - tr * kTile;
+    const int gr = r0 + tr, gcol = c0 + tc;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    X[p] = fmaf(alpha, P[p], X[p]);
+    const float r = fmaf(-alpha, Q[p], Rr[p]);
+    Rr[p] = r;
+    rz2 += (double)(r * r * a.Minv[p]);
+    rr2 += (double)(r * r);
+  }
+  block_sum3(rz2, rr2, 0.0, a.part_rz + o_nxt + blk, a.part_rr + o_nxt + blk, nullptr);
+}
+
+// Number of systems still above tolerance, from the partials in buffer `buf`.
+__global__ void check_kernel(const double* part_rr, const double* part_bb, int R, int nb,
+                             double rtol2, int buf, int* active) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < R; j += blockDim.x / 32) {
+    double rr = 0, bb = 0;
+    for (int i = lane; i < nb; i += 32) {
+      rr += part_rr[((long long)buf * R + j) * nb + i];
+      bb += part_bb[(long long)j * nb + i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      rr += __shfl_down_sync(0xffffffffu, rr, off);
+      bb += __shfl_down_sync(0xffffffffu, bb, off);
+    }
+    if (lane == 0 && !(rr <= rtol2 * bb)) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *active = cnt;
+}
+
+// Eq. update_q0_x from E = X[0] and the RBMC variance, with cap and damping.
+__global__ void site0_kernel(CgArgs a, float* tau0, float* nu0, float min_tau, float damping,
+                             unsigned* status, unsigned long long* counters) {
+  const long long N = a.c.N;
+  unsigned capped = 0;
+  bool bad = false;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    const float minv = a.Minv[p];
+    const float qii = a.c.g0_xi + a.D[p];
+    const float sd = sqrtf(a.D[p]);
+    float acc = 0.f;
+    for (int s = 0; s < a.S; ++s) {
+      const long long o = (long long)s * N + p;
+      const float w = a.E1[o] + sd * a.E2[o];
+      const float off = w - qii * a.X[(long long)(s + 1) * N + p];
+      acc = fmaf(off, off, acc);
+    }
+    const float var = minv + minv * minv * acc / (float)a.S;
+    const float E = a.X[p];
+    const float d = a.D[p];
+    float tn = 1.0f / var - d;
+    if (!(tn >= min_tau)) {
+      tn = min_tau;
+      ++capped;
+    }
+    const float nn = tn * E + d * E - a.Ncav[p];  // tau E + (E - m) / c
+    const float t_new = damping * tn + (1.0f - damping) * tau0[p];
+    const float n_new = damping * nn + (1.0f - damping) * nu0[p];
+    tau0[p] = t_new;
+    nu0[p] = n_new;
+    bad |= !(isfinite(t_new) && isfinite(n_new));
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+  if (capped) atomicAdd(&counters[DC_CAPPED], (unsigned long long)capped);
+}
+
+// out = scale * H^T in (periodic), one plane per blockIdx.y; one-time setup.
+__global__ void conv_t_kernel(const float* in, float* out, int H, int W, const float* k, int kh,
+                              int kw, float scale, int planes) {
+  const long long N = (long long)H * W;
+  const int pl = blockIdx.y;
+  if (pl >= planes) return;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(p / W), c = (int)(p - (long long)r * W);
+    double acc = 0.0;
+    for (int a = 0; a < kh; ++a)
+      for (int b = 0; b < kw; ++b) {
+        const int rr = wrapi(r + a - kh / 2, H), cc = wrapi(c + b - kw / 2, W);
+        acc += (double)k[a * kw + b] * (double)in[(long long)pl * N + (long long)rr * W + cc];
+      }
+    out[(long long)pl * N + p] = (float)(acc * scale);
+  }
+}
+
+// Standard normals from SplitMix64 (Steele, Lea and Flood, 2014) used as a
+// counter-based generator: draw t is the output for state seed + (t+1) * golden
+// gamma; two 24-bit uniforms feed the Box-Muller transform.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                         unsigned long long t) {
+  unsigned long long z = seed + (t + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void normals_kernel(float* out, long long count, unsigned long long seed,
+                               unsigned long long base) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long t = 2ull * (base + (unsigned long long)i);
+    const double u1 = ((double)(splitmix64(seed, t) >> 40) + 0.5) * (1.0 / 16777216.0);
+    const double u2 = ((double)(splitmix64(seed, t + 1) >> 40) + 0.5) * (1.0 / 16777216.0);
+    out[i] = (float)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+  }
+}
+
+__global__ void set_status_kernel(unsigned* status, unsigned bit) { atomicOr(status, bit); }
+__global__ void store_iters_kernel(unsigned long long* counters, unsigned long long v) {
+  counters[DC_CG_ITERS] = v;
+}
+
+inline int grid1d(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 1 << 20);
+}
+
+}  // namespace
+
+struct LikelihoodState {
+  ConvDesc c;
+  int S = 0, R = 0;
+  float inv_xi = 0.f;
+  double rtol2 = 0.0;
+  int max_iter = 0;
+  unsigned long long seed = 0;
+  float damping = 0.5f, min_tau = 1e-8f;
+  float* d_k = nullptr;
+  float* d_g = nullptr;     // gr then gc
+  float* Hty = nullptr;
+  float* E1 = nullptr;
+  float* E2 = nullptr;
+  float* D = nullptr;
+  float* Ncav = nullptr;
+  float* Minv = nullptr;
+  float* X = nullptr;
+  float* Rr = nullptr;
+  float* P = nullptr;
+  float* Qp = nullptr;
+  double* part = nullptr;   // pq, rz[2], rr[2], bb
+  int* d_active = nullptr;
+  int* h_active = nullptr;  // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int nb = 0;
+  size_t smem = 0;
+  int last_iters = 0;
+};
+
+namespace {
+
+CgArgs cg_args(LikelihoodState* L) {
+  CgArgs a;
+  a.c = L->c;
+  a.R = L->R;
+  a.S = L->S;
+  a.X = L->X;
+  a.Rr = L->Rr;
+  a.P = L->P;
+  a.Qp = L->Qp;
+  a.D = L->D;
+  a.Ncav = L->Ncav;
+  a.Minv = L->Minv;
+  a.Hty = L->Hty;
+  a.E1 = L->E1;
+  a.E2 = L->E2;
+  const long long rn = (long long)L->R * L->nb;
+  a.part_pq = L->part;
+  a.part_rz = L->part + rn;
+  a.part_rr = L->part + 3 * rn;
+  a.part_bb = L->part + 5 * rn;
+  a.rtol2 = L->rtol2;
+  a.nb = L->nb;
+  a.counters = nullptr;
+  return a;
+}
+
+// E1 = H^T eps1 / sqrt(xi) from E1 holding eps1 (in place through Rr as scratch).
+ep_tv_status finish_probes(LikelihoodState* L, cudaStream_t s) {
+  const long long N = L->c.N;
+  // Rr has R >= S planes: use it as scratch for the transform
+  if (cudaMemcpyAsync(L->Rr, L->E1, sizeof(float) * L->S * N, cudaMemcpyDeviceToDevice, s) !=
+      cudaSuccess)
+    return EP_TV_ERR_CUDA;
+  dim3 g(grid1d(N), L->S);
+  conv_t_kernel<<<g, 256, 0, s>>>(L->Rr, L->E1, L->c.H, L->c.W, L->d_k, L->c.kh, L->c.kw,
+                                  (float)std::sqrt((double)L->inv_xi), L->S);
+  return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+}
+
+}  // namespace
+
+ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, LikelihoodState** out,
+                               float* mu0) {
+  *out = nullptr;
+  const ep_tv_operator* op = cfg.op;
+  if (op->op != EP_TV_OP_CONV_PERIODIC) return EP_TV_ERR_UNSUPPORTED;
+  if (op->kh > 2 * kMaxHalf / 2 + 1 || op->kw > 2 * kMaxHalf / 2 + 1) return EP_TV_ERR_UNSUPPORTED;
+  LikelihoodState* L = new (std::nothrow) LikelihoodState();
+  if (!L) return EP_TV_ERR_NOMEM;
+  const int kh = op->kh, kw = op->kw;
+  // host: kernel, autocorrelation factors, separability
+  std::vector<double> k(kh * kw);
+  double kmax = 0.0;
+  int ai = 0, bi = 0;
+  for (int i = 0; i < kh * kw; ++i) {
+    k[i] = op->kernel[i];
+    if (!std::isfinite(k[i])) { delete L; return EP_TV_ERR_ARG; }
+    if (std::fabs(k[i]) > kmax) { kmax = std::fabs(k[i]); ai = i / kw; bi = i % kw; }
+  }
+  if (kmax == 0.0) { delete L; return EP_TV_ERR_ARG; }
+  std::vector<double> u(kh), v(kw);
+  for (int a = 0; a < kh; ++a) u[a] = k[a * kw + bi];
+  for (int b = 0; b < kw; ++b) v[b] = k[ai * kw + b] / k[ai * kw + bi];
+  bool sep = true;
+  for (int a = 0; a < kh && sep; ++a)
+    for (int b = 0; b < kw; ++b)
+      if (std::fabs(k[a * kw + b] - u[a] * v[b]) > 1e-7 * kmax) { sep = false; break; }
+  const int hr = kh - 1, hc = kw - 1;
+  std::vector<float> g;
+  double g0 = 0.0;
+  for (int i = 0; i < kh * kw; ++i) g0 += k[i] * k[i];
+  if (sep) {
+    for (int a = -hr; a <= hr; ++a) {
+      double acc = 0;
+      for (int t = 0; t < kh; ++t)
+        if (t + a >= 0 && t + a < kh) acc += u[t] * u[t + a];
+      g.push_back((float)acc);
+    }
+    for (int b = -hc; b <= hc; ++b) {
+      double acc = 0;
+      for (int t = 0; t < kw; ++t)
+        if (t + b >= 0 && t + b < kw) acc += v[t] * v[t + b];
+      g.push_back((float)acc);
+    }
+  }
+  L->S = cfg.p->rbmc_samples;
+  L->R = 1 + L->S;
+  L->inv_xi = (float)(1.0 / cfg.p->xi);
+  L->rtol2 = cfg.p->cg_rtol * cfg.p->cg_rtol;
+  L->max_iter = cfg.p->cg_max_iter;
+  L->seed = cfg.p->seed;
+  L->damping = (float)cfg.p->damping;
+  L->min_tau = (float)(1.0 / cfg.p->var_cap);
+  ConvDesc& c = L->c;
+  c.H = cfg.height;
+  c.W = cfg.width;
+  c.N = cfg.n;
+  c.kh = kh;
+  c.kw = kw;
+  c.hr = hr;
+  c.hc = hc;
+  c.separable = sep ? 1 : 0;
+  c.inv_xi = L->inv_xi;
+  c.g0_xi = (float)(g0 / cfg.p->xi);
+  c.tiles_x = (c.W + kTile - 1) / kTile;
+  c.tiles_y = (c.H + kTile - 1) / kTile;
+  L->nb = c.tiles_x * c.tiles_y;
+  const long long N = c.N;
+  const size_t RN = (size_t)L->R * N;
+  const size_t region = (size_t)(kTile + 2 * hr) * (kTile + 2 * hc);
+  const size_t tmp = std::max((size_t)(kTile + 2 * hr) * kTile,
+                              (size_t)(kTile + 2 * (kh / 2)) * (kTile + 2 * (kw / 2)));
+  L->smem = sizeof(float) * (512 + region + tmp);
+  std::vector<float> kf(kh * kw);
+  for (int i = 0; i < kh * kw; ++i) kf[i] = (float)k[i];
+  bool ok = cudaMalloc(&L->d_k, sizeof(float) * kh * kw) == cudaSuccess &&
+            cudaMalloc(&L->d_g, sizeof(float) * std::max<size_t>(g.size(), 1)) == cudaSuccess &&
+            cudaMalloc(&L->Hty, sizeof(float) * N) == cudaSuccess &&
+            cudaMalloc(&L->E1, sizeof(float) * L->S * N) == cudaSuccess &&
+            cudaMalloc(&L->E2, sizeof(float) * L->S * N) == cudaSuccess &&
+            cudaMalloc(&L->D, sizeof(float) * N) == cudaSuccess &&
+            cudaMalloc(&L->Ncav, sizeof(float) * N) == cudaSuccess &&
+            cudaMalloc(&L->Minv, sizeof(float) * N) == cudaSuccess &&
+            cudaMalloc(&L->X, sizeof(float) * RN) == cudaSuccess &&
+            cudaMalloc(&L->Rr, sizeof(float) * RN) == cudaSuccess &&
+            cudaMalloc(&L->P, sizeof(float) * RN) == cudaSuccess &&
+            cudaMalloc(&L->Qp, sizeof(float) * RN) == cudaSuccess &&
+            cudaMalloc(&L->part, sizeof(double) * 6 * L->R * L->nb) == cudaSuccess &&
+            cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
+            cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
+            cudaEventCreateWithFlags(&L->ev[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&L->ev[1], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    likelihood_destroy(L);
+    return EP_TV_ERR_NOMEM;
+  }
+  c.k = L->d_k;
+  c.gr = L->d_g;
+  c.gc = L->d_g + (2 * hr + 1);
+  if (cudaMemcpyAsync(L->d_k, kf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      (sep && cudaMemcpyAsync(L->d_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice,
+                              s) != cudaSuccess)) {
+    likelihood_destroy(L);
+    return EP_TV_ERR_CUDA;
+  }
+  if (L->smem > 48 * 1024) {
+    cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+    cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+  }
+  // H^T y / xi
+  conv_t_kernel<<<dim3(grid1d(N), 1), 256, 0, s>>>(cfg.y, L->Hty, c.H, c.W, L->d_k, kh, kw,
+                                                   L->inv_xi, 1);
+  // Algorithm 1 initialises q_{x,0} at mean y (M = N here)
+  if (cudaMemcpyAsync(mu0, cfg.y, sizeof(float) * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    likelihood_destroy(L);
+    return EP_TV_ERR_CUDA;
+  }
+  // library-drawn probes: eps1 then eps2 from one SplitMix64 counter stream
+  normals_kernel<<<grid1d((long long)L->S * N), 256, 0, s>>>(L->E1, (long long)L->S * N, L->seed, 0);
+  normals_kernel<<<grid1d((long long)L->S * N), 256, 0, s>>>(L->E2, (long long)L->S * N, L->seed,
+                                                             (unsigned long long)L->S * N);
+  ep_tv_status st = finish_probes(L, s);
+  if (st != EP_TV_OK) {
+    likelihood_destroy(L);
+    return st;
+  }
+  *out = L;
+  return EP_TV_OK;
+}
+
+void likelihood_destroy(LikelihoodState* L) {
+  if (!L) return;
+  cudaFree(L->d_k);
+  cudaFree(L->d_g);
+  cudaFree(L->Hty);
+  cudaFree(L->E1);
+  cudaFree(L->E2);
+  cudaFree(L->D);
+  cudaFree(L->Ncav);
+  cudaFree(L->Minv);
+  cudaFree(L->X);
+  cudaFree(L->Rr);
+  cudaFree(L->P);
+  cudaFree(L->Qp);
+  cudaFree(L->part);
+  cudaFree(L->d_active);
+  if (L->h_active) cudaFreeHost(L->h_active);
+  if (L->ev[0]) cudaEventDestroy(L->ev[0]);
+  if (L->ev[1]) cudaEventDestroy(L->ev[1]);
+  delete L;
+}
+
+ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s) {
+  if (cudaMemsetAsync(L->X, 0, sizeof(float) * L->R * L->c.N, s) != cudaSuccess) return EP_TV_ERR_CUDA;
+  L->last_iters = 0;
+  return EP_TV_OK;
+}
+
+ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const float* eps2,
+                                   int n_samples, cudaStream_t s) {
+  if (n_samples != L->S) return EP_TV_ERR_ARG;
+  const long long N = L->c.N;
+  if (cudaMemcpyAsync(L->E1, eps1, sizeof(float) * L->S * N, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(L->E2, eps2, sizeof(float) * L->S * N, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+    return EP_TV_ERR_CUDA;
+  return finish_probes(L, s);
+}
+
+ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, unsigned* status,
+                               unsigned long long* counters, Tracer* tr, cudaStream_t s) {
+  const ConvDesc& c = L->c;
+  const long long N = c.N;
+  prep_kernel<<<grid1d(N), 256, 0, s>>>(tau, nu, N, c.g0_xi, L->D, L->Ncav, L->Minv);
+  CgArgs a = cg_args(L);
+  a.counters = counters;
+  dim3 grid(c.tiles_x, c.tiles_y, L->R);
+  tr->begin(EP_TV_K_CG_RESIDUAL, s);
+  residual_kernel<<<grid, kThreads, L->smem, s>>>(a);
+  tr->end(s, (double)L->R * N);
+  int launched = 0, pending = -1, slot = 0, iters = -1;
+  bool ran_out = false;
+  while (true) {
+    const int n = std::min(kChunk, L->max_iter - launched);
+    for (int t = 0; t < n; ++t) {
+      tr->begin(EP_TV_K_CG_DIRECTION, s);
+      direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
+      tr->end(s, -1.0);
+      tr->begin(EP_TV_K_CG_UPDATE, s);
+      update_kernel<<<grid, kThreads, 0, s>>>(a, launched);
+      tr->end(s, -1.0);
+      ++launched;
+    }
+    check_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2, launched & 1,
+                                    L->d_active);
+    if (cudaMemcpyAsync(L->h_active + slot, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaEventRecord(L->ev[slot], s) != cudaSuccess)
+      return EP_TV_ERR_CUDA;
+    if (pending >= 0) {
+      if (cudaEventSynchronize(L->ev[pending & 1]) != cudaSuccess) return EP_TV_ERR_CUDA;
+      if (L->h_active[pending & 1] == 0) {
+        iters = pending >> 1;
+        break;
+      }
+    }
+    pending = (launched << 1) | slot;
+    slot ^= 1;
+    if (launched >= L->max_iter) {
+      if (cudaEventSynchronize(L->ev[pending & 1]) != cudaSuccess) return EP_TV_ERR_CUDA;
+      if (L->h_active[pending & 1] == 0) {
+        iters = launched;
+      } else {
+        iters = launched;
+        ran_out = true;
+      }
+      break;
+    }
+  }
+  L->last_iters = iters;
+  if (ran_out) set_status_kernel<<<1, 1, 0, s>>>(status, ST_CG_NOCONV);
+  store_iters_kernel<<<1, 1, 0, s>>>(counters, (unsigned long long)iters);
+  tr->begin(EP_TV_K_SITE0, s);
+  site0_kernel<<<grid1d(N), 256, 0, s>>>(a, tau, nu, L->min_tau, L->damping, status, counters);
+  tr->end(s, (double)N);
+  return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+}
+
+double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
+  switch (kernel) {
+    case EP_TV_K_CG_DIRECTION: return 16.0;  // read r, p; write p, q (per system pixel)
+    case EP_TV_K_CG_UPDATE: return 24.0;     // read x, r, p, q; write x, r
+    case EP_TV_K_CG_RESIDUAL: return 12.0;   // read x and the rhs source; write r
+    case EP_TV_K_SITE0:                      // read X (R planes), E1, E2, D, Ncav, Minv,
+      return 4.0 * (L->R + 2 * L->S + 5) + 8.0;  // tau0, nu0; write tau0, nu0
+  }
+  return 0.0;
+}
+
+int likelihood_systems(const LikelihoodState* L) { return L->R; }
+
+int likelihood_last_iters(const LikelihoodState* L) { return L->last_iters; }
+
+size_t likelihood_state_bytes(const LikelihoodState* L) {
+  return sizeof(float) * (size_t)L->R * L->c.N;
+}
+
+ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_t s) {
+  return cudaMemcpyAsync(host, L->X, likelihood_state_bytes(L), cudaMemcpyDeviceToHost, s) ==
+                 cudaSuccess
+             ? EP_TV_OK
+             : EP_TV_ERR_CUDA;
+}
+
+ep_tv_status likelihood_state_import(LikelihoodState* L, const void* host, cudaStream_t s) {
+  return cudaMemcpyAsync(L->X, host, likelihood_state_bytes(L), cudaMemcpyHostToDevice, s) ==
+                 cudaSuccess
+             ? EP_TV_OK
+             : EP_TV_ERR_CUDA;
+}
+
+}  // namespace eptv

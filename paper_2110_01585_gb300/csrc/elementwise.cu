@@ -1,0 +1,75 @@
+// Elementwise kernels: site initialisation (Algorithm 1) and the recombination
+// of the five sites into the posterior (Eq. Q_x_final).
+#include "internal.cuh"
+
+namespace eptv {
+
+namespace {
+
+constexpr int kEwThreads = 256;
+
+inline int ew_blocks(long long n) {
+  long long b = (n + kEwThreads - 1) / kEwThreads;
+  if (b > (1ll << 20)) b = 1ll << 20;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// q_{x,0} = N(mu0, xi I) and q_{x,k} = N(0, var_cap I), in natural parameters.
+__global__ void init_sites_kernel(float* tau, float* nu, const float* mu0, long long n,
+                                  float inv_xi, float min_tau) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    tau[p] = inv_xi;
+    nu[p] = mu0[p] * inv_xi;
+#pragma unroll
+    for (int s = 1; s < 5; ++s) {
+      tau[s * n + p] = min_tau;
+      nu[s * n + p] = 0.0f;
+    }
+  }
+}
+
+__global__ void fill_site0_kernel(float* tau, float* nu, const float* y, long long n,
+                                  float inv_xi) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    tau[p] = inv_xi;
+    nu[p] = y[p] * inv_xi;
+  }
+}
+
+// mean = (sum_s nu_s) / (sum_s tau_s), var = 1 / (sum_s tau_s)
+__global__ void posterior_kernel(const float* __restrict__ tau, const float* __restrict__ nu,
+                                 long long n, float* mean, float* var) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    float t = tau[p], v = nu[p];
+#pragma unroll
+    for (int s = 1; s < 5; ++s) {
+      t += tau[s * n + p];
+      v += nu[s * n + p];
+    }
+    const float sig = 1.0f / t;
+    if (mean) mean[p] = v * sig;
+    if (var) var[p] = sig;
+  }
+}
+
+}  // namespace
+
+void launch_init_sites(float* tau, float* nu, const float* mu0, long long n, float inv_xi,
+                       float min_tau, cudaStream_t s) {
+  init_sites_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau, nu, mu0, n, inv_xi, min_tau);
+}
+
+void launch_fill_site0_identity(float* tau, float* nu, const float* y, long long n, float inv_xi,
+                                cudaStream_t s) {
+  fill_site0_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau, nu, y, n, inv_xi);
+}
+
+void launch_posterior(const float* tau, const float* nu, long long n, float* mean, float* var,
+                      cudaStream_t s) {
+  posterior_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau, nu, n, mean, var);
+}
+
+}  // namespace eptv

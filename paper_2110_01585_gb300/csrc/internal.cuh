@@ -1,0 +1,126 @@
+// Internal declarations shared by the CUDA translation units of libeptv.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ep_tv.h"
+
+namespace eptv {
+
+// Device status bits (latched with atomicOr, read by synchronising calls).
+enum : unsigned {
+  ST_NONFINITE = 1u,
+  ST_CG_NOCONV = 2u,
+  ST_TIMEOUT = 4u,
+};
+
+// Slots of the per-context FP64 device scalars.
+enum : int {
+  DS_BETA = 0,   // current beta (lambda)
+  DS_ABAR = 1,   // a_u of the last sweep (after reduction)
+  DS_COUNT = 4,
+};
+
+// Counters (uint64 on the device).
+enum : int {
+  DC_FP64 = 0,
+  DC_CAPPED = 1,
+  DC_CG_ITERS = 2,
+  DC_CG_DIR_UNITS = 3,   // active systems summed over direction launches
+  DC_CG_UPD_UNITS = 4,   // active systems summed over update launches
+  DC_COUNT = 8,
+};
+
+// Host-side tracer: CUDA events around kernel launches, per kernel class.
+struct Tracer {
+  static constexpr int kPairs = 8192;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // 2 * kPairs
+  std::vector<int> kid;          // class of each recorded pair
+  std::vector<double> units;     // host-known units of each pair (or -1)
+  int used = 0;
+  double ms[EP_TV_K_COUNT] = {};
+  long long launches[EP_TV_K_COUNT] = {};
+  double host_units[EP_TV_K_COUNT] = {};
+
+  ~Tracer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  bool ensure() {
+    if (!ev.empty()) return true;
+    ev.resize(2 * kPairs);
+    kid.resize(kPairs);
+    units.resize(kPairs);
+    for (auto& e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return false;
+    return true;
+  }
+  void reset() {
+    used = 0;
+    for (int i = 0; i < EP_TV_K_COUNT; ++i) { ms[i] = 0; launches[i] = 0; host_units[i] = 0; }
+  }
+  // Waits for the recorded pairs and folds them into the totals.
+  void harvest() {
+    for (int i = 0; i < used; ++i) {
+      float t = 0.f;
+      cudaEventSynchronize(ev[2 * i + 1]);
+      if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+        ms[kid[i]] += t;
+        launches[kid[i]] += 1;
+        if (units[i] > 0) host_units[kid[i]] += units[i];
+      }
+    }
+    used = 0;
+  }
+  void begin(int k, cudaStream_t s) {
+    if (!on) return;
+    if (used == kPairs) harvest();
+    kid[used] = k;
+    cudaEventRecord(ev[2 * used], s);
+  }
+  void end(cudaStream_t s, double u) {
+    if (!on) return;
+    units[used] = u;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+  }
+};
+
+struct SweepArgs {
+  float* tau;                 // [5][N] site precisions, row 0 = likelihood site
+  float* nu;                  // [5][N] site precision-times-mean
+  const float* y;             // identity operator: observation (site 0 = (1/xi, y/xi))
+  float inv_xi;               // 1 / xi as float (identity operator)
+  int height, width;
+  long long n;
+  int periodic;
+  float damping;
+  float min_tau;              // 1 / var_cap
+  const double* beta;         // device scalar
+  int order;                  // four 4-bit k values, first update in the low nibble
+  int fp64_tail;              // 1: recompute poorly conditioned edges in FP64
+  double* abar_partial;       // one FP64 partial sum of E|u| per block
+  unsigned* status;
+  unsigned long long* counters;
+};
+
+// Prior-site sweep over V_1..V_4 for one image; site 0 implicit (identity) or stored.
+void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s);
+// Algorithmic DRAM bytes per pixel of one prior-site pass.
+double prior_sweep_bytes_per_pixel(bool site0_from_y);
+int prior_sweep_blocks(int height, int width);
+
+// abar = sum(partials) in a fixed order; if do_em, beta = n / abar.
+void launch_abar_reduce(const double* partial, int n_partial, double* dscal, double n_pixels,
+                        int do_em, cudaStream_t s);
+
+void launch_init_sites(float* tau, float* nu, const float* mu0, long long n, float inv_xi,
+                       float min_tau, cudaStream_t s);
+void launch_posterior(const float* tau, const float* nu, long long n, float* mean, float* var,
+                      cudaStream_t s);
+void launch_fill_site0_identity(float* tau, float* nu, const float* y, long long n, float inv_xi,
+                                cudaStream_t s);
+
+}  // namespace eptv

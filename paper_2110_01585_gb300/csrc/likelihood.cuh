@@ -1,0 +1,45 @@
+// Likelihood-site (q_{x,0}) update for non-diagonal H^T H: interface between
+// the C ABI and the operator-specific kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/ep_tv.h"
+
+namespace eptv {
+
+struct Tracer;
+
+struct LikelihoodConfig {
+  const ep_tv_operator* op;
+  const ep_tv_params* p;
+  int height, width;
+  long long n;
+  int m;
+  const float* y;  // device copy owned by the context
+};
+
+struct LikelihoodState;
+
+// Builds operator data and solver buffers; writes the initial mean of site 0
+// (Algorithm 1: y; H^T y when y is shorter than x) into mu0 (device, n floats).
+ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, LikelihoodState** out,
+                               float* mu0);
+void likelihood_destroy(LikelihoodState* L);
+// Clears solver warm starts (called on init/reset).
+ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s);
+ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const float* eps2,
+                                   int n_samples, cudaStream_t s);
+// One q_{x,0} update: cavity from sites 1..4, tilted moments of P_0
+// (Eq. tilted_P_1), site update (Eq. update_q0_x) with cap and damping.
+ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, unsigned* status,
+                               unsigned long long* counters, Tracer* tr, cudaStream_t s);
+// Algorithmic DRAM bytes per unit of the traced likelihood kernels.
+double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel);
+int likelihood_systems(const LikelihoodState* L);
+int likelihood_last_iters(const LikelihoodState* L);
+size_t likelihood_state_bytes(const LikelihoodState* L);
+ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_t s);
+ep_tv_status likelihood_state_import(LikelihoodState* L, const void* host, cudaStream_t s);
+
+}  // namespace eptv

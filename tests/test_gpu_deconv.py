@@ -1,0 +1,196 @@
+"""GPU parity of the deconvolution path (prior sweep + CG/RBMC likelihood site)."""
+import numpy as np
+import pytest
+
+from oracle import operators
+from oracle.ep import EPOracle
+from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC
+from paper_2110_01585_gb300 import synthetic as syn
+
+from ._parity import assert_parity, cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _probes(S, n, seed):
+    return syn.rbmc_probes(S, n, n, seed=seed)
+
+
+def _gpu(p, sweeps, S, probes, em_every=0, cg_rtol=1e-6, **kw):
+    torch = cuda()
+    yt = torch.as_tensor(p.y.astype(np.float32), device="cuda")
+    ep = EPTV(yt, p.xi, p.beta, op=OP_CONV_PERIODIC, kernel=p.kernel, rbmc_samples=S,
+              cg_rtol=cg_rtol, **kw)
+    ep.set_probes(torch.as_tensor(probes[0], dtype=torch.float32, device="cuda"),
+                  torch.as_tensor(probes[1], dtype=torch.float32, device="cuda"))
+    ep.sweep(sweeps, em_every=em_every)
+    mu, var = ep.posterior()
+    st = ep.status()
+    out = mu.cpu().numpy(), var.cpu().numpy(), ep
+    assert st == 0, st
+    return out
+
+
+def _oracle(p, sweeps, probes, em_every=0, order="prior_first"):
+    h, w = p.shape
+    o = EPOracle("deconv", p.y, p.xi, p.beta, h, w, kernel=p.kernel, site0="rbmc",
+                 probes=probes, order=order)
+    o.run(sweeps, em_every=em_every)
+    mu, var = o.posterior()
+    return mu, var, o
+
+
+def test_deconv_32_uniform9_em():
+    p = syn.deconv_problem(32, 32, kernel=syn.uniform_kernel(9), bsnr_db=40.0, beta0=1.0,
+                           seed=0, grf_length=8.0)
+    pr = _probes(8, 32 * 32, 1)
+    mu, var, ep = _gpu(p, 10, 8, pr, em_every=5)
+    mu_r, var_r, o = _oracle(p, 10, pr, em_every=5)
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    ep.close()
+
+
+def test_deconv_multi_tile_ragged_uniform5():
+    p = syn.deconv_problem(48, 80, kernel=syn.uniform_kernel(5), bsnr_db=30.0, beta0=3.0,
+                           seed=2, grf_length=8.0)
+    pr = _probes(4, 48 * 80, 3)
+    mu, var, ep = _gpu(p, 6, 4, pr, em_every=3)
+    mu_r, var_r, _ = _oracle(p, 6, pr, em_every=3)
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    ep.close()
+
+
+def test_deconv_non_separable_kernel():
+    rng = np.random.default_rng(4)
+    k = rng.random((5, 3)) ** 2
+    k /= k.sum()
+    p = syn.deconv_problem(40, 36, kernel=k, bsnr_db=35.0, beta0=5.0, seed=5, grf_length=6.0)
+    pr = _probes(6, 40 * 36, 6)
+    mu, var, ep = _gpu(p, 5, 6, pr)
+    mu_r, var_r, _ = _oracle(p, 5, pr)
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    ep.close()
+
+
+def test_deconv_gaussian15():
+    p = syn.deconv_problem(48, 48, kernel=syn.gaussian_kernel(15, 2.0), bsnr_db=30.0, beta0=2.0,
+                           seed=7, grf_length=8.0)
+    pr = _probes(4, 48 * 48, 8)
+    mu, var, ep = _gpu(p, 4, 4, pr)
+    mu_r, var_r, _ = _oracle(p, 4, pr)
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    ep.close()
+
+
+def test_deconv_q0_first_order():
+    p = syn.deconv_problem(32, 40, kernel=syn.uniform_kernel(3), bsnr_db=30.0, beta0=4.0,
+                           seed=9, grf_length=8.0)
+    pr = _probes(4, 32 * 40, 10)
+    mu, var, ep = _gpu(p, 5, 4, pr, order_mode=1)
+    mu_r, var_r, _ = _oracle(p, 5, pr, order="q0_first")
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    ep.close()
+
+
+def test_unit_kernel_equals_denoising_path():
+    """H = I through the CG/RBMC route: diagonal precision, exact RB estimate."""
+    torch = cuda()
+    p = syn.denoise_problem(32, 64, sigma=0.1, beta=10.0, seed=11)
+    p.kernel = np.ones((1, 1))
+    pr = _probes(2, 32 * 64, 12)
+    mu, var, ep = _gpu(p, 8, 2, pr)
+    yt = torch.as_tensor(p.y.astype(np.float32), device="cuda")
+    with EPTV(yt, p.xi, p.beta) as d:
+        d.sweep(8)
+        mu_d, var_d = (t.cpu().numpy() for t in d.posterior())
+    np.testing.assert_allclose(mu, mu_d, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(var, var_d, rtol=1e-5)
+    ep.close()
+
+
+def test_checkpoint_resume_deconv():
+    torch = cuda()
+    p = syn.deconv_problem(32, 32, kernel=syn.uniform_kernel(5), bsnr_db=30.0, seed=13,
+                           grf_length=8.0)
+    pr = _probes(4, 1024, 14)
+    _, _, a = _gpu(p, 4, 4, pr, em_every=2)
+    _, _, b = _gpu(p, 0, 4, pr, em_every=2)
+    blob = a.state_export()
+    a.sweep(4, em_every=2)
+    b.state_import(blob)
+    b.sweep(4, em_every=2)
+    ma, va = a.posterior()
+    mb, vb = b.posterior()
+    assert torch.equal(ma, mb) and torch.equal(va, vb)
+    a.close()
+    b.close()
+
+
+def test_library_probes_have_standard_normal_statistics():
+    """The library's own SplitMix64/Box-Muller probes (no caller probes): run and
+    check that the variance estimate is close to the exact-solve oracle."""
+    torch = cuda()
+    p = syn.deconv_problem(32, 32, kernel=syn.uniform_kernel(5), bsnr_db=30.0, seed=15,
+                           grf_length=8.0)
+    yt = torch.as_tensor(p.y.astype(np.float32), device="cuda")
+    with EPTV(yt, p.xi, p.beta, op=OP_CONV_PERIODIC, kernel=p.kernel, rbmc_samples=64) as ep:
+        ep.sweep(3)
+        mu, var = (t.cpu().numpy() for t in ep.posterior())
+    o = EPOracle("deconv", p.y, p.xi, p.beta, 32, 32, kernel=p.kernel, site0="exact")
+    o.run(3)
+    mu_r, var_r = o.posterior()
+    # Monte Carlo error of the variance with 64 probes: a few percent at most
+    assert np.median(np.abs(var / var_r - 1)) < 0.05
+    assert np.max(np.abs(mu - mu_r)) < 0.05 * (p.y.max() - p.y.min())
+
+
+def test_full_size_512_residual_and_site0_samples():
+    """512^2, 9x9 uniform blur, BSNR 40 dB: after a sweep, the mean solve satisfies
+    Q E = b everywhere (checked in FP64 with the oracle's operator), and the new
+    likelihood site at sampled pixels follows the RB estimate and Eq. update_q0_x."""
+    torch = cuda()
+    h = w = 512
+    S = 32
+    p = syn.deconv_problem(h, w, kernel=syn.uniform_kernel(9), bsnr_db=40.0, beta0=1.0, seed=0)
+    pr = _probes(S, h * w, 21)
+    _, _, ep = _gpu(p, 2, S, pr, em_every=0)
+    tau0, nu0 = (t.cpu().numpy().astype(np.float64) for t in ep.sites())
+    ep.sweep(1)
+    tau1, nu1 = (t.cpu().numpy().astype(np.float64) for t in ep.sites())
+    blob = np.frombuffer(ep.state_export(), dtype=np.uint8)
+    n = h * w
+    off = 4 * 8 + 4 * 8 + 2 * 4 * 5 * n
+    X = np.frombuffer(blob[off:].tobytes(), dtype=np.float32).reshape(1 + S, h, w).astype(np.float64)
+    ep.close()
+    d = tau1[1:].sum(axis=0)          # cavity precision of site 0 (prior sites of this sweep)
+    ncav = nu1[1:].sum(axis=0)
+    k = p.kernel
+    def Q(v):
+        return operators.conv_periodic_t(operators.conv_periodic(v, k), k) / p.xi + d * v
+    b = operators.conv_periodic_t(p.y, k) / p.xi + ncav
+    r = b - Q(X[0])
+    assert np.linalg.norm(r) <= 1e-5 * np.linalg.norm(b)
+    # probe systems
+    g0 = float(np.sum(k * k)) / p.xi
+    Ws = []
+    for s in range(S):
+        w_s = (operators.conv_periodic_t(pr[0][s].reshape(h, w), k) / np.sqrt(p.xi)
+               + np.sqrt(d) * pr[1][s].reshape(h, w))
+        rs = w_s - Q(X[s + 1])
+        assert np.linalg.norm(rs) <= 1e-5 * np.linalg.norm(w_s), s
+        Ws.append(w_s)
+    # site 0 at sampled pixels
+    rng = np.random.default_rng(22)
+    for rr, cc in rng.integers(0, 512, size=(50, 2)):
+        qii = g0 + d[rr, cc]
+        acc = 0.0
+        for s in range(S):
+            acc += (Ws[s][rr, cc] - qii * X[s + 1, rr, cc]) ** 2
+        var = 1 / qii + acc / S / qii ** 2
+        E = X[0, rr, cc]
+        t_new = max(1 / var - d[rr, cc], 1e-8)
+        n_new = t_new * E + d[rr, cc] * E - ncav[rr, cc]
+        t_exp = 0.5 * t_new + 0.5 * tau0[0, rr, cc]
+        n_exp = 0.5 * n_new + 0.5 * nu0[0, rr, cc]
+        assert abs(tau1[0, rr, cc] / t_exp - 1) < 1e-4
+        assert abs(nu1[0, rr, cc] - n_exp) <= 1e-4 * abs(t_exp) * (abs(E) + 0.1)

@@ -338,3 +338,18 @@ def test_site_invariants_after_sweeps():
         for s in range(5):
             c, _ = o.cavity(s)
             assert np.all(c > 0)
+
+
+def test_cg_mode_equals_dense_mode():
+    """The CG/FFT route for large images gives the dense-solve result."""
+    rng = np.random.default_rng(16)
+    k = rng.random((3, 5))
+    k /= k.sum()
+    p = syn.deconv_problem(12, 10, kernel=k, bsnr_db=30.0, seed=17, grf_length=4.0)
+    pr = syn.rbmc_probes(3, 120, 120, seed=18)
+    a = EPOracle("deconv", p.y, p.xi, 3.0, 12, 10, kernel=k, site0="rbmc", probes=pr)
+    b = EPOracle("deconv", p.y, p.xi, 3.0, 12, 10, kernel=k, site0="rbmc_cg", probes=pr)
+    a.run(3)
+    b.run(3)
+    for u, v in zip(a.posterior(), b.posterior()):
+        np.testing.assert_allclose(u, v, rtol=1e-8)
