@@ -98,7 +98,8 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = sorted(float(s[0]) for s in self.samples)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[2 + i]})
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[2 + i].strip().lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(self.samples[0][1]),
                 "reasons": reasons, "samples": len(sm)}
 

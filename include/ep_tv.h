@@ -179,7 +179,8 @@ typedef enum {
   EP_TV_K_CG_UPDATE = 2,     /* CG x / r update, unit = pixel of one active system */
   EP_TV_K_CG_RESIDUAL = 3,   /* initial CG residual, unit = pixel of one system */
   EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
-  EP_TV_K_COUNT = 5
+  EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one system */
+  EP_TV_K_COUNT = 6
 } ep_tv_kernel;
 
 /* Tracing: with on != 0, every launch of the kernel classes above is bracketed

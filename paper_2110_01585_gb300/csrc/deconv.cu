@@ -140,10 +140,11 @@ __device__ __forceinline__ StencilSmem carve(const ConvDesc& c, float* base) {
   return sm;
 }
 
-// FP64 block sum of up to three per-thread values, written by thread 0.
+// FP64 block sum of up to three per-thread values, written by thread 0 (any block
+// size up to 1024 threads, a multiple of 32).
 __device__ __forceinline__ void block_sum3(double a, double b, double c3, double* out_a,
                                            double* out_b, double* out_c) {
-  __shared__ double red[3][kThreads / 32];
+  __shared__ double red[3][32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, off);
@@ -159,7 +160,7 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c3, double
   __syncthreads();
   if (threadIdx.x == 0) {
     double sa = 0, sb = 0, sc = 0;
-    for (int i = 0; i < kThreads / 32; ++i) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       sa += red[0][i];
       sb += red[1][i];
       sc += red[2][i];
@@ -201,12 +202,15 @@ struct CgArgs {
   const float* Hty;      // H^T y / xi
   const float* E1;       // S planes, H^T eps1 / sqrt(xi)
   const float* E2;       // S planes, eps2
+  float* Z;              // R planes, preconditioned residual (FFT preconditioner)
   double* part_pq;       // [R][nb]
-  double* part_rz;       // [2][R][nb]
+  double* part_rz;       // [2][R][nbz]
   double* part_rr;       // [2][R][nb]
   double* part_bb;       // [R][nb]
   double rtol2;
-  int nb;
+  int nb;                // tile blocks per system
+  int nbz;               // blocks per system producing r.z partials
+  int fft;               // 1: z = M^{-1} r by the circulant preconditioner, else Jacobi
   unsigned long long* counters;
 };
 
@@ -215,9 +219,12 @@ __device__ __forceinline__ float rhs_value(const CgArgs& a, int j, long long p) 
   return a.E1[(long long)(j - 1) * a.c.N + p] + sqrtf(a.D[p]) * a.E2[(long long)(j - 1) * a.c.N + p];
 }
 
-// d = sum tau_k, n = sum nu_k (k = 1..4), Minv = 1 / (sum k^2 / xi + d)
-__global__ void prep_kernel(const float* __restrict__ tau, const float* __restrict__ nu,
-                            long long N, float g0_xi, float* D, float* Ncav, float* Minv) {
+// d = sum tau_k, n = sum nu_k (k = 1..4), Minv = 1 / (sum k^2 / xi + d); block sums of d.
+__global__ void __launch_bounds__(kThreads) prep_kernel(const float* __restrict__ tau,
+                                                        const float* __restrict__ nu, long long N,
+                                                        float g0_xi, float* D, float* Ncav,
+                                                        float* Minv, double* dpart) {
+  double acc = 0.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
        p += (long long)gridDim.x * blockDim.x) {
     const float d = tau[N + p] + tau[2 * N + p] + tau[3 * N + p] + tau[4 * N + p];
@@ -225,7 +232,23 @@ __global__ void prep_kernel(const float* __restrict__ tau, const float* __restri
     D[p] = d;
     Ncav[p] = n;
     Minv[p] = 1.0f / (g0_xi + d);
+    acc += (double)d;
   }
+  block_sum3(acc, 0.0, 0.0, dpart + blockIdx.x, nullptr, nullptr);
+}
+
+// dbar = mean of d over the image (fixed-order reduction of the block sums).
+__global__ void mean_kernel(const double* dpart, int n, double inv_count, double* out) {
+  __shared__ double buf[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += dpart[i];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) buf[threadIdx.x] += buf[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = buf[0] * inv_count;
 }
 
 // r = b - Q x for every RHS (blockIdx.z), with partials r.Minv.r, r.r, b.b.
@@ -257,12 +280,12 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
     const float b = rhs_value(a, j, p);
     const float r = b - qx;
     a.Rr[(long long)j * c.N + p] = r;
-    rz += (double)(r * r * a.Minv[p]);
+    if (!a.fft) rz += (double)(r * r * a.Minv[p]);
     rr2 += (double)(r * r);
     bb += (double)(b * b);
   }
   const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
-  block_sum3(rz, rr2, bb, a.part_rz + o, a.part_rr + o, a.part_bb + o);
+  block_sum3(rz, rr2, bb, a.fft ? nullptr : a.part_rz + o, a.part_rr + o, a.part_bb + o);
 }
 
 // Direction and product: p = Minv r + beta p, q = Q p, partial p.q.
@@ -279,8 +302,8 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
     atomicAdd(&a.counters[DC_CG_DIR_UNITS], 1ull);
   float beta = 0.f;
   if (it > 0) {
-    const double rz_new = sum_partials(a.part_rz + ((long long)buf * a.R + j) * a.nb, a.nb);
-    const double rz_old = sum_partials(a.part_rz + ((long long)(buf ^ 1) * a.R + j) * a.nb, a.nb);
+    const double rz_new = sum_partials(a.part_rz + ((long long)buf * a.R + j) * a.nbz, a.nbz);
+    const double rz_old = sum_partials(a.part_rz + ((long long)(buf ^ 1) * a.R + j) * a.nbz, a.nbz);
     beta = (float)(rz_new / rz_old);
   }
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
@@ -289,12 +312,13 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
   stage_taps(c, sm.taps);
   const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
   const float* r = a.Rr + (long long)j * c.N;
+  const float* z = a.Z + (long long)j * c.N;
   float* P = a.P + (long long)j * c.N;
   for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
     const int rr_ = idx / RW, cc = idx - rr_ * RW;
     const int gr = wrapi(r0 - c.hr + rr_, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
     const long long p = (long long)gr * c.W + gcol;
-    float v = r[p] * a.Minv[p];
+    float v = a.fft ? z[p] : r[p] * a.Minv[p];
     if (it > 0) v = fmaf(beta, P[p], v);
     sm.v[idx] = v;
   }
@@ -323,6 +347,8 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const int buf = it & 1, nbuf = buf ^ 1;
   const long long o_cur = ((long long)buf * a.R + j) * a.nb;
   const long long o_nxt = ((long long)nbuf * a.R + j) * a.nb;
+  const long long oz_cur = ((long long)buf * a.R + j) * a.nbz;
+  const long long oz_nxt = ((long long)nbuf * a.R + j) * a.nbz;
   const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
   const double rr = sum_partials(a.part_rr + o_cur, a.nb);
   const double bb = sum_partials(a.part_bb + (long long)j * a.nb, a.nb);
@@ -330,13 +356,13 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
     // converged: carry this block's partials forward so the state stays converged
     if (threadIdx.x == 0) {
       a.part_rr[o_nxt + blk] = a.part_rr[o_cur + blk];
-      a.part_rz[o_nxt + blk] = a.part_rz[o_cur + blk];
+      if (!a.fft) a.part_rz[oz_nxt + blk] = a.part_rz[oz_cur + blk];
     }
     return;
   }
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&a.counters[DC_CG_UPD_UNITS], 1ull);
-  const double rz = sum_partials(a.part_rz + o_cur, a.nb);
+  const double rz = sum_partials(a.part_rz + oz_cur, a.nbz);
   const double pq = sum_partials(a.part_pq + (long long)j * a.nb, a.nb);
   const float alpha = (float)(rz / pq);
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
@@ -353,10 +379,212 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
     X[p] = fmaf(alpha, P[p], X[p]);
     const float r = fmaf(-alpha, Q[p], Rr[p]);
     Rr[p] = r;
-    rz2 += (double)(r * r * a.Minv[p]);
+    if (!a.fft) rz2 += (double)(r * r * a.Minv[p]);
     rr2 += (double)(r * r);
   }
-  block_sum3(rz2, rr2, 0.0, a.part_rz + o_nxt + blk, a.part_rr + o_nxt + blk, nullptr);
+  block_sum3(rz2, rr2, 0.0, a.fft ? nullptr : a.part_rz + oz_nxt + blk, a.part_rr + o_nxt + blk,
+             nullptr);
+}
+
+
+// ---------------------------------------------------------------------------
+// Circulant preconditioner for power-of-two H and W:
+//   M = H^T H / xi + dbar I,  dbar = mean(d),  M^{-1} r = F^{-1}[F r / (|h_f|^2 / xi + dbar)].
+// H^T H is circulant, so M differs from Q only by d - dbar on the diagonal; CG
+// on M^{-1} Q needs a few tens of iterations where Jacobi needs hundreds.
+// Two real systems share one complex transform (z = r_a + i r_b): the filter is
+// real and even in frequency, so the real and imaginary parts of the result are
+// M^{-1} r_a and M^{-1} r_b.  Transforms are radix-2 in shared memory: rows,
+// then columns (forward, filter, inverse in one pass), then rows again.
+struct FftDesc {
+  int H, W, logH, logW;
+  int R, pairs;
+  int cw;            // columns per block in the column pass
+  int rpb;           // rows per block in the forward row pass
+  int nbz;           // blocks per pair in the inverse row pass
+  float2* tmp;       // pairs x H x W
+  const float* hth;  // |h_f|^2 / xi, H x W
+  const double* dbar;
+};
+
+__device__ __forceinline__ unsigned brev_n(unsigned x, int logn) {
+  return logn ? (__brev(x) >> (32 - logn)) : 0u;
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// tw[k] = exp(-2 pi i k / n), k < n / 2
+__device__ __forceinline__ void make_twiddles(float2* tw, int n) {
+  for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
+    float sn, cs;
+    sincospif(-2.0f * (float)k / (float)n, &sn, &cs);
+    tw[k] = make_float2(cs, sn);
+  }
+}
+
+// Forward radix-2 decimation in time, in place, bit-reversed input, natural
+// output; `count` transforms, element i of transform t at a[i * stride + t * tstride].
+__device__ void fft_dit(float2* a, int n, int logn, int count, int stride, int tstride,
+                        const float2* tw) {
+  const int half_n = n >> 1;
+  const int nbf = half_n * count;
+  for (int sh = 1; sh <= logn; ++sh) {
+    const int len = 1 << sh, half = len >> 1, twstep = n >> sh;
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+      const int t = b / half_n, q = b - t * half_n;
+      const int grp = q >> (sh - 1), pos = q & (half - 1);
+      const int i = grp * len + pos, j = i + half;
+      float2* base = a + t * tstride;
+      const float2 u = base[i * stride];
+      const float2 v = cmul(base[j * stride], tw[pos * twstep]);
+      base[i * stride] = make_float2(u.x + v.x, u.y + v.y);
+      base[j * stride] = make_float2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse (exp(+)) radix-2 decimation in frequency, in place, natural input,
+// bit-reversed output, unscaled.
+__device__ void ifft_dif(float2* a, int n, int logn, int count, int stride, int tstride,
+                         const float2* tw) {
+  const int half_n = n >> 1;
+  const int nbf = half_n * count;
+  for (int sh = logn; sh >= 1; --sh) {
+    const int len = 1 << sh, half = len >> 1, twstep = n >> sh;
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+      const int t = b / half_n, q = b - t * half_n;
+      const int grp = q >> (sh - 1), pos = q & (half - 1);
+      const int i = grp * len + pos, j = i + half;
+      float2* base = a + t * tstride;
+      const float2 u = base[i * stride], v = base[j * stride];
+      const float2 w = tw[pos * twstep];
+      base[i * stride] = make_float2(u.x + v.x, u.y + v.y);
+      base[j * stride] = cmul(make_float2(u.x - v.x, u.y - v.y), make_float2(w.x, -w.y));
+    }
+    __syncthreads();
+  }
+}
+
+// Pack two residual planes into complex rows and transform them.
+__global__ void __launch_bounds__(512) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
+  extern __shared__ float2 sm2[];
+  float2* tw = sm2;
+  float2* s = sm2 + f.W / 2;
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const long long N = (long long)f.H * f.W;
+  const int row0 = blockIdx.x * f.rpb;
+  make_twiddles(tw, f.W);
+  for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x) {
+    const int rr = idx >> f.logW, c = idx & (f.W - 1);
+    const long long p = (long long)(row0 + rr) * f.W + c;
+    const float re = Rr[(long long)j0 * N + p];
+    const float im = j1 < f.R ? Rr[(long long)j1 * N + p] : 0.f;
+    s[rr * f.W + brev_n(c, f.logW)] = make_float2(re, im);
+  }
+  __syncthreads();
+  fft_dit(s, f.W, f.logW, f.rpb, 1, f.W, tw);
+  float2* out = f.tmp + (long long)pair * N + (long long)row0 * f.W;
+  for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x) out[idx] = s[idx];
+}
+
+// Column transforms, the preconditioner filter and the inverse column transforms.
+__global__ void __launch_bounds__(512) fft_cols_filter_kernel(FftDesc f) {
+  extern __shared__ float2 sm2[];
+  float2* tw = sm2;
+  float2* s = sm2 + f.H / 2;
+  const int pair = blockIdx.y;
+  const int c0 = blockIdx.x * f.cw;
+  const long long N = (long long)f.H * f.W;
+  float2* t = f.tmp + (long long)pair * N;
+  make_twiddles(tw, f.H);
+  for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
+    const int i = idx / f.cw, c = idx - i * f.cw;
+    s[brev_n(i, f.logH) * f.cw + c] = t[(long long)i * f.W + c0 + c];
+  }
+  __syncthreads();
+  fft_dit(s, f.H, f.logH, f.cw, f.cw, 1, tw);
+  const float dbar = (float)(*f.dbar);
+  for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
+    const int i = idx / f.cw, c = idx - i * f.cw;
+    const float g = 1.0f / (f.hth[(long long)i * f.W + c0 + c] + dbar);
+    s[idx] = make_float2(s[idx].x * g, s[idx].y * g);
+  }
+  __syncthreads();
+  ifft_dif(s, f.H, f.logH, f.cw, f.cw, 1, tw);
+  for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
+    const int i = idx / f.cw, c = idx - i * f.cw;
+    t[(long long)i * f.W + c0 + c] = s[brev_n(i, f.logH) * f.cw + c];
+  }
+}
+
+// Inverse row transforms, scale 1/N, unpack into z planes, partial r.z per system.
+__global__ void __launch_bounds__(512) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
+                                                           float* Z, double* part_rz) {
+  extern __shared__ float2 sm2[];
+  float2* tw = sm2;
+  float2* s = sm2 + f.W / 2;
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const long long N = (long long)f.H * f.W;
+  const float scale = 1.0f / (float)N;
+  const int rows_per = f.H / f.nbz;
+  const int rpb = min(f.rpb, rows_per);
+  make_twiddles(tw, f.W);
+  float rz0 = 0.f, rz1 = 0.f;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int r0 = blockIdx.x * rows_per; r0 < (blockIdx.x + 1) * rows_per; r0 += rpb) {
+    const float2* in = f.tmp + (long long)pair * N + (long long)r0 * f.W;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) s[idx] = in[idx];
+    __syncthreads();
+    ifft_dif(s, f.W, f.logW, rpb, 1, f.W, tw);
+    rz0 = 0.f;
+    rz1 = 0.f;
+    for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) {
+      const int rr = idx >> f.logW, c = idx & (f.W - 1);
+      const float2 v = s[rr * f.W + brev_n(c, f.logW)];
+      const long long p = (long long)(r0 + rr) * f.W + c;
+      const float z0 = v.x * scale;
+      Z[(long long)j0 * N + p] = z0;
+      rz0 = fmaf(Rr[(long long)j0 * N + p], z0, rz0);
+      if (j1 < f.R) {
+        const float z1 = v.y * scale;
+        Z[(long long)j1 * N + p] = z1;
+        rz1 = fmaf(Rr[(long long)j1 * N + p], z1, rz1);
+      }
+    }
+    acc0 += (double)rz0;
+    acc1 += (double)rz1;
+  }
+  __syncthreads();
+  block_sum3(acc0, acc1, 0.0, part_rz + (long long)j0 * f.nbz + blockIdx.x,
+             j1 < f.R ? part_rz + (long long)j1 * f.nbz + blockIdx.x : nullptr, nullptr);
+}
+
+// |h_f|^2 / xi on the H x W frequency grid (phases reduced exactly in integers).
+__global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int kw, float inv_xi) {
+  const long long N = (long long)H * W;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int fr = (int)(p / W), fc = (int)(p - (long long)fr * W);
+    double re = 0.0, im = 0.0;
+    for (int a = 0; a < kh; ++a) {
+      const long long pr = ((long long)fr * a) % H;
+      for (int b = 0; b < kw; ++b) {
+        const long long pc = ((long long)fc * b) % W;
+        // phase / pi = -2 (pr / H + pc / W)
+        const double ph = -2.0 * ((double)pr / H + (double)pc / W);
+        double sn, cs;
+        sincospi(ph, &sn, &cs);
+        re += (double)k[a * kw + b] * cs;
+        im += (double)k[a * kw + b] * sn;
+      }
+    }
+    out[p] = (float)((re * re + im * im) * inv_xi);
+  }
 }
 
 // Number of systems still above tolerance, from the partials in buffer `buf`.
@@ -494,6 +722,17 @@ struct LikelihoodState {
   float* P = nullptr;
   float* Qp = nullptr;
   double* part = nullptr;   // pq, rz[2], rr[2], bb
+  int nbz = 0, nbmax = 0;
+  // circulant FFT preconditioner (power-of-two sizes)
+  bool fft = false;
+  FftDesc fd;
+  float2* ftmp = nullptr;
+  float* Z = nullptr;
+  float* hth = nullptr;
+  double* dpart = nullptr;
+  double* dbar = nullptr;
+  int prep_blocks = 0;
+  size_t smem_rows = 0, smem_cols = 0;
   int* d_active = nullptr;
   int* h_active = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -519,15 +758,33 @@ CgArgs cg_args(LikelihoodState* L) {
   a.Hty = L->Hty;
   a.E1 = L->E1;
   a.E2 = L->E2;
-  const long long rn = (long long)L->R * L->nb;
+  a.Z = L->Z;
+  const long long rn = (long long)L->R * L->nbmax;
   a.part_pq = L->part;
   a.part_rz = L->part + rn;
   a.part_rr = L->part + 3 * rn;
   a.part_bb = L->part + 5 * rn;
   a.rtol2 = L->rtol2;
   a.nb = L->nb;
+  a.nbz = L->nbz;
+  a.fft = L->fft ? 1 : 0;
   a.counters = nullptr;
   return a;
+}
+
+bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// z = M^{-1} r for all systems; r.z partials into rz_buf ([R][nbz]).
+void precond_apply(LikelihoodState* L, double* rz_buf, cudaStream_t s) {
+  const FftDesc& f = L->fd;
+  fft_rows_fwd_kernel<<<dim3(f.H / f.rpb, f.pairs), 512, L->smem_rows, s>>>(f, L->Rr);
+  fft_cols_filter_kernel<<<dim3(f.W / f.cw, f.pairs), 512, L->smem_cols, s>>>(f);
+  fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), 512, L->smem_rows, s>>>(f, L->Rr, L->Z, rz_buf);
 }
 
 // E1 = H^T eps1 / sqrt(xi) from E1 holding eps1 (in place through Rr as scratch).
@@ -611,6 +868,25 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   c.tiles_x = (c.W + kTile - 1) / kTile;
   c.tiles_y = (c.H + kTile - 1) / kTile;
   L->nb = c.tiles_x * c.tiles_y;
+  L->fft = is_pow2(c.H) && is_pow2(c.W) && c.H <= 8192 && c.W <= 8192;
+  L->nbz = L->nb;
+  if (L->fft) {
+    FftDesc& f = L->fd;
+    f.H = c.H;
+    f.W = c.W;
+    f.logH = ilog2(c.H);
+    f.logW = ilog2(c.W);
+    f.R = L->R;
+    f.pairs = (L->R + 1) / 2;
+    f.rpb = std::max(1, std::min(c.H, 2048 / c.W));
+    f.cw = std::min(c.W, c.H <= 1024 ? 16 : std::max(1, 16384 / c.H));
+    f.nbz = std::min(c.H, 64);
+    L->nbz = f.nbz;
+    L->smem_rows = sizeof(float2) * ((size_t)c.W / 2 + (size_t)f.rpb * c.W);
+    L->smem_cols = sizeof(float2) * ((size_t)c.H / 2 + (size_t)c.H * f.cw);
+  }
+  L->nbmax = std::max(L->nb, L->nbz);
+  L->prep_blocks = (int)std::min<long long>(std::max<long long>((c.N + 255) / 256, 1), 2048);
   const long long N = c.N;
   const size_t RN = (size_t)L->R * N;
   const size_t region = (size_t)(kTile + 2 * hr) * (kTile + 2 * hc);
@@ -631,7 +907,12 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->Rr, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->P, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->Qp, sizeof(float) * RN) == cudaSuccess &&
-            cudaMalloc(&L->part, sizeof(double) * 6 * L->R * L->nb) == cudaSuccess &&
+            cudaMalloc(&L->part, sizeof(double) * 6 * L->R * L->nbmax) == cudaSuccess &&
+            cudaMalloc(&L->dpart, sizeof(double) * L->prep_blocks) == cudaSuccess &&
+            cudaMalloc(&L->dbar, sizeof(double)) == cudaSuccess &&
+            (!L->fft || (cudaMalloc(&L->ftmp, sizeof(float2) * ((L->R + 1) / 2) * N) == cudaSuccess &&
+                         cudaMalloc(&L->Z, sizeof(float) * RN) == cudaSuccess &&
+                         cudaMalloc(&L->hth, sizeof(float) * N) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
             cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
             cudaEventCreateWithFlags(&L->ev[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -654,6 +935,21 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   if (L->smem > 48 * 1024) {
     cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
     cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+  }
+  if (L->fft) {
+    L->fd.tmp = L->ftmp;
+    L->fd.hth = L->hth;
+    L->fd.dbar = L->dbar;
+    if (cudaFuncSetAttribute(fft_rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L->smem_rows) != cudaSuccess ||
+        cudaFuncSetAttribute(fft_rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L->smem_rows) != cudaSuccess ||
+        cudaFuncSetAttribute(fft_cols_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L->smem_cols) != cudaSuccess) {
+      likelihood_destroy(L);
+      return EP_TV_ERR_CUDA;
+    }
+    hth_kernel<<<grid1d(N), 256, 0, s>>>(L->hth, c.H, c.W, L->d_k, kh, kw, L->inv_xi);
   }
   // H^T y / xi
   conv_t_kernel<<<dim3(grid1d(N), 1), 256, 0, s>>>(cfg.y, L->Hty, c.H, c.W, L->d_k, kh, kw,
@@ -691,6 +987,11 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->P);
   cudaFree(L->Qp);
   cudaFree(L->part);
+  cudaFree(L->dpart);
+  cudaFree(L->dbar);
+  cudaFree(L->ftmp);
+  cudaFree(L->Z);
+  cudaFree(L->hth);
   cudaFree(L->d_active);
   if (L->h_active) cudaFreeHost(L->h_active);
   if (L->ev[0]) cudaEventDestroy(L->ev[0]);
@@ -720,13 +1021,20 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, unsign
                                unsigned long long* counters, Tracer* tr, cudaStream_t s) {
   const ConvDesc& c = L->c;
   const long long N = c.N;
-  prep_kernel<<<grid1d(N), 256, 0, s>>>(tau, nu, N, c.g0_xi, L->D, L->Ncav, L->Minv);
+  prep_kernel<<<L->prep_blocks, kThreads, 0, s>>>(tau, nu, N, c.g0_xi, L->D, L->Ncav, L->Minv,
+                                                  L->dpart);
+  mean_kernel<<<1, 1024, 0, s>>>(L->dpart, L->prep_blocks, 1.0 / (double)N, L->dbar);
   CgArgs a = cg_args(L);
   a.counters = counters;
   dim3 grid(c.tiles_x, c.tiles_y, L->R);
   tr->begin(EP_TV_K_CG_RESIDUAL, s);
   residual_kernel<<<grid, kThreads, L->smem, s>>>(a);
   tr->end(s, (double)L->R * N);
+  if (L->fft) {
+    tr->begin(EP_TV_K_CG_PRECOND, s);
+    precond_apply(L, a.part_rz, s);
+    tr->end(s, (double)L->R * N);
+  }
   int launched = 0, pending = -1, slot = 0, iters = -1;
   bool ran_out = false;
   while (true) {
@@ -738,6 +1046,11 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, unsign
       tr->begin(EP_TV_K_CG_UPDATE, s);
       update_kernel<<<grid, kThreads, 0, s>>>(a, launched);
       tr->end(s, -1.0);
+      if (L->fft) {
+        tr->begin(EP_TV_K_CG_PRECOND, s);
+        precond_apply(L, a.part_rz + (long long)((launched + 1) & 1) * L->R * L->nbz, s);
+        tr->end(s, (double)L->R * N);
+      }
       ++launched;
     }
     check_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2, launched & 1,
@@ -780,6 +1093,8 @@ double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
     case EP_TV_K_CG_DIRECTION: return 16.0;  // read r, p; write p, q (per system pixel)
     case EP_TV_K_CG_UPDATE: return 24.0;     // read x, r, p, q; write x, r
     case EP_TV_K_CG_RESIDUAL: return 12.0;   // read x and the rhs source; write r
+    case EP_TV_K_CG_PRECOND: return 28.0;    // rows: r in, half-complex out; columns: complex
+                                             // in/out; rows: complex, r in, z out (per system)
     case EP_TV_K_SITE0:                      // read X (R planes), E1, E2, D, Ncav, Minv,
       return 4.0 * (L->R + 2 * L->S + 5) + 8.0;  // tau0, nu0; write tau0, nu0
   }
