@@ -92,15 +92,18 @@ typedef struct {
                             first, as Algorithm 1 lists it. */
   int32_t rbmc_samples;  /* CONV_PERIODIC: S probes of the Rao-Blackwellised Monte Carlo
                             variance estimator (default 32) */
-  int32_t cg_max_iter;   /* CONV_PERIODIC: iteration cap of the conjugate-gradient solves */
-  double cg_rtol;        /* CONV_PERIODIC: relative residual target of those solves */
+  int32_t cg_max_iter;   /* CONV_PERIODIC: cap on the conjugate-gradient iterations of one
+                            likelihood-site update (all refinement passes together) */
+  double cg_rtol;        /* CONV_PERIODIC: target of the true relative residual ||b - Q x|| /
+                            ||b|| of every solve; the residual is recomputed with the blur
+                            accumulated in FP64 between FP32 CG passes (default 1e-9) */
   int32_t precision;     /* 0: FP32 with FP64 for edges whose tilted moments lose
                             FP32 accuracy; 1: FP32 only */
   uint64_t seed;         /* seed of the library's own probe generator */
 } ep_tv_params;
 
 /* Fills *p with defaults: damping 0.5, var_cap 1e8, periodic 1, order_mode 0,
-   rbmc_samples 32, cg_max_iter 1000, cg_rtol 1e-6, precision 0, seed 1234.
+   rbmc_samples 32, cg_max_iter 1000, cg_rtol 1e-9, precision 0, seed 1234.
    xi and beta are set to 0 and must be provided. */
 ep_tv_status ep_tv_default_params(ep_tv_params* p);
 

@@ -159,7 +159,7 @@ ep_tv_status ep_tv_default_params(ep_tv_params* p) {
   p->order_mode = 0;
   p->rbmc_samples = 32;
   p->cg_max_iter = 1000;
-  p->cg_rtol = 1e-6;
+  p->cg_rtol = 1e-9;
   p->precision = 0;
   p->seed = 1234;
   return EP_TV_OK;

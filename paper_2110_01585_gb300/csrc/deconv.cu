@@ -49,7 +49,10 @@ struct ConvDesc {
   const float* k;        // kh x kw
   const float* gr;       // 2 hr + 1 (separable)
   const float* gc;       // 2 hc + 1 (separable)
+  const double* hd;      // forward-blur taps, FP64: separable u (kh) then v (kw), else k
+  const float* hf;       // the same taps in FP32
   float inv_xi;
+  double inv_xi_d;
   float g0_xi;           // diag of H^T H / xi = sum k^2 / xi
   int tiles_x, tiles_y;
 };
@@ -192,7 +195,7 @@ struct CgArgs {
   ConvDesc c;
   int R;                 // right-hand sides (1 + S)
   int S;
-  float* X;              // R planes
+  double* X;             // R planes, FP64 solutions
   float* Rr;             // R planes
   float* P;              // R planes
   float* Qp;             // R planes
@@ -202,6 +205,9 @@ struct CgArgs {
   const float* Hty;      // H^T y / xi
   const float* E1;       // S planes, H^T eps1 / sqrt(xi)
   const float* E2;       // S planes, eps2
+  const float* Y0;       // observation y
+  const float* Y1;       // S planes, sqrt(xi) eps1 (data-space probe)
+  const double* thr;     // [R] inner-loop convergence threshold on r.r
   float* Z;              // R planes, preconditioned residual (FFT preconditioner)
   double* part_pq;       // [R][nb]
   double* part_rz;       // [2][R][nbz]
@@ -251,41 +257,160 @@ __global__ void mean_kernel(const double* dpart, int n, double inv_count, double
   if (threadIdx.x == 0) *out = buf[0] * inv_count;
 }
 
-// r = b - Q x for every RHS (blockIdx.z), with partials r.Minv.r, r.r, b.b.
+// True residual of every system (blockIdx.z),
+//   r = H^T (y' - H x) / xi + (n' - d x),
+// y' = y, n' = n for the mean system and y' = sqrt(xi) eps1_s, n' = sqrt(d) eps2_s for
+// probe s, so that r = b - Q x with b as in rhs_value.  H x is accumulated in FP64
+// from the FP64 solution: y' - H x is small next to y', and forming it in FP32
+// would leave an error of order eps |y'| / xi in r, which the conditioning of Q
+// (1e4..1e5) turns into percent-level errors in x.  The rest is FP32.
+// Partials: r.r (buffer 0), b.b, and r.Minv.r in Jacobi mode.
 __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ double smd[];
+  __shared__ double tapd[232];
+  __shared__ float tapf[232];
+  __shared__ float outb[kTile * kTile];
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
-  StencilSmem sm = carve(c, smem);
-  __shared__ float outb[kTile * kTile];
-  stage_taps(c, sm.taps);
-  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
-  const float* x = a.X + (long long)j * c.N;
+  const int hh = c.kh / 2, hw = c.kw / 2;
+  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;  // x region, halo kh - 1
+  const int MH = kTile + 2 * hh, MW = kTile + 2 * hw;      // y' - H x region, halo kh / 2
+  double* xs = smd;                                        // RH x RW
+  double* rowp = xs + RH * RW;                             // RH x MW (separable)
+  float* vs = (float*)(rowp + (c.separable ? RH * MW : 0));  // MH x MW
+  float* tmpf = vs + MH * MW;                              // MH x kTile (separable)
+  const int ntap = c.separable ? c.kh + c.kw : c.kh * c.kw;
+  for (int i = threadIdx.x; i < ntap; i += kThreads) {
+    tapd[i] = c.hd[i];
+    tapf[i] = c.hf[i];
+  }
+  const double* x = a.X + (long long)j * c.N;
   for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
     const int rr = idx / RW, cc = idx - rr * RW;
     const int gr = wrapi(r0 - c.hr + rr, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
-    sm.v[idx] = x[(long long)gr * c.W + gcol];
+    xs[idx] = x[(long long)gr * c.W + gcol];
   }
   __syncthreads();
-  hth_tile(c, sm, outb);
+  const float* yp = j == 0 ? a.Y0 : a.Y1 + (long long)(j - 1) * c.N;
+  if (c.separable) {
+    const double* u = tapd;
+    const double* v = tapd + c.kh;
+    // along rows: rowp(rr, mc) = sum_b v[b] x(rr, mc - b + 2 hw)
+    for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
+      const int rr = idx / MW, mc = idx - rr * MW;
+      const double* row = xs + rr * RW + mc + 2 * hw;
+      double acc = 0.0;
+      for (int b = 0; b < c.kw; ++b) acc = fma(v[b], row[-b], acc);
+      rowp[idx] = acc;
+    }
+    __syncthreads();
+    // along columns, then v = y' - H x
+    for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
+      const int mr = idx / MW, mc = idx - mr * MW;
+      const double* col = rowp + (mr + 2 * hh) * MW + mc;
+      double acc = 0.0;
+      for (int aa = 0; aa < c.kh; ++aa) acc = fma(u[aa], col[-aa * MW], acc);
+      const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
+      const long long pp = (long long)gr * c.W + gcol;
+      const double yv = (double)yp[pp];
+      vs[idx] = (float)(yv - acc);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
+      const int mr = idx / MW, mc = idx - mr * MW;
+      double acc = 0.0;
+      for (int aa = 0; aa < c.kh; ++aa) {
+        const double* xrow = xs + (mr + 2 * hh - aa) * RW + mc + 2 * hw;
+        const double* krow = tapd + aa * c.kw;
+        for (int b = 0; b < c.kw; ++b) acc = fma(krow[b], xrow[-b], acc);
+      }
+      const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
+      const long long pp = (long long)gr * c.W + gcol;
+      const double yv = (double)yp[pp];
+      vs[idx] = (float)(yv - acc);
+    }
+  }
+  __syncthreads();
+  // H^T v on the tile, FP32: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
+  if (c.separable) {
+    const float* u = tapf;
+    const float* v = tapf + c.kh;
+    for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
+      const int mr = idx / kTile, tc = idx - mr * kTile;
+      const float* row = vs + mr * MW + tc;
+      float acc = 0.f;
+      for (int b = 0; b < c.kw; ++b) acc = fmaf(v[b], row[b], acc);
+      tmpf[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+      const int tr = idx / kTile, tc = idx - tr * kTile;
+      const float* col = tmpf + tr * kTile + tc;
+      float acc = 0.f;
+      for (int aa = 0; aa < c.kh; ++aa) acc = fmaf(u[aa], col[aa * kTile], acc);
+      outb[idx] = acc;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+      const int tr = idx / kTile, tc = idx - tr * kTile;
+      float acc = 0.f;
+      for (int aa = 0; aa < c.kh; ++aa) {
+        const float* vrow = vs + (tr + aa) * MW + tc;
+        const float* krow = tapf + aa * c.kw;
+        for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], vrow[b], acc);
+      }
+      outb[idx] = acc;
+    }
+  }
+  __syncthreads();
   double rz = 0, rr2 = 0, bb = 0;
   for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
     const int tr = idx / kTile, tc = idx - tr * kTile;
     const int gr = r0 + tr, gcol = c0 + tc;
     if (gr >= c.H || gcol >= c.W) continue;
     const long long p = (long long)gr * c.W + gcol;
-    const float xv = sm.v[(tr + c.hr) * RW + tc + c.hc];
-    const float qx = outb[idx] * c.inv_xi + a.D[p] * xv;
-    const float b = rhs_value(a, j, p);
-    const float r = b - qx;
+    const double xv = xs[(tr + c.hr) * RW + tc + c.hc];
+    const double np = j == 0 ? (double)a.Ncav[p]
+                             : sqrt((double)a.D[p]) * (double)a.E2[(long long)(j - 1) * c.N + p];
+    const float r = outb[idx] * c.inv_xi + (float)(np - (double)a.D[p] * xv);
     a.Rr[(long long)j * c.N + p] = r;
+    const float b = rhs_value(a, j, p);
     if (!a.fft) rz += (double)(r * r * a.Minv[p]);
     rr2 += (double)(r * r);
     bb += (double)(b * b);
   }
   const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
   block_sum3(rz, rr2, bb, a.fft ? nullptr : a.part_rz + o, a.part_rr + o, a.part_bb + o);
+}
+
+// Per system after a true residual: done if r.r <= rtol^2 b.b (threshold +inf),
+// otherwise the inner loop runs until r.r <= max(eta^2 r.r, (rtol/2)^2 b.b).
+__global__ void thresholds_kernel(const double* part_rr, const double* part_bb, int R, int nb,
+                                  double rtol2, double eta2, double* thr, int* active) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < R; j += blockDim.x / 32) {
+    double rr = 0, bb = 0;
+    for (int i = lane; i < nb; i += 32) {
+      rr += part_rr[(long long)j * nb + i];
+      bb += part_bb[(long long)j * nb + i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      rr += __shfl_down_sync(0xffffffffu, rr, off);
+      bb += __shfl_down_sync(0xffffffffu, bb, off);
+    }
+    if (lane == 0) {
+      const bool done = rr <= rtol2 * bb;
+      thr[j] = done ? INFINITY : fmax(eta2 * rr, 0.25 * rtol2 * bb);
+      if (!done) atomicAdd(&cnt, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *active = cnt;
 }
 
 // Direction and product: p = Minv r + beta p, q = Q p, partial p.q.
@@ -296,8 +421,7 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
   const int buf = it & 1;
   const double* rr_cur = a.part_rr + ((long long)buf * a.R + j) * a.nb;
   const double rr = sum_partials(rr_cur, a.nb);
-  const double bb = sum_partials(a.part_bb + (long long)j * a.nb, a.nb);
-  if (rr <= a.rtol2 * bb) return;  // this system has converged
+  if (rr <= a.thr[j]) return;  // this system has converged
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&a.counters[DC_CG_DIR_UNITS], 1ull);
   float beta = 0.f;
@@ -351,8 +475,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const long long oz_nxt = ((long long)nbuf * a.R + j) * a.nbz;
   const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
   const double rr = sum_partials(a.part_rr + o_cur, a.nb);
-  const double bb = sum_partials(a.part_bb + (long long)j * a.nb, a.nb);
-  if (rr <= a.rtol2 * bb) {
+  if (rr <= a.thr[j]) {
     // converged: carry this block's partials forward so the state stays converged
     if (threadIdx.x == 0) {
       a.part_rr[o_nxt + blk] = a.part_rr[o_cur + blk];
@@ -366,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const double pq = sum_partials(a.part_pq + (long long)j * a.nb, a.nb);
   const float alpha = (float)(rz / pq);
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
-  float* X = a.X + (long long)j * c.N;
+  double* X = a.X + (long long)j * c.N;
   float* Rr = a.Rr + (long long)j * c.N;
   const float* P = a.P + (long long)j * c.N;
   const float* Q = a.Qp + (long long)j * c.N;
@@ -376,7 +499,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
     const int gr = r0 + tr, gcol = c0 + tc;
     if (gr >= c.H || gcol >= c.W) continue;
     const long long p = (long long)gr * c.W + gcol;
-    X[p] = fmaf(alpha, P[p], X[p]);
+    X[p] += (double)(alpha * P[p]);
     const float r = fmaf(-alpha, Q[p], Rr[p]);
     Rr[p] = r;
     if (!a.fft) rz2 += (double)(r * r * a.Minv[p]);
@@ -588,24 +711,18 @@ __global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int
 }
 
 // Number of systems still above tolerance, from the partials in buffer `buf`.
-__global__ void check_kernel(const double* part_rr, const double* part_bb, int R, int nb,
-                             double rtol2, int buf, int* active) {
+__global__ void check_kernel(const double* part_rr, const double* thr, int R, int nb, int buf,
+                             int* active) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = warp; j < R; j += blockDim.x / 32) {
-    double rr = 0, bb = 0;
-    for (int i = lane; i < nb; i += 32) {
-      rr += part_rr[((long long)buf * R + j) * nb + i];
-      bb += part_bb[(long long)j * nb + i];
-    }
+    double rr = 0;
+    for (int i = lane; i < nb; i += 32) rr += part_rr[((long long)buf * R + j) * nb + i];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      rr += __shfl_down_sync(0xffffffffu, rr, off);
-      bb += __shfl_down_sync(0xffffffffu, bb, off);
-    }
-    if (lane == 0 && !(rr <= rtol2 * bb)) atomicAdd(&cnt, 1);
+    for (int off = 16; off > 0; off >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, off);
+    if (lane == 0 && !(rr <= thr[j])) atomicAdd(&cnt, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) *active = cnt;
@@ -626,11 +743,11 @@ __global__ void site0_kernel(CgArgs a, float* tau0, float* nu0, float min_tau, f
     for (int s = 0; s < a.S; ++s) {
       const long long o = (long long)s * N + p;
       const float w = a.E1[o] + sd * a.E2[o];
-      const float off = w - qii * a.X[(long long)(s + 1) * N + p];
+      const float off = w - qii * (float)a.X[(long long)(s + 1) * N + p];
       acc = fmaf(off, off, acc);
     }
     const float var = minv + minv * minv * acc / (float)a.S;
-    const float E = a.X[p];
+    const float E = (float)a.X[p];
     const float d = a.D[p];
     float tn = 1.0f / var - d;
     if (!(tn >= min_tau)) {
@@ -690,6 +807,11 @@ __global__ void normals_kernel(float* out, long long count, unsigned long long s
 }
 
 __global__ void set_status_kernel(unsigned* status, unsigned bit) { atomicOr(status, bit); }
+__global__ void scale_kernel(float* out, const float* in, long long n, float scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = in[i] * scale;
+}
 __global__ void store_iters_kernel(unsigned long long* counters, unsigned long long v) {
   counters[DC_CG_ITERS] = v;
 }
@@ -712,12 +834,19 @@ struct LikelihoodState {
   float* d_k = nullptr;
   float* d_g = nullptr;     // gr then gc
   float* Hty = nullptr;
+  const float* Y0 = nullptr;  // the context's copy of y
   float* E1 = nullptr;
   float* E2 = nullptr;
   float* D = nullptr;
   float* Ncav = nullptr;
   float* Minv = nullptr;
-  float* X = nullptr;
+  double* X = nullptr;      // FP64 solutions (warm starts across sweeps)
+  float* Y1 = nullptr;      // sqrt(xi) eps1
+  double* thr = nullptr;    // inner convergence thresholds
+  double* d_hd = nullptr;   // forward-blur taps FP64
+  float* d_hf = nullptr;    // forward-blur taps FP32
+  double rtol2_true = 0.0;  // target of the true relative residual, squared
+  int max_outer = 12;
   float* Rr = nullptr;
   float* P = nullptr;
   float* Qp = nullptr;
@@ -738,6 +867,7 @@ struct LikelihoodState {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int nb = 0;
   size_t smem = 0;
+  size_t smem_res = 0;
   int last_iters = 0;
 };
 
@@ -758,6 +888,9 @@ CgArgs cg_args(LikelihoodState* L) {
   a.Hty = L->Hty;
   a.E1 = L->E1;
   a.E2 = L->E2;
+  a.Y0 = L->Y0;
+  a.Y1 = L->Y1;
+  a.thr = L->thr;
   a.Z = L->Z;
   const long long rn = (long long)L->R * L->nbmax;
   a.part_pq = L->part;
@@ -797,6 +930,8 @@ ep_tv_status finish_probes(LikelihoodState* L, cudaStream_t s) {
   dim3 g(grid1d(N), L->S);
   conv_t_kernel<<<g, 256, 0, s>>>(L->Rr, L->E1, L->c.H, L->c.W, L->d_k, L->c.kh, L->c.kw,
                                   (float)std::sqrt((double)L->inv_xi), L->S);
+  scale_kernel<<<grid1d((long long)L->S * N), 256, 0, s>>>(L->Y1, L->Rr, (long long)L->S * N,
+                                                            (float)std::sqrt(1.0 / L->inv_xi));
   return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
 }
 
@@ -850,6 +985,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   L->R = 1 + L->S;
   L->inv_xi = (float)(1.0 / cfg.p->xi);
   L->rtol2 = cfg.p->cg_rtol * cfg.p->cg_rtol;
+  L->rtol2_true = L->rtol2;
   L->max_iter = cfg.p->cg_max_iter;
   L->seed = cfg.p->seed;
   L->damping = (float)cfg.p->damping;
@@ -864,6 +1000,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   c.hc = hc;
   c.separable = sep ? 1 : 0;
   c.inv_xi = L->inv_xi;
+  c.inv_xi_d = 1.0 / cfg.p->xi;
   c.g0_xi = (float)(g0 / cfg.p->xi);
   c.tiles_x = (c.W + kTile - 1) / kTile;
   c.tiles_y = (c.H + kTile - 1) / kTile;
@@ -893,6 +1030,12 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   const size_t tmp = std::max((size_t)(kTile + 2 * hr) * kTile,
                               (size_t)(kTile + 2 * (kh / 2)) * (kTile + 2 * (kw / 2)));
   L->smem = sizeof(float) * (512 + region + tmp);
+  {
+    const size_t MH = kTile + 2 * (kh / 2), MW = kTile + 2 * (kw / 2);
+    const size_t RH = kTile + 2 * hr, RW = kTile + 2 * hc;
+    L->smem_res = sizeof(double) * (RH * RW + (sep ? RH * MW : 0)) +
+                  sizeof(float) * (MH * MW + (sep ? MH * kTile : 0));
+  }
   std::vector<float> kf(kh * kw);
   for (int i = 0; i < kh * kw; ++i) kf[i] = (float)k[i];
   bool ok = cudaMalloc(&L->d_k, sizeof(float) * kh * kw) == cudaSuccess &&
@@ -903,7 +1046,11 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->D, sizeof(float) * N) == cudaSuccess &&
             cudaMalloc(&L->Ncav, sizeof(float) * N) == cudaSuccess &&
             cudaMalloc(&L->Minv, sizeof(float) * N) == cudaSuccess &&
-            cudaMalloc(&L->X, sizeof(float) * RN) == cudaSuccess &&
+            cudaMalloc(&L->X, sizeof(double) * RN) == cudaSuccess &&
+            cudaMalloc(&L->Y1, sizeof(float) * L->S * N) == cudaSuccess &&
+            cudaMalloc(&L->thr, sizeof(double) * L->R) == cudaSuccess &&
+            cudaMalloc(&L->d_hd, sizeof(double) * kh * kw) == cudaSuccess &&
+            cudaMalloc(&L->d_hf, sizeof(float) * kh * kw) == cudaSuccess &&
             cudaMalloc(&L->Rr, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->P, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->Qp, sizeof(float) * RN) == cudaSuccess &&
@@ -925,6 +1072,27 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   c.k = L->d_k;
   c.gr = L->d_g;
   c.gc = L->d_g + (2 * hr + 1);
+  c.hd = L->d_hd;
+  c.hf = L->d_hf;
+  L->Y0 = cfg.y;
+  {
+    std::vector<double> hd;
+    if (sep) {
+      hd.insert(hd.end(), u.begin(), u.end());
+      hd.insert(hd.end(), v.begin(), v.end());
+    } else {
+      hd = k;
+    }
+    std::vector<float> hf(hd.begin(), hd.end());
+    if (cudaMemcpyAsync(L->d_hd, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(L->d_hf, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      likelihood_destroy(L);
+      return EP_TV_ERR_CUDA;
+    }
+  }
   if (cudaMemcpyAsync(L->d_k, kf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       (sep && cudaMemcpyAsync(L->d_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice,
@@ -932,9 +1100,12 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     likelihood_destroy(L);
     return EP_TV_ERR_CUDA;
   }
-  if (L->smem > 48 * 1024) {
-    cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
-    cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+  if (cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)L->smem) != cudaSuccess ||
+      cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)L->smem_res) != cudaSuccess) {
+    likelihood_destroy(L);
+    return EP_TV_ERR_CUDA;
   }
   if (L->fft) {
     L->fd.tmp = L->ftmp;
@@ -983,6 +1154,10 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->Ncav);
   cudaFree(L->Minv);
   cudaFree(L->X);
+  cudaFree(L->Y1);
+  cudaFree(L->thr);
+  cudaFree(L->d_hd);
+  cudaFree(L->d_hf);
   cudaFree(L->Rr);
   cudaFree(L->P);
   cudaFree(L->Qp);
@@ -1000,7 +1175,7 @@ void likelihood_destroy(LikelihoodState* L) {
 }
 
 ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s) {
-  if (cudaMemsetAsync(L->X, 0, sizeof(float) * L->R * L->c.N, s) != cudaSuccess) return EP_TV_ERR_CUDA;
+  if (cudaMemsetAsync(L->X, 0, sizeof(double) * L->R * L->c.N, s) != cudaSuccess) return EP_TV_ERR_CUDA;
   L->last_iters = 0;
   return EP_TV_OK;
 }
@@ -1027,58 +1202,71 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, unsign
   CgArgs a = cg_args(L);
   a.counters = counters;
   dim3 grid(c.tiles_x, c.tiles_y, L->R);
-  tr->begin(EP_TV_K_CG_RESIDUAL, s);
-  residual_kernel<<<grid, kThreads, L->smem, s>>>(a);
-  tr->end(s, (double)L->R * N);
-  if (L->fft) {
-    tr->begin(EP_TV_K_CG_PRECOND, s);
-    precond_apply(L, a.part_rz, s);
+  // Iterative refinement: true residual (FP64 blur), then FP32 preconditioned CG
+  // on the correction until the residual has dropped by eta, repeated until
+  // ||r|| <= cg_rtol ||b|| for every system.
+  const double eta2 = 1e-6;  // eta = 1e-3
+  int total = 0, iters = 0;
+  bool converged = false;
+  for (int outer = 0;; ++outer) {
+    tr->begin(EP_TV_K_CG_RESIDUAL, s);
+    residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
     tr->end(s, (double)L->R * N);
-  }
-  int launched = 0, pending = -1, slot = 0, iters = -1;
-  bool ran_out = false;
-  while (true) {
-    const int n = std::min(kChunk, L->max_iter - launched);
-    for (int t = 0; t < n; ++t) {
-      tr->begin(EP_TV_K_CG_DIRECTION, s);
-      direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
-      tr->end(s, -1.0);
-      tr->begin(EP_TV_K_CG_UPDATE, s);
-      update_kernel<<<grid, kThreads, 0, s>>>(a, launched);
-      tr->end(s, -1.0);
-      if (L->fft) {
-        tr->begin(EP_TV_K_CG_PRECOND, s);
-        precond_apply(L, a.part_rz + (long long)((launched + 1) & 1) * L->R * L->nbz, s);
-        tr->end(s, (double)L->R * N);
-      }
-      ++launched;
-    }
-    check_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2, launched & 1,
-                                    L->d_active);
-    if (cudaMemcpyAsync(L->h_active + slot, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+    thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2_true, eta2,
+                                         L->thr, L->d_active);
+    if (cudaMemcpyAsync(L->h_active, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
-        cudaEventRecord(L->ev[slot], s) != cudaSuccess)
+        cudaStreamSynchronize(s) != cudaSuccess)
       return EP_TV_ERR_CUDA;
-    if (pending >= 0) {
-      if (cudaEventSynchronize(L->ev[pending & 1]) != cudaSuccess) return EP_TV_ERR_CUDA;
-      if (L->h_active[pending & 1] == 0) {
-        iters = pending >> 1;
+    if (L->h_active[0] == 0) {
+      converged = true;
+      break;
+    }
+    if (outer >= L->max_outer || total >= L->max_iter) break;
+    if (L->fft) {
+      tr->begin(EP_TV_K_CG_PRECOND, s);
+      precond_apply(L, a.part_rz, s);
+      tr->end(s, (double)L->R * N);
+    }
+    int launched = 0, pending = -1, slot = 0;
+    while (true) {
+      const int n = std::min(kChunk, L->max_iter - total - launched);
+      for (int t = 0; t < n; ++t) {
+        tr->begin(EP_TV_K_CG_DIRECTION, s);
+        direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
+        tr->end(s, -1.0);
+        tr->begin(EP_TV_K_CG_UPDATE, s);
+        update_kernel<<<grid, kThreads, 0, s>>>(a, launched);
+        tr->end(s, -1.0);
+        if (L->fft) {
+          tr->begin(EP_TV_K_CG_PRECOND, s);
+          precond_apply(L, a.part_rz + (long long)((launched + 1) & 1) * L->R * L->nbz, s);
+          tr->end(s, (double)L->R * N);
+        }
+        ++launched;
+      }
+      check_kernel<<<1, 1024, 0, s>>>(a.part_rr, L->thr, L->R, L->nb, launched & 1, L->d_active);
+      if (cudaMemcpyAsync(L->h_active + slot, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaEventRecord(L->ev[slot], s) != cudaSuccess)
+        return EP_TV_ERR_CUDA;
+      if (pending >= 0) {
+        if (cudaEventSynchronize(L->ev[pending & 1]) != cudaSuccess) return EP_TV_ERR_CUDA;
+        if (L->h_active[pending & 1] == 0) break;
+      }
+      pending = (launched << 1) | slot;
+      slot ^= 1;
+      if (n == 0 || total + launched >= L->max_iter) {
+        if (cudaEventSynchronize(L->ev[pending & 1]) != cudaSuccess) return EP_TV_ERR_CUDA;
         break;
       }
     }
-    pending = (launched << 1) | slot;
-    slot ^= 1;
-    if (launched >= L->max_iter) {
-      if (cudaEventSynchronize(L->ev[pending & 1]) != cudaSuccess) return EP_TV_ERR_CUDA;
-      if (L->h_active[pending & 1] == 0) {
-        iters = launched;
-      } else {
-        iters = launched;
-        ran_out = true;
-      }
-      break;
-    }
+    // the solution and the partials of every launched iteration are final; count
+    // the iterations up to the poll that found all systems converged
+    total += launched;
   }
+  iters = total;
+  const bool ran_out = !converged;
   L->last_iters = iters;
   if (ran_out) set_status_kernel<<<1, 1, 0, s>>>(status, ST_CG_NOCONV);
   store_iters_kernel<<<1, 1, 0, s>>>(counters, (unsigned long long)iters);
@@ -1106,7 +1294,7 @@ int likelihood_systems(const LikelihoodState* L) { return L->R; }
 int likelihood_last_iters(const LikelihoodState* L) { return L->last_iters; }
 
 size_t likelihood_state_bytes(const LikelihoodState* L) {
-  return sizeof(float) * (size_t)L->R * L->c.N;
+  return sizeof(double) * (size_t)L->R * L->c.N;
 }
 
 ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_t s) {

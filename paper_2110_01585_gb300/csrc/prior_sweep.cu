@@ -22,7 +22,7 @@
 //
 // Arithmetic: FP32 with the cancellation-free forms of tilted.cuh; the new
 // precision uses tau_i = rho / (c_j + q c_i), which equals 1/Var_i - 1/c_i of
-// Eq. update_qk_x (rho = 1 - q, q = Sbar / s^2) without subtracting.  Edges with
+// Eq. update_qk_x (q = Sbar / s^2, rho = 1 - q) without subtracting.  Edges with
 // lam * s < 1e-3 (where rho is a small difference of O(1) numbers) are redone in
 // FP64 when fp64_tail is set.
 #include "internal.cuh"
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
       const float s2 = ci + cj;
       // a_u and the counters take each edge once, from the tile owning its first pixel
       const bool owned = rr >= 2 && rr < 2 + kTH && cc >= 2 && cc < 2 + kTW && gri < H && gci < W;
-      float d, q, eab;
+      float d, q, rho, eab;
       const bool tail = a.fp64_tail && lam > 0.0f && (lam * sqrtf(s2) < 1e-3f);
       if (tail) {
         const double ci_d = 1.0 / (double)ti, cj_d = 1.0 / (double)tj;
@@ -152,15 +152,16 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
         TiltedOut<double> od = laplace_tilted<double>(mu_d, ci_d + cj_d, lam_d);
         d = (float)od.d;
         q = (float)od.q;
+        rho = (float)od.rho;
         eab = (float)od.eab;
         n_fp64 += owned;
       } else {
         TiltedOut<float> o = laplace_tilted<float>(mu, s2, lam);
         d = o.d;
         q = o.q;
+        rho = o.rho;
         eab = o.eab;
       }
-      const float rho = 1.0f - q;
       // Eq. update_qk_x: tau = 1/Var - 1/c, Var from the projection; cap, then mean
       float tni = rho / (cj + q * ci);
       float tnj = rho / (ci + q * cj);

@@ -9,10 +9,14 @@
 // and with the inverse Mills ratio h(a) = sqrt(2/pi) / erfcx(a/sqrt2),
 // g(a) = h(a) - a and v(a) = 1 - h(a) g(a) the halves have
 //     E+ / s = g(a+),  E- / s = -g(a-),  V+- / s^2 = v(a+-).
-// The site update needs only three numbers, formed without cancellation:
+// The site update needs four numbers, each formed from its own formula so that
+// it keeps its relative accuracy where it is small:
 //     d   = (ubar - mu) / s^2 = [w+ (h+ - l) - w- (h- - l)] / s
 //     q   = Sbar / s^2        = w+ v+ + w- v- + w+ w- (g+ + g-)^2
+//     rho = 1 - q             = w+ h+ g+ + w- h- g- - w+ w- (g+ + g-)^2
 //     eab = E|u|              = s (w+ g+ + w- g-)
+// (1 - v = h g, so rho needs no subtraction from 1; it still cancels when
+// l -> 0 with both halves weighted, which is where the FP64 path takes over.)
 // For a >= CF_SWITCH, g and v come from Laplace's continued fraction of the
 // Mills ratio, g = t_1, v = t_1 (t_2 - t_1), t_k = k / (a + t_{k+1}).
 #pragma once
@@ -60,6 +64,7 @@ template <typename T>
 struct TiltedOut {
   T d;    // (ubar - mu) / s^2
   T q;    // Sbar / s^2
+  T rho;  // 1 - Sbar / s^2
   T eab;  // E|u|
 };
 
@@ -86,7 +91,11 @@ __device__ __forceinline__ TiltedOut<T> laplace_tilted(T mu, T s2, T lam) {
   T dm = wm > T(0) ? wm * (hm - l) : T(0);
   o.d = (dp - dm) / s;
   T gs = gp + gm;
-  o.q = wp * vp + wm * vm + wp * wm * gs * gs;
+  T mix = wp * wm * gs * gs;
+  o.q = wp * vp + wm * vm + mix;
+  T hgp = wp > T(0) ? wp * hp * gp : T(0);
+  T hgm = wm > T(0) ? wm * hm * gm : T(0);
+  o.rho = hgp + hgm - mix;
   o.eab = s * (wp * gp + wm * gm);
   return o;
 }
