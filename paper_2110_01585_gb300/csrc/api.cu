@@ -23,8 +23,11 @@ struct ep_tv_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
 
-  float* tau = nullptr;       // [5][N]
-  float* nu = nullptr;        // [5][N]
+  float* tau0 = nullptr;      // [N] likelihood site
+  float* nu0 = nullptr;
+  float* ptau[2] = {nullptr, nullptr};  // [4][N] prior sites, two buffers
+  float* pnu[2] = {nullptr, nullptr};
+  int cur = 0;                // buffer holding the current prior sites
   float* y = nullptr;         // [M]
   float* mu0 = nullptr;       // initial mean of site 0 (y, or H^T y for DENSE)
   double* dscal = nullptr;    // DS_*
@@ -84,8 +87,12 @@ ep_tv_status check_params(const ep_tv_operator* op, const ep_tv_params* p) {
 void free_ctx(ep_tv_ctx* c) {
   if (!c) return;
   if (c->lik) likelihood_destroy(c->lik);
-  cudaFree(c->tau);
-  cudaFree(c->nu);
+  cudaFree(c->tau0);
+  cudaFree(c->nu0);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->ptau[b]);
+    cudaFree(c->pnu[b]);
+  }
   cudaFree(c->y);
   cudaFree(c->mu0);
   cudaFree(c->dscal);
@@ -98,7 +105,9 @@ void free_ctx(ep_tv_ctx* c) {
 ep_tv_status init_state(ep_tv_ctx* c) {
   const float inv_xi = (float)(1.0 / c->p.xi);
   const float min_tau = (float)(1.0 / c->p.var_cap);
-  launch_init_sites(c->tau, c->nu, c->mu0, c->n, inv_xi, min_tau, c->stream);
+  c->cur = 0;
+  launch_init_sites(c->tau0, c->nu0, c->ptau[0], c->pnu[0], c->mu0, c->n, inv_xi, min_tau,
+                    c->stream);
   double ds[DS_COUNT] = {c->p.beta, 0.0, 0.0, 0.0};
   CK(cudaMemcpyAsync(c->dscal, ds, sizeof(ds), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
@@ -127,8 +136,12 @@ ep_tv_status latched(ep_tv_ctx* c) {
 
 SweepArgs sweep_args(ep_tv_ctx* c, int order) {
   SweepArgs a;
-  a.tau = c->tau;
-  a.nu = c->nu;
+  a.tau0 = c->tau0;
+  a.nu0 = c->nu0;
+  a.tin = c->ptau[c->cur];
+  a.nin = c->pnu[c->cur];
+  a.tout = c->ptau[c->cur ^ 1];
+  a.nout = c->pnu[c->cur ^ 1];
   a.y = c->y;
   a.inv_xi = (float)(1.0 / c->p.xi);
   a.height = c->height;
@@ -183,8 +196,12 @@ ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_pa
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return EP_TV_ERR_CUDA; }
   c->n_partial = prior_sweep_blocks(c->height, c->width);
-  bool ok = cudaMalloc(&c->tau, sizeof(float) * 5 * c->n) == cudaSuccess &&
-            cudaMalloc(&c->nu, sizeof(float) * 5 * c->n) == cudaSuccess &&
+  bool ok = cudaMalloc(&c->tau0, sizeof(float) * c->n) == cudaSuccess &&
+            cudaMalloc(&c->nu0, sizeof(float) * c->n) == cudaSuccess &&
+            cudaMalloc(&c->ptau[0], sizeof(float) * 4 * c->n) == cudaSuccess &&
+            cudaMalloc(&c->ptau[1], sizeof(float) * 4 * c->n) == cudaSuccess &&
+            cudaMalloc(&c->pnu[0], sizeof(float) * 4 * c->n) == cudaSuccess &&
+            cudaMalloc(&c->pnu[1], sizeof(float) * 4 * c->n) == cudaSuccess &&
             cudaMalloc(&c->y, sizeof(float) * c->m) == cudaSuccess &&
             cudaMalloc(&c->mu0, sizeof(float) * c->n) == cudaSuccess &&
             cudaMalloc(&c->dscal, sizeof(double) * DS_COUNT) == cudaSuccess &&
@@ -263,16 +280,17 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
       order |= k << (4 * u);
     }
     if (c->lik && c->p.order_mode == 1) {
-      ep_tv_status st = likelihood_update(c->lik, c->tau, c->nu, c->status, c->counters,
-                                          &c->tracer, c->stream);
+      ep_tv_status st = likelihood_update(c->lik, c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur],
+                                          c->status, c->counters, &c->tracer, c->stream);
       if (st != EP_TV_OK) return st;
     }
     c->tracer.begin(EP_TV_K_PRIOR_SWEEP, c->stream);
     launch_prior_sweep(sweep_args(c, order), c->op.op == EP_TV_OP_IDENTITY, c->stream);
     c->tracer.end(c->stream, (double)c->n);
+    c->cur ^= 1;
     if (c->lik && c->p.order_mode == 0) {
-      ep_tv_status st = likelihood_update(c->lik, c->tau, c->nu, c->status, c->counters,
-                                          &c->tracer, c->stream);
+      ep_tv_status st = likelihood_update(c->lik, c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur],
+                                          c->status, c->counters, &c->tracer, c->stream);
       if (st != EP_TV_OK) return st;
     }
     ++c->sweeps;
@@ -310,15 +328,18 @@ ep_tv_status ep_tv_set_beta(ep_tv_ctx* c, double beta) {
 
 ep_tv_status ep_tv_posterior(ep_tv_ctx* c, float* mean, float* var) {
   if (!c || (!mean && !var)) return EP_TV_ERR_ARG;
-  launch_posterior(c->tau, c->nu, c->n, mean, var, c->stream);
+  launch_posterior(c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur], c->n, mean, var, c->stream);
   if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
   return EP_TV_OK;
 }
 
 ep_tv_status ep_tv_get_sites(ep_tv_ctx* c, float* tau, float* nu) {
   if (!c || !tau || !nu) return EP_TV_ERR_ARG;
-  CK(cudaMemcpyAsync(tau, c->tau, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(nu, c->nu, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  const size_t nb = sizeof(float) * c->n;
+  CK(cudaMemcpyAsync(tau, c->tau0, nb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(tau + c->n, c->ptau[c->cur], 4 * nb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(nu, c->nu0, nb, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(nu + c->n, c->pnu[c->cur], 4 * nb, cudaMemcpyDeviceToDevice, c->stream));
   return EP_TV_OK;
 }
 
@@ -355,10 +376,13 @@ ep_tv_status ep_tv_state_export(ep_tv_ctx* c, void* host_buf, size_t* bytes) {
   b += sizeof(hdr);
   CK(cudaMemcpyAsync(b, c->dscal, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost, c->stream));
   b += sizeof(double) * DS_COUNT;
-  CK(cudaMemcpyAsync(b, c->tau, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToHost, c->stream));
-  b += sizeof(float) * 5 * c->n;
-  CK(cudaMemcpyAsync(b, c->nu, sizeof(float) * 5 * c->n, cudaMemcpyDeviceToHost, c->stream));
-  b += sizeof(float) * 5 * c->n;
+  const size_t nb = sizeof(float) * c->n;
+  CK(cudaMemcpyAsync(b, c->tau0, nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(b + nb, c->ptau[c->cur], 4 * nb, cudaMemcpyDeviceToHost, c->stream));
+  b += 5 * nb;
+  CK(cudaMemcpyAsync(b, c->nu0, nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(b + nb, c->pnu[c->cur], 4 * nb, cudaMemcpyDeviceToHost, c->stream));
+  b += 5 * nb;
   if (c->lik) {
     ep_tv_status st = likelihood_state_export(c->lik, b, c->stream);
     if (st != EP_TV_OK) return st;
@@ -380,10 +404,13 @@ ep_tv_status ep_tv_state_import(ep_tv_ctx* c, const void* host_buf, size_t bytes
   b += sizeof(hdr);
   CK(cudaMemcpyAsync(c->dscal, b, sizeof(double) * DS_COUNT, cudaMemcpyHostToDevice, c->stream));
   b += sizeof(double) * DS_COUNT;
-  CK(cudaMemcpyAsync(c->tau, b, sizeof(float) * 5 * c->n, cudaMemcpyHostToDevice, c->stream));
-  b += sizeof(float) * 5 * c->n;
-  CK(cudaMemcpyAsync(c->nu, b, sizeof(float) * 5 * c->n, cudaMemcpyHostToDevice, c->stream));
-  b += sizeof(float) * 5 * c->n;
+  const size_t nb = sizeof(float) * c->n;
+  CK(cudaMemcpyAsync(c->tau0, b, nb, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ptau[c->cur], b + nb, 4 * nb, cudaMemcpyHostToDevice, c->stream));
+  b += 5 * nb;
+  CK(cudaMemcpyAsync(c->nu0, b, nb, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->pnu[c->cur], b + nb, 4 * nb, cudaMemcpyHostToDevice, c->stream));
+  b += 5 * nb;
   if (c->lik) {
     ep_tv_status st = likelihood_state_import(c->lik, b, c->stream);
     if (st != EP_TV_OK) return st;

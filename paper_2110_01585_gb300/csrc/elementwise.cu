@@ -15,39 +15,31 @@ inline int ew_blocks(long long n) {
 }
 
 // q_{x,0} = N(mu0, xi I) and q_{x,k} = N(0, var_cap I), in natural parameters.
-__global__ void init_sites_kernel(float* tau, float* nu, const float* mu0, long long n,
-                                  float inv_xi, float min_tau) {
+__global__ void init_sites_kernel(float* tau0, float* nu0, float* tp, float* np,
+                                  const float* mu0, long long n, float inv_xi, float min_tau) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    tau[p] = inv_xi;
-    nu[p] = mu0[p] * inv_xi;
+    tau0[p] = inv_xi;
+    nu0[p] = mu0[p] * inv_xi;
 #pragma unroll
-    for (int s = 1; s < 5; ++s) {
-      tau[s * n + p] = min_tau;
-      nu[s * n + p] = 0.0f;
+    for (int s = 0; s < 4; ++s) {
+      tp[s * n + p] = min_tau;
+      np[s * n + p] = 0.0f;
     }
   }
 }
 
-__global__ void fill_site0_kernel(float* tau, float* nu, const float* y, long long n,
-                                  float inv_xi) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    tau[p] = inv_xi;
-    nu[p] = y[p] * inv_xi;
-  }
-}
-
 // mean = (sum_s nu_s) / (sum_s tau_s), var = 1 / (sum_s tau_s)
-__global__ void posterior_kernel(const float* __restrict__ tau, const float* __restrict__ nu,
+__global__ void posterior_kernel(const float* __restrict__ tau0, const float* __restrict__ nu0,
+                                 const float* __restrict__ tp, const float* __restrict__ np,
                                  long long n, float* mean, float* var) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    float t = tau[p], v = nu[p];
+    float t = tau0[p], v = nu0[p];
 #pragma unroll
-    for (int s = 1; s < 5; ++s) {
-      t += tau[s * n + p];
-      v += nu[s * n + p];
+    for (int s = 0; s < 4; ++s) {
+      t += tp[s * n + p];
+      v += np[s * n + p];
     }
     const float sig = 1.0f / t;
     if (mean) mean[p] = v * sig;
@@ -57,19 +49,14 @@ __global__ void posterior_kernel(const float* __restrict__ tau, const float* __r
 
 }  // namespace
 
-void launch_init_sites(float* tau, float* nu, const float* mu0, long long n, float inv_xi,
-                       float min_tau, cudaStream_t s) {
-  init_sites_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau, nu, mu0, n, inv_xi, min_tau);
+void launch_init_sites(float* tau0, float* nu0, float* tp, float* np, const float* mu0, long long n,
+                       float inv_xi, float min_tau, cudaStream_t s) {
+  init_sites_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau0, nu0, tp, np, mu0, n, inv_xi, min_tau);
 }
 
-void launch_fill_site0_identity(float* tau, float* nu, const float* y, long long n, float inv_xi,
-                                cudaStream_t s) {
-  fill_site0_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau, nu, y, n, inv_xi);
-}
-
-void launch_posterior(const float* tau, const float* nu, long long n, float* mean, float* var,
-                      cudaStream_t s) {
-  posterior_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau, nu, n, mean, var);
+void launch_posterior(const float* tau0, const float* nu0, const float* tp, const float* np,
+                      long long n, float* mean, float* var, cudaStream_t s) {
+  posterior_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau0, nu0, tp, np, n, mean, var);
 }
 
 }  // namespace eptv

@@ -89,8 +89,12 @@ struct Tracer {
 };
 
 struct SweepArgs {
-  float* tau;                 // [5][N] site precisions, row 0 = likelihood site
-  float* nu;                  // [5][N] site precision-times-mean
+  const float* tau0;          // [N] likelihood-site precision
+  const float* nu0;           // [N] likelihood-site precision-times-mean
+  const float* tin;           // [4][N] prior sites k = 1..4 before the sweep (row k - 1)
+  const float* nin;
+  float* tout;                // [4][N] prior sites after the sweep (a different buffer:
+  float* nout;                // halo tiles read while other tiles write)
   const float* y;             // identity operator: observation (site 0 = (1/xi, y/xi))
   float inv_xi;               // 1 / xi as float (identity operator)
   int height, width;
@@ -116,11 +120,9 @@ int prior_sweep_blocks(int height, int width);
 void launch_abar_reduce(const double* partial, int n_partial, double* dscal, double n_pixels,
                         int do_em, cudaStream_t s);
 
-void launch_init_sites(float* tau, float* nu, const float* mu0, long long n, float inv_xi,
-                       float min_tau, cudaStream_t s);
-void launch_posterior(const float* tau, const float* nu, long long n, float* mean, float* var,
-                      cudaStream_t s);
-void launch_fill_site0_identity(float* tau, float* nu, const float* y, long long n, float inv_xi,
-                                cudaStream_t s);
+void launch_init_sites(float* tau0, float* nu0, float* tp, float* np, const float* mu0, long long n,
+                       float inv_xi, float min_tau, cudaStream_t s);
+void launch_posterior(const float* tau0, const float* nu0, const float* tp, const float* np,
+                      long long n, float* mean, float* var, cudaStream_t s);
 
 }  // namespace eptv

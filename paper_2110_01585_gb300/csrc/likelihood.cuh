@@ -32,8 +32,10 @@ ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const 
                                    int n_samples, cudaStream_t s);
 // One q_{x,0} update: cavity from sites 1..4, tilted moments of P_0
 // (Eq. tilted_P_1), site update (Eq. update_q0_x) with cap and damping.
-ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, unsigned* status,
-                               unsigned long long* counters, Tracer* tr, cudaStream_t s);
+// tau0, nu0: likelihood site (updated in place); tp, np: prior sites, [4][N].
+ep_tv_status likelihood_update(LikelihoodState* L, float* tau0, float* nu0, const float* tp,
+                               const float* np, unsigned* status, unsigned long long* counters,
+                               Tracer* tr, cudaStream_t s);
 // Algorithmic DRAM bytes per unit of the traced likelihood kernels.
 double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel);
 int likelihood_systems(const LikelihoodState* L);

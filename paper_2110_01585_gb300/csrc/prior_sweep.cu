@@ -11,6 +11,10 @@
 //   V3 vertical   (2b,c)-(2b+1,c)   V4 vertical   (2b+1,c)-(2b+2 mod H,c)
 // The free boundary drops the wrap-around edges.
 //
+// The prior-site planes are read from one buffer and written to another: a
+// tile's halo belongs to neighbouring tiles, which may already have written
+// their results when it is staged.
+//
 // Temporal blocking: a CTA owns a TH x TW tile and stages a (TH+4) x (TW+4)
 // region (2-pixel halo) of all ten site planes in shared memory.  Each of the
 // two horizontal updates can spoil at most one halo column per side, each of
@@ -74,13 +78,13 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
         sT[idx] = a.inv_xi;
         sV[idx] = a.y[p] * a.inv_xi;
       } else {
-        sT[idx] = a.tau[p];
-        sV[idx] = a.nu[p];
+        sT[idx] = a.tau0[p];
+        sV[idx] = a.nu0[p];
       }
 #pragma unroll
       for (int s = 1; s < 5; ++s) {
-        sT[s * kRN + idx] = a.tau[s * N + p];
-        sV[s * kRN + idx] = a.nu[s * N + p];
+        sT[s * kRN + idx] = a.tin[(s - 1) * N + p];
+        sV[s * kRN + idx] = a.nin[(s - 1) * N + p];
       }
     } else {
 #pragma unroll
@@ -196,8 +200,8 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
     const int sidx = (tr + 2) * kRW + tc + 2;
 #pragma unroll
     for (int s = 1; s < 5; ++s) {
-      a.tau[s * N + p] = sT[s * kRN + sidx];
-      a.nu[s * N + p] = sV[s * kRN + sidx];
+      a.tout[(s - 1) * N + p] = sT[s * kRN + sidx];
+      a.nout[(s - 1) * N + p] = sV[s * kRN + sidx];
     }
   }
 
