@@ -260,16 +260,15 @@ __global__ void mean_kernel(const double* dpart, int n, double inv_count, double
 // True residual of every system (blockIdx.z),
 //   r = H^T (y' - H x) / xi + (n' - d x),
 // y' = y, n' = n for the mean system and y' = sqrt(xi) eps1_s, n' = sqrt(d) eps2_s for
-// probe s, so that r = b - Q x with b as in rhs_value.  H x is accumulated in FP64
-// from the FP64 solution: y' - H x is small next to y', and forming it in FP32
-// would leave an error of order eps |y'| / xi in r, which the conditioning of Q
-// (1e4..1e5) turns into percent-level errors in x.  The rest is FP32.
-// Partials: r.r (buffer 0), b.b, and r.Minv.r in Jacobi mode.
+// probe s, so that r = b - Q x with b as in rhs_value.  Computed in FP64 from the
+// FP64 solution: the terms H^T H x / xi and d x are several times larger than r
+// near the solution, and an FP32 evaluation leaves an error of order
+// eps |H^T (y' - H x)| / xi, which the conditioning of Q (1e4..1e5) turns into
+// percent-level errors in x.  Partials: r.r (buffer 0), b.b, r.Minv.r (Jacobi).
 __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   extern __shared__ double smd[];
   __shared__ double tapd[232];
-  __shared__ float tapf[232];
-  __shared__ float outb[kTile * kTile];
+  __shared__ double outd[kTile * kTile];
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
@@ -278,13 +277,10 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   const int MH = kTile + 2 * hh, MW = kTile + 2 * hw;      // y' - H x region, halo kh / 2
   double* xs = smd;                                        // RH x RW
   double* rowp = xs + RH * RW;                             // RH x MW (separable)
-  float* vs = (float*)(rowp + (c.separable ? RH * MW : 0));  // MH x MW
-  float* tmpf = vs + MH * MW;                              // MH x kTile (separable)
+  double* vs = rowp + (c.separable ? RH * MW : 0);         // MH x MW
+  double* tmpd = vs + MH * MW;                             // MH x kTile (separable)
   const int ntap = c.separable ? c.kh + c.kw : c.kh * c.kw;
-  for (int i = threadIdx.x; i < ntap; i += kThreads) {
-    tapd[i] = c.hd[i];
-    tapf[i] = c.hf[i];
-  }
+  for (int i = threadIdx.x; i < ntap; i += kThreads) tapd[i] = c.hd[i];
   const double* x = a.X + (long long)j * c.N;
   for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
     const int rr = idx / RW, cc = idx - rr * RW;
@@ -293,10 +289,10 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   }
   __syncthreads();
   const float* yp = j == 0 ? a.Y0 : a.Y1 + (long long)(j - 1) * c.N;
+  // v = y' - H x on the (kh/2, kw/2)-halo region: (H x)(r,c) = sum k[a,b] x(r-a+hh, c-b+hw)
   if (c.separable) {
     const double* u = tapd;
     const double* v = tapd + c.kh;
-    // along rows: rowp(rr, mc) = sum_b v[b] x(rr, mc - b + 2 hw)
     for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
       const int rr = idx / MW, mc = idx - rr * MW;
       const double* row = xs + rr * RW + mc + 2 * hw;
@@ -305,16 +301,13 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
       rowp[idx] = acc;
     }
     __syncthreads();
-    // along columns, then v = y' - H x
     for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
       const int mr = idx / MW, mc = idx - mr * MW;
       const double* col = rowp + (mr + 2 * hh) * MW + mc;
       double acc = 0.0;
       for (int aa = 0; aa < c.kh; ++aa) acc = fma(u[aa], col[-aa * MW], acc);
       const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-      const long long pp = (long long)gr * c.W + gcol;
-      const double yv = (double)yp[pp];
-      vs[idx] = (float)(yv - acc);
+      vs[idx] = (double)yp[(long long)gr * c.W + gcol] - acc;
     }
   } else {
     for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
@@ -326,41 +319,39 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
         for (int b = 0; b < c.kw; ++b) acc = fma(krow[b], xrow[-b], acc);
       }
       const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-      const long long pp = (long long)gr * c.W + gcol;
-      const double yv = (double)yp[pp];
-      vs[idx] = (float)(yv - acc);
+      vs[idx] = (double)yp[(long long)gr * c.W + gcol] - acc;
     }
   }
   __syncthreads();
-  // H^T v on the tile, FP32: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
+  // H^T v on the tile: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
   if (c.separable) {
-    const float* u = tapf;
-    const float* v = tapf + c.kh;
+    const double* u = tapd;
+    const double* v = tapd + c.kh;
     for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
       const int mr = idx / kTile, tc = idx - mr * kTile;
-      const float* row = vs + mr * MW + tc;
-      float acc = 0.f;
-      for (int b = 0; b < c.kw; ++b) acc = fmaf(v[b], row[b], acc);
-      tmpf[idx] = acc;
+      const double* row = vs + mr * MW + tc;
+      double acc = 0.0;
+      for (int b = 0; b < c.kw; ++b) acc = fma(v[b], row[b], acc);
+      tmpd[idx] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
       const int tr = idx / kTile, tc = idx - tr * kTile;
-      const float* col = tmpf + tr * kTile + tc;
-      float acc = 0.f;
-      for (int aa = 0; aa < c.kh; ++aa) acc = fmaf(u[aa], col[aa * kTile], acc);
-      outb[idx] = acc;
+      const double* col = tmpd + tr * kTile + tc;
+      double acc = 0.0;
+      for (int aa = 0; aa < c.kh; ++aa) acc = fma(u[aa], col[aa * kTile], acc);
+      outd[idx] = acc;
     }
   } else {
     for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
       const int tr = idx / kTile, tc = idx - tr * kTile;
-      float acc = 0.f;
+      double acc = 0.0;
       for (int aa = 0; aa < c.kh; ++aa) {
-        const float* vrow = vs + (tr + aa) * MW + tc;
-        const float* krow = tapf + aa * c.kw;
-        for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], vrow[b], acc);
+        const double* vrow = vs + (tr + aa) * MW + tc;
+        const double* krow = tapd + aa * c.kw;
+        for (int b = 0; b < c.kw; ++b) acc = fma(krow[b], vrow[b], acc);
       }
-      outb[idx] = acc;
+      outd[idx] = acc;
     }
   }
   __syncthreads();
@@ -373,11 +364,12 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
     const double xv = xs[(tr + c.hr) * RW + tc + c.hc];
     const double np = j == 0 ? (double)a.Ncav[p]
                              : sqrt((double)a.D[p]) * (double)a.E2[(long long)(j - 1) * c.N + p];
-    const float r = outb[idx] * c.inv_xi + (float)(np - (double)a.D[p] * xv);
+    const double rd = outd[idx] * c.inv_xi_d + (np - (double)a.D[p] * xv);
+    const float r = (float)rd;
     a.Rr[(long long)j * c.N + p] = r;
     const float b = rhs_value(a, j, p);
     if (!a.fft) rz += (double)(r * r * a.Minv[p]);
-    rr2 += (double)(r * r);
+    rr2 += rd * rd;
     bb += (double)(b * b);
   }
   const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
@@ -1041,8 +1033,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   {
     const size_t MH = kTile + 2 * (kh / 2), MW = kTile + 2 * (kw / 2);
     const size_t RH = kTile + 2 * hr, RW = kTile + 2 * hc;
-    L->smem_res = sizeof(double) * (RH * RW + (sep ? RH * MW : 0)) +
-                  sizeof(float) * (MH * MW + (sep ? MH * kTile : 0));
+    L->smem_res = sizeof(double) * (RH * RW + (sep ? RH * MW : 0) + MH * MW + (sep ? MH * kTile : 0));
   }
   std::vector<float> kf(kh * kw);
   for (int i = 0; i < kh * kw; ++i) kf[i] = (float)k[i];

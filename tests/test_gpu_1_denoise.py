@@ -124,7 +124,9 @@ def test_sites_after_one_sweep():
             o.sweep()
             tau, nu = (t.cpu().numpy().reshape(5, -1).astype(np.float64) for t in ep.sites())
             np.testing.assert_allclose(tau, o.tau, rtol=2e-4, atol=1e-7)
-            scale = np.abs(o.tau) * (np.abs(p.y.reshape(-1)) + 1.0)
+            # a capped site (precision 1/var_cap) keeps nu = tau E + (E - m) / c, which
+            # is not small: compare nu on the scale of |nu| + |tau| (|y| + 1)
+            scale = np.abs(o.nu) + np.abs(o.tau) * (np.abs(p.y.reshape(-1)) + 1.0)
             assert np.max(np.abs(nu - o.nu) / scale) < 2e-4
 
 
