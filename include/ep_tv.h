@@ -156,6 +156,13 @@ ep_tv_status ep_tv_status_check(ep_tv_ctx* ctx);
 ep_tv_status ep_tv_stats(ep_tv_ctx* ctx, int32_t* cg_iters, uint64_t* n_fp64,
                          uint64_t* n_capped);
 
+/* Solver report of the last likelihood-site update (CONV_PERIODIC; zeros otherwise):
+   refinement passes, conjugate-gradient iterations, and the final true relative
+   residual ||b - Q x|| / ||b|| of the mean solve and the largest over the probe
+   solves.  HOST out-pointers may be NULL.  Synchronises. */
+ep_tv_status ep_tv_solver_report(ep_tv_ctx* ctx, int32_t* passes, int32_t* iterations,
+                                 double* relres_mean, double* relres_probe_max);
+
 /* Checkpoint: the full EP state (sites, beta, a_u, solver warm starts, counters).
    With host_buf == NULL, *bytes receives the size.  Otherwise host_buf (HOST,
    *bytes long) receives the state; synchronises.  A run resumed with

@@ -168,6 +168,16 @@ class EPTV:
                    "ep_tv_stats")
         return {"cg_iters": it.value, "n_fp64": f64.value, "n_capped": cap.value}
 
+    def solver_report(self):
+        """Last likelihood-site update: refinement passes, CG iterations, final
+        relative residual of the mean solve and worst probe solve."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        rm, rp = ctypes.c_double(), ctypes.c_double()
+        _lib.check(self._lib.ep_tv_solver_report(self._ctx, ctypes.byref(a), ctypes.byref(b),
+                                                 ctypes.byref(rm), ctypes.byref(rp)), "ep_tv_solver_report")
+        return {"passes": a.value, "iterations": b.value, "relres_mean": rm.value,
+                "relres_probe_max": rp.value}
+
     def trace(self, on: bool = True):
         """Enable (and reset) or disable per-kernel CUDA-event tracing."""
         _lib.check(self._lib.ep_tv_trace_enable(self._ctx, int(bool(on))), "ep_tv_trace_enable")

@@ -53,6 +53,8 @@ SIGNATURES = {
     "ep_tv_status_check": (c_int32, [c_void_p]),
     "ep_tv_stats": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(ctypes.c_uint64),
                               ctypes.POINTER(ctypes.c_uint64)]),
+    "ep_tv_solver_report": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                      ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "ep_tv_state_export": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(c_size_t)]),
     "ep_tv_state_import": (c_int32, [c_void_p, c_void_p, c_size_t]),
     "ep_tv_reset": (c_int32, [c_void_p]),

@@ -359,6 +359,20 @@ ep_tv_status ep_tv_stats(ep_tv_ctx* c, int32_t* cg_iters, uint64_t* n_fp64, uint
   return EP_TV_OK;
 }
 
+ep_tv_status ep_tv_solver_report(ep_tv_ctx* c, int32_t* passes, int32_t* iterations,
+                                 double* relres_mean, double* relres_probe_max) {
+  if (!c) return EP_TV_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  int outer = 0;
+  double rm = 0.0, rp = 0.0;
+  if (c->lik) likelihood_report(c->lik, &outer, &rm, &rp);
+  if (passes) *passes = outer;
+  if (iterations) *iterations = c->lik ? likelihood_last_iters(c->lik) : 0;
+  if (relres_mean) *relres_mean = rm;
+  if (relres_probe_max) *relres_probe_max = rp;
+  return EP_TV_OK;
+}
+
 // State layout: header (magic, n, m, sweeps), dscal, tau, nu, likelihood blob.
 ep_tv_status ep_tv_state_export(ep_tv_ctx* c, void* host_buf, size_t* bytes) {
   if (!c || !bytes) return EP_TV_ERR_ARG;

@@ -21,6 +21,8 @@
 // Layout: every vector is one FP32 plane of N = H*W pixels, row-major; the
 // 1 + S right-hand sides are consecutive planes ([0] = mean system).
 #include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
 // otherwise the inner loop runs until r.r <= max(eta^2 r.r, (rtol/2)^2 b.b).
 __global__ void thresholds_kernel(const double* part_rr, const double* part_bb, int R, int nb,
                                   double rtol2_mean, double rtol2_probe, double eta2, double* thr,
-                                  int* active) {
+                                  double* relres, int* active) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -399,6 +401,7 @@ __global__ void thresholds_kernel(const double* part_rr, const double* part_bb, 
     if (lane == 0) {
       const double rtol2 = j == 0 ? rtol2_mean : rtol2_probe;
       const bool done = rr <= rtol2 * bb;
+      relres[j] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
       thr[j] = done ? INFINITY : fmax(eta2 * rr, 0.25 * rtol2 * bb);
       if (!done) atomicAdd(&cnt, 1);
     }
@@ -864,6 +867,11 @@ struct LikelihoodState {
   size_t smem = 0;
   size_t smem_res = 0;
   int last_iters = 0;
+  double* d_relres = nullptr;  // [R] sqrt(r.r / b.b) after the last true residual
+  double* h_relres = nullptr;  // pinned copy
+  double rep_mean = 0.0, rep_probe = 0.0;
+  int rep_outer = 0;
+  bool debug = false;
 };
 
 namespace {
@@ -987,6 +995,10 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   // moves an RB variance term by about Q_ii / d * 1e-6 relative, below 1e-4.
   L->rtol2_probe = std::max(L->rtol2, 1e-12);
   L->max_iter = cfg.p->cg_max_iter;
+  {
+    const char* dbg = getenv("EPTV_DEBUG");
+    L->debug = dbg && dbg[0] == '1';
+  }
   L->seed = cfg.p->seed;
   L->damping = (float)cfg.p->damping;
   L->min_tau = (float)(1.0 / cfg.p->var_cap);
@@ -1060,6 +1072,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
                          cudaMalloc(&L->Z, sizeof(float) * RN) == cudaSuccess &&
                          cudaMalloc(&L->hth, sizeof(float) * N) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&L->d_relres, sizeof(double) * L->R) == cudaSuccess &&
+            cudaHostAlloc(&L->h_relres, sizeof(double) * L->R, cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
             cudaEventCreateWithFlags(&L->ev[0], cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&L->ev[1], cudaEventDisableTiming) == cudaSuccess;
@@ -1167,6 +1181,8 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->Z);
   cudaFree(L->hth);
   cudaFree(L->d_active);
+  cudaFree(L->d_relres);
+  if (L->h_relres) cudaFreeHost(L->h_relres);
   if (L->h_active) cudaFreeHost(L->h_active);
   if (L->ev[0]) cudaEventDestroy(L->ev[0]);
   if (L->ev[1]) cudaEventDestroy(L->ev[1]);
@@ -1213,11 +1229,23 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
     tr->end(s, (double)L->R * N);
     thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2_true,
-                                         L->rtol2_probe, eta2, L->thr, L->d_active);
+                                         L->rtol2_probe, eta2, L->thr, L->d_relres, L->d_active);
     if (cudaMemcpyAsync(L->h_active, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
+        cudaMemcpyAsync(L->h_relres, L->d_relres, sizeof(double) * L->R, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return EP_TV_ERR_CUDA;
+    {
+      double pm = 0.0;
+      for (int jj = 1; jj < L->R; ++jj) pm = std::max(pm, L->h_relres[jj]);
+      L->rep_mean = L->h_relres[0];
+      L->rep_probe = pm;
+      L->rep_outer = outer;
+      if (L->debug)
+        fprintf(stderr, "[eptv cg] outer %d inner-total %d relres mean %.3e probes max %.3e active %d\n",
+                outer, total, L->rep_mean, pm, L->h_active[0]);
+    }
     if (L->h_active[0] == 0) {
       converged = true;
       break;
@@ -1292,6 +1320,13 @@ double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
 int likelihood_systems(const LikelihoodState* L) { return L->R; }
 
 int likelihood_last_iters(const LikelihoodState* L) { return L->last_iters; }
+
+void likelihood_report(const LikelihoodState* L, int* outer, double* relres_mean,
+                       double* relres_probe) {
+  if (outer) *outer = L->rep_outer;
+  if (relres_mean) *relres_mean = L->rep_mean;
+  if (relres_probe) *relres_probe = L->rep_probe;
+}
 
 size_t likelihood_state_bytes(const LikelihoodState* L) {
   return sizeof(double) * (size_t)L->R * L->c.N;

@@ -40,6 +40,9 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau0, float* nu0, cons
 double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel);
 int likelihood_systems(const LikelihoodState* L);
 int likelihood_last_iters(const LikelihoodState* L);
+// Outer refinement passes and final relative residuals of the last update.
+void likelihood_report(const LikelihoodState* L, int* outer, double* relres_mean,
+                       double* relres_probe);
 size_t likelihood_state_bytes(const LikelihoodState* L);
 ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_t s);
 ep_tv_status likelihood_state_import(LikelihoodState* L, const void* host, cudaStream_t s);
