@@ -199,7 +199,10 @@ struct CgArgs {
   int S;
   double* X;             // R planes, FP64 solutions
   float* Rr;             // R planes
-  float* P;              // R planes
+  float* P;              // R planes: search directions of even iterations
+  float* P2;             // R planes: search directions of odd iterations.  Two buffers
+                         // because a tile reads the previous direction over its halo
+                         // while neighbouring tiles write the new one.
   float* Qp;             // R planes
   const float* D;        // cavity precision
   const float* Ncav;     // cavity natural mean
@@ -434,16 +437,17 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
   const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
   const float* r = a.Rr + (long long)j * c.N;
   const float* z = a.Z + (long long)j * c.N;
-  float* P = a.P + (long long)j * c.N;
+  const float* Pold = ((it & 1) ? a.P : a.P2) + (long long)j * c.N;
+  float* P = ((it & 1) ? a.P2 : a.P) + (long long)j * c.N;
   for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
     const int rr_ = idx / RW, cc = idx - rr_ * RW;
     const int gr = wrapi(r0 - c.hr + rr_, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
     const long long p = (long long)gr * c.W + gcol;
     float v = a.fft ? z[p] : r[p] * a.Minv[p];
-    if (it > 0) v = fmaf(beta, P[p], v);
+    if (it > 0) v = fmaf(beta, Pold[p], v);
     sm.v[idx] = v;
   }
-  __syncthreads();  // all reads of the old P are done before any write below
+  __syncthreads();
   hth_tile(c, sm, outb);
   double pq = 0;
   for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
@@ -488,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
   double* X = a.X + (long long)j * c.N;
   float* Rr = a.Rr + (long long)j * c.N;
-  const float* P = a.P + (long long)j * c.N;
+  const float* P = ((it & 1) ? a.P2 : a.P) + (long long)j * c.N;
   const float* Q = a.Qp + (long long)j * c.N;
   double rz2 = 0, rr2 = 0;
   for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
@@ -847,6 +851,7 @@ struct LikelihoodState {
   int max_outer = 12;
   float* Rr = nullptr;
   float* P = nullptr;
+  float* P2 = nullptr;
   float* Qp = nullptr;
   double* part = nullptr;   // pq, rz[2], rr[2], bb
   int nbz = 0, nbmax = 0;
@@ -884,6 +889,7 @@ CgArgs cg_args(LikelihoodState* L) {
   a.X = L->X;
   a.Rr = L->Rr;
   a.P = L->P;
+  a.P2 = L->P2;
   a.Qp = L->Qp;
   a.D = L->D;
   a.Ncav = L->Ncav;
@@ -1064,6 +1070,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->d_hf, sizeof(float) * (kh * kw + kh + kw)) == cudaSuccess &&
             cudaMalloc(&L->Rr, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->P, sizeof(float) * RN) == cudaSuccess &&
+            cudaMalloc(&L->P2, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->Qp, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->part, sizeof(double) * 6 * L->R * L->nbmax) == cudaSuccess &&
             cudaMalloc(&L->dpart, sizeof(double) * L->prep_blocks) == cudaSuccess &&
@@ -1173,6 +1180,7 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->d_hf);
   cudaFree(L->Rr);
   cudaFree(L->P);
+  cudaFree(L->P2);
   cudaFree(L->Qp);
   cudaFree(L->part);
   cudaFree(L->dpart);
