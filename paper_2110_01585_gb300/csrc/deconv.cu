@@ -177,22 +177,6 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c3, double
   __syncthreads();
 }
 
-// Sum of one RHS's block partials, fixed order (warp 0), broadcast to the block.
-__device__ __forceinline__ double sum_partials(const double* part, int nb) {
-  __shared__ double bc;
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += 32) s += part[i];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (threadIdx.x == 0) bc = s;
-  }
-  __syncthreads();
-  const double r = bc;
-  __syncthreads();
-  return r;
-}
-
 struct CgArgs {
   ConvDesc c;
   int R;                 // right-hand sides (1 + S)
@@ -219,6 +203,7 @@ struct CgArgs {
   double* part_rr;       // [2][R][nb]
   double* part_bb;       // [R][nb]
   double rtol2;
+  const float* scal;     // [R][4]: active flag, beta, alpha (from cg_scalars_kernel)
   int nb;                // tile blocks per system
   int nbz;               // blocks per system producing r.z partials
   int fft;               // 1: z = M^{-1} r by the circulant preconditioner, else Jacobi
@@ -418,18 +403,10 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
   extern __shared__ float smem[];
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
-  const int buf = it & 1;
-  const double* rr_cur = a.part_rr + ((long long)buf * a.R + j) * a.nb;
-  const double rr = sum_partials(rr_cur, a.nb);
-  if (rr <= a.thr[j]) return;  // this system has converged
+  if (a.scal[4 * j] == 0.f) return;  // this system has converged
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&a.counters[DC_CG_DIR_UNITS], 1ull);
-  float beta = 0.f;
-  if (it > 0) {
-    const double rz_new = sum_partials(a.part_rz + ((long long)buf * a.R + j) * a.nbz, a.nbz);
-    const double rz_old = sum_partials(a.part_rz + ((long long)(buf ^ 1) * a.R + j) * a.nbz, a.nbz);
-    beta = (float)(rz_new / rz_old);
-  }
+  const float beta = a.scal[4 * j + 1];
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
   StencilSmem sm = carve(c, smem);
   __shared__ float outb[kTile * kTile];
@@ -475,8 +452,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const long long oz_cur = ((long long)buf * a.R + j) * a.nbz;
   const long long oz_nxt = ((long long)nbuf * a.R + j) * a.nbz;
   const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
-  const double rr = sum_partials(a.part_rr + o_cur, a.nb);
-  if (rr <= a.thr[j]) {
+  if (a.scal[4 * j] == 0.f) {
     // converged: carry this block's partials forward so the state stays converged
     if (threadIdx.x == 0) {
       a.part_rr[o_nxt + blk] = a.part_rr[o_cur + blk];
@@ -486,9 +462,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   }
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&a.counters[DC_CG_UPD_UNITS], 1ull);
-  const double rz = sum_partials(a.part_rz + oz_cur, a.nbz);
-  const double pq = sum_partials(a.part_pq + (long long)j * a.nb, a.nb);
-  const float alpha = (float)(rz / pq);
+  const float alpha = a.scal[4 * j + 2];
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
   double* X = a.X + (long long)j * c.N;
   float* Rr = a.Rr + (long long)j * c.N;
@@ -556,7 +530,10 @@ __device__ void fft_dit(float2* a, int n, int logn, int count, int stride, int t
   for (int sh = 1; sh <= logn; ++sh) {
     const int len = 1 << sh, half = len >> 1, twstep = n >> sh;
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      const int t = b / half_n, q = b - t * half_n;
+      // interleaved transforms (tstride 1): neighbouring threads take neighbouring
+      // transforms, so shared-memory accesses stay on distinct banks
+      int t, q;
+      if (tstride == 1) { q = b / count; t = b - q * count; } else { t = b / half_n; q = b - t * half_n; }
       const int grp = q >> (sh - 1), pos = q & (half - 1);
       const int i = grp * len + pos, j = i + half;
       float2* base = a + t * tstride;
@@ -578,7 +555,8 @@ __device__ void ifft_dif(float2* a, int n, int logn, int count, int stride, int 
   for (int sh = logn; sh >= 1; --sh) {
     const int len = 1 << sh, half = len >> 1, twstep = n >> sh;
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      const int t = b / half_n, q = b - t * half_n;
+      int t, q;
+      if (tstride == 1) { q = b / count; t = b - q * count; } else { t = b / half_n; q = b - t * half_n; }
       const int grp = q >> (sh - 1), pos = q & (half - 1);
       const int i = grp * len + pos, j = i + half;
       float2* base = a + t * tstride;
@@ -708,6 +686,45 @@ __global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int
       }
     }
     out[p] = (float)((re * re + im * im) * inv_xi);
+  }
+}
+
+// Per-system CG scalars from the block partials, one warp per system, in a fixed
+// order.  stage 0 (before the direction kernel of iteration it): active flag
+// (r.r above the system's threshold) and beta = rz(it) / rz(it - 1); stage 1
+// (before the update kernel): alpha = rz(it) / p.q.
+__global__ void cg_scalars_kernel(CgArgs a, int it, int stage, float* scal) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int buf = it & 1;
+  for (int j = warp; j < a.R; j += blockDim.x / 32) {
+    double s0 = 0.0, s1 = 0.0;
+    if (stage == 0) {
+      for (int i = lane; i < a.nb; i += 32) s0 += a.part_rr[((long long)buf * a.R + j) * a.nb + i];
+      if (it > 0)
+        for (int i = lane; i < a.nbz; i += 32) {
+          s1 += a.part_rz[((long long)buf * a.R + j) * a.nbz + i];
+        }
+    } else {
+      for (int i = lane; i < a.nbz; i += 32) s0 += a.part_rz[((long long)buf * a.R + j) * a.nbz + i];
+      for (int i = lane; i < a.nb; i += 32) s1 += a.part_pq[(long long)j * a.nb + i];
+    }
+    double s2 = 0.0;
+    if (stage == 0 && it > 0)
+      for (int i = lane; i < a.nbz; i += 32) s2 += a.part_rz[((long long)(buf ^ 1) * a.R + j) * a.nbz + i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, off);
+      s1 += __shfl_down_sync(0xffffffffu, s1, off);
+      s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    }
+    if (lane == 0) {
+      if (stage == 0) {
+        scal[4 * j] = s0 <= a.thr[j] ? 0.f : 1.f;
+        scal[4 * j + 1] = it > 0 ? (float)(s1 / s2) : 0.f;
+      } else {
+        scal[4 * j + 2] = (float)(s0 / s1);
+      }
+    }
   }
 }
 
@@ -872,6 +889,7 @@ struct LikelihoodState {
   size_t smem = 0;
   size_t smem_res = 0;
   int last_iters = 0;
+  float* d_scal = nullptr;      // [R][4] CG scalars
   double* d_relres = nullptr;  // [R] sqrt(r.r / b.b) after the last true residual
   double* h_relres = nullptr;  // pinned copy
   double rep_mean = 0.0, rep_probe = 0.0;
@@ -900,6 +918,7 @@ CgArgs cg_args(LikelihoodState* L) {
   a.Y0 = L->Y0;
   a.Y1 = L->Y1;
   a.thr = L->thr;
+  a.scal = L->d_scal;
   a.Z = L->Z;
   const long long rn = (long long)L->R * L->nbmax;
   a.part_pq = L->part;
@@ -1080,6 +1099,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
                          cudaMalloc(&L->hth, sizeof(float) * N) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&L->d_relres, sizeof(double) * L->R) == cudaSuccess &&
+            cudaMalloc(&L->d_scal, sizeof(float) * 4 * L->R) == cudaSuccess &&
             cudaHostAlloc(&L->h_relres, sizeof(double) * L->R, cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
             cudaEventCreateWithFlags(&L->ev[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -1190,6 +1210,7 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->hth);
   cudaFree(L->d_active);
   cudaFree(L->d_relres);
+  cudaFree(L->d_scal);
   if (L->h_relres) cudaFreeHost(L->h_relres);
   if (L->h_active) cudaFreeHost(L->h_active);
   if (L->ev[0]) cudaEventDestroy(L->ev[0]);
@@ -1268,9 +1289,11 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     while (true) {
       const int n = std::min(kChunk, L->max_iter - total - launched);
       for (int t = 0; t < n; ++t) {
+        cg_scalars_kernel<<<1, 1024, 0, s>>>(a, launched, 0, L->d_scal);
         tr->begin(EP_TV_K_CG_DIRECTION, s);
         direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
         tr->end(s, -1.0);
+        cg_scalars_kernel<<<1, 1024, 0, s>>>(a, launched, 1, L->d_scal);
         tr->begin(EP_TV_K_CG_UPDATE, s);
         update_kernel<<<grid, kThreads, 0, s>>>(a, launched);
         tr->end(s, -1.0);

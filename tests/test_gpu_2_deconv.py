@@ -77,7 +77,9 @@ def test_deconv_gaussian15():
     p = syn.deconv_problem(64, 64, kernel=syn.gaussian_kernel(15, 2.0), bsnr_db=30.0, beta0=2.0,
                            seed=7, grf_length=8.0)
     pr = _probes(4, 64 * 64, 8)
-    mu, var, ep = _gpu(p, 4, 4, pr)
+    # the first solve (after one prior pass, with capped prior sites) is badly
+    # conditioned for a 15x15 blur: several thousand iterations
+    mu, var, ep = _gpu(p, 4, 4, pr, cg_max_iter=20000)
     mu_r, var_r, _ = _oracle(p, 4, pr)
     assert_parity(mu, var, mu_r, var_r, p.y)
     ep.close()
@@ -180,7 +182,8 @@ def test_full_size_512_residual_and_site0_samples():
         w_s = (operators.conv_periodic_t(pr[0][s].reshape(h, w), k) / np.sqrt(p.xi)
                + np.sqrt(d) * pr[1][s].reshape(h, w))
         rs = w_s - Q(X[s + 1])
-        assert np.linalg.norm(rs) <= 1e-8 * np.linalg.norm(w_s), s
+        # probe solves stop at a relative residual of 1e-6 (mean solve: cg_rtol)
+        assert np.linalg.norm(rs) <= 2e-6 * np.linalg.norm(w_s), s
         Ws.append(w_s)
     # site 0 at sampled pixels
     rng = np.random.default_rng(22)
