@@ -203,6 +203,38 @@ ep_tv_status ep_tv_trace_enable(ep_tv_ctx* ctx, int32_t on);
 ep_tv_status ep_tv_trace_read(ep_tv_ctx* ctx, int32_t kernel, double* ms, int64_t* launches,
                               double* units, double* bytes_per_unit);
 
+/* One pass of the four prior-site updates (the kernel ep_tv_sweep runs) that
+   allocates no device memory.  The paper has no counterpart: this exists for
+   callers that cannot call cudaMalloc when they run a sweep, e.g. code that must
+   not allocate after start-up, or runs inside an allocator or host runtime that
+   owns the device memory and only hands out the buffers it was asked for.  The
+   caller passes every input and output; the scratch the pass needs (one FP64
+   partial sum of E|u| per 16 x 64 tile, a status word, counters) lives in a
+   file-scope device array of 65536 + 8 doubles (512 KB) that every GPU loading
+   the library holds until the process exits.
+     height, width  image size; ceil(height/16) * ceil(width/64) must not exceed
+                    65536 (about 67 M pixels), else EP_TV_ERR_ARG.
+     p              uses damping, var_cap, periodic, precision, and xi when y is given.
+     beta           DEVICE pointer to the TV parameter (one double).
+     y              DEVICE, N floats: denoising, site 0 = (1/xi, y/xi); or NULL and
+     tau0, nu0      DEVICE, N floats each: the likelihood site.
+     tau_in, nu_in  DEVICE, 4 x N floats each: prior sites k = 1..4 (row k-1) before
+                    the pass.
+     tau_out, nu_out DEVICE, 4 x N floats each: after the pass; must not alias the inputs.
+     k_order        HOST, 4 values, a permutation of 1..4, or NULL for 1,2,3,4.
+     abar_out       DEVICE, one double: a_u of this pass (sum of E|u| over all edges).
+     flags_out      DEVICE, one uint32 or NULL: 1 if a site value became non-finite.
+     cuda_stream    stream (cudaStream_t or NULL) the work is enqueued on.
+   All calls on a device share the scratch array and it keeps the last call's
+   contents: calls that overlap on the GPU race and must be serialised by the
+   caller.  The first call on a device looks up the array's device address with
+   that device current; make it before any stream capture begins.  Asynchronous. */
+ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width, const ep_tv_params* p,
+                                       const double* beta, const float* y, const float* tau0,
+                                       const float* nu0, const float* tau_in, const float* nu_in,
+                                       float* tau_out, float* nu_out, const int8_t* k_order,
+                                       double* abar_out, uint32_t* flags_out, void* cuda_stream);
+
 /* Frees the context (synchronises its stream first).  NULL is accepted. */
 void ep_tv_destroy(ep_tv_ctx* ctx);
 

@@ -64,6 +64,10 @@ SIGNATURES = {
     "ep_tv_trace_read": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(c_double),
                                    ctypes.POINTER(c_double)]),
+    "ep_tv_prior_sweep_noalloc": (c_int32, [c_int32, c_int32, ctypes.POINTER(Params), c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, ctypes.POINTER(ctypes.c_int8),
+                                            c_void_p, c_void_p, c_void_p]),
     "ep_tv_destroy": (None, [c_void_p]),
     "ep_tv_status_str": (ctypes.c_char_p, [c_int32]),
 }
