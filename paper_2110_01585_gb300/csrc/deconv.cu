@@ -64,6 +64,12 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Wrapped global column of each region column, computed once per block
+// (region columns < 64 + 2 * 28).  Rows are wrapped once per row in the loops.
+__device__ __forceinline__ void column_table(int* tab, int c_first, int n_cols, int W) {
+  for (int cc = threadIdx.x; cc < n_cols; cc += blockDim.x) tab[cc] = wrapi(c_first + cc, W);
+}
+
 struct StencilSmem {
   float* v;    // region (kTile + 2 hr) x (kTile + 2 hc)
   float* tmp;  // separable: (kTile + 2 hr) x kTile; otherwise (kTile + hr) x (kTile + hc)
@@ -272,10 +278,15 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   const int ntap = c.separable ? c.kh + c.kw : c.kh * c.kw;
   for (int i = threadIdx.x; i < ntap; i += kThreads) tapd[i] = c.hd[i];
   const double* x = a.X + (long long)j * c.N;
-  for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
-    const int rr = idx / RW, cc = idx - rr * RW;
-    const int gr = wrapi(r0 - c.hr + rr, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
-    xs[idx] = x[(long long)gr * c.W + gcol];
+  __shared__ int ctab[kTile + 2 * kMaxHalf];
+  column_table(ctab, c0 - c.hc, RW, c.W);
+  __syncthreads();
+  {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int rr = ty; rr < RH; rr += kThreads / 32) {
+      const long long rowp = (long long)wrapi(r0 - c.hr + rr, c.H) * c.W;
+      for (int cc = tx; cc < RW; cc += 32) xs[rr * RW + cc] = x[rowp + ctab[cc]];
+    }
   }
   __syncthreads();
   const float* yp = j == 0 ? a.Y0 : a.Y1 + (long long)(j - 1) * c.N;
@@ -416,30 +427,35 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
   const float* z = a.Z + (long long)j * c.N;
   const float* Pold = ((it & 1) ? a.P : a.P2) + (long long)j * c.N;
   float* P = ((it & 1) ? a.P2 : a.P) + (long long)j * c.N;
-  for (int idx = threadIdx.x; idx < RH * RW; idx += kThreads) {
-    const int rr_ = idx / RW, cc = idx - rr_ * RW;
-    const int gr = wrapi(r0 - c.hr + rr_, c.H), gcol = wrapi(c0 - c.hc + cc, c.W);
-    const long long p = (long long)gr * c.W + gcol;
-    float v = a.fft ? z[p] : r[p] * a.Minv[p];
-    if (it > 0) v = fmaf(beta, Pold[p], v);
-    sm.v[idx] = v;
+  __shared__ int ctab[kTile + 2 * kMaxHalf];
+  column_table(ctab, c0 - c.hc, RW, c.W);
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr_ = ty; rr_ < RH; rr_ += kThreads / 32) {
+    const long long rowp = (long long)wrapi(r0 - c.hr + rr_, c.H) * c.W;
+    for (int cc = tx; cc < RW; cc += 32) {
+      const long long p = rowp + ctab[cc];
+      float v = a.fft ? z[p] : r[p] * a.Minv[p];
+      if (it > 0) v = fmaf(beta, Pold[p], v);
+      sm.v[rr_ * RW + cc] = v;
+    }
   }
   __syncthreads();
   hth_tile(c, sm, outb);
-  double pq = 0;
-  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-    const int tr = idx / kTile, tc = idx - tr * kTile;
-    const int gr = r0 + tr, gcol = c0 + tc;
+  float pq = 0.f;
+  for (int tr = ty; tr < kTile; tr += kThreads / 32) {
+    const int gr = r0 + tr, gcol = c0 + tx;
     if (gr >= c.H || gcol >= c.W) continue;
     const long long p = (long long)gr * c.W + gcol;
-    const float pv = sm.v[(tr + c.hr) * RW + tc + c.hc];
-    const float q = outb[idx] * c.inv_xi + a.D[p] * pv;
+    const float pv = sm.v[(tr + c.hr) * RW + tx + c.hc];
+    const float q = outb[tr * kTile + tx] * c.inv_xi + a.D[p] * pv;
     P[p] = pv;
     a.Qp[(long long)j * c.N + p] = q;
-    pq += (double)(pv * q);
+    pq = fmaf(pv, q, pq);
   }
-  block_sum3(pq, 0.0, 0.0, a.part_pq + (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x,
-             nullptr, nullptr);
+  block_sum3((double)pq, 0.0, 0.0,
+             a.part_pq + (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x, nullptr,
+             nullptr);
 }
 
 // x += alpha p, r -= alpha q, partials of the new r.Minv.r and r.r.
@@ -468,20 +484,20 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   float* Rr = a.Rr + (long long)j * c.N;
   const float* P = ((it & 1) ? a.P2 : a.P) + (long long)j * c.N;
   const float* Q = a.Qp + (long long)j * c.N;
-  double rz2 = 0, rr2 = 0;
-  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-    const int tr = idx / kTile, tc = idx - tr * kTile;
-    const int gr = r0 + tr, gcol = c0 + tc;
+  float rz2 = 0.f, rr2 = 0.f;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int tr = ty; tr < kTile; tr += kThreads / 32) {
+    const int gr = r0 + tr, gcol = c0 + tx;
     if (gr >= c.H || gcol >= c.W) continue;
     const long long p = (long long)gr * c.W + gcol;
     X[p] += (double)(alpha * P[p]);
     const float r = fmaf(-alpha, Q[p], Rr[p]);
     Rr[p] = r;
-    if (!a.fft) rz2 += (double)(r * r * a.Minv[p]);
-    rr2 += (double)(r * r);
+    if (!a.fft) rz2 = fmaf(r * r, a.Minv[p], rz2);
+    rr2 = fmaf(r, r, rr2);
   }
-  block_sum3(rz2, rr2, 0.0, a.fft ? nullptr : a.part_rz + oz_nxt + blk, a.part_rr + o_nxt + blk,
-             nullptr);
+  block_sum3((double)rz2, (double)rr2, 0.0, a.fft ? nullptr : a.part_rz + oz_nxt + blk,
+             a.part_rr + o_nxt + blk, nullptr);
 }
 
 
@@ -505,150 +521,202 @@ struct FftDesc {
   const double* dbar;
 };
 
-__device__ __forceinline__ unsigned brev_n(unsigned x, int logn) {
-  return logn ? (__brev(x) >> (32 - logn)) : 0u;
-}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// tw[k] = exp(-2 pi i k / n), k < n / 2
-__device__ __forceinline__ void make_twiddles(float2* tw, int n) {
-  for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// In-register forward DFTs of length 2, 4 and 8 (output in natural order).
+template <int R> __device__ __forceinline__ void dft_reg(float2* v);
+template <> __device__ __forceinline__ void dft_reg<2>(float2* v) {
+  const float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+template <> __device__ __forceinline__ void dft_reg<4>(float2* v) {
+  const float2 a0 = cadd(v[0], v[2]), a2 = csub(v[0], v[2]);
+  const float2 a1 = cadd(v[1], v[3]), a3 = cmul_mi(csub(v[1], v[3]));
+  v[0] = cadd(a0, a1);
+  v[1] = cadd(a2, a3);
+  v[2] = csub(a0, a1);
+  v[3] = csub(a2, a3);
+}
+template <> __device__ __forceinline__ void dft_reg<8>(float2* v) {
+  const float s2 = 0.70710678118654752440f;
+  const float2 a0 = cadd(v[0], v[4]), a1 = cadd(v[1], v[5]), a2 = cadd(v[2], v[6]),
+               a3 = cadd(v[3], v[7]);
+  const float2 d4 = csub(v[0], v[4]), d5 = csub(v[1], v[5]), d6 = csub(v[2], v[6]),
+               d7 = csub(v[3], v[7]);
+  // twiddles exp(-2 pi i m / 8) for m = 1, 2, 3
+  const float2 a5 = make_float2(s2 * (d5.x + d5.y), s2 * (d5.y - d5.x));
+  const float2 a6 = cmul_mi(d6);
+  const float2 a7 = make_float2(s2 * (d7.y - d7.x), -s2 * (d7.x + d7.y));
+  const float2 b0 = cadd(a0, a2), b1 = cadd(a1, a3), b2 = csub(a0, a2), b3 = cmul_mi(csub(a1, a3));
+  const float2 b4 = cadd(d4, a6), b5 = cadd(a5, a7), b6 = csub(d4, a6), b7 = cmul_mi(csub(a5, a7));
+  v[0] = cadd(b0, b1);
+  v[4] = csub(b0, b1);
+  v[2] = cadd(b2, b3);
+  v[6] = csub(b2, b3);
+  v[1] = cadd(b4, b5);
+  v[5] = csub(b4, b5);
+  v[3] = cadd(b6, b7);
+  v[7] = csub(b6, b7);
+}
+
+constexpr int kFftMaxItems = 2;  // work items per thread in one pass
+
+// One Stockham autosort pass of radix R: `count` transforms of length n, element i
+// of transform t at s[t * tstride + i * stride]; Ns = product of earlier radices.
+// Item j reads x[j + r n/R], multiplies by exp(-2 pi i r k / (Ns R)), k = j mod Ns,
+// applies the length-R DFT and writes y[(j - k) R + k + q Ns].  In place: every
+// item is read into registers before the barrier, written after it.
+template <int R>
+__device__ __forceinline__ void stockham_pass(float2* s, int n, int count, int stride, int tstride,
+                                              int Ns, const float2* tw) {
+  const int nq = n / R;
+  const int items = nq * count;
+  const int twstep = n / (Ns * R);
+  float2 v[kFftMaxItems][R];
+#pragma unroll
+  for (int it = 0; it < kFftMaxItems; ++it) {
+    const int w = threadIdx.x + it * blockDim.x;
+    if (w < items) {
+      int t, j;
+      if (tstride == 1) { j = w / count; t = w - j * count; } else { t = w / nq; j = w - t * nq; }
+      const int k = j & (Ns - 1);
+      const float2* base = s + t * tstride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float2 x = base[(j + r * nq) * stride];
+        v[it][r] = r ? cmul(x, tw[(k * r * twstep) & (n - 1)]) : x;
+      }
+      dft_reg<R>(v[it]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kFftMaxItems; ++it) {
+    const int w = threadIdx.x + it * blockDim.x;
+    if (w < items) {
+      int t, j;
+      if (tstride == 1) { j = w / count; t = w - j * count; } else { t = w / nq; j = w - t * nq; }
+      const int k = j & (Ns - 1);
+      float2* base = s + t * tstride;
+      const int ob = (j - k) * R + k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) base[(ob + q * Ns) * stride] = v[it][q];
+    }
+  }
+  __syncthreads();
+}
+
+// Forward transform (exp(-)) in natural order, radix 8 first, then one 4 or 2.
+__device__ void fft_forward(float2* s, int n, int count, int stride, int tstride, const float2* tw) {
+  for (int Ns = 1; Ns < n;) {
+    const int rem = n / Ns;
+    if (rem >= 8) {
+      stockham_pass<8>(s, n, count, stride, tstride, Ns, tw);
+      Ns *= 8;
+    } else if (rem == 4) {
+      stockham_pass<4>(s, n, count, stride, tstride, Ns, tw);
+      Ns *= 4;
+    } else {
+      stockham_pass<2>(s, n, count, stride, tstride, Ns, tw);
+      Ns *= 2;
+    }
+  }
+}
+
+// tw[m] = exp(-2 pi i m / n), m < n
+__device__ __forceinline__ void make_table(float2* tw, int n) {
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
     float sn, cs;
-    sincospif(-2.0f * (float)k / (float)n, &sn, &cs);
-    tw[k] = make_float2(cs, sn);
-  }
-}
-
-// Forward radix-2 decimation in time, in place, bit-reversed input, natural
-// output; `count` transforms, element i of transform t at a[i * stride + t * tstride].
-__device__ void fft_dit(float2* a, int n, int logn, int count, int stride, int tstride,
-                        const float2* tw) {
-  const int half_n = n >> 1;
-  const int nbf = half_n * count;
-  for (int sh = 1; sh <= logn; ++sh) {
-    const int len = 1 << sh, half = len >> 1, twstep = n >> sh;
-    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      // interleaved transforms (tstride 1): neighbouring threads take neighbouring
-      // transforms, so shared-memory accesses stay on distinct banks
-      int t, q;
-      if (tstride == 1) { q = b / count; t = b - q * count; } else { t = b / half_n; q = b - t * half_n; }
-      const int grp = q >> (sh - 1), pos = q & (half - 1);
-      const int i = grp * len + pos, j = i + half;
-      float2* base = a + t * tstride;
-      const float2 u = base[i * stride];
-      const float2 v = cmul(base[j * stride], tw[pos * twstep]);
-      base[i * stride] = make_float2(u.x + v.x, u.y + v.y);
-      base[j * stride] = make_float2(u.x - v.x, u.y - v.y);
-    }
-    __syncthreads();
-  }
-}
-
-// Inverse (exp(+)) radix-2 decimation in frequency, in place, natural input,
-// bit-reversed output, unscaled.
-__device__ void ifft_dif(float2* a, int n, int logn, int count, int stride, int tstride,
-                         const float2* tw) {
-  const int half_n = n >> 1;
-  const int nbf = half_n * count;
-  for (int sh = logn; sh >= 1; --sh) {
-    const int len = 1 << sh, half = len >> 1, twstep = n >> sh;
-    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      int t, q;
-      if (tstride == 1) { q = b / count; t = b - q * count; } else { t = b / half_n; q = b - t * half_n; }
-      const int grp = q >> (sh - 1), pos = q & (half - 1);
-      const int i = grp * len + pos, j = i + half;
-      float2* base = a + t * tstride;
-      const float2 u = base[i * stride], v = base[j * stride];
-      const float2 w = tw[pos * twstep];
-      base[i * stride] = make_float2(u.x + v.x, u.y + v.y);
-      base[j * stride] = cmul(make_float2(u.x - v.x, u.y - v.y), make_float2(w.x, -w.y));
-    }
-    __syncthreads();
+    sincospif(-2.0f * (float)m / (float)n, &sn, &cs);
+    tw[m] = make_float2(cs, sn);
   }
 }
 
 // Pack two residual planes into complex rows and transform them.
-__global__ void __launch_bounds__(512) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
+__global__ void __launch_bounds__(512, 2) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
-  float2* s = sm2 + f.W / 2;
+  float2* s = sm2 + f.W;
   const int pair = blockIdx.y;
   const int j0 = 2 * pair, j1 = 2 * pair + 1;
   const long long N = (long long)f.H * f.W;
   const int row0 = blockIdx.x * f.rpb;
-  make_twiddles(tw, f.W);
-  for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x) {
-    const int rr = idx >> f.logW, c = idx & (f.W - 1);
-    const long long p = (long long)(row0 + rr) * f.W + c;
-    const float re = Rr[(long long)j0 * N + p];
-    const float im = j1 < f.R ? Rr[(long long)j1 * N + p] : 0.f;
-    s[rr * f.W + brev_n(c, f.logW)] = make_float2(re, im);
-  }
+  make_table(tw, f.W);
+  const float* r0p = Rr + (long long)j0 * N + (long long)row0 * f.W;
+  const float* r1p = Rr + (long long)j1 * N + (long long)row0 * f.W;
+  for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x)
+    s[idx] = make_float2(r0p[idx], j1 < f.R ? r1p[idx] : 0.f);
   __syncthreads();
-  fft_dit(s, f.W, f.logW, f.rpb, 1, f.W, tw);
+  fft_forward(s, f.W, f.rpb, 1, f.W, tw);
   float2* out = f.tmp + (long long)pair * N + (long long)row0 * f.W;
   for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x) out[idx] = s[idx];
 }
 
 // Column transforms, the preconditioner filter and the inverse column transforms.
-__global__ void __launch_bounds__(512) fft_cols_filter_kernel(FftDesc f) {
+__global__ void __launch_bounds__(512, 2) fft_cols_filter_kernel(FftDesc f) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
-  float2* s = sm2 + f.H / 2;
+  float2* s = sm2 + f.H;
   const int pair = blockIdx.y;
   const int c0 = blockIdx.x * f.cw;
   const long long N = (long long)f.H * f.W;
   float2* t = f.tmp + (long long)pair * N;
-  make_twiddles(tw, f.H);
+  make_table(tw, f.H);
   for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    s[brev_n(i, f.logH) * f.cw + c] = t[(long long)i * f.W + c0 + c];
+    s[idx] = t[(long long)i * f.W + c0 + c];
   }
   __syncthreads();
-  fft_dit(s, f.H, f.logH, f.cw, f.cw, 1, tw);
+  fft_forward(s, f.H, f.cw, f.cw, 1, tw);
+  // filter, then the inverse column transform as conj(F(conj(.)))
   const float dbar = (float)(*f.dbar);
   for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    const float g = 1.0f / (f.hth[(long long)i * f.W + c0 + c] + dbar);
-    s[idx] = make_float2(s[idx].x * g, s[idx].y * g);
+    const float g = __frcp_rn(f.hth[(long long)i * f.W + c0 + c] + dbar);
+    s[idx] = make_float2(s[idx].x * g, -s[idx].y * g);
   }
   __syncthreads();
-  ifft_dif(s, f.H, f.logH, f.cw, f.cw, 1, tw);
+  fft_forward(s, f.H, f.cw, f.cw, 1, tw);
   for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    t[(long long)i * f.W + c0 + c] = s[brev_n(i, f.logH) * f.cw + c];
+    t[(long long)i * f.W + c0 + c] = cconj(s[idx]);
   }
 }
 
 // Inverse row transforms, scale 1/N, unpack into z planes, partial r.z per system.
-__global__ void __launch_bounds__(512) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
+__global__ void __launch_bounds__(512, 2) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
                                                            float* Z, double* part_rz) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
-  float2* s = sm2 + f.W / 2;
+  float2* s = sm2 + f.W;
   const int pair = blockIdx.y;
   const int j0 = 2 * pair, j1 = 2 * pair + 1;
   const long long N = (long long)f.H * f.W;
   const float scale = 1.0f / (float)N;
   const int rows_per = f.H / f.nbz;
   const int rpb = min(f.rpb, rows_per);
-  make_twiddles(tw, f.W);
+  make_table(tw, f.W);
   float rz0 = 0.f, rz1 = 0.f;
   double acc0 = 0.0, acc1 = 0.0;
   for (int r0 = blockIdx.x * rows_per; r0 < (blockIdx.x + 1) * rows_per; r0 += rpb) {
     const float2* in = f.tmp + (long long)pair * N + (long long)r0 * f.W;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) s[idx] = in[idx];
+    for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) s[idx] = cconj(in[idx]);
     __syncthreads();
-    ifft_dif(s, f.W, f.logW, rpb, 1, f.W, tw);
+    fft_forward(s, f.W, rpb, 1, f.W, tw);
     rz0 = 0.f;
     rz1 = 0.f;
     for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) {
-      const int rr = idx >> f.logW, c = idx & (f.W - 1);
-      const float2 v = s[rr * f.W + brev_n(c, f.logW)];
-      const long long p = (long long)(r0 + rr) * f.W + c;
+      const float2 v = cconj(s[idx]);
+      const long long p = (long long)r0 * f.W + idx;
       const float z0 = v.x * scale;
       Z[(long long)j0 * N + p] = z0;
       rz0 = fmaf(Rr[(long long)j0 * N + p], z0, rz0);
@@ -1052,12 +1120,16 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     f.logW = ilog2(c.W);
     f.R = L->R;
     f.pairs = (L->R + 1) / 2;
-    f.rpb = std::max(1, std::min(c.H, 2048 / c.W));
-    f.cw = std::min(c.W, c.H <= 1024 ? 16 : std::max(1, 16384 / c.H));
+    // smallest radix of a length-n plan: 8 if log2 n is a multiple of 3, else 4 or 2
+    auto rmin = [](int logn) { return logn % 3 == 0 ? 8 : (logn % 3 == 2 ? 4 : 2); };
+    // one pass handles at most kFftMaxItems * 512 work items of n / R points
+    const int cap = kFftMaxItems * 512;
+    f.rpb = std::max(1, std::min({c.H, 2048 / c.W, cap * rmin(f.logW) / c.W}));
+    f.cw = std::max(1, std::min({c.W, 16, cap * rmin(f.logH) / c.H}));
     f.nbz = std::min(c.H, 64);
     L->nbz = f.nbz;
-    L->smem_rows = sizeof(float2) * ((size_t)c.W / 2 + (size_t)f.rpb * c.W);
-    L->smem_cols = sizeof(float2) * ((size_t)c.H / 2 + (size_t)c.H * f.cw);
+    L->smem_rows = sizeof(float2) * ((size_t)c.W + (size_t)f.rpb * c.W);
+    L->smem_cols = sizeof(float2) * ((size_t)c.H + (size_t)c.H * f.cw);
   }
   L->nbmax = std::max(L->nb, L->nbz);
   L->prep_blocks = (int)std::min<long long>(std::max<long long>((c.N + 255) / 256, 1), 2048);

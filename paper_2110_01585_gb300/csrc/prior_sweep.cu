@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
         tj += sT[s * kRN + j];
         nj += sV[s * kRN + j];
       }
-      const float ci = 1.0f / ti, cj = 1.0f / tj;
+      const float ci = __frcp_rn(ti), cj = __frcp_rn(tj);
       const float mi = ni * ci, mj = nj * cj;
       const float mu = mi - mj;
       const float s2 = ci + cj;
@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
         eab = o.eab;
       }
       // Eq. update_qk_x: tau = 1/Var - 1/c, Var from the projection; cap, then mean
-      float tni = rho / (cj + q * ci);
-      float tnj = rho / (ci + q * cj);
+      float tni = rho * __frcp_rn(cj + q * ci);
+      float tnj = rho * __frcp_rn(ci + q * cj);
       if (!(tni >= a.min_tau)) { tni = a.min_tau; n_capped += owned; }
       if (!(tnj >= a.min_tau)) { tnj = a.min_tau; n_capped += owned; }
       const float Ei = mi + ci * d;
