@@ -253,128 +253,194 @@ __global__ void mean_kernel(const double* dpart, int n, double inv_count, double
   if (threadIdx.x == 0) *out = buf[0] * inv_count;
 }
 
+// Float-float ("double-single") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2,
+// giving about 44 significant bits from FP32 operations only (GB300's FP64 rate is a
+// small fraction of its FP32 rate).  TwoSum is Knuth's, TwoProduct uses the FMA
+// (Dekker's splitting is not needed with a fused multiply-add).
+struct ff {
+  float hi, lo;
+};
+// The _rn intrinsics keep the compiler from fusing these products and sums into
+// FMAs, which would break the error-free transformations.
+__device__ __forceinline__ ff ff_from_double(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// acc + x * g with g = g_hi + g_lo
+__device__ __forceinline__ ff ff_fma(ff acc, ff x, float g_hi, float g_lo) {
+  const float p = __fmul_rn(x.hi, g_hi);
+  float e = fmaf(x.hi, g_hi, -p);
+  e = fmaf(x.hi, g_lo, fmaf(x.lo, g_hi, e));
+  const ff s = two_sum(acc.hi, p);
+  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, acc.lo), e));
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// a * b for float b
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = fmaf(a.hi, b, -p);
+  return fast_two_sum(p, fmaf(a.lo, b, e));
+}
+
 // True residual of every system (blockIdx.z),
 //   r = H^T (y' - H x) / xi + (n' - d x),
 // y' = y, n' = n for the mean system and y' = sqrt(xi) eps1_s, n' = sqrt(d) eps2_s for
-// probe s, so that r = b - Q x with b as in rhs_value.  Computed in FP64 from the
-// FP64 solution: the terms H^T H x / xi and d x are several times larger than r
-// near the solution, and an FP32 evaluation leaves an error of order
-// eps |H^T (y' - H x)| / xi, which the conditioning of Q (1e4..1e5) turns into
-// percent-level errors in x.  Partials: r.r (buffer 0), b.b, r.Minv.r (Jacobi).
+// probe s, so that r = b - Q x with b as in rhs_value.  Near the solution H^T H x / xi
+// and d x are several times larger than r; evaluated in FP32 they leave an error of
+// order eps |H^T y'| / xi, which the conditioning of Q (1e4..1e5) turns into
+// percent-level errors in x.  So H x and n' - d x are formed in float-float from the
+// FP64 solution; y' - H x is then small and its H^T / xi runs in FP32, which bounds
+// the relative residual error by about 1e-10 for the mean system and 1e-7 for the
+// probes, below their targets.  Partials: r.r (buffer 0), b.b, r.Minv.r (Jacobi).
 __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
-  extern __shared__ double smd[];
-  __shared__ double tapd[232];
-  __shared__ double outd[kTile * kTile];
+  extern __shared__ float smf[];
+  __shared__ float taph[232], tapl[232];
+  __shared__ float outb[kTile * kTile];
+  __shared__ int ctab[kTile + 2 * kMaxHalf];
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
   const int hh = c.kh / 2, hw = c.kw / 2;
   const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;  // x region, halo kh - 1
   const int MH = kTile + 2 * hh, MW = kTile + 2 * hw;      // y' - H x region, halo kh / 2
-  double* xs = smd;                                        // RH x RW
-  double* rowp = xs + RH * RW;                             // RH x MW (separable)
-  double* vs = rowp + (c.separable ? RH * MW : 0);         // MH x MW
-  double* tmpd = vs + MH * MW;                             // MH x kTile (separable)
+  float* xh = smf;                                         // RH x RW (hi)
+  float* xl = xh + RH * RW;                                // RH x RW (lo)
+  float* ph = xl + RH * RW;                                // RH x MW (separable, hi)
+  float* pl = ph + (c.separable ? RH * MW : 0);            // RH x MW (lo)
+  float* vs = pl + (c.separable ? RH * MW : 0);            // MH x MW, y' - H x (FP32)
+  float* tmpf = vs + MH * MW;                              // MH x kTile (separable)
   const int ntap = c.separable ? c.kh + c.kw : c.kh * c.kw;
-  for (int i = threadIdx.x; i < ntap; i += kThreads) tapd[i] = c.hd[i];
-  const double* x = a.X + (long long)j * c.N;
-  __shared__ int ctab[kTile + 2 * kMaxHalf];
+  for (int i = threadIdx.x; i < ntap; i += kThreads) {
+    const ff t = ff_from_double(c.hd[i]);
+    taph[i] = t.hi;
+    tapl[i] = t.lo;
+  }
   column_table(ctab, c0 - c.hc, RW, c.W);
   __syncthreads();
-  {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int rr = ty; rr < RH; rr += kThreads / 32) {
-      const long long rowp = (long long)wrapi(r0 - c.hr + rr, c.H) * c.W;
-      for (int cc = tx; cc < RW; cc += 32) xs[rr * RW + cc] = x[rowp + ctab[cc]];
+  const double* x = a.X + (long long)j * c.N;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr = ty; rr < RH; rr += kThreads / 32) {
+    const long long rowp = (long long)wrapi(r0 - c.hr + rr, c.H) * c.W;
+    for (int cc = tx; cc < RW; cc += 32) {
+      const ff t = ff_from_double(x[rowp + ctab[cc]]);
+      xh[rr * RW + cc] = t.hi;
+      xl[rr * RW + cc] = t.lo;
     }
   }
   __syncthreads();
   const float* yp = j == 0 ? a.Y0 : a.Y1 + (long long)(j - 1) * c.N;
   // v = y' - H x on the (kh/2, kw/2)-halo region: (H x)(r,c) = sum k[a,b] x(r-a+hh, c-b+hw)
   if (c.separable) {
-    const double* u = tapd;
-    const double* v = tapd + c.kh;
+    const float* uh = taph;
+    const float* ul = tapl;
+    const float* vh = taph + c.kh;
+    const float* vl = tapl + c.kh;
     for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
       const int rr = idx / MW, mc = idx - rr * MW;
-      const double* row = xs + rr * RW + mc + 2 * hw;
-      double acc = 0.0;
-      for (int b = 0; b < c.kw; ++b) acc = fma(v[b], row[-b], acc);
-      rowp[idx] = acc;
+      const int base = rr * RW + mc + 2 * hw;
+      ff acc = {0.f, 0.f};
+      for (int b = 0; b < c.kw; ++b) acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, vh[b], vl[b]);
+      ph[idx] = acc.hi;
+      pl[idx] = acc.lo;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
       const int mr = idx / MW, mc = idx - mr * MW;
-      const double* col = rowp + (mr + 2 * hh) * MW + mc;
-      double acc = 0.0;
-      for (int aa = 0; aa < c.kh; ++aa) acc = fma(u[aa], col[-aa * MW], acc);
+      const int base = (mr + 2 * hh) * MW + mc;
+      ff acc = {0.f, 0.f};
+      for (int aa = 0; aa < c.kh; ++aa)
+        acc = ff_fma(acc, ff{ph[base - aa * MW], pl[base - aa * MW]}, uh[aa], ul[aa]);
       const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-      vs[idx] = (double)yp[(long long)gr * c.W + gcol] - acc;
+      const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
+      vs[idx] = v.hi + v.lo;
     }
   } else {
     for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
       const int mr = idx / MW, mc = idx - mr * MW;
-      double acc = 0.0;
+      ff acc = {0.f, 0.f};
       for (int aa = 0; aa < c.kh; ++aa) {
-        const double* xrow = xs + (mr + 2 * hh - aa) * RW + mc + 2 * hw;
-        const double* krow = tapd + aa * c.kw;
-        for (int b = 0; b < c.kw; ++b) acc = fma(krow[b], xrow[-b], acc);
+        const int base = (mr + 2 * hh - aa) * RW + mc + 2 * hw;
+        for (int b = 0; b < c.kw; ++b)
+          acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, taph[aa * c.kw + b], tapl[aa * c.kw + b]);
       }
       const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-      vs[idx] = (double)yp[(long long)gr * c.W + gcol] - acc;
+      const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
+      vs[idx] = v.hi + v.lo;
     }
   }
   __syncthreads();
-  // H^T v on the tile: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
+  // H^T v on the tile in FP32: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
   if (c.separable) {
-    const double* u = tapd;
-    const double* v = tapd + c.kh;
+    const float* u = taph;
+    const float* v = taph + c.kh;
     for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
       const int mr = idx / kTile, tc = idx - mr * kTile;
-      const double* row = vs + mr * MW + tc;
-      double acc = 0.0;
-      for (int b = 0; b < c.kw; ++b) acc = fma(v[b], row[b], acc);
-      tmpd[idx] = acc;
+      const float* row = vs + mr * MW + tc;
+      float acc = 0.f;
+      for (int b = 0; b < c.kw; ++b) acc = fmaf(v[b], row[b], acc);
+      tmpf[idx] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
       const int tr = idx / kTile, tc = idx - tr * kTile;
-      const double* col = tmpd + tr * kTile + tc;
-      double acc = 0.0;
-      for (int aa = 0; aa < c.kh; ++aa) acc = fma(u[aa], col[aa * kTile], acc);
-      outd[idx] = acc;
+      const float* col = tmpf + tr * kTile + tc;
+      float acc = 0.f;
+      for (int aa = 0; aa < c.kh; ++aa) acc = fmaf(u[aa], col[aa * kTile], acc);
+      outb[idx] = acc;
     }
   } else {
     for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
       const int tr = idx / kTile, tc = idx - tr * kTile;
-      double acc = 0.0;
+      float acc = 0.f;
       for (int aa = 0; aa < c.kh; ++aa) {
-        const double* vrow = vs + (tr + aa) * MW + tc;
-        const double* krow = tapd + aa * c.kw;
-        for (int b = 0; b < c.kw; ++b) acc = fma(krow[b], vrow[b], acc);
+        const float* vrow = vs + (tr + aa) * MW + tc;
+        const float* krow = taph + aa * c.kw;
+        for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], vrow[b], acc);
       }
-      outd[idx] = acc;
+      outb[idx] = acc;
     }
   }
   __syncthreads();
-  double rz = 0, rr2 = 0, bb = 0;
-  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-    const int tr = idx / kTile, tc = idx - tr * kTile;
-    const int gr = r0 + tr, gcol = c0 + tc;
+  float rz = 0.f, rr2 = 0.f, bb = 0.f;
+  for (int tr = ty; tr < kTile; tr += kThreads / 32) {
+    const int gr = r0 + tr, gcol = c0 + tx;
     if (gr >= c.H || gcol >= c.W) continue;
     const long long p = (long long)gr * c.W + gcol;
-    const double xv = xs[(tr + c.hr) * RW + tc + c.hc];
-    const double np = j == 0 ? (double)a.Ncav[p]
-                             : sqrt((double)a.D[p]) * (double)a.E2[(long long)(j - 1) * c.N + p];
-    const double rd = outd[idx] * c.inv_xi_d + (np - (double)a.D[p] * xv);
-    const float r = (float)rd;
+    const int xi_ = (tr + c.hr) * RW + tx + c.hc;
+    const float d = a.D[p];
+    // n' - d x in float-float
+    ff np;
+    if (j == 0) {
+      np = {a.Ncav[p], 0.f};
+    } else {
+      const float sd = sqrtf(d), e2 = a.E2[(long long)(j - 1) * c.N + p];
+      const float pr = __fmul_rn(sd, e2);
+      np = {pr, fmaf(sd, e2, -pr)};
+    }
+    const ff t = ff_add(np, ff_neg(ff_mul_f(ff{xh[xi_], xl[xi_]}, d)));
+    const float r = outb[tr * kTile + tx] * c.inv_xi + (t.hi + t.lo);
     a.Rr[(long long)j * c.N + p] = r;
     const float b = rhs_value(a, j, p);
-    if (!a.fft) rz += (double)(r * r * a.Minv[p]);
-    rr2 += rd * rd;
-    bb += (double)(b * b);
+    if (!a.fft) rz = fmaf(r * r, a.Minv[p], rz);
+    rr2 = fmaf(r, r, rr2);
+    bb = fmaf(b, b, bb);
   }
   const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
-  block_sum3(rz, rr2, bb, a.fft ? nullptr : a.part_rz + o, a.part_rr + o, a.part_bb + o);
+  block_sum3((double)rz, (double)rr2, (double)bb, a.fft ? nullptr : a.part_rz + o,
+             a.part_rr + o, a.part_bb + o);
 }
 
 // Per system after a true residual: done if r.r <= rtol^2 b.b (threshold +inf),
@@ -1124,7 +1190,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     auto rmin = [](int logn) { return logn % 3 == 0 ? 8 : (logn % 3 == 2 ? 4 : 2); };
     // one pass handles at most kFftMaxItems * 512 work items of n / R points
     const int cap = kFftMaxItems * 512;
-    f.rpb = std::max(1, std::min({c.H, 2048 / c.W, cap * rmin(f.logW) / c.W}));
+    f.rpb = std::max(1, std::min({c.H, 4096 / c.W, cap * rmin(f.logW) / c.W}));
     f.cw = std::max(1, std::min({c.W, 16, cap * rmin(f.logH) / c.H}));
     f.nbz = std::min(c.H, 64);
     L->nbz = f.nbz;
@@ -1142,7 +1208,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   {
     const size_t MH = kTile + 2 * (kh / 2), MW = kTile + 2 * (kw / 2);
     const size_t RH = kTile + 2 * hr, RW = kTile + 2 * hc;
-    L->smem_res = sizeof(double) * (RH * RW + (sep ? RH * MW : 0) + MH * MW + (sep ? MH * kTile : 0));
+    L->smem_res = sizeof(float) * (2 * RH * RW + (sep ? 2 * RH * MW : 0) + MH * MW +
+                                   (sep ? MH * kTile : 0));
   }
   std::vector<float> kf(kh * kw);
   for (int i = 0; i < kh * kw; ++i) kf[i] = (float)k[i];
