@@ -95,8 +95,10 @@ typedef struct {
   int32_t cg_max_iter;   /* CONV_PERIODIC: cap on the conjugate-gradient iterations of one
                             likelihood-site update (all refinement passes together) */
   double cg_rtol;        /* CONV_PERIODIC: target of the true relative residual ||b - Q x|| /
-                            ||b|| of every solve; the residual is recomputed with the blur
-                            accumulated in FP64 between FP32 CG passes (default 1e-9) */
+                            ||b|| of the mean solve (probe solves: max(cg_rtol, 1e-6)).  The
+                            residual is recomputed in float-float arithmetic between FP32
+                            CG passes; a solve also stops when a pass no longer halves a
+                            residual already below 1e-6 (the evaluation floor).  Default 1e-9. */
   int32_t precision;     /* 0: FP32 with FP64 for edges whose tilted moments lose
                             FP32 accuracy; 1: FP32 only */
   uint64_t seed;         /* seed of the library's own probe generator */

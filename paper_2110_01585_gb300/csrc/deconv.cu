@@ -76,9 +76,56 @@ struct StencilSmem {
   float* taps; // kernel taps staged in shared memory
 };
 
+// Separable H^T H with compile-time half-widths: row pass fully unrolled, column
+// pass with each thread producing four consecutive rows of one column, so the
+// 2 HR + 4 inputs it loads serve four outputs.
+template <int HR, int HC>
+__device__ __forceinline__ void hth_tile_sep(StencilSmem& sm, float* out) {
+  constexpr int RH = kTile + 2 * HR, RW = kTile + 2 * HC;
+  const float* gr = sm.taps;
+  const float* gc = sm.taps + (2 * HR + 1);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float wc[2 * HC + 1];
+#pragma unroll
+  for (int b = 0; b <= 2 * HC; ++b) wc[b] = gc[b];
+  for (int rr = ty; rr < RH; rr += kThreads / 32) {
+    const float* row = sm.v + rr * RW + tx;
+    float acc = 0.f;
+#pragma unroll
+    for (int b = 0; b <= 2 * HC; ++b) acc = fmaf(wc[b], row[b], acc);
+    sm.tmp[rr * kTile + tx] = acc;
+  }
+  __syncthreads();
+  float wr[2 * HR + 1];
+#pragma unroll
+  for (int a = 0; a <= 2 * HR; ++a) wr[a] = gr[a];
+  // 8 warps x 4 rows = 32 output rows
+  const int tr0 = ty * 4;
+  float in[2 * HR + 4];
+#pragma unroll
+  for (int i = 0; i < 2 * HR + 4; ++i) in[i] = sm.tmp[(tr0 + i) * kTile + tx];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a <= 2 * HR; ++a) acc = fmaf(wr[a], in[o + a], acc);
+    out[(tr0 + o) * kTile + tx] = acc;
+  }
+  __syncthreads();
+}
+
 // out[tr * kTile + tc] = (H^T H v)(tile pixel) for the region staged in sm.v.
 // All threads of the block participate; ends with __syncthreads().
 __device__ void hth_tile(const ConvDesc& c, StencilSmem& sm, float* out) {
+  if (c.separable && c.hr == c.hc) {
+    switch (c.hr) {
+      case 2: hth_tile_sep<2, 2>(sm, out); return;
+      case 4: hth_tile_sep<4, 4>(sm, out); return;
+      case 8: hth_tile_sep<8, 8>(sm, out); return;
+      case 14: hth_tile_sep<14, 14>(sm, out); return;
+      default: break;
+    }
+  }
   const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
   const int tid = threadIdx.x;
   if (c.separable) {
@@ -447,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
 // otherwise the inner loop runs until r.r <= max(eta^2 r.r, (rtol/2)^2 b.b).
 __global__ void thresholds_kernel(const double* part_rr, const double* part_bb, int R, int nb,
                                   double rtol2_mean, double rtol2_probe, double eta2, double* thr,
-                                  double* relres, int* active) {
+                                  double* relres, double* prev_rr, int first, int* active) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -465,7 +512,12 @@ __global__ void thresholds_kernel(const double* part_rr, const double* part_bb, 
     }
     if (lane == 0) {
       const double rtol2 = j == 0 ? rtol2_mean : rtol2_probe;
-      const bool done = rr <= rtol2 * bb;
+      // Converged at the target, or at the floor of the residual evaluation: a pass
+      // that failed to halve the true residual once it is below 1e-6 relative (for a
+      // well-conditioned Q the floor, about 1e-8, already means an accurate x).
+      const bool floor_hit = !first && rr <= 1e-12 * bb && rr > 0.25 * prev_rr[j];
+      const bool done = rr <= rtol2 * bb || floor_hit;
+      prev_rr[j] = rr;
       relres[j] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
       thr[j] = done ? INFINITY : fmax(eta2 * rr, 0.25 * rtol2 * bb);
       if (!done) atomicAdd(&cnt, 1);
@@ -551,16 +603,43 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const float* P = ((it & 1) ? a.P2 : a.P) + (long long)j * c.N;
   const float* Q = a.Qp + (long long)j * c.N;
   float rz2 = 0.f, rr2 = 0.f;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int tr = ty; tr < kTile; tr += kThreads / 32) {
-    const int gr = r0 + tr, gcol = c0 + tx;
-    if (gr >= c.H || gcol >= c.W) continue;
-    const long long p = (long long)gr * c.W + gcol;
-    X[p] += (double)(alpha * P[p]);
-    const float r = fmaf(-alpha, Q[p], Rr[p]);
-    Rr[p] = r;
-    if (!a.fft) rz2 = fmaf(r * r, a.Minv[p], rz2);
-    rr2 = fmaf(r, r, rr2);
+  if ((c.W & 3) == 0 && c0 + kTile <= c.W && r0 + kTile <= c.H) {
+    // full tile, rows 16-byte aligned: one float4 of each plane per thread
+    const int tr = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
+    const long long p = (long long)(r0 + tr) * c.W + c0 + c4;
+    const float4 pv = *reinterpret_cast<const float4*>(P + p);
+    const float4 qv = *reinterpret_cast<const float4*>(Q + p);
+    float4 rv = *reinterpret_cast<const float4*>(Rr + p);
+    double2 x01 = *reinterpret_cast<const double2*>(X + p);
+    double2 x23 = *reinterpret_cast<const double2*>(X + p + 2);
+    x01.x += (double)(alpha * pv.x);
+    x01.y += (double)(alpha * pv.y);
+    x23.x += (double)(alpha * pv.z);
+    x23.y += (double)(alpha * pv.w);
+    rv.x = fmaf(-alpha, qv.x, rv.x);
+    rv.y = fmaf(-alpha, qv.y, rv.y);
+    rv.z = fmaf(-alpha, qv.z, rv.z);
+    rv.w = fmaf(-alpha, qv.w, rv.w);
+    *reinterpret_cast<double2*>(X + p) = x01;
+    *reinterpret_cast<double2*>(X + p + 2) = x23;
+    *reinterpret_cast<float4*>(Rr + p) = rv;
+    rr2 = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    if (!a.fft) {
+      const float4 mv = *reinterpret_cast<const float4*>(a.Minv + p);
+      rz2 = rv.x * rv.x * mv.x + rv.y * rv.y * mv.y + rv.z * rv.z * mv.z + rv.w * rv.w * mv.w;
+    }
+  } else {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int tr = ty; tr < kTile; tr += kThreads / 32) {
+      const int gr = r0 + tr, gcol = c0 + tx;
+      if (gr >= c.H || gcol >= c.W) continue;
+      const long long p = (long long)gr * c.W + gcol;
+      X[p] += (double)(alpha * P[p]);
+      const float r = fmaf(-alpha, Q[p], Rr[p]);
+      Rr[p] = r;
+      if (!a.fft) rz2 = fmaf(r * r, a.Minv[p], rz2);
+      rr2 = fmaf(r, r, rr2);
+    }
   }
   block_sum3((double)rz2, (double)rr2, 0.0, a.fft ? nullptr : a.part_rz + oz_nxt + blk,
              a.part_rr + o_nxt + blk, nullptr);
@@ -1025,6 +1104,7 @@ struct LikelihoodState {
   int last_iters = 0;
   float* d_scal = nullptr;      // [R][4] CG scalars
   double* d_relres = nullptr;  // [R] sqrt(r.r / b.b) after the last true residual
+  double* d_prev_rr = nullptr; // [R] r.r of the previous refinement pass
   double* h_relres = nullptr;  // pinned copy
   double rep_mean = 0.0, rep_probe = 0.0;
   int rep_outer = 0;
@@ -1238,6 +1318,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
                          cudaMalloc(&L->hth, sizeof(float) * N) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&L->d_relres, sizeof(double) * L->R) == cudaSuccess &&
+            cudaMalloc(&L->d_prev_rr, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_scal, sizeof(float) * 4 * L->R) == cudaSuccess &&
             cudaHostAlloc(&L->h_relres, sizeof(double) * L->R, cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
@@ -1349,6 +1430,7 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->hth);
   cudaFree(L->d_active);
   cudaFree(L->d_relres);
+  cudaFree(L->d_prev_rr);
   cudaFree(L->d_scal);
   if (L->h_relres) cudaFreeHost(L->h_relres);
   if (L->h_active) cudaFreeHost(L->h_active);
@@ -1397,7 +1479,8 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
     tr->end(s, (double)L->R * N);
     thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2_true,
-                                         L->rtol2_probe, eta2, L->thr, L->d_relres, L->d_active);
+                                         L->rtol2_probe, eta2, L->thr, L->d_relres, L->d_prev_rr,
+                                         outer == 0, L->d_active);
     if (cudaMemcpyAsync(L->h_active, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(L->h_relres, L->d_relres, sizeof(double) * L->R, cudaMemcpyDeviceToHost,
