@@ -713,6 +713,7 @@ template <> __device__ __forceinline__ void dft_reg<8>(float2* v) {
 }
 
 constexpr int kFftMaxItems = 2;  // work items per thread in one pass
+constexpr int kFftThreads = 256; // threads per FFT block (four resident blocks per SM)
 
 // One Stockham autosort pass of radix R: `count` transforms of length n, element i
 // of transform t at s[t * tstride + i * stride]; Ns = product of earlier radices.
@@ -786,7 +787,7 @@ __device__ __forceinline__ void make_table(float2* tw, int n) {
 }
 
 // Pack two residual planes into complex rows and transform them.
-__global__ void __launch_bounds__(512, 2) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
+__global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
   float2* s = sm2 + f.W;
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(512, 2) fft_rows_fwd_kernel(FftDesc f, const f
 }
 
 // Column transforms, the preconditioner filter and the inverse column transforms.
-__global__ void __launch_bounds__(512, 2) fft_cols_filter_kernel(FftDesc f) {
+__global__ void __launch_bounds__(kFftThreads, 4) fft_cols_filter_kernel(FftDesc f) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
   float2* s = sm2 + f.H;
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(512, 2) fft_cols_filter_kernel(FftDesc f) {
 }
 
 // Inverse row transforms, scale 1/N, unpack into z planes, partial r.z per system.
-__global__ void __launch_bounds__(512, 2) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
+__global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
                                                            float* Z, double* part_rz) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
@@ -1157,9 +1158,9 @@ int ilog2(int v) {
 // z = M^{-1} r for all systems; r.z partials into rz_buf ([R][nbz]).
 void precond_apply(LikelihoodState* L, double* rz_buf, cudaStream_t s) {
   const FftDesc& f = L->fd;
-  fft_rows_fwd_kernel<<<dim3(f.H / f.rpb, f.pairs), 512, L->smem_rows, s>>>(f, L->Rr);
-  fft_cols_filter_kernel<<<dim3(f.W / f.cw, f.pairs), 512, L->smem_cols, s>>>(f);
-  fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), 512, L->smem_rows, s>>>(f, L->Rr, L->Z, rz_buf);
+  fft_rows_fwd_kernel<<<dim3(f.H / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr);
+  fft_cols_filter_kernel<<<dim3(f.W / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
+  fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z, rz_buf);
 }
 
 // E1 = H^T eps1 / sqrt(xi) from E1 holding eps1 (in place through Rr as scratch).
@@ -1268,8 +1269,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     f.pairs = (L->R + 1) / 2;
     // smallest radix of a length-n plan: 8 if log2 n is a multiple of 3, else 4 or 2
     auto rmin = [](int logn) { return logn % 3 == 0 ? 8 : (logn % 3 == 2 ? 4 : 2); };
-    // one pass handles at most kFftMaxItems * 512 work items of n / R points
-    const int cap = kFftMaxItems * 512;
+    // one pass handles at most kFftMaxItems * kFftThreads work items of n / R points
+    const int cap = kFftMaxItems * kFftThreads;
     f.rpb = std::max(1, std::min({c.H, 4096 / c.W, cap * rmin(f.logW) / c.W}));
     f.cw = std::max(1, std::min({c.W, 16, cap * rmin(f.logH) / c.H}));
     f.nbz = std::min(c.H, 64);
