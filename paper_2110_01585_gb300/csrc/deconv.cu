@@ -656,13 +656,14 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
 // M^{-1} r_a and M^{-1} r_b.  Transforms are radix-2 in shared memory: rows,
 // then columns (forward, filter, inverse in one pass), then rows again.
 struct FftDesc {
-  int H, W, logH, logW;
+  int H, W;          // image
+  int HP, WP;        // power-of-two transform sizes, HP >= H, WP >= W
   int R, pairs;
   int cw;            // columns per block in the column pass
-  int rpb;           // rows per block in the forward row pass
+  int rpb;           // rows per block in the row passes
   int nbz;           // blocks per pair in the inverse row pass
-  float2* tmp;       // pairs x H x W
-  const float* hth;  // |h_f|^2 / xi, H x W
+  float2* tmp;       // pairs x H x WP (rows of the padded grid beyond H are zero)
+  const float* hth;  // |h_f|^2 / xi on the HP x WP grid
   const double* dbar;
 };
 
@@ -786,90 +787,111 @@ __device__ __forceinline__ void make_table(float2* tw, int n) {
   }
 }
 
-// Pack two residual planes into complex rows and transform them.
+// Pack two residual planes into complex rows (zero-padded to WP) and transform them.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
-  float2* s = sm2 + f.W;
+  float2* s = sm2 + f.WP;
   const int pair = blockIdx.y;
   const int j0 = 2 * pair, j1 = 2 * pair + 1;
   const long long N = (long long)f.H * f.W;
   const int row0 = blockIdx.x * f.rpb;
-  make_table(tw, f.W);
-  const float* r0p = Rr + (long long)j0 * N + (long long)row0 * f.W;
-  const float* r1p = Rr + (long long)j1 * N + (long long)row0 * f.W;
-  for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x)
-    s[idx] = make_float2(r0p[idx], j1 < f.R ? r1p[idx] : 0.f);
+  make_table(tw, f.WP);
+  const float* r0p = Rr + (long long)j0 * N;
+  const float* r1p = Rr + (long long)j1 * N;
+  for (int rr = 0; rr < f.rpb; ++rr) {
+    const int row = row0 + rr;
+    for (int cc = threadIdx.x; cc < f.WP; cc += blockDim.x) {
+      float2 v = make_float2(0.f, 0.f);
+      if (row < f.H && cc < f.W) {
+        const long long p = (long long)row * f.W + cc;
+        v = make_float2(r0p[p], j1 < f.R ? r1p[p] : 0.f);
+      }
+      s[rr * f.WP + cc] = v;
+    }
+  }
   __syncthreads();
-  fft_forward(s, f.W, f.rpb, 1, f.W, tw);
-  float2* out = f.tmp + (long long)pair * N + (long long)row0 * f.W;
-  for (int idx = threadIdx.x; idx < f.rpb * f.W; idx += blockDim.x) out[idx] = s[idx];
+  fft_forward(s, f.WP, f.rpb, 1, f.WP, tw);
+  float2* out = f.tmp + (long long)pair * f.H * f.WP;
+  for (int rr = 0; rr < f.rpb; ++rr) {
+    const int row = row0 + rr;
+    if (row >= f.H) break;
+    for (int cc = threadIdx.x; cc < f.WP; cc += blockDim.x)
+      out[(long long)row * f.WP + cc] = s[rr * f.WP + cc];
+  }
 }
 
-// Column transforms, the preconditioner filter and the inverse column transforms.
+// Column transforms (rows beyond H are zero), the preconditioner filter and the
+// inverse column transforms; only rows below H are kept.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_cols_filter_kernel(FftDesc f) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
-  float2* s = sm2 + f.H;
+  float2* s = sm2 + f.HP;
   const int pair = blockIdx.y;
   const int c0 = blockIdx.x * f.cw;
-  const long long N = (long long)f.H * f.W;
-  float2* t = f.tmp + (long long)pair * N;
-  make_table(tw, f.H);
-  for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
+  float2* t = f.tmp + (long long)pair * f.H * f.WP;
+  make_table(tw, f.HP);
+  for (int idx = threadIdx.x; idx < f.HP * f.cw; idx += blockDim.x) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    s[idx] = t[(long long)i * f.W + c0 + c];
+    s[idx] = i < f.H ? t[(long long)i * f.WP + c0 + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_forward(s, f.H, f.cw, f.cw, 1, tw);
+  fft_forward(s, f.HP, f.cw, f.cw, 1, tw);
   // filter, then the inverse column transform as conj(F(conj(.)))
   const float dbar = (float)(*f.dbar);
-  for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < f.HP * f.cw; idx += blockDim.x) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    const float g = __frcp_rn(f.hth[(long long)i * f.W + c0 + c] + dbar);
+    const float g = __frcp_rn(f.hth[(long long)i * f.WP + c0 + c] + dbar);
     s[idx] = make_float2(s[idx].x * g, -s[idx].y * g);
   }
   __syncthreads();
-  fft_forward(s, f.H, f.cw, f.cw, 1, tw);
+  fft_forward(s, f.HP, f.cw, f.cw, 1, tw);
   for (int idx = threadIdx.x; idx < f.H * f.cw; idx += blockDim.x) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    t[(long long)i * f.W + c0 + c] = cconj(s[idx]);
+    t[(long long)i * f.WP + c0 + c] = cconj(s[idx]);
   }
 }
 
-// Inverse row transforms, scale 1/N, unpack into z planes, partial r.z per system.
+// Inverse row transforms, scale 1/(HP WP), crop to W, unpack into z planes,
+// partial r.z per system.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
-                                                           float* Z, double* part_rz) {
+                                                                      float* Z, double* part_rz) {
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
-  float2* s = sm2 + f.W;
+  float2* s = sm2 + f.WP;
   const int pair = blockIdx.y;
   const int j0 = 2 * pair, j1 = 2 * pair + 1;
   const long long N = (long long)f.H * f.W;
-  const float scale = 1.0f / (float)N;
-  const int rows_per = f.H / f.nbz;
-  const int rpb = min(f.rpb, rows_per);
-  make_table(tw, f.W);
-  float rz0 = 0.f, rz1 = 0.f;
+  const float scale = 1.0f / ((float)f.HP * (float)f.WP);
+  const int rows_per = (f.H + f.nbz - 1) / f.nbz;
+  const int rbeg = blockIdx.x * rows_per, rend = min(f.H, rbeg + rows_per);
+  make_table(tw, f.WP);
   double acc0 = 0.0, acc1 = 0.0;
-  for (int r0 = blockIdx.x * rows_per; r0 < (blockIdx.x + 1) * rows_per; r0 += rpb) {
-    const float2* in = f.tmp + (long long)pair * N + (long long)r0 * f.W;
+  const float2* tin = f.tmp + (long long)pair * f.H * f.WP;
+  for (int r0 = rbeg; r0 < rend; r0 += f.rpb) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) s[idx] = cconj(in[idx]);
+    for (int rr = 0; rr < f.rpb; ++rr) {
+      const int row = r0 + rr;
+      for (int cc = threadIdx.x; cc < f.WP; cc += blockDim.x)
+        s[rr * f.WP + cc] = row < rend ? cconj(tin[(long long)row * f.WP + cc]) : make_float2(0.f, 0.f);
+    }
     __syncthreads();
-    fft_forward(s, f.W, rpb, 1, f.W, tw);
-    rz0 = 0.f;
-    rz1 = 0.f;
-    for (int idx = threadIdx.x; idx < rpb * f.W; idx += blockDim.x) {
-      const float2 v = cconj(s[idx]);
-      const long long p = (long long)r0 * f.W + idx;
-      const float z0 = v.x * scale;
-      Z[(long long)j0 * N + p] = z0;
-      rz0 = fmaf(Rr[(long long)j0 * N + p], z0, rz0);
-      if (j1 < f.R) {
-        const float z1 = v.y * scale;
-        Z[(long long)j1 * N + p] = z1;
-        rz1 = fmaf(Rr[(long long)j1 * N + p], z1, rz1);
+    fft_forward(s, f.WP, f.rpb, 1, f.WP, tw);
+    float rz0 = 0.f, rz1 = 0.f;
+    for (int rr = 0; rr < f.rpb; ++rr) {
+      const int row = r0 + rr;
+      if (row >= rend) break;
+      for (int cc = threadIdx.x; cc < f.W; cc += blockDim.x) {
+        const float2 v = cconj(s[rr * f.WP + cc]);
+        const long long p = (long long)row * f.W + cc;
+        const float z0 = v.x * scale;
+        Z[(long long)j0 * N + p] = z0;
+        rz0 = fmaf(Rr[(long long)j0 * N + p], z0, rz0);
+        if (j1 < f.R) {
+          const float z1 = v.y * scale;
+          Z[(long long)j1 * N + p] = z1;
+          rz1 = fmaf(Rr[(long long)j1 * N + p], z1, rz1);
+        }
       }
     }
     acc0 += (double)rz0;
@@ -1148,7 +1170,6 @@ CgArgs cg_args(LikelihoodState* L) {
   return a;
 }
 
-bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
 int ilog2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
@@ -1158,8 +1179,9 @@ int ilog2(int v) {
 // z = M^{-1} r for all systems; r.z partials into rz_buf ([R][nbz]).
 void precond_apply(LikelihoodState* L, double* rz_buf, cudaStream_t s) {
   const FftDesc& f = L->fd;
-  fft_rows_fwd_kernel<<<dim3(f.H / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr);
-  fft_cols_filter_kernel<<<dim3(f.W / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
+  fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(
+      f, L->Rr);
+  fft_cols_filter_kernel<<<dim3(f.WP / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
   fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z, rz_buf);
 }
 
@@ -1257,26 +1279,37 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   c.tiles_x = (c.W + kTile - 1) / kTile;
   c.tiles_y = (c.H + kTile - 1) / kTile;
   L->nb = c.tiles_x * c.tiles_y;
-  L->fft = is_pow2(c.H) && is_pow2(c.W) && c.H <= 8192 && c.W <= 8192;
+  // circulant preconditioner on the smallest power-of-two torus that holds the image
+  // (padding keeps it symmetric positive definite: crop * C^-1 * pad)
+  auto next_pow2 = [](int v) {
+    int p2 = 2;
+    while (p2 < v) p2 <<= 1;
+    return p2;
+  };
+  const int HP = next_pow2(c.H), WP = next_pow2(c.W);
+  L->fft = HP <= 8192 && WP <= 8192;
   L->nbz = L->nb;
   if (L->fft) {
     FftDesc& f = L->fd;
     f.H = c.H;
     f.W = c.W;
-    f.logH = ilog2(c.H);
-    f.logW = ilog2(c.W);
+    f.HP = HP;
+    f.WP = WP;
     f.R = L->R;
     f.pairs = (L->R + 1) / 2;
     // smallest radix of a length-n plan: 8 if log2 n is a multiple of 3, else 4 or 2
-    auto rmin = [](int logn) { return logn % 3 == 0 ? 8 : (logn % 3 == 2 ? 4 : 2); };
+    auto rmin = [](int n) {
+      const int logn = ilog2(n);
+      return logn % 3 == 0 ? 8 : (logn % 3 == 2 ? 4 : 2);
+    };
     // one pass handles at most kFftMaxItems * kFftThreads work items of n / R points
     const int cap = kFftMaxItems * kFftThreads;
-    f.rpb = std::max(1, std::min({c.H, 4096 / c.W, cap * rmin(f.logW) / c.W}));
-    f.cw = std::max(1, std::min({c.W, 16, cap * rmin(f.logH) / c.H}));
+    f.rpb = std::max(1, std::min({HP, 4096 / WP, cap * rmin(WP) / WP}));
+    f.cw = std::max(1, std::min({WP, 16, cap * rmin(HP) / HP}));
     f.nbz = std::min(c.H, 64);
     L->nbz = f.nbz;
-    L->smem_rows = sizeof(float2) * ((size_t)c.W + (size_t)f.rpb * c.W);
-    L->smem_cols = sizeof(float2) * ((size_t)c.H + (size_t)c.H * f.cw);
+    L->smem_rows = sizeof(float2) * ((size_t)WP + (size_t)f.rpb * WP);
+    L->smem_cols = sizeof(float2) * ((size_t)HP + (size_t)HP * f.cw);
   }
   L->nbmax = std::max(L->nb, L->nbz);
   L->prep_blocks = (int)std::min<long long>(std::max<long long>((c.N + 255) / 256, 1), 2048);
@@ -1314,9 +1347,10 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->part, sizeof(double) * 6 * L->R * L->nbmax) == cudaSuccess &&
             cudaMalloc(&L->dpart, sizeof(double) * L->prep_blocks) == cudaSuccess &&
             cudaMalloc(&L->dbar, sizeof(double)) == cudaSuccess &&
-            (!L->fft || (cudaMalloc(&L->ftmp, sizeof(float2) * ((L->R + 1) / 2) * N) == cudaSuccess &&
-                         cudaMalloc(&L->Z, sizeof(float) * RN) == cudaSuccess &&
-                         cudaMalloc(&L->hth, sizeof(float) * N) == cudaSuccess)) &&
+            (!L->fft ||
+             (cudaMalloc(&L->ftmp, sizeof(float2) * ((L->R + 1) / 2) * c.H * L->fd.WP) == cudaSuccess &&
+              cudaMalloc(&L->Z, sizeof(float) * RN) == cudaSuccess &&
+              cudaMalloc(&L->hth, sizeof(float) * L->fd.HP * L->fd.WP) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&L->d_relres, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_prev_rr, sizeof(double) * L->R) == cudaSuccess &&
@@ -1381,7 +1415,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
       likelihood_destroy(L);
       return EP_TV_ERR_CUDA;
     }
-    hth_kernel<<<grid1d(N), 256, 0, s>>>(L->hth, c.H, c.W, L->d_k, kh, kw, L->inv_xi);
+    hth_kernel<<<grid1d((long long)L->fd.HP * L->fd.WP), 256, 0, s>>>(L->hth, L->fd.HP, L->fd.WP,
+                                                                      L->d_k, kh, kw, L->inv_xi);
   }
   // H^T y / xi
   conv_t_kernel<<<dim3(grid1d(N), 1), 256, 0, s>>>(cfg.y, L->Hty, c.H, c.W, L->d_k, kh, kw,
