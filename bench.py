@@ -36,6 +36,7 @@ WORKLOADS = {
                       em_every=5, S=32, seed=0),
     "denoise4096": dict(kind="denoise", h=4096, w=4096, sigma=0.1, beta0=20.0, em_every=0,
                         seed=0, n_rect=40),
+    "batched256": dict(kind="batch", n=256, h=None, w=None, em_every=5, beta0=1.0, S=32, seed=0),
 }
 
 
@@ -126,6 +127,84 @@ def _ncu_traffic(kernel_name):
     return None
 
 
+def run_batch(args, rank, world):
+    """256 uneven problems (denoising and deconvolution) advanced by ep_tv_batch_sweep."""
+    import numpy as np
+    import torch
+
+    from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC, Batch
+    from paper_2110_01585_gb300 import synthetic as syn
+
+    cfg = WORKLOADS[args.workload]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    probs = syn.batched_problems(cfg["n"], seed=cfg["seed"] + 1000 * rank)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ctxs = []
+    with torch.cuda.stream(stream):
+        for p in probs:
+            yt = torch.as_tensor(p.y.astype(np.float32), device=dev)
+            if p.kind == "denoise":
+                ctxs.append(EPTV(yt, p.xi, p.beta, stream=stream))
+            else:
+                ctxs.append(EPTV(yt, p.xi, p.beta, op=OP_CONV_PERIODIC, kernel=p.kernel,
+                                 rbmc_samples=cfg["S"], cg_max_iter=100000, stream=stream))
+    n_px = sum(p.n_pixels for p in probs)
+    batch = Batch(ctxs)
+    idx = [0]
+
+    def step():
+        idx[0] += 1
+        batch.sweep(1, em_every=1 if idx[0] % cfg["em_every"] == 0 else 0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.trace(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cs = ClockSampler(dev.index)
+    with cs:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[i][0].record(stream)
+            step()
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    ms_total = sum(a.elapsed_time(b) for a, b in ev)
+    trace = {}
+    for c in ctxs:
+        for k, v in c.trace_read().items():
+            t = trace.setdefault(k, [0.0, 0, 0.0, v[3]])
+            t[0] += v[0]
+            t[1] += v[1]
+            t[2] += v[2]
+            t[3] = v[3] or t[3]
+    status = max(c.status() for c in ctxs)
+    batch.close()
+    for c in ctxs:
+        c.close()
+    value = n_px * args.steps / (ms_total / 1e3) / 1e6
+    # kernel classes overlap across worker streams: shares are of summed kernel time
+    tot_k = sum(v[0] for v in trace.values()) or 1.0
+    name, (kms, kl, units, bpu) = max(trace.items(), key=lambda kv: kv[1][0])
+    peak, peak_src = _peaks()
+    achieved = units * bpu / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "note": "per-launch event times summed over concurrent streams",
+                "share_of_kernel_time": round(kms / tot_k, 4)}
+    return dict(value=value, ms_per_step=ms_total / args.steps, roofline=roofline,
+                clocks=cs.summary(), launches=sum(v[1] for v in trace.values()),
+                trace={k: tuple(v) for k, v in trace.items()},
+                stats={"cg_iters": None, "n_fp64": None}, status=status, e2e=None, n_px=n_px)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -133,6 +212,8 @@ def run_ours(args, rank, world):
     from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC, OP_IDENTITY, solve_host
 
     cfg = WORKLOADS[args.workload]
+    if cfg["kind"] == "batch":
+        return run_batch(args, rank, world)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     prob = _problem(cfg, rank)
@@ -226,11 +307,13 @@ def run_oracle_sample(cfg, budget_s=20.0):
     operator and parameters at a reduced size, sweeps until the time budget."""
     from oracle.ep import EPOracle
     from paper_2110_01585_gb300 import synthetic as syn
-    if cfg["kind"] == "deconv":
-        side = 128
-        p = syn.deconv_problem(side, side, kernel=syn.uniform_kernel(cfg["kernel"][1]),
-                               bsnr_db=cfg["bsnr_db"], beta0=cfg["beta0"], seed=cfg["seed"],
-                               grf_length=cfg.get("grf", 32.0) * side / cfg["h"])
+    if cfg["kind"] in ("deconv", "batch"):
+        side = 64
+        width = cfg["kernel"][1] if cfg["kind"] == "deconv" else 9
+        bsnr = cfg.get("bsnr_db", 40.0)
+        grf = cfg.get("grf", 32.0) * side / (cfg["h"] or 512)
+        p = syn.deconv_problem(side, side, kernel=syn.uniform_kernel(width), bsnr_db=bsnr,
+                               beta0=cfg["beta0"], seed=cfg["seed"], grf_length=grf)
         pr = syn.rbmc_probes(cfg["S"], side * side, side * side, seed=1)
         o = EPOracle("deconv", p.y, p.xi, p.beta, side, side, kernel=p.kernel, site0="rbmc_cg",
                      probes=pr)
@@ -270,7 +353,11 @@ def main():
     cfg = WORKLOADS[args.workload]
     config = {"workload": args.workload, "height": cfg["h"], "width": cfg["w"],
               "l2": "flushed before every timed step (256 MB write, untimed)"}
-    if cfg["kind"] == "deconv":
+    if cfg["kind"] == "batch":
+        config.update(problems=cfg["n"], sides="log-uniform 64..1024, even",
+                      sigma="U[0.02, 0.2]", blur_widths=[1, 5, 9, 15], em_every=cfg["em_every"],
+                      rbmc_probes=cfg["S"])
+    elif cfg["kind"] == "deconv":
         config.update(kernel="uniform 9x9 periodic", bsnr_db=cfg["bsnr_db"], beta0=cfg["beta0"],
                       em_every=cfg["em_every"], rbmc_probes=cfg["S"])
     else:
@@ -303,7 +390,7 @@ def main():
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and cfg["kind"] != "batch":
         cpu = run_oracle_sample(cfg, budget_s=20.0)
     line = {"metric": "Mpixel-EP-sweeps/s", "value": round(res["value"], 3), "unit": "Mpixel-EP-sweeps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -313,6 +400,7 @@ def main():
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "solver": {"cg_iters_last_sweep": res["stats"]["cg_iters"],
                        "fp64_edges": res["stats"]["n_fp64"], "status": res["status"]},
+            "pixels_per_step": res["n_px"],
             "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in res["trace"].items() if v[1]}}
     print(json.dumps(line))
 

@@ -237,6 +237,23 @@ ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width, const ep_t
                                        float* tau_out, float* nu_out, const int8_t* k_order,
                                        double* abar_out, uint32_t* flags_out, void* cuda_stream);
 
+/* Batches (not in the paper): advance many independent problems together.  All
+   contexts must live on the same device and stream and use order_mode 0; a
+   context belongs to at most one batch at a time and stays usable on its own
+   (posterior, sites, EM) between batch sweeps.  The batch keeps the context
+   pointers (the caller still owns and frees the contexts, after the batch). */
+typedef struct ep_tv_batch ep_tv_batch;
+ep_tv_status ep_tv_batch_create(int32_t n, ep_tv_ctx* const* ctxs, ep_tv_batch** out);
+/* n_sweeps sweeps of every context: one launch runs the prior-site pass of all
+   images (blocks mapped to images through a table), then the likelihood-site
+   updates run concurrently on one worker stream per context, each driven by a host
+   thread of a pool of up to 16; with em_every > 0 every context's beta is updated
+   after each em_every-th sweep.  Returns when all work is enqueued (the likelihood
+   solvers synchronise with their own streams while they run). */
+ep_tv_status ep_tv_batch_sweep(ep_tv_batch* batch, int32_t n_sweeps, int32_t em_every);
+/* Synchronises and frees the batch (not the contexts).  NULL is accepted. */
+void ep_tv_batch_destroy(ep_tv_batch* batch);
+
 /* Frees the context (synchronises its stream first).  NULL is accepted. */
 void ep_tv_destroy(ep_tv_ctx* ctx);
 

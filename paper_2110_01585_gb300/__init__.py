@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 from ._lib import OP_CONV_PERIODIC, OP_DENSE, OP_IDENTITY, EPTVError
 
-__all__ = ["EPTV", "solve_host", "EPTVError", "OP_IDENTITY", "OP_CONV_PERIODIC", "OP_DENSE",
+__all__ = ["EPTV", "Batch", "solve_host", "EPTVError", "OP_IDENTITY", "OP_CONV_PERIODIC", "OP_DENSE",
            "default_params"]
 
 
@@ -205,6 +205,43 @@ class EPTV:
 
     def reset(self):
         _lib.check(self._lib.ep_tv_reset(self._ctx), "ep_tv_reset")
+
+
+class Batch:
+    """Many EPTV problems advanced together (``ep_tv_batch_*``).
+
+    The problems must share one device and one stream and use order_mode 0.
+    The batch keeps references to them; close the batch before the problems.
+    """
+
+    def __init__(self, problems):
+        self._lib = _lib.load()
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p._ctx.value for p in self.problems])
+        out = ctypes.c_void_p()
+        _lib.check(self._lib.ep_tv_batch_create(len(self.problems), arr, ctypes.byref(out)),
+                   "ep_tv_batch_create")
+        self._b = out
+
+    def sweep(self, n: int = 1, em_every: int = 0):
+        _lib.check(self._lib.ep_tv_batch_sweep(self._b, int(n), int(em_every)), "ep_tv_batch_sweep")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.ep_tv_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def solve_host(y: np.ndarray, xi: float, beta: float, n_sweeps: int, em_every: int = 0,

@@ -68,6 +68,9 @@ SIGNATURES = {
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, ctypes.POINTER(ctypes.c_int8),
                                             c_void_p, c_void_p, c_void_p]),
+    "ep_tv_batch_create": (c_int32, [c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p)]),
+    "ep_tv_batch_sweep": (c_int32, [c_void_p, c_int32, c_int32]),
+    "ep_tv_batch_destroy": (None, [c_void_p]),
     "ep_tv_destroy": (None, [c_void_p]),
     "ep_tv_status_str": (ctypes.c_char_p, [c_int32]),
 }

@@ -5,8 +5,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -519,6 +523,190 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* c, int32_t kernel, double* ms, int64_t*
   if (units) *units = u;
   if (bytes_per_unit) *bytes_per_unit = bpu;
   return EP_TV_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many contexts advanced together.  One launch runs the prior-site
+// pass of every image (a block -> image table); the likelihood-site updates of
+// the contexts that have one run concurrently on worker streams, each driven by
+// a host thread of a small pool (their CG loops poll their own convergence).
+struct ep_tv_batch {
+  std::vector<ep_tv_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  BatchItem* d_items[2] = {nullptr, nullptr};
+  BatchItem* h_items[2] = {nullptr, nullptr};
+  cudaEvent_t items_ev[2] = {nullptr, nullptr};
+  int slot = 0;
+  int total_blocks = 0;
+  std::vector<int> lik;                 // contexts with a likelihood state
+  std::vector<cudaStream_t> wstream;    // one worker stream per such context
+  std::vector<cudaEvent_t> wdone;
+  cudaEvent_t prior_done = nullptr;
+  // pool
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_job, cv_done;
+  int next_job = 0, jobs_total = 0, jobs_done = 0;
+  bool stop = false;
+  ep_tv_status job_err = EP_TV_OK;
+};
+
+namespace {
+
+void batch_worker(ep_tv_batch* b) {
+  cudaSetDevice(b->device);
+  for (;;) {
+    int job;
+    {
+      std::unique_lock<std::mutex> lock(b->mu);
+      b->cv_job.wait(lock, [b] { return b->stop || b->next_job < b->jobs_total; });
+      if (b->stop) return;
+      job = b->next_job++;
+    }
+    ep_tv_ctx* c = b->ctx[b->lik[job]];
+    ep_tv_status st = EP_TV_OK;
+    if (cudaStreamWaitEvent(b->wstream[job], b->prior_done, 0) != cudaSuccess) st = EP_TV_ERR_CUDA;
+    if (st == EP_TV_OK)
+      st = likelihood_update(c->lik, c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur], c->status,
+                             c->counters, &c->tracer, b->wstream[job]);
+    if (st == EP_TV_OK && cudaEventRecord(b->wdone[job], b->wstream[job]) != cudaSuccess)
+      st = EP_TV_ERR_CUDA;
+    {
+      std::lock_guard<std::mutex> lock(b->mu);
+      if (st != EP_TV_OK && b->job_err == EP_TV_OK) b->job_err = st;
+      if (++b->jobs_done == b->jobs_total) b->cv_done.notify_one();
+    }
+  }
+}
+
+void batch_free(ep_tv_batch* b) {
+  {
+    std::lock_guard<std::mutex> lock(b->mu);
+    b->stop = true;
+  }
+  b->cv_job.notify_all();
+  for (auto& t : b->threads) t.join();
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(b->d_items[i]);
+    if (b->h_items[i]) cudaFreeHost(b->h_items[i]);
+    if (b->items_ev[i]) cudaEventDestroy(b->items_ev[i]);
+  }
+  for (auto s : b->wstream) cudaStreamDestroy(s);
+  for (auto e : b->wdone) cudaEventDestroy(e);
+  if (b->prior_done) cudaEventDestroy(b->prior_done);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+ep_tv_status ep_tv_batch_create(int32_t n, ep_tv_ctx* const* ctxs, ep_tv_batch** out) {
+  if (!out || n < 1 || !ctxs) return EP_TV_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return EP_TV_ERR_ARG;
+    if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
+      return EP_TV_ERR_ARG;
+    if (ctxs[i]->p.order_mode != 0) return EP_TV_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return EP_TV_ERR_ARG;
+  }
+  ep_tv_batch* b = new (std::nothrow) ep_tv_batch();
+  if (!b) return EP_TV_ERR_NOMEM;
+  b->ctx.assign(ctxs, ctxs + n);
+  b->stream = ctxs[0]->stream;
+  b->device = ctxs[0]->device;
+  for (int i = 0; i < n; ++i) {
+    b->total_blocks += prior_sweep_blocks(ctxs[i]->height, ctxs[i]->width);
+    if (ctxs[i]->lik) b->lik.push_back(i);
+  }
+  bool ok = true;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = cudaMalloc(&b->d_items[i], sizeof(BatchItem) * n) == cudaSuccess &&
+         cudaHostAlloc(&b->h_items[i], sizeof(BatchItem) * n, cudaHostAllocDefault) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->items_ev[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->prior_done, cudaEventDisableTiming) == cudaSuccess;
+  for (size_t k = 0; k < b->lik.size() && ok; ++k) {
+    cudaStream_t ws;
+    cudaEvent_t ev;
+    ok = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->wstream.push_back(ws);
+    ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->wdone.push_back(ev);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(b);
+    return EP_TV_ERR_NOMEM;
+  }
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nthreads = (int)std::min<size_t>(b->lik.size(), std::min(16u, hw));
+  for (int t = 0; t < nthreads; ++t) b->threads.emplace_back(batch_worker, b);
+  *out = b;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_every) {
+  if (!b || n_sweeps < 0 || em_every < 0) return EP_TV_ERR_ARG;
+  const int n = (int)b->ctx.size();
+  for (ep_tv_ctx* c : b->ctx)
+    if (c->failed) return EP_TV_ERR_STATE;
+  for (int t = 0; t < n_sweeps; ++t) {
+    // image table of this sweep (prior buffers alternate per context)
+    CK(cudaEventSynchronize(b->items_ev[b->slot]));
+    BatchItem* h = b->h_items[b->slot];
+    int block = 0;
+    for (int i = 0; i < n; ++i) {
+      ep_tv_ctx* c = b->ctx[i];
+      h[i].a = sweep_args(c, 0x4321);
+      h[i].site0_from_y = c->op.op == EP_TV_OP_IDENTITY;
+      h[i].tiles_x = prior_sweep_tiles_x(c->width);
+      h[i].block_begin = block;
+      block += prior_sweep_blocks(c->height, c->width);
+    }
+    CK(cudaMemcpyAsync(b->d_items[b->slot], h, sizeof(BatchItem) * n, cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaEventRecord(b->items_ev[b->slot], b->stream));
+    launch_prior_sweep_batch(b->d_items[b->slot], n, b->total_blocks, b->stream);
+    b->slot ^= 1;
+    for (ep_tv_ctx* c : b->ctx) {
+      c->cur ^= 1;
+      ++c->sweeps;
+    }
+    if (!b->lik.empty()) {
+      CK(cudaEventRecord(b->prior_done, b->stream));
+      {
+        std::lock_guard<std::mutex> lock(b->mu);
+        b->next_job = 0;
+        b->jobs_done = 0;
+        b->jobs_total = (int)b->lik.size();
+        b->job_err = EP_TV_OK;
+      }
+      b->cv_job.notify_all();
+      {
+        std::unique_lock<std::mutex> lock(b->mu);
+        b->cv_done.wait(lock, [b] { return b->jobs_done == b->jobs_total; });
+        b->jobs_total = 0;
+        b->next_job = 0;
+        if (b->job_err != EP_TV_OK) return b->job_err;
+      }
+      for (size_t k = 0; k < b->lik.size(); ++k) CK(cudaStreamWaitEvent(b->stream, b->wdone[k], 0));
+    }
+    if (em_every > 0 && (t + 1) % em_every == 0)
+      for (ep_tv_ctx* c : b->ctx)
+        launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, b->stream);
+  }
+  return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+}
+
+void ep_tv_batch_destroy(ep_tv_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
 }
 
 void ep_tv_destroy(ep_tv_ctx* c) {

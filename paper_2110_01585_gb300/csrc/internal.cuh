@@ -110,11 +110,22 @@ struct SweepArgs {
   unsigned long long* counters;
 };
 
+// One image of a batched prior-site launch.
+struct BatchItem {
+  SweepArgs a;
+  int site0_from_y;
+  int tiles_x;
+  int block_begin;   // first block of this image in the launch
+};
+
 // Prior-site sweep over V_1..V_4 for one image; site 0 implicit (identity) or stored.
 void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s);
 // Algorithmic DRAM bytes per pixel of one prior-site pass.
 double prior_sweep_bytes_per_pixel(bool site0_from_y);
 int prior_sweep_blocks(int height, int width);
+int prior_sweep_tiles_x(int width);
+void launch_prior_sweep_batch(const BatchItem* items, int n_items, int total_blocks,
+                              cudaStream_t s);
 
 // abar = sum(partials) in a fixed order; if do_em, beta = n / abar.
 void launch_abar_reduce(const double* partial, int n_partial, double* dscal, double n_pixels,

@@ -50,15 +50,16 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// One tile (bx, by) of one image; `part` indexes its a_u partial sum.
 template <bool kSite0FromY>
-__global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
-  extern __shared__ float smem[];
+__device__ __forceinline__ void prior_tile(const SweepArgs& a, int bx, int by, int part,
+                                           float* smem) {
   float* sT = smem;             // [5][kRN]
   float* sV = smem + 5 * kRN;   // [5][kRN]
   const int H = a.height, W = a.width;
   const long long N = a.n;
-  const int r0 = blockIdx.y * kTH;
-  const int c0 = blockIdx.x * kTW;
+  const int r0 = by * kTH;
+  const int c0 = bx * kTW;
   const int tid = threadIdx.x;
 
   // ---- stage the region (positions outside a free-boundary image stay unused)
@@ -221,10 +222,36 @@ __global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
   if (tid == 0) {
     double s = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) s += red[w];
-    a.abar_partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    a.abar_partial[part] = s;
     if (red_cnt[0]) atomicAdd(&a.counters[DC_FP64], (unsigned long long)red_cnt[0]);
     if (red_cnt[1]) atomicAdd(&a.counters[DC_CAPPED], (unsigned long long)red_cnt[1]);
   }
+}
+
+template <bool kSite0FromY>
+__global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
+  extern __shared__ float smem[];
+  prior_tile<kSite0FromY>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, smem);
+}
+
+// Many images in one launch: block b belongs to the image whose block range holds
+// it (binary search over the first blocks); its tiles are numbered row-major.
+__global__ void __launch_bounds__(kThreads) prior_sweep_batch_kernel(const BatchItem* items,
+                                                                     int n_items) {
+  extern __shared__ float smem[];
+  const int b = blockIdx.x;
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  const BatchItem& it = items[lo];
+  const int local = b - it.block_begin;
+  const int by = local / it.tiles_x, bx = local - by * it.tiles_x;
+  if (it.site0_from_y)
+    prior_tile<true>(it.a, bx, by, local, smem);
+  else
+    prior_tile<false>(it.a, bx, by, local, smem);
 }
 
 __global__ void abar_reduce_kernel(const double* partial, int n, double* dscal, double n_pixels,
@@ -253,6 +280,19 @@ double prior_sweep_bytes_per_pixel(bool site0_from_y) {
 
 int prior_sweep_blocks(int height, int width) {
   return ((width + kTW - 1) / kTW) * ((height + kTH - 1) / kTH);
+}
+
+int prior_sweep_tiles_x(int width) { return (width + kTW - 1) / kTW; }
+
+void launch_prior_sweep_batch(const BatchItem* items, int n_items, int total_blocks,
+                              cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(prior_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmemBytes);
+    attr = true;
+  }
+  prior_sweep_batch_kernel<<<total_blocks, kThreads, kSmemBytes, s>>>(items, n_items);
 }
 
 void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s) {
