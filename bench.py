@@ -138,7 +138,8 @@ def run_batch(args, rank, world):
     cfg = WORKLOADS[args.workload]
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    probs = syn.batched_problems(cfg["n"], seed=cfg["seed"] + 1000 * rank)
+    n_prob = args.batch_n or cfg["n"]
+    probs = syn.batched_problems(n_prob, seed=cfg["seed"] + 1000 * rank)
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     ctxs = []
@@ -345,6 +346,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="deconv512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=None,
+                    help="number of problems of the batched256 workload (default 256)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

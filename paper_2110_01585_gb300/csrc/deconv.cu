@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1202,6 +1203,36 @@ ep_tv_status finish_probes(LikelihoodState* L, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// Raises the dynamic shared-memory limit of the solver kernels to the device's
+// opt-in maximum minus their static shared memory (once per device).
+bool raise_smem_limits() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return true;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  const void* fns[] = {(const void*)direction_kernel, (const void*)residual_kernel,
+                       (const void*)fft_rows_fwd_kernel, (const void*)fft_rows_inv_kernel,
+                       (const void*)fft_cols_filter_kernel};
+  for (const void* f : fns) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+      return false;
+  }
+  done[dev] = true;
+  return true;
+}
+
+}  // namespace
+
 ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, LikelihoodState** out,
                                float* mu0) {
   *out = nullptr;
@@ -1395,26 +1426,27 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     likelihood_destroy(L);
     return EP_TV_ERR_CUDA;
   }
-  if (cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)L->smem) != cudaSuccess ||
-      cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)L->smem_res) != cudaSuccess) {
+  // The dynamic shared-memory limit is a property of the kernel, shared by every
+  // context: raise it once to what the device allows, never lower it per context.
+  if (!raise_smem_limits()) {
     likelihood_destroy(L);
     return EP_TV_ERR_CUDA;
+  }
+  {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t need = std::max({L->smem + 8192, L->smem_res + 16384,
+                                  L->fft ? std::max(L->smem_rows, L->smem_cols) + 1024 : (size_t)0});
+    if (need > (size_t)optin) {
+      likelihood_destroy(L);
+      return EP_TV_ERR_UNSUPPORTED;
+    }
   }
   if (L->fft) {
     L->fd.tmp = L->ftmp;
     L->fd.hth = L->hth;
     L->fd.dbar = L->dbar;
-    if (cudaFuncSetAttribute(fft_rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L->smem_rows) != cudaSuccess ||
-        cudaFuncSetAttribute(fft_rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L->smem_rows) != cudaSuccess ||
-        cudaFuncSetAttribute(fft_cols_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L->smem_cols) != cudaSuccess) {
-      likelihood_destroy(L);
-      return EP_TV_ERR_CUDA;
-    }
     hth_kernel<<<grid1d((long long)L->fd.HP * L->fd.WP), 256, 0, s>>>(L->hth, L->fd.HP, L->fd.WP,
                                                                       L->d_k, kh, kw, L->inv_xi);
   }
