@@ -37,6 +37,7 @@ WORKLOADS = {
     "denoise4096": dict(kind="denoise", h=4096, w=4096, sigma=0.1, beta0=20.0, em_every=0,
                         seed=0, n_rect=40),
     "batched256": dict(kind="batch", n=256, h=None, w=None, em_every=5, beta0=1.0, S=32, seed=0),
+    "cs128": dict(kind="cs", h=128, w=128, ratio=0.3, sigma=0.01, beta0=1.0, em_every=5, seed=0),
 }
 
 
@@ -56,6 +57,9 @@ def _problem(cfg, rank=0):
         k = syn.uniform_kernel(cfg["kernel"][1])
         return syn.deconv_problem(cfg["h"], cfg["w"], kernel=k, bsnr_db=cfg["bsnr_db"],
                                   beta0=cfg["beta0"], seed=seed)
+    if cfg["kind"] == "cs":
+        return syn.cs_problem(cfg["h"], cfg["w"], ratio=cfg["ratio"], sigma=cfg["sigma"],
+                              beta0=cfg["beta0"], seed=seed)
     return syn.denoise_problem(cfg["h"], cfg["w"], sigma=cfg["sigma"], beta=cfg["beta0"],
                                seed=seed, n_rect=cfg.get("n_rect", 8))
 
@@ -210,7 +214,7 @@ def run_ours(args, rank, world):
     import numpy as np
     import torch
 
-    from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC, OP_IDENTITY, solve_host
+    from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC, OP_DENSE, OP_IDENTITY, solve_host
 
     cfg = WORKLOADS[args.workload]
     if cfg["kind"] == "batch":
@@ -225,6 +229,9 @@ def run_ours(args, rank, world):
     if cfg["kind"] == "deconv":
         kw = dict(op=OP_CONV_PERIODIC, kernel=prob.kernel, rbmc_samples=cfg["S"])
     with torch.cuda.stream(stream):
+        if cfg["kind"] == "cs":
+            At = torch.as_tensor(prob.A.astype(np.float32), device=dev)
+            kw = dict(op=OP_DENSE, dense=At, height=cfg["h"], width=cfg["w"])
         yt = torch.as_tensor(prob.y.astype(np.float32), device=dev)
         ep = EPTV(yt, prob.xi, prob.beta, stream=stream, **kw)
     em_every = cfg["em_every"]
@@ -275,8 +282,12 @@ def run_ours(args, rank, world):
     achieved = units * bpu / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     traffic = _ncu_traffic(name)
     traffic_per_launch = traffic * units / kl if (traffic is not None and kl) else None
-    roofline = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+    bound, unit = "hbm", "GB/s"
+    if name == "cs_woodbury":
+        # FP64 ALU: per-unit figure is FP64 flops; GB300 nominal FP64 1.25 TFLOP/s
+        bound, unit, peak, peak_src = "alu", "GFLOP/s (FP64)", 1250.0, "nominal FP64, GB300"
+    roofline = {"bound": bound, "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_src, "unit": unit, "frac": round(achieved / peak, 4),
                 "traffic": traffic_per_launch,
                 "algorithmic_bytes_per_launch": units * bpu / kl if kl else None,
                 "avg_launch_us": kms / kl * 1e3 if kl else None,
@@ -292,6 +303,8 @@ def run_ours(args, rank, world):
         extra = {}
         if cfg["kind"] == "deconv":
             extra = dict(op=OP_CONV_PERIODIC, kernel=prob.kernel, rbmc_samples=cfg["S"])
+        if cfg["kind"] == "cs":
+            extra = dict(op=OP_DENSE, dense=At, height=cfg["h"], width=cfg["w"])
         solve_host(y32, prob.xi, prob.beta, n_e2e, em_every=em_every, **extra)
         t1 = time.perf_counter()
         e2e = {"value": round(n_px * n_e2e / (t1 - t0) / 1e6, 3), "unit": "Mpixel-EP-sweeps/s",
@@ -319,6 +332,12 @@ def run_oracle_sample(cfg, budget_s=20.0):
         o = EPOracle("deconv", p.y, p.xi, p.beta, side, side, kernel=p.kernel, site0="rbmc_cg",
                      probes=pr)
         sample = f"{side}x{side} crop-size instance of the same generator/blur/BSNR, CG mode"
+    elif cfg["kind"] == "cs":
+        side = 64
+        p = syn.cs_problem(side, side, ratio=cfg["ratio"], sigma=cfg["sigma"], beta0=cfg["beta0"],
+                           seed=cfg["seed"])
+        o = EPOracle("cs", p.y, p.xi, p.beta, side, side, A=p.A, site0="woodbury")
+        sample = f"{side}x{side} instance (M = {p.A.shape[0]}) of the same generator"
     else:
         side = 512
         p = syn.denoise_problem(side, side, sigma=cfg["sigma"], beta=cfg["beta0"], seed=cfg["seed"])
@@ -334,7 +353,15 @@ def run_oracle_sample(cfg, budget_s=20.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(side * side * n / dt / 1e6, 5), "unit": "Mpixel-EP-sweeps/s", "cores": 1,
+    cores = 1
+    if cfg["kind"] == "cs":
+        # the dense Woodbury step runs in multithreaded BLAS
+        try:
+            from threadpoolctl import threadpool_info
+            cores = max(i.get("num_threads", 1) for i in threadpool_info()) or 1
+        except Exception:
+            cores = os.cpu_count() or 1
+    return {"value": round(side * side * n / dt / 1e6, 5), "unit": "Mpixel-EP-sweeps/s", "cores": cores,
             "kind": "oracle", "sample": f"{sample}, {n} sweeps in {dt:.1f} s"}
 
 
@@ -356,7 +383,10 @@ def main():
     cfg = WORKLOADS[args.workload]
     config = {"workload": args.workload, "height": cfg["h"], "width": cfg["w"],
               "l2": "flushed before every timed step (256 MB write, untimed)"}
-    if cfg["kind"] == "batch":
+    if cfg["kind"] == "cs":
+        config.update(m=int(0.3 * cfg["h"] * cfg["w"]), sigma=cfg["sigma"], beta0=cfg["beta0"],
+                      em_every=cfg["em_every"], precision="Woodbury in FP64")
+    elif cfg["kind"] == "batch":
         config.update(problems=cfg["n"], sides="log-uniform 64..1024, even",
                       sigma="U[0.02, 0.2]", blur_widths=[1, 5, 9, 15], em_every=cfg["em_every"],
                       rbmc_probes=cfg["S"])
@@ -393,7 +423,7 @@ def main():
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and cfg["kind"] != "batch":
+    if world == 1 and not args.no_cpu_baseline and cfg["kind"] not in ("batch",):
         cpu = run_oracle_sample(cfg, budget_s=20.0)
     line = {"metric": "Mpixel-EP-sweeps/s", "value": round(res["value"], 3), "unit": "Mpixel-EP-sweeps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

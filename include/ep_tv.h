@@ -62,7 +62,8 @@ typedef enum {
 typedef enum {
   EP_TV_OP_IDENTITY = 0,        /* denoising, M = N */
   EP_TV_OP_CONV_PERIODIC = 1,   /* periodic convolution with a centred odd kernel, M = N */
-  EP_TV_OP_DENSE = 2            /* compressive sensing, dense M x N matrix */
+  EP_TV_OP_DENSE = 2            /* compressive sensing, dense M x N matrix; the likelihood
+                                   site uses the Woodbury identity in FP64 */
 } ep_tv_op;
 
 typedef struct {
@@ -192,7 +193,9 @@ typedef enum {
   EP_TV_K_CG_RESIDUAL = 3,   /* initial CG residual, unit = pixel of one system */
   EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
   EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one system */
-  EP_TV_K_COUNT = 6
+  EP_TV_K_CS = 6,            /* dense-operator likelihood site (Woodbury, FP64), unit = pixel;
+                                its per-unit figure is FP64 flops, not bytes */
+  EP_TV_K_COUNT = 7
 } ep_tv_kernel;
 
 /* Tracing: with on != 0, every launch of the kernel classes above is bracketed

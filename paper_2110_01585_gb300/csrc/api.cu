@@ -518,6 +518,7 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* c, int32_t kernel, double* ms, int64_t*
     bpu = prior_sweep_bytes_per_pixel(c->op.op == EP_TV_OP_IDENTITY);
   else if (c->lik)
     bpu = likelihood_bytes_per_unit(c->lik, kernel);
+  if (kernel == EP_TV_K_CS && c->n > 0) bpu /= (double)c->n;  // FP64 flops per pixel
   if (ms) *ms = c->tracer.ms[kernel];
   if (launches) *launches = c->tracer.launches[kernel];
   if (units) *units = u;

@@ -1079,6 +1079,7 @@ inline int grid1d(long long n) {
 }  // namespace
 
 struct LikelihoodState {
+  CsState* cs = nullptr;    // dense operator: everything below is unused
   ConvDesc c;
   int S = 0, R = 0;
   float inv_xi = 0.f;
@@ -1237,6 +1238,17 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
                                float* mu0) {
   *out = nullptr;
   const ep_tv_operator* op = cfg.op;
+  if (op->op == EP_TV_OP_DENSE) {
+    LikelihoodState* L = new (std::nothrow) LikelihoodState();
+    if (!L) return EP_TV_ERR_NOMEM;
+    ep_tv_status st = cs_create(cfg, s, &L->cs, mu0);
+    if (st != EP_TV_OK) {
+      delete L;
+      return st;
+    }
+    *out = L;
+    return EP_TV_OK;
+  }
   if (op->op != EP_TV_OP_CONV_PERIODIC) return EP_TV_ERR_UNSUPPORTED;
   if (op->kh > 2 * kMaxHalf / 2 + 1 || op->kw > 2 * kMaxHalf / 2 + 1) return EP_TV_ERR_UNSUPPORTED;
   LikelihoodState* L = new (std::nothrow) LikelihoodState();
@@ -1473,6 +1485,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
 
 void likelihood_destroy(LikelihoodState* L) {
   if (!L) return;
+  if (L->cs) cs_destroy(L->cs);
   cudaFree(L->d_k);
   cudaFree(L->d_g);
   cudaFree(L->Hty);
@@ -1508,6 +1521,7 @@ void likelihood_destroy(LikelihoodState* L) {
 }
 
 ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s) {
+  if (L->cs) return EP_TV_OK;
   if (cudaMemsetAsync(L->X, 0, sizeof(double) * L->R * L->c.N, s) != cudaSuccess) return EP_TV_ERR_CUDA;
   L->last_iters = 0;
   return EP_TV_OK;
@@ -1515,7 +1529,7 @@ ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s) {
 
 ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const float* eps2,
                                    int n_samples, cudaStream_t s) {
-  if (n_samples != L->S) return EP_TV_ERR_ARG;
+  if (L->cs || n_samples != L->S) return EP_TV_ERR_ARG;
   const long long N = L->c.N;
   if (cudaMemcpyAsync(L->E1, eps1, sizeof(float) * L->S * N, cudaMemcpyDeviceToDevice, s) !=
           cudaSuccess ||
@@ -1528,6 +1542,7 @@ ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const 
 ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const float* tp,
                                const float* np, unsigned* status, unsigned long long* counters,
                                Tracer* tr, cudaStream_t s) {
+  if (L->cs) return cs_update(L->cs, tau, nu, tp, np, status, counters, tr, s);
   const ConvDesc& c = L->c;
   const long long N = c.N;
   prep_kernel<<<L->prep_blocks, kThreads, 0, s>>>(tp, np, N, c.g0_xi, L->D, L->Ncav, L->Minv,
@@ -1626,6 +1641,7 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
 }
 
 double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
+  if (L->cs) return kernel == EP_TV_K_CS ? cs_flops(L->cs) : 0.0;
   switch (kernel) {
     case EP_TV_K_CG_DIRECTION: return 16.0;  // read r, p; write p, q (per system pixel)
     case EP_TV_K_CG_UPDATE: return 24.0;     // read x, r, p, q; write x, r
@@ -1650,10 +1666,12 @@ void likelihood_report(const LikelihoodState* L, int* outer, double* relres_mean
 }
 
 size_t likelihood_state_bytes(const LikelihoodState* L) {
+  if (L->cs) return 0;
   return sizeof(double) * (size_t)L->R * L->c.N;
 }
 
 ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_t s) {
+  if (L->cs) return EP_TV_OK;
   return cudaMemcpyAsync(host, L->X, likelihood_state_bytes(L), cudaMemcpyDeviceToHost, s) ==
                  cudaSuccess
              ? EP_TV_OK
@@ -1661,6 +1679,7 @@ ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_
 }
 
 ep_tv_status likelihood_state_import(LikelihoodState* L, const void* host, cudaStream_t s) {
+  if (L->cs) return EP_TV_OK;
   return cudaMemcpyAsync(L->X, host, likelihood_state_bytes(L), cudaMemcpyHostToDevice, s) ==
                  cudaSuccess
              ? EP_TV_OK

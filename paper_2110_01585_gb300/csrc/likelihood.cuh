@@ -47,4 +47,12 @@ size_t likelihood_state_bytes(const LikelihoodState* L);
 ep_tv_status likelihood_state_export(LikelihoodState* L, void* host, cudaStream_t s);
 ep_tv_status likelihood_state_import(LikelihoodState* L, const void* host, cudaStream_t s);
 
+// Dense sensing matrix (compressive sensing): Woodbury form in FP64 (cs.cu).
+struct CsState;
+ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** out, float* mu0);
+void cs_destroy(CsState* S);
+ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, const float* np,
+                       unsigned* status, unsigned long long* counters, Tracer* tr, cudaStream_t s);
+double cs_flops(const CsState* S);  // FP64 flops of one update
+
 }  // namespace eptv
