@@ -541,7 +541,7 @@ struct ep_tv_batch {
   BatchItem* h_items[2] = {nullptr, nullptr};
   cudaEvent_t items_ev[2] = {nullptr, nullptr};
   int slot = 0;
-  int total_blocks = 0;
+  long long total_units = 0;             // prior-sweep work units of all images
   std::vector<int> lik;                 // contexts with a likelihood state
   std::vector<cudaStream_t> wstream;    // one worker stream per such context
   std::vector<cudaEvent_t> wdone;
@@ -622,7 +622,7 @@ ep_tv_status ep_tv_batch_create(int32_t n, ep_tv_ctx* const* ctxs, ep_tv_batch**
   b->stream = ctxs[0]->stream;
   b->device = ctxs[0]->device;
   for (int i = 0; i < n; ++i) {
-    b->total_blocks += prior_sweep_blocks(ctxs[i]->height, ctxs[i]->width);
+    b->total_units += prior_sweep_blocks(ctxs[i]->height, ctxs[i]->width);
     if (ctxs[i]->lik) b->lik.push_back(i);
   }
   bool ok = true;
@@ -660,19 +660,20 @@ ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_ever
     // image table of this sweep (prior buffers alternate per context)
     CK(cudaEventSynchronize(b->items_ev[b->slot]));
     BatchItem* h = b->h_items[b->slot];
-    int block = 0;
+    long long unit = 0;
     for (int i = 0; i < n; ++i) {
       ep_tv_ctx* c = b->ctx[i];
       h[i].a = sweep_args(c, 0x4321);
+      prior_sweep_prepare(h[i].a);
       h[i].site0_from_y = c->op.op == EP_TV_OP_IDENTITY;
-      h[i].tiles_x = prior_sweep_tiles_x(c->width);
-      h[i].block_begin = block;
-      block += prior_sweep_blocks(c->height, c->width);
+      h[i].units = prior_sweep_blocks(c->height, c->width);
+      h[i].unit_begin = unit;
+      unit += h[i].units;
     }
     CK(cudaMemcpyAsync(b->d_items[b->slot], h, sizeof(BatchItem) * n, cudaMemcpyHostToDevice,
                        b->stream));
     CK(cudaEventRecord(b->items_ev[b->slot], b->stream));
-    launch_prior_sweep_batch(b->d_items[b->slot], n, b->total_blocks, b->stream);
+    launch_prior_sweep_batch(b->d_items[b->slot], n, b->total_units, b->stream);
     b->slot ^= 1;
     for (ep_tv_ctx* c : b->ctx) {
       c->cur ^= 1;

@@ -105,7 +105,8 @@ struct SweepArgs {
   const double* beta;         // device scalar
   int order;                  // four 4-bit k values, first update in the low nibble
   int fp64_tail;              // 1: recompute poorly conditioned edges in FP64
-  double* abar_partial;       // one FP64 partial sum of E|u| per block
+  double* abar_partial;       // one FP64 partial sum of E|u| per work unit
+  int vec2;                   // set by prior_sweep_prepare: float2 loads and stores allowed
   unsigned* status;
   unsigned long long* counters;
 };
@@ -114,17 +115,19 @@ struct SweepArgs {
 struct BatchItem {
   SweepArgs a;
   int site0_from_y;
-  int tiles_x;
-  int block_begin;   // first block of this image in the launch
+  long long units;        // work units of this image
+  long long unit_begin;   // first unit of this image in the launch
 };
 
 // Prior-site sweep over V_1..V_4 for one image; site 0 implicit (identity) or stored.
 void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s);
 // Algorithmic DRAM bytes per pixel of one prior-site pass.
 double prior_sweep_bytes_per_pixel(bool site0_from_y);
+// Fills the fields of `a` that the launch derives (vector access).
+void prior_sweep_prepare(SweepArgs& a);
+// Work units (and E|u| partial sums) of one image's prior-site pass.
 int prior_sweep_blocks(int height, int width);
-int prior_sweep_tiles_x(int width);
-void launch_prior_sweep_batch(const BatchItem* items, int n_items, int total_blocks,
+void launch_prior_sweep_batch(const BatchItem* items, int n_items, long long total_units,
                               cudaStream_t s);
 
 // abar = sum(partials) in a fixed order; if do_em, beta = n / abar.

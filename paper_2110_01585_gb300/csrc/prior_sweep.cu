@@ -11,247 +11,670 @@
 //   V3 vertical   (2b,c)-(2b+1,c)   V4 vertical   (2b+1,c)-(2b+2 mod H,c)
 // The free boundary drops the wrap-around edges.
 //
-// The prior-site planes are read from one buffer and written to another: a
-// tile's halo belongs to neighbouring tiles, which may already have written
-// their results when it is staged.
+// Streaming schedule.  A warp owns a strip of 60 columns and walks down it one
+// row pair (2b, 2b+1) at a time; lane l holds columns 2l-2 and 2l-1 of the
+// strip (lanes 0 and 31 are the 2-column halo), all five sites of those four
+// pixels in registers.  V1 is then inside a lane, V2 pairs a lane's right column
+// with the next lane's left column (warp shuffles), V3 is inside a row pair and
+// V4 joins the last row of one pair with the first row of the next.  For any
+// order of V1..V4, a row pair can take every update ordered before V4 as soon as
+// it is loaded; V4 then joins it to the previous pair, which takes the updates
+// ordered after V4 and is final.  A sweep reads each site plane once and writes
+// each prior-site plane once, plus one halo pair per chunk of rows and the
+// 2-column strip halo; there is no shared memory and no block barrier.
 //
-// Temporal blocking: a CTA owns a TH x TW tile and stages a (TH+4) x (TW+4)
-// region (2-pixel halo) of all ten site planes in shared memory.  Each of the
-// two horizontal updates can spoil at most one halo column per side, each of
-// the vertical ones one halo row, so after any order of V1..V4 the tile itself
-// holds exactly the values a one-update-per-launch schedule would produce.  The
-// sweep therefore reads every site plane once and writes the four prior-site
-// planes once: 36 B read + 32 B written per pixel for denoising, where site 0 is
-// (1/xi, y/xi) and only y is read.
+// Work units are 16 row pairs of one strip.  A persistent grid of warps takes
+// contiguous ranges of units (images of a batch laid end to end), so one launch
+// serves any number of images.  The E|u| sum of each unit is reduced in FP64 in
+// a fixed order and stored in its own slot, which makes the result independent
+// of how units are spread over warps.
 //
-// Arithmetic: FP32 with the cancellation-free forms of tilted.cuh; the new
-// precision uses tau_i = rho / (c_j + q c_i), which equals 1/Var_i - 1/c_i of
-// Eq. update_qk_x (q = Sbar / s^2, rho = 1 - q) without subtracting.  Edges with
-// lam * s < 1e-3 (where rho is a small difference of O(1) numbers) are redone in
-// FP64 when fp64_tail is set.
+// Arithmetic: FP32 with the cancellation-free forms below; the new precision
+// uses tau_i = rho / (c_j + q c_i), which equals 1/Var_i - 1/c_i of Eq. update_qk_x
+// (q = Sbar / s^2, rho = 1 - q) without subtracting.  Edges with lam * s < 1e-3
+// (where rho is a small difference of O(1) numbers) are redone in FP64 when
+// fp64_tail is set.
+#include <mutex>
+
 #include "internal.cuh"
+#include "mills_poly.cuh"
 #include "tilted.cuh"
 
 namespace eptv {
 
 namespace {
 
-constexpr int kTH = 16;
-constexpr int kTW = 64;
-constexpr int kThreads = 256;
-constexpr int kRH = kTH + 4;
-constexpr int kRW = kTW + 4;
-constexpr int kRN = kRH * kRW;
-constexpr int kPlanes = 10;  // tau0..tau4, nu0..nu4
-constexpr size_t kSmemBytes = size_t(kPlanes) * kRN * sizeof(float);
+constexpr int kStripCols = 60;     // owned columns per warp (lanes 1..30, two each)
+constexpr int kStepsPerUnit = 16;  // row-pair steps per work unit
+constexpr int kWarpsPerBlock = 4;
+constexpr int kThreads = 32 * kWarpsPerBlock;
+constexpr int kMinBlocks = 3;      // blocks per SM the register budget is sized for
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
-// One tile (bx, by) of one image; `part` indexes its a_u partial sum.
+// ------------------------------------------------------------ tilted moments
+//
+// Sec. III-C, Eq. marginal_tilted_un: for an edge with cavity means m_i, m_j and
+// variances c_i, c_j, the tilted law of u = x_i - x_j is N(u; mu, s^2) exp(-lam|u|),
+// mu = m_i - m_j, s^2 = c_i + c_j: two Gaussians truncated at zero.  In standard
+// units z = mu / s, l = lam s, a+ = l - z, a- = l + z; for a standard normal
+// truncated to [a, inf) let h(a) be the inverse Mills ratio, g = h - a its mean
+// offset and v = 1 - h g its variance.  The half weights are w+ = h- / (h+ + h-),
+// w- = h+ / (h+ + h-) (the erfcx factors of each half are sqrt(2/pi) / h), and
+//   d   = (ubar - mu) / s^2 = [w+ (h+ - l) - w- (h- - l)] / s
+//   q   = Sbar / s^2        = w+ v+ + w- v- + w+ w- (g+ + g-)^2
+//   rho = 1 - q             = w+ h+ g+ + w- h- g- - w+ w- (g+ + g-)^2
+//   eab = E|u|              = s (w+ g+ + w- g-)
+// g and v for a >= 0 come from the polynomial fits of mills_poly.cuh (about
+// 3e-7 relative), so no erfcx is evaluated; for a = -b < 0 the reflection
+// Q(-b) = 1 - Q(b) of the upper tail Q gives h(a) = phi(b) h(b) / (h(b) - phi(b)).
+
+struct Mills {
+  float h, g, v;
+};
+
+__device__ __forceinline__ Mills mills_fast(float a) {
+  const float b = fabsf(a);
+  const float r = rcp_approx(kMillsK + b);
+  const float u = (kMillsK - b) * r;
+  const float kr = kMillsK * r;
+  Mills m;
+  m.g = mills_G(u) * kr;
+  m.v = mills_V(u) * kr * kr;
+  m.h = m.g + b;
+  if (a < 0.0f) {
+    const float phi = 0.398942280f * __expf(-0.5f * b * b);
+    const float h = phi * m.h * rcp_approx(m.h - phi);  // h(b) - phi(b) >= 0.4
+    m.h = h;
+    m.g = h + b;
+    m.v = 1.0f - h * m.g;
+  }
+  return m;
+}
+
+struct Moments {
+  float d, q, rho, eab;
+};
+
+__device__ __forceinline__ Moments tilted_fast(float mu, float s2, float lam) {
+  const float rs = rsqrtf(s2);
+  const float s = s2 * rs;
+  const float z = mu * rs;
+  const float l = lam * s;
+  const Mills p = mills_fast(l - z);
+  const Mills m = mills_fast(l + z);
+  const float inv = rcp_approx(p.h + m.h);  // a+ + a- = 2 l >= 0: not both h vanish
+  const float wp = m.h * inv, wm = p.h * inv;
+  Moments o;
+  o.d = (wp * (p.h - l) - wm * (m.h - l)) * rs;
+  const float gs = p.g + m.g;
+  const float mix = wp * wm * gs * gs;
+  o.q = wp * p.v + wm * m.v + mix;
+  o.rho = wp * p.h * p.g + wm * m.h * m.g - mix;
+  o.eab = s * (wp * p.g + wm * m.g);
+  return o;
+}
+
+// The same moments in FP64 from the cavity natural parameters (rare; kept out of
+// line so that the streaming loop stays small).
+__device__ __noinline__ Moments tilted_fp64(float ti, float ni, float tj, float nj, double lam) {
+  const double ci = 1.0 / (double)ti, cj = 1.0 / (double)tj;
+  const double mu = (double)ni * ci - (double)nj * cj;
+  const TiltedOut<double> od = laplace_tilted<double>(mu, ci + cj, lam);
+  Moments o;
+  o.d = (float)od.d;
+  o.q = (float)od.q;
+  o.rho = (float)od.rho;
+  o.eab = (float)od.eab;
+  return o;
+}
+
+// ------------------------------------------------------------------ state
+
+struct Px {
+  float t[5];  // site precisions, t[0] = likelihood site
+  float n[5];  // site precision-times-means
+};
+
+struct Row {
+  Px x[2];  // the lane's two columns
+  bool ok;  // the row exists (always, on the torus)
+};
+
+struct Ctx {
+  float lam, min_tau, damp, keep;
+  double lam_d;
+  bool tail;
+  float eab;  // E|u| of the counted edges of this lane since the last flush
+  unsigned n_fp64, n_capped;
+  bool bad;
+};
+
+// Geometry of one lane: which of its pixels exist and which it owns.
+struct Lane {
+  int lane;
+  bool col_ok[2];  // column exists (always, on the torus)
+  bool right_ok;   // the next lane's left column exists
+  bool own_col;    // the lane owns its columns (lanes 1..30, inside the image)
+};
+
+template <int K>
+__device__ __forceinline__ void cavity(const Px& x, float& ct, float& cn) {
+  ct = 0.0f;
+  cn = 0.0f;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (s == K) continue;
+    ct += x.t[s];
+    cn += x.n[s];
+  }
+}
+
+// One edge of the current update: cavities of site k at both endpoints in, the
+// new (capped, undamped) site k at both endpoints out.
+struct Edge {
+  float ti, ni, tj, nj;
+  bool valid, count;
+  float tni, nni, tnj, nnj;
+};
+
+__device__ __noinline__ Moments tilted_fast_ool(float mu, float s2, float lam) {
+  return tilted_fast(mu, s2, lam);
+}
+
+// Eq. update_qk_x from the tilted moments: tau = rho / (c_j + q c_i), the variance
+// cap, then nu = tau E + (E - m) / c.
+__device__ __forceinline__ void edge_finish(Ctx& c, Edge& e, float ci, float cj, float mi, float mj,
+                                            const Moments& o) {
+  const bool cnt = e.valid && e.count;
+  float tni = o.rho * rcp_approx(cj + o.q * ci);
+  float tnj = o.rho * rcp_approx(ci + o.q * cj);
+  if (!(tni >= c.min_tau)) {
+    tni = c.min_tau;
+    c.n_capped += cnt;
+  }
+  if (!(tnj >= c.min_tau)) {
+    tnj = c.min_tau;
+    c.n_capped += cnt;
+  }
+  e.tni = tni;
+  e.tnj = tnj;
+  e.nni = tni * (mi + ci * o.d) + o.d;
+  e.nnj = tnj * (mj - cj * o.d) - o.d;
+  if (cnt) c.eab += o.eab;
+}
+
+// The two independent edges of one update step, in straight-line code; the FP64
+// moments only when some lane of the warp needs them.
+__device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
+  const float ci0 = rcp_approx(e0.ti), cj0 = rcp_approx(e0.tj);
+  const float ci1 = rcp_approx(e1.ti), cj1 = rcp_approx(e1.tj);
+  const float mi0 = e0.ni * ci0, mj0 = e0.nj * cj0;
+  const float mi1 = e1.ni * ci1, mj1 = e1.nj * cj1;
+  const float s20 = ci0 + cj0, s21 = ci1 + cj1;
+  const float l2 = c.lam * c.lam;
+  const bool t0 = c.tail && e0.valid && l2 * s20 < 1e-6f;
+  const bool t1 = c.tail && e1.valid && l2 * s21 < 1e-6f;
+  Moments o0, o1;
+  if (__any_sync(0xffffffffu, t0 || t1)) {
+    o0 = t0 ? tilted_fp64(e0.ti, e0.ni, e0.tj, e0.nj, c.lam_d) : tilted_fast_ool(mi0 - mj0, s20, c.lam);
+    o1 = t1 ? tilted_fp64(e1.ti, e1.ni, e1.tj, e1.nj, c.lam_d) : tilted_fast_ool(mi1 - mj1, s21, c.lam);
+    c.n_fp64 += (t0 && e0.count) + (t1 && e1.count);
+  } else {
+    o0 = tilted_fast(mi0 - mj0, s20, c.lam);
+    o1 = tilted_fast(mi1 - mj1, s21, c.lam);
+  }
+  edge_finish(c, e0, ci0, cj0, mi0, mj0, o0);
+  edge_finish(c, e1, ci1, cj1, mi1, mj1, o1);
+}
+
+template <int K>
+__device__ __forceinline__ void damp_into(const Ctx& c, Px& x, bool valid, float tn, float nn) {
+  if (valid) {
+    x.t[K] = c.damp * tn + c.keep * x.t[K];
+    x.n[K] = c.damp * nn + c.keep * x.n[K];
+  }
+}
+
+// V1 on two rows: the edge (2a, 2a+1) inside the lane.
+__device__ __forceinline__ void hstep1(Ctx& c, const Lane& L, Row& a, Row& b, bool cnt_a,
+                                       bool cnt_b) {
+  Edge e0, e1;
+  cavity<1>(a.x[0], e0.ti, e0.ni);
+  cavity<1>(a.x[1], e0.tj, e0.nj);
+  cavity<1>(b.x[0], e1.ti, e1.ni);
+  cavity<1>(b.x[1], e1.tj, e1.nj);
+  const bool cols = L.col_ok[0] && L.col_ok[1];
+  e0.valid = a.ok && cols;
+  e1.valid = b.ok && cols;
+  e0.count = cnt_a && L.own_col;
+  e1.count = cnt_b && L.own_col;
+  edges2(c, e0, e1);
+  damp_into<1>(c, a.x[0], e0.valid, e0.tni, e0.nni);
+  damp_into<1>(c, a.x[1], e0.valid, e0.tnj, e0.nnj);
+  damp_into<1>(c, b.x[0], e1.valid, e1.tni, e1.nni);
+  damp_into<1>(c, b.x[1], e1.valid, e1.tnj, e1.nnj);
+}
+
+// V2 on two rows: the edge (2a+1, 2a+2) from a lane's right column to the next
+// lane's left column; the lane on the left computes it and hands back the
+// partner's new site.
+__device__ __forceinline__ void hstep2(Ctx& c, const Lane& L, Row& a, Row& b, bool cnt_a,
+                                       bool cnt_b) {
+  Edge e0, e1;
+  float tla, nla, tlb, nlb;
+  cavity<2>(a.x[0], tla, nla);
+  cavity<2>(a.x[1], e0.ti, e0.ni);
+  cavity<2>(b.x[0], tlb, nlb);
+  cavity<2>(b.x[1], e1.ti, e1.ni);
+  e0.tj = __shfl_down_sync(0xffffffffu, tla, 1);
+  e0.nj = __shfl_down_sync(0xffffffffu, nla, 1);
+  e1.tj = __shfl_down_sync(0xffffffffu, tlb, 1);
+  e1.nj = __shfl_down_sync(0xffffffffu, nlb, 1);
+  const bool cols = L.col_ok[1] && L.right_ok && L.lane < 31;
+  e0.valid = a.ok && cols;
+  e1.valid = b.ok && cols;
+  e0.count = cnt_a && L.own_col;
+  e1.count = cnt_b && L.own_col;
+  edges2(c, e0, e1);
+  const float rta = __shfl_up_sync(0xffffffffu, e0.tnj, 1);
+  const float rna = __shfl_up_sync(0xffffffffu, e0.nnj, 1);
+  const float rtb = __shfl_up_sync(0xffffffffu, e1.tnj, 1);
+  const float rnb = __shfl_up_sync(0xffffffffu, e1.nnj, 1);
+  const unsigned va = __shfl_up_sync(0xffffffffu, e0.valid ? 1u : 0u, 1);
+  const unsigned vb = __shfl_up_sync(0xffffffffu, e1.valid ? 1u : 0u, 1);
+  damp_into<2>(c, a.x[1], e0.valid, e0.tni, e0.nni);
+  damp_into<2>(c, b.x[1], e1.valid, e1.tni, e1.nni);
+  damp_into<2>(c, a.x[0], va && L.lane > 0, rta, rna);
+  damp_into<2>(c, b.x[0], vb && L.lane > 0, rtb, rnb);
+}
+
+// V3 or V4 between two vertically adjacent rows (top holds the first pixel of
+// each edge), both columns of the lane.
+template <int K>
+__device__ __forceinline__ void vstep(Ctx& c, const Lane& L, Row& top, Row& bot, bool cnt) {
+  Edge e0, e1;
+  cavity<K>(top.x[0], e0.ti, e0.ni);
+  cavity<K>(bot.x[0], e0.tj, e0.nj);
+  cavity<K>(top.x[1], e1.ti, e1.ni);
+  cavity<K>(bot.x[1], e1.tj, e1.nj);
+  const bool rows = top.ok && bot.ok;
+  e0.valid = rows && L.col_ok[0];
+  e1.valid = rows && L.col_ok[1];
+  e0.count = cnt && L.own_col;
+  e1.count = cnt && L.own_col;
+  edges2(c, e0, e1);
+  damp_into<K>(c, top.x[0], e0.valid, e0.tni, e0.nni);
+  damp_into<K>(c, bot.x[0], e0.valid, e0.tnj, e0.nnj);
+  damp_into<K>(c, top.x[1], e1.valid, e1.tni, e1.nni);
+  damp_into<K>(c, bot.x[1], e1.valid, e1.tnj, e1.nnj);
+}
+
+// Row staging.  Each lane copies its own two pixels of every site plane of the
+// next row pair into shared memory with cp.async while it computes on the
+// current pair; a warp owns kSlots pair slots of [plane][row][lane] float2.
+constexpr int kSlots = 2;
+constexpr int kMaxPlanes = 10;
+constexpr int kSlotFloats2 = kMaxPlanes * 2 * 32;
+constexpr size_t kSmemPerWarp = size_t(kSlots) * kSlotFloats2 * sizeof(float2);
+constexpr size_t kSmemBytes = kSmemPerWarp * kWarpsPerBlock;
+
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, bool fill) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int src_size = fill ? bytes : 0;  // 0: write zeros, read nothing
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_size));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_size));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Source planes of the pass: site 0 (y, or tau0 and nu0), then tau1..4, nu1..4.
 template <bool kSite0FromY>
-__device__ __forceinline__ void prior_tile(const SweepArgs& a, int bx, int by, int part,
-                                           float* smem) {
-  float* sT = smem;             // [5][kRN]
-  float* sV = smem + 5 * kRN;   // [5][kRN]
-  const int H = a.height, W = a.width;
+__device__ __forceinline__ const float* plane_ptr(const SweepArgs& a, int q) {
+  if (kSite0FromY) {
+    if (q == 0) return a.y;
+    q -= 1;
+  } else {
+    if (q == 0) return a.tau0;
+    if (q == 1) return a.nu0;
+    q -= 2;
+  }
+  return q < 4 ? a.tin + q * a.n : a.nin + (q - 4) * a.n;
+}
+
+// Issues the copies of image row `gr` (wrapped on the torus) into row slot `r`
+// of pair slot `slot`; returns whether the row exists.
+template <bool kSite0FromY>
+__device__ __forceinline__ bool issue_row(const SweepArgs& a, const Lane& L, const int (&gcol)[2],
+                                          int gr, float2* stage, int slot, int r) {
+  constexpr int kPlanes = kSite0FromY ? 9 : 10;
+  bool ok;
+  if (a.periodic) {
+    gr = wrap(gr, a.height);
+    ok = true;
+  } else {
+    ok = gr >= 0 && gr < a.height;
+  }
+  const long long base = ok ? (long long)gr * a.width : 0;
+  float2* dst = stage + slot * kSlotFloats2 + r * 32 + L.lane;
+  if (a.vec2) {
+    const bool fill = ok && L.col_ok[0];
+    const long long p = fill ? base + gcol[0] : 0;
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) cp_async(dst + q * 64, plane_ptr<kSite0FromY>(a, q) + p, 8, fill);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool fill = ok && L.col_ok[k];
+      const long long p = fill ? base + gcol[k] : 0;
+#pragma unroll
+      for (int q = 0; q < kPlanes; ++q)
+        cp_async(reinterpret_cast<float*>(dst + q * 64) + k, plane_ptr<kSite0FromY>(a, q) + p, 4, fill);
+    }
+  }
+  return ok;
+}
+
+// Reads a staged row into registers (missing pixels read as zeros and are never
+// the endpoint of a valid edge).
+template <bool kSite0FromY>
+__device__ __forceinline__ void read_row(const SweepArgs& a, const Lane& L, const float2* stage,
+                                         int slot, int r, bool ok, Row& R) {
+  const float2* src = stage + slot * kSlotFloats2 + r * 32 + L.lane;
+  R.ok = ok;
+  int q = 0;
+  if (kSite0FromY) {
+    const float2 y = src[0];
+    R.x[0].t[0] = a.inv_xi;
+    R.x[1].t[0] = a.inv_xi;
+    R.x[0].n[0] = y.x * a.inv_xi;
+    R.x[1].n[0] = y.y * a.inv_xi;
+    q = 1;
+  } else {
+    const float2 t = src[0], n = src[64];
+    R.x[0].t[0] = t.x;
+    R.x[1].t[0] = t.y;
+    R.x[0].n[0] = n.x;
+    R.x[1].n[0] = n.y;
+    q = 2;
+  }
+#pragma unroll
+  for (int s = 1; s < 5; ++s) {
+    const float2 t = src[(q + s - 1) * 64];
+    const float2 n = src[(q + 4 + s - 1) * 64];
+    R.x[0].t[s] = t.x;
+    R.x[1].t[s] = t.y;
+    R.x[0].n[s] = n.x;
+    R.x[1].n[s] = n.y;
+  }
+}
+
+// Stores a final row (rows outside [0, H) are copies or do not exist).
+__device__ __forceinline__ void store_row(const SweepArgs& a, Ctx& c, const Lane& L,
+                                          const int (&gcol)[2], int gr, const Row& R) {
+  if (!L.own_col || gr < 0 || gr >= a.height) return;
   const long long N = a.n;
-  const int r0 = by * kTH;
-  const int c0 = bx * kTW;
-  const int tid = threadIdx.x;
-
-  // ---- stage the region (positions outside a free-boundary image stay unused)
-  for (int idx = tid; idx < kRN; idx += kThreads) {
-    const int rr = idx / kRW, cc = idx - rr * kRW;
-    int gr = r0 - 2 + rr, gc = c0 - 2 + cc;
-    bool present = true;
-    if (a.periodic) {
-      gr = wrap(gr, H);
-      gc = wrap(gc, W);
-    } else {
-      present = gr >= 0 && gr < H && gc >= 0 && gc < W;
-    }
-    if (present) {
-      const long long p = (long long)gr * W + gc;
-      if (kSite0FromY) {
-        sT[idx] = a.inv_xi;
-        sV[idx] = a.y[p] * a.inv_xi;
-      } else {
-        sT[idx] = a.tau0[p];
-        sV[idx] = a.nu0[p];
-      }
-#pragma unroll
-      for (int s = 1; s < 5; ++s) {
-        sT[s * kRN + idx] = a.tin[(s - 1) * N + p];
-        sV[s * kRN + idx] = a.nin[(s - 1) * N + p];
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < 5; ++s) {
-        sT[s * kRN + idx] = 1.0f;
-        sV[s * kRN + idx] = 0.0f;
-      }
-    }
-  }
-  __syncthreads();
-
-  const float lam = (float)(*a.beta);
-  const double lam_d = *a.beta;
-  const float damp = a.damping, keep = 1.0f - a.damping;
-  float eab_acc = 0.0f;
-  unsigned n_fp64 = 0, n_capped = 0;
-  bool bad = false;
-
-  for (int t = 0; t < 4; ++t) {
-    const int k = (a.order >> (4 * t)) & 0xF;
-    const bool horiz = k <= 2;
-    const int parity = (k == 1 || k == 3) ? 0 : 1;
-    // edges (i, i + step) whose first endpoint has the given parity along the axis
-    const int along = horiz ? kRW : kRH;
-    const int across = horiz ? kRH : kRW;
-    const int per_line = (along - parity) / 2;
-    const int total = per_line * across;
-    for (int e = tid; e < total; e += kThreads) {
-      int line, pos;
-      if (horiz) {
-        line = e / per_line;
-        pos = parity + 2 * (e - line * per_line);
-      } else {
-        // consecutive threads take consecutive columns (conflict-free smem)
-        line = e % across;
-        pos = parity + 2 * (e / across);
-      }
-      const int rr = horiz ? line : pos;
-      const int cc = horiz ? pos : line;
-      const int i = rr * kRW + cc;
-      const int j = horiz ? i + 1 : i + kRW;
-      // global coordinates of both endpoints (before wrapping)
-      const int gri = r0 - 2 + rr, gci = c0 - 2 + cc;
-      const int grj = horiz ? gri : gri + 1, gcj = horiz ? gci + 1 : gci;
-      if (!a.periodic) {
-        if (gri < 0 || gci < 0 || grj >= H || gcj >= W) continue;
-      }
-      // cavity of site k: sum of the other four sites
-      float ti = 0.f, ni = 0.f, tj = 0.f, nj = 0.f;
-#pragma unroll
-      for (int s = 0; s < 5; ++s) {
-        if (s == k) continue;
-        ti += sT[s * kRN + i];
-        ni += sV[s * kRN + i];
-        tj += sT[s * kRN + j];
-        nj += sV[s * kRN + j];
-      }
-      const float ci = __frcp_rn(ti), cj = __frcp_rn(tj);
-      const float mi = ni * ci, mj = nj * cj;
-      const float mu = mi - mj;
-      const float s2 = ci + cj;
-      // a_u and the counters take each edge once, from the tile owning its first pixel
-      const bool owned = rr >= 2 && rr < 2 + kTH && cc >= 2 && cc < 2 + kTW && gri < H && gci < W;
-      float d, q, rho, eab;
-      const bool tail = a.fp64_tail && lam > 0.0f && (lam * sqrtf(s2) < 1e-3f);
-      if (tail) {
-        const double ci_d = 1.0 / (double)ti, cj_d = 1.0 / (double)tj;
-        const double mu_d = (double)ni * ci_d - (double)nj * cj_d;
-        TiltedOut<double> od = laplace_tilted<double>(mu_d, ci_d + cj_d, lam_d);
-        d = (float)od.d;
-        q = (float)od.q;
-        rho = (float)od.rho;
-        eab = (float)od.eab;
-        n_fp64 += owned;
-      } else {
-        TiltedOut<float> o = laplace_tilted<float>(mu, s2, lam);
-        d = o.d;
-        q = o.q;
-        rho = o.rho;
-        eab = o.eab;
-      }
-      // Eq. update_qk_x: tau = 1/Var - 1/c, Var from the projection; cap, then mean
-      float tni = rho * __frcp_rn(cj + q * ci);
-      float tnj = rho * __frcp_rn(ci + q * cj);
-      if (!(tni >= a.min_tau)) { tni = a.min_tau; n_capped += owned; }
-      if (!(tnj >= a.min_tau)) { tnj = a.min_tau; n_capped += owned; }
-      const float Ei = mi + ci * d;
-      const float Ej = mj - cj * d;
-      const float nni = tni * Ei + d;   // tau E + (E - m) / c
-      const float nnj = tnj * Ej - d;
-      float* Tk = sT + k * kRN;
-      float* Vk = sV + k * kRN;
-      const float ti_new = damp * tni + keep * Tk[i];
-      const float tj_new = damp * tnj + keep * Tk[j];
-      const float vi_new = damp * nni + keep * Vk[i];
-      const float vj_new = damp * nnj + keep * Vk[j];
-      Tk[i] = ti_new;
-      Tk[j] = tj_new;
-      Vk[i] = vi_new;
-      Vk[j] = vj_new;
-      bad |= !(isfinite(ti_new) && isfinite(tj_new) && isfinite(vi_new) && isfinite(vj_new));
-      if (owned) eab_acc += eab;
-    }
-    __syncthreads();
-  }
-
-  // ---- write the tile's four prior-site planes
-  for (int idx = tid; idx < kTH * kTW; idx += kThreads) {
-    const int tr = idx / kTW, tc = idx - tr * kTW;
-    const int gr = r0 + tr, gc = c0 + tc;
-    if (gr >= H || gc >= W) continue;
-    const long long p = (long long)gr * W + gc;
-    const int sidx = (tr + 2) * kRW + tc + 2;
+  const long long base = (long long)gr * a.width;
+  float sum = 0.0f;
+  if (a.vec2) {
+    const long long p = base + gcol[0];
 #pragma unroll
     for (int s = 1; s < 5; ++s) {
-      a.tout[(s - 1) * N + p] = sT[s * kRN + sidx];
-      a.nout[(s - 1) * N + p] = sV[s * kRN + sidx];
+      *reinterpret_cast<float2*>(a.tout + (s - 1) * N + p) = make_float2(R.x[0].t[s], R.x[1].t[s]);
+      *reinterpret_cast<float2*>(a.nout + (s - 1) * N + p) = make_float2(R.x[0].n[s], R.x[1].n[s]);
+      sum += R.x[0].t[s] + R.x[1].t[s] + R.x[0].n[s] + R.x[1].n[s];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!L.col_ok[k]) continue;
+      const long long p = base + gcol[k];
+#pragma unroll
+      for (int s = 1; s < 5; ++s) {
+        a.tout[(s - 1) * N + p] = R.x[k].t[s];
+        a.nout[(s - 1) * N + p] = R.x[k].n[s];
+        sum += R.x[k].t[s] + R.x[k].n[s];
+      }
     }
   }
+  // a NaN or infinity in any stored site value makes the sum non-finite
+  c.bad |= !isfinite(sum);
+}
 
-  // ---- block partial of a_u in FP64, fixed order
-  double v = (double)eab_acc;
+// Warp sum of the lanes' E|u| in FP64 (fixed tree), stored in the unit's slot.
+__device__ __forceinline__ void flush_unit(const SweepArgs& a, float lane_sum, long long unit) {
+  double v = (double)lane_sum;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  __shared__ double red[kThreads / 32];
-  __shared__ unsigned red_cnt[2];
-  if (tid == 0) { red_cnt[0] = 0; red_cnt[1] = 0; }
-  __syncthreads();
-  if ((tid & 31) == 0) red[tid >> 5] = v;
-  if (n_fp64) atomicAdd(&red_cnt[0], n_fp64);
-  if (n_capped) atomicAdd(&red_cnt[1], n_capped);
-  if (bad) atomicOr(a.status, ST_NONFINITE);
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
-    a.abar_partial[part] = s;
-    if (red_cnt[0]) atomicAdd(&a.counters[DC_FP64], (unsigned long long)red_cnt[0]);
-    if (red_cnt[1]) atomicAdd(&a.counters[DC_CAPPED], (unsigned long long)red_cnt[1]);
+  if ((threadIdx.x & 31) == 0) a.abar_partial[unit] = v;
+}
+
+// Steps per strip: step b finalises rows 2b - o - 1 and 2b - o (o = 0 when V4 is
+// the later vertical update of the order, 1 when V3 is); one spare step covers
+// both offsets and odd heights.
+__host__ __device__ __forceinline__ int steps_of(int height) { return (height + 1) / 2 + 1; }
+__host__ __device__ __forceinline__ int units_per_strip(int height) {
+  return (steps_of(height) + kStepsPerUnit - 1) / kStepsPerUnit;
+}
+__host__ __device__ __forceinline__ int strips_of(int width) {
+  return (width + kStripCols - 1) / kStripCols;
+}
+
+// Position of the update k in the order word.
+__device__ __forceinline__ int order_pos(int order, int k) {
+  int t = 0;
+  while (t < 3 && ((order >> (4 * t)) & 0xF) != k) ++t;
+  return t;
+}
+
+// Steps [b_lo, b_hi) of one strip.  kX is the later of V3 and V4 in the update
+// order: it joins consecutive row pairs, the other (kI) lies inside a pair.
+// Step b loads the pair of rows (2b - o, 2b - o + 1), applies the updates ordered
+// before kX to it, joins its first row to the carried last row of the previous
+// pair by kX, applies the updates ordered after kX (horizontal ones only) to
+// those two rows, which are then final, and carries its second row on.
+template <bool kSite0FromY, int kX>
+__device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, int b_hi,
+                                       long long unit_base, float2* stage) {
+  constexpr int kI = 7 - kX;
+  constexpr int kOff = kX == 4 ? 0 : 1;
+  const int W = a.width, H = a.height;
+  Lane L;
+  L.lane = threadIdx.x & 31;
+  const int gc0 = strip * kStripCols - 2 + 2 * L.lane;  // unwrapped column of the left pixel
+  int gcol[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int g = gc0 + k;
+    if (a.periodic) {
+      gcol[k] = wrap(g, W);
+      L.col_ok[k] = true;
+    } else {
+      gcol[k] = g;
+      L.col_ok[k] = g >= 0 && g < W;
+    }
+  }
+  L.right_ok = a.periodic || (gc0 + 2 >= 0 && gc0 + 2 < W);
+  L.own_col = L.lane >= 1 && L.lane <= 30 && gc0 < W;
+
+  Ctx c;
+  c.lam = (float)(*a.beta);
+  c.lam_d = *a.beta;
+  c.tail = a.fp64_tail && c.lam > 0.0f;
+  c.min_tau = a.min_tau;
+  c.damp = a.damping;
+  c.keep = 1.0f - a.damping;
+  c.eab = 0.0f;
+  c.n_fp64 = 0;
+  c.n_capped = 0;
+  c.bad = false;
+  const int order = a.order;
+  const int posX = order_pos(order, kX);
+
+  // pair b lives in slot b & 1
+  Row carry, r0, r1;
+  bool ok0, ok1, nok0, nok1;
+  {
+    const int rw = 2 * (b_lo - 1) - kOff;
+    ok0 = issue_row<kSite0FromY>(a, L, gcol, rw, stage, (b_lo - 1) & 1, 0);
+    ok1 = issue_row<kSite0FromY>(a, L, gcol, rw + 1, stage, (b_lo - 1) & 1, 1);
+    cp_async_commit();
+    nok0 = issue_row<kSite0FromY>(a, L, gcol, rw + 2, stage, b_lo & 1, 0);
+    nok1 = issue_row<kSite0FromY>(a, L, gcol, rw + 3, stage, b_lo & 1, 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    read_row<kSite0FromY>(a, L, stage, (b_lo - 1) & 1, 0, ok0, r0);
+    read_row<kSite0FromY>(a, L, stage, (b_lo - 1) & 1, 1, ok1, r1);
+  }
+  // the pair before the first step: its updates before kX give the carried row
+  for (int t = 0; t < posX; ++t) {
+    const int k = (order >> (4 * t)) & 0xF;
+    if (k == kI) vstep<kI>(c, L, r0, r1, false);
+    else if (k == 1) hstep1(c, L, r0, r1, false, false);
+    else hstep2(c, L, r0, r1, false, false);
+  }
+  carry = r1;
+  for (int b = b_lo; b < b_hi; ++b) {
+    const int row0 = 2 * b - kOff;
+    ok0 = nok0;
+    ok1 = nok1;
+    if (b + 1 < b_hi) {
+      // slot (b + 1) & 1 held pair b - 1, already read
+      nok0 = issue_row<kSite0FromY>(a, L, gcol, row0 + 2, stage, (b + 1) & 1, 0);
+      nok1 = issue_row<kSite0FromY>(a, L, gcol, row0 + 3, stage, (b + 1) & 1, 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    read_row<kSite0FromY>(a, L, stage, b & 1, 0, ok0, r0);
+    read_row<kSite0FromY>(a, L, stage, b & 1, 1, ok1, r1);
+    // an edge is counted by the step that computes it for its first pixel's row
+    // in [0, H) (rows outside are torus copies or do not exist)
+    const bool cc = row0 - 1 >= 0 && row0 - 1 < H;
+    const bool c0 = row0 >= 0 && row0 < H;
+    const bool c1 = row0 + 1 >= 0 && row0 + 1 < H;
+    for (int t = 0; t < posX; ++t) {
+      const int k = (order >> (4 * t)) & 0xF;
+      if (k == kI) vstep<kI>(c, L, r0, r1, c0);
+      else if (k == 1) hstep1(c, L, r0, r1, c0, c1);
+      else hstep2(c, L, r0, r1, c0, c1);
+    }
+    vstep<kX>(c, L, carry, r0, cc);
+    for (int t = posX + 1; t < 4; ++t) {
+      const int k = (order >> (4 * t)) & 0xF;
+      if (k == 1) hstep1(c, L, carry, r0, cc, c0);
+      else hstep2(c, L, carry, r0, cc, c0);
+    }
+    store_row(a, c, L, gcol, row0 - 1, carry);
+    store_row(a, c, L, gcol, row0, r0);
+    if ((b + 1) % kStepsPerUnit == 0 || b + 1 == b_hi) {
+      flush_unit(a, c.eab, unit_base + b / kStepsPerUnit);
+      c.eab = 0.0f;
+    }
+    carry = r1;
+  }
+  if (c.bad) atomicOr(a.status, ST_NONFINITE);
+  if (c.n_fp64) atomicAdd(&a.counters[DC_FP64], (unsigned long long)c.n_fp64);
+  if (c.n_capped) atomicAdd(&a.counters[DC_CAPPED], (unsigned long long)c.n_capped);
+}
+
+// The later of V3 and V4 in an order word.
+__host__ __device__ __forceinline__ int later_vertical(int order) {
+  for (int t = 3; t >= 0; --t) {
+    const int k = (order >> (4 * t)) & 0xF;
+    if (k == 3 || k == 4) return k;
+  }
+  return 4;
+}
+
+// Units [u_lo, u_hi) of one image (strip-major: unit = strip * units_per_strip + block).
+template <bool kSite0FromY, int kX>
+__device__ void run_units(const SweepArgs& a, long long u_lo, long long u_hi, float2* stage) {
+  const int ups = units_per_strip(a.height);
+  const int nsteps = steps_of(a.height);
+  long long u = u_lo;
+  while (u < u_hi) {
+    const int strip = (int)(u / ups);
+    const long long strip_end = (long long)(strip + 1) * ups;
+    const long long e = u_hi < strip_end ? u_hi : strip_end;
+    const int k_lo = (int)(u - (long long)strip * ups), k_hi = (int)(e - (long long)strip * ups);
+    run_strip<kSite0FromY, kX>(a, strip, k_lo * kStepsPerUnit, min(k_hi * kStepsPerUnit, nsteps),
+                               (long long)strip * ups, stage);
+    u = e;
   }
 }
 
 template <bool kSite0FromY>
-__global__ void __launch_bounds__(kThreads) prior_sweep_kernel(SweepArgs a) {
-  extern __shared__ float smem[];
-  prior_tile<kSite0FromY>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, smem);
+__device__ __forceinline__ void run_units_any(const SweepArgs& a, long long u_lo, long long u_hi,
+                                              float2* stage) {
+  if (later_vertical(a.order) == 4)
+    run_units<kSite0FromY, 4>(a, u_lo, u_hi, stage);
+  else
+    run_units<kSite0FromY, 3>(a, u_lo, u_hi, stage);
 }
 
-// Many images in one launch: block b belongs to the image whose block range holds
-// it (binary search over the first blocks); its tiles are numbered row-major.
-__global__ void __launch_bounds__(kThreads) prior_sweep_batch_kernel(const BatchItem* items,
-                                                                     int n_items) {
-  extern __shared__ float smem[];
-  const int b = blockIdx.x;
-  int lo = 0, hi = n_items - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (items[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+__device__ __forceinline__ float2* warp_stage() {
+  extern __shared__ float2 stage_all[];
+  return stage_all + (threadIdx.x >> 5) * (kSlots * kSlotFloats2);
+}
+
+__device__ __forceinline__ int global_warp() { return blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); }
+
+// One image: warp w takes strip w % S and the w / S-th of n_seg contiguous
+// ranges of that strip's units, so that the warps on neighbouring strips walk
+// the same rows at the same time (the strips' halo columns meet in L2).
+template <bool kSite0FromY, int kX>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_kernel(SweepArgs a, int n_seg) {
+  const int S = strips_of(a.width);
+  const int w = global_warp();
+  if (w >= S * n_seg) return;
+  const int strip = w % S, seg = w / S;
+  const long long ups = units_per_strip(a.height);
+  const long long lo = ups * seg / n_seg, hi = ups * (seg + 1) / n_seg;
+  if (lo < hi) run_units<kSite0FromY, kX>(a, strip * ups + lo, strip * ups + hi, warp_stage());
+}
+
+// Many images in one launch; units of image i start at items[i].unit_begin and
+// warp w of n_warps takes units [U w / n_warps, U (w + 1) / n_warps).
+__global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_batch_kernel(const BatchItem* items,
+                                                                     int n_items, long long total,
+                                                                     int n_warps) {
+  const int w = global_warp();
+  if (w >= n_warps) return;
+  const long long lo = total * w / n_warps, hi = total * (w + 1) / n_warps;
+  if (lo >= hi) return;
+  int it = 0, top = n_items - 1;
+  while (it < top) {  // last image whose first unit is <= lo
+    const int mid = (it + top + 1) >> 1;
+    if (items[mid].unit_begin <= lo) it = mid; else top = mid - 1;
   }
-  const BatchItem& it = items[lo];
-  const int local = b - it.block_begin;
-  const int by = local / it.tiles_x, bx = local - by * it.tiles_x;
-  if (it.site0_from_y)
-    prior_tile<true>(it.a, bx, by, local, smem);
-  else
-    prior_tile<false>(it.a, bx, by, local, smem);
+  long long u = lo;
+  while (u < hi && it < n_items) {
+    const BatchItem& b = items[it];
+    const long long end = b.unit_begin + b.units;
+    const long long e = hi < end ? hi : end;
+    if (e > u) {
+      if (b.site0_from_y)
+        run_units_any<true>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+      else
+        run_units_any<false>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+      u = e;
+    }
+    ++it;
+  }
 }
 
 __global__ void abar_reduce_kernel(const double* partial, int n, double* dscal, double n_pixels,
@@ -271,6 +694,49 @@ __global__ void abar_reduce_kernel(const double* partial, int n, double* dscal, 
   }
 }
 
+// Warps the whole GPU holds at once for a kernel (cached per device).
+template <typename Kern>
+int resident_warps(Kern kernel, int slot) {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static int cache[kMaxDev][5] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152 * 8;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev][slot]) {
+    int per_sm = 0, sms = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kSmemBytes) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 152 * 8;
+    }
+    cache[dev][slot] = (per_sm > 0 ? per_sm : 1) * sms * kWarpsPerBlock;
+  }
+  return cache[dev][slot];
+}
+
+void launch_units(long long total, int resident, int& n_warps, int& blocks) {
+  long long w = total < resident ? total : resident;
+  if (w < 1) w = 1;
+  n_warps = (int)w;
+  blocks = (n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+}
+
+template <bool kSite0FromY, int kX>
+void launch_single(const SweepArgs& a, int slot, cudaStream_t s) {
+  const int S = strips_of(a.width);
+  const int ups = units_per_strip(a.height);
+  const int resident = resident_warps(prior_sweep_kernel<kSite0FromY, kX>, slot);
+  int n_seg = resident / S;
+  if (n_seg < 1) n_seg = 1;
+  if (n_seg > ups) n_seg = ups;
+  const int blocks = (S * n_seg + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  prior_sweep_kernel<kSite0FromY, kX><<<blocks, kThreads, kSmemBytes, s>>>(a, n_seg);
+}
+
 }  // namespace
 
 double prior_sweep_bytes_per_pixel(bool site0_from_y) {
@@ -278,41 +744,31 @@ double prior_sweep_bytes_per_pixel(bool site0_from_y) {
   return site0_from_y ? (9 + 8) * 4.0 : (10 + 8) * 4.0;
 }
 
+void prior_sweep_prepare(SweepArgs& a) {
+  auto al = [](const void* p) { return ((uintptr_t)p & 7) == 0; };
+  a.vec2 = (a.width % 2 == 0) && al(a.tau0) && al(a.nu0) && al(a.tin) && al(a.nin) && al(a.tout) &&
+           al(a.nout) && al(a.y);
+}
+
 int prior_sweep_blocks(int height, int width) {
-  return ((width + kTW - 1) / kTW) * ((height + kTH - 1) / kTH);
+  return strips_of(width) * units_per_strip(height);
 }
 
-int prior_sweep_tiles_x(int width) { return (width + kTW - 1) / kTW; }
-
-void launch_prior_sweep_batch(const BatchItem* items, int n_items, int total_blocks,
+void launch_prior_sweep_batch(const BatchItem* items, int n_items, long long total_units,
                               cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(prior_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSmemBytes);
-    attr = true;
-  }
-  prior_sweep_batch_kernel<<<total_blocks, kThreads, kSmemBytes, s>>>(items, n_items);
+  int n_warps, blocks;
+  launch_units(total_units, resident_warps(prior_sweep_batch_kernel, 4), n_warps, blocks);
+  prior_sweep_batch_kernel<<<blocks, kThreads, kSmemBytes, s>>>(items, n_items, total_units, n_warps);
 }
 
-void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s) {
-  dim3 grid((a.width + kTW - 1) / kTW, (a.height + kTH - 1) / kTH);
+void launch_prior_sweep(const SweepArgs& args, bool site0_from_y, cudaStream_t s) {
+  SweepArgs a = args;
+  prior_sweep_prepare(a);
+  const bool x4 = later_vertical(a.order) == 4;
   if (site0_from_y) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(prior_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kSmemBytes);
-      attr = true;
-    }
-    prior_sweep_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(a);
+    if (x4) launch_single<true, 4>(a, 0, s); else launch_single<true, 3>(a, 1, s);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(prior_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kSmemBytes);
-      attr = true;
-    }
-    prior_sweep_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(a);
+    if (x4) launch_single<false, 4>(a, 2, s); else launch_single<false, 3>(a, 3, s);
   }
 }
 
