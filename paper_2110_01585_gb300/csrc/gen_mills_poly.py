@@ -22,7 +22,8 @@ import numpy as np
 from numpy.polynomial import chebyshev as C
 
 K = 2.0
-DEGREE = 14
+import os
+DEGREE = int(os.environ.get("MILLS_DEGREE", "14"))
 NODES = 200
 
 

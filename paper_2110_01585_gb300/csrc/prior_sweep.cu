@@ -245,10 +245,15 @@ __device__ __forceinline__ void damp_into(const Ctx& c, Px& x, bool valid, float
   }
 }
 
-// V1 on two rows: the edge (2a, 2a+1) inside the lane.
-__device__ __forceinline__ void hstep1(Ctx& c, const Lane& L, Row& a, Row& b, bool cnt_a,
-                                       bool cnt_b) {
-  Edge e0, e1;
+// Gather and scatter of the update steps.  A step updates site K on two
+// independent edges; the gather forms the cavities of site K at their endpoints,
+// edges2 computes the new sites, the scatter damps them into place.
+//   h1: V1, the edge (2a, 2a+1) inside the lane, on rows a and b
+//   h2: V2, the edge (2a+1, 2a+2) from a lane's right column to the next lane's
+//       left column, on rows a and b; the lane on the left computes it
+//   v:  V3 or V4 between vertically adjacent rows, both columns of the lane
+__device__ __forceinline__ void gather_h1(const Lane& L, const Row& a, const Row& b, bool cnt_a,
+                                          bool cnt_b, Edge& e0, Edge& e1) {
   cavity<1>(a.x[0], e0.ti, e0.ni);
   cavity<1>(a.x[1], e0.tj, e0.nj);
   cavity<1>(b.x[0], e1.ti, e1.ni);
@@ -258,19 +263,18 @@ __device__ __forceinline__ void hstep1(Ctx& c, const Lane& L, Row& a, Row& b, bo
   e1.valid = b.ok && cols;
   e0.count = cnt_a && L.own_col;
   e1.count = cnt_b && L.own_col;
-  edges2(c, e0, e1);
+}
+
+__device__ __forceinline__ void scatter_h1(const Ctx& c, Row& a, Row& b, const Edge& e0,
+                                           const Edge& e1) {
   damp_into<1>(c, a.x[0], e0.valid, e0.tni, e0.nni);
   damp_into<1>(c, a.x[1], e0.valid, e0.tnj, e0.nnj);
   damp_into<1>(c, b.x[0], e1.valid, e1.tni, e1.nni);
   damp_into<1>(c, b.x[1], e1.valid, e1.tnj, e1.nnj);
 }
 
-// V2 on two rows: the edge (2a+1, 2a+2) from a lane's right column to the next
-// lane's left column; the lane on the left computes it and hands back the
-// partner's new site.
-__device__ __forceinline__ void hstep2(Ctx& c, const Lane& L, Row& a, Row& b, bool cnt_a,
-                                       bool cnt_b) {
-  Edge e0, e1;
+__device__ __forceinline__ void gather_h2(const Lane& L, const Row& a, const Row& b, bool cnt_a,
+                                          bool cnt_b, Edge& e0, Edge& e1) {
   float tla, nla, tlb, nlb;
   cavity<2>(a.x[0], tla, nla);
   cavity<2>(a.x[1], e0.ti, e0.ni);
@@ -285,7 +289,10 @@ __device__ __forceinline__ void hstep2(Ctx& c, const Lane& L, Row& a, Row& b, bo
   e1.valid = b.ok && cols;
   e0.count = cnt_a && L.own_col;
   e1.count = cnt_b && L.own_col;
-  edges2(c, e0, e1);
+}
+
+__device__ __forceinline__ void scatter_h2(const Ctx& c, const Lane& L, Row& a, Row& b,
+                                           const Edge& e0, const Edge& e1) {
   const float rta = __shfl_up_sync(0xffffffffu, e0.tnj, 1);
   const float rna = __shfl_up_sync(0xffffffffu, e0.nnj, 1);
   const float rtb = __shfl_up_sync(0xffffffffu, e1.tnj, 1);
@@ -298,11 +305,9 @@ __device__ __forceinline__ void hstep2(Ctx& c, const Lane& L, Row& a, Row& b, bo
   damp_into<2>(c, b.x[0], vb && L.lane > 0, rtb, rnb);
 }
 
-// V3 or V4 between two vertically adjacent rows (top holds the first pixel of
-// each edge), both columns of the lane.
 template <int K>
-__device__ __forceinline__ void vstep(Ctx& c, const Lane& L, Row& top, Row& bot, bool cnt) {
-  Edge e0, e1;
+__device__ __forceinline__ void gather_v(const Lane& L, const Row& top, const Row& bot, bool cnt,
+                                         Edge& e0, Edge& e1) {
   cavity<K>(top.x[0], e0.ti, e0.ni);
   cavity<K>(bot.x[0], e0.tj, e0.nj);
   cavity<K>(top.x[1], e1.ti, e1.ni);
@@ -312,7 +317,11 @@ __device__ __forceinline__ void vstep(Ctx& c, const Lane& L, Row& top, Row& bot,
   e1.valid = rows && L.col_ok[1];
   e0.count = cnt && L.own_col;
   e1.count = cnt && L.own_col;
-  edges2(c, e0, e1);
+}
+
+template <int K>
+__device__ __forceinline__ void scatter_v(const Ctx& c, Row& top, Row& bot, const Edge& e0,
+                                          const Edge& e1) {
   damp_into<K>(c, top.x[0], e0.valid, e0.tni, e0.nni);
   damp_into<K>(c, bot.x[0], e0.valid, e0.tnj, e0.nnj);
   damp_into<K>(c, top.x[1], e1.valid, e1.tni, e1.nni);
@@ -326,7 +335,8 @@ constexpr int kSlots = 2;
 constexpr int kMaxPlanes = 10;
 constexpr int kSlotFloats2 = kMaxPlanes * 2 * 32;
 constexpr size_t kSmemPerWarp = size_t(kSlots) * kSlotFloats2 * sizeof(float2);
-constexpr size_t kSmemBytes = kSmemPerWarp * kWarpsPerBlock;
+constexpr size_t kIoBytes = 128;  // per-warp copy of the loop's argument fields
+constexpr size_t kSmemBytes = (kSmemPerWarp + kIoBytes) * kWarpsPerBlock;
 
 __device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, bool fill) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -340,67 +350,102 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Source planes of the pass: site 0 (y, or tau0 and nu0), then tau1..4, nu1..4.
-template <bool kSite0FromY>
-__device__ __forceinline__ const float* plane_ptr(const SweepArgs& a, int q) {
-  if (kSite0FromY) {
-    if (q == 0) return a.y;
-    q -= 1;
-  } else {
-    if (q == 0) return a.tau0;
-    if (q == 1) return a.nu0;
-    q -= 2;
-  }
-  return q < 4 ? a.tin + q * a.n : a.nin + (q - 4) * a.n;
+// The fields of SweepArgs the streaming loop touches.  Each warp keeps a copy in
+// shared memory and reads it at every use: cheap loads that cost no registers.
+struct __align__(16) Io {
+  const float* s0;   // y (site 0 from y) or tau0
+  const float* s1;   // nu0
+  const float* tin;
+  const float* nin;
+  float* tout;
+  float* nout;
+  int n;             // plane stride (pixels; images are below 2^31 pixels)
+  int height, width;
+  bool periodic, vec2;
+  float inv_xi;
+};
+
+static_assert(sizeof(Io) <= kIoBytes, "argument copy exceeds its shared-memory slot");
+
+__device__ __forceinline__ Io make_io(const SweepArgs& a, bool site0_from_y) {
+  Io io;
+  io.s0 = site0_from_y ? a.y : a.tau0;
+  io.s1 = a.nu0;
+  io.tin = a.tin;
+  io.nin = a.nin;
+  io.tout = a.tout;
+  io.nout = a.nout;
+  io.n = (int)a.n;
+  io.height = a.height;
+  io.width = a.width;
+  io.periodic = a.periodic != 0;
+  io.vec2 = a.vec2 != 0;
+  io.inv_xi = a.inv_xi;
+  return io;
 }
 
-// Issues the copies of image row `gr` (wrapped on the torus) into row slot `r`
-// of pair slot `slot`; returns whether the row exists.
-template <bool kSite0FromY>
-__device__ __forceinline__ bool issue_row(const SweepArgs& a, const Lane& L, const int (&gcol)[2],
-                                          int gr, float2* stage, int slot, int r) {
-  constexpr int kPlanes = kSite0FromY ? 9 : 10;
-  bool ok;
-  if (a.periodic) {
-    gr = wrap(gr, a.height);
+// Image row of the (unwrapped) row index r and whether it exists.
+__device__ __forceinline__ int image_row(const Io& io, int r, bool& ok) {
+  if (io.periodic) {
+    if (r < 0) r += io.height;
+    if (r >= io.height) r -= io.height;
+    if (r < 0 || r >= io.height) r = wrap(r, io.height);  // tiny heights
     ok = true;
-  } else {
-    ok = gr >= 0 && gr < a.height;
+    return r;
   }
-  const long long base = ok ? (long long)gr * a.width : 0;
+  ok = r >= 0 && r < io.height;
+  return r;
+}
+
+// Plane q of the staged set: site 0 (y, or tau0 and nu0), then tau1..4, nu1..4.
+template <bool kSite0FromY>
+__device__ __forceinline__ const float* plane_at(const Io& io, int q, int p) {
+  constexpr int k0 = kSite0FromY ? 1 : 2;
+  if (q == 0) return io.s0 + p;
+  if (!kSite0FromY && q == 1) return io.s1 + p;
+  q -= k0;
+  return q < 4 ? io.tin + q * io.n + p : io.nin + (q - 4) * io.n + p;
+}
+
+// Issues the copies of image row gr (already wrapped; ok = it exists) into row
+// slot r of pair slot `slot`.
+template <bool kSite0FromY>
+__device__ __forceinline__ void issue_row(const Io& io, const Lane& L, const int (&gcol)[2], int gr,
+                                          bool ok, float2* stage, int slot, int r) {
+  constexpr int kPlanes = kSite0FromY ? 9 : 10;
+  const int base = ok ? gr * io.width : 0;
   float2* dst = stage + slot * kSlotFloats2 + r * 32 + L.lane;
-  if (a.vec2) {
+  if (io.vec2) {
     const bool fill = ok && L.col_ok[0];
-    const long long p = fill ? base + gcol[0] : 0;
+    const int p = fill ? base + gcol[0] : 0;
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) cp_async(dst + q * 64, plane_ptr<kSite0FromY>(a, q) + p, 8, fill);
+    for (int q = 0; q < kPlanes; ++q) cp_async(dst + q * 64, plane_at<kSite0FromY>(io, q, p), 8, fill);
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const bool fill = ok && L.col_ok[k];
-      const long long p = fill ? base + gcol[k] : 0;
+      const int p = fill ? base + gcol[k] : 0;
 #pragma unroll
       for (int q = 0; q < kPlanes; ++q)
-        cp_async(reinterpret_cast<float*>(dst + q * 64) + k, plane_ptr<kSite0FromY>(a, q) + p, 4, fill);
+        cp_async(reinterpret_cast<float*>(dst + q * 64) + k, plane_at<kSite0FromY>(io, q, p), 4, fill);
     }
   }
-  return ok;
 }
 
 // Reads a staged row into registers (missing pixels read as zeros and are never
 // the endpoint of a valid edge).
 template <bool kSite0FromY>
-__device__ __forceinline__ void read_row(const SweepArgs& a, const Lane& L, const float2* stage,
-                                         int slot, int r, bool ok, Row& R) {
+__device__ __forceinline__ void read_row(const Io& io, const Lane& L, const float2* stage, int slot,
+                                         int r, bool ok, Row& R) {
   const float2* src = stage + slot * kSlotFloats2 + r * 32 + L.lane;
   R.ok = ok;
   int q = 0;
   if (kSite0FromY) {
     const float2 y = src[0];
-    R.x[0].t[0] = a.inv_xi;
-    R.x[1].t[0] = a.inv_xi;
-    R.x[0].n[0] = y.x * a.inv_xi;
-    R.x[1].n[0] = y.y * a.inv_xi;
+    R.x[0].t[0] = io.inv_xi;
+    R.x[1].t[0] = io.inv_xi;
+    R.x[0].n[0] = y.x * io.inv_xi;
+    R.x[1].n[0] = y.y * io.inv_xi;
     q = 1;
   } else {
     const float2 t = src[0], n = src[64];
@@ -421,30 +466,30 @@ __device__ __forceinline__ void read_row(const SweepArgs& a, const Lane& L, cons
   }
 }
 
-// Stores a final row (rows outside [0, H) are copies or do not exist).
-__device__ __forceinline__ void store_row(const SweepArgs& a, Ctx& c, const Lane& L,
-                                          const int (&gcol)[2], int gr, const Row& R) {
-  if (!L.own_col || gr < 0 || gr >= a.height) return;
-  const long long N = a.n;
-  const long long base = (long long)gr * a.width;
+// Stores a final row; gr is the unwrapped row index (rows outside [0, H) are
+// torus copies or do not exist and are not stored).
+__device__ __forceinline__ void store_row(const Io& io, Ctx& c, const Lane& L, const int (&gcol)[2],
+                                          int gr, const Row& R) {
+  if (!L.own_col || gr < 0 || gr >= io.height) return;
+  const int base = gr * io.width;
   float sum = 0.0f;
-  if (a.vec2) {
-    const long long p = base + gcol[0];
+  if (io.vec2) {
+    const int p = base + gcol[0];
 #pragma unroll
     for (int s = 1; s < 5; ++s) {
-      *reinterpret_cast<float2*>(a.tout + (s - 1) * N + p) = make_float2(R.x[0].t[s], R.x[1].t[s]);
-      *reinterpret_cast<float2*>(a.nout + (s - 1) * N + p) = make_float2(R.x[0].n[s], R.x[1].n[s]);
+      *reinterpret_cast<float2*>(io.tout + (s - 1) * io.n + p) = make_float2(R.x[0].t[s], R.x[1].t[s]);
+      *reinterpret_cast<float2*>(io.nout + (s - 1) * io.n + p) = make_float2(R.x[0].n[s], R.x[1].n[s]);
       sum += R.x[0].t[s] + R.x[1].t[s] + R.x[0].n[s] + R.x[1].n[s];
     }
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (!L.col_ok[k]) continue;
-      const long long p = base + gcol[k];
+      const int p = base + gcol[k];
 #pragma unroll
       for (int s = 1; s < 5; ++s) {
-        a.tout[(s - 1) * N + p] = R.x[k].t[s];
-        a.nout[(s - 1) * N + p] = R.x[k].n[s];
+        io.tout[(s - 1) * io.n + p] = R.x[k].t[s];
+        io.nout[(s - 1) * io.n + p] = R.x[k].n[s];
         sum += R.x[k].t[s] + R.x[k].n[s];
       }
     }
@@ -454,11 +499,11 @@ __device__ __forceinline__ void store_row(const SweepArgs& a, Ctx& c, const Lane
 }
 
 // Warp sum of the lanes' E|u| in FP64 (fixed tree), stored in the unit's slot.
-__device__ __forceinline__ void flush_unit(const SweepArgs& a, float lane_sum, long long unit) {
+__device__ __forceinline__ void flush_unit(double* abar_partial, float lane_sum, long long unit) {
   double v = (double)lane_sum;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) a.abar_partial[unit] = v;
+  if ((threadIdx.x & 31) == 0) abar_partial[unit] = v;
 }
 
 // Steps per strip: step b finalises rows 2b - o - 1 and 2b - o (o = 0 when V4 is
@@ -522,67 +567,71 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
   c.bad = false;
   const int order = a.order;
   const int posX = order_pos(order, kX);
+  Io* const io_smem = reinterpret_cast<Io*>(stage + kSlots * kSlotFloats2);
+  if (L.lane == 0) *io_smem = make_io(a, kSite0FromY);
+  __syncwarp();
+  const Io& io = *io_smem;
+  double* const abar_partial = a.abar_partial;
 
-  // pair b lives in slot b & 1
+  // Step b_lo - 1 only applies the updates before kX to its pair, whose second
+  // row is carried into step b_lo.  Pair b lives in staging slot b & 1.
   Row carry, r0, r1;
-  bool ok0, ok1, nok0, nok1;
+  bool nok0, nok1;
   {
     const int rw = 2 * (b_lo - 1) - kOff;
-    ok0 = issue_row<kSite0FromY>(a, L, gcol, rw, stage, (b_lo - 1) & 1, 0);
-    ok1 = issue_row<kSite0FromY>(a, L, gcol, rw + 1, stage, (b_lo - 1) & 1, 1);
+    const int g0 = image_row(io, rw, nok0), g1 = image_row(io, rw + 1, nok1);
+    issue_row<kSite0FromY>(io, L, gcol, g0, nok0, stage, (b_lo - 1) & 1, 0);
+    issue_row<kSite0FromY>(io, L, gcol, g1, nok1, stage, (b_lo - 1) & 1, 1);
     cp_async_commit();
-    nok0 = issue_row<kSite0FromY>(a, L, gcol, rw + 2, stage, b_lo & 1, 0);
-    nok1 = issue_row<kSite0FromY>(a, L, gcol, rw + 3, stage, b_lo & 1, 1);
-    cp_async_commit();
-    cp_async_wait<1>();
-    read_row<kSite0FromY>(a, L, stage, (b_lo - 1) & 1, 0, ok0, r0);
-    read_row<kSite0FromY>(a, L, stage, (b_lo - 1) & 1, 1, ok1, r1);
   }
-  // the pair before the first step: its updates before kX give the carried row
-  for (int t = 0; t < posX; ++t) {
-    const int k = (order >> (4 * t)) & 0xF;
-    if (k == kI) vstep<kI>(c, L, r0, r1, false);
-    else if (k == 1) hstep1(c, L, r0, r1, false, false);
-    else hstep2(c, L, r0, r1, false, false);
-  }
-  carry = r1;
-  for (int b = b_lo; b < b_hi; ++b) {
+  for (int b = b_lo - 1; b < b_hi; ++b) {
+    const bool warm = b < b_lo;
     const int row0 = 2 * b - kOff;
-    ok0 = nok0;
-    ok1 = nok1;
+    const bool ok0 = nok0, ok1 = nok1;
     if (b + 1 < b_hi) {
       // slot (b + 1) & 1 held pair b - 1, already read
-      nok0 = issue_row<kSite0FromY>(a, L, gcol, row0 + 2, stage, (b + 1) & 1, 0);
-      nok1 = issue_row<kSite0FromY>(a, L, gcol, row0 + 3, stage, (b + 1) & 1, 1);
+      const int g0 = image_row(io, row0 + 2, nok0), g1 = image_row(io, row0 + 3, nok1);
+      issue_row<kSite0FromY>(io, L, gcol, g0, nok0, stage, (b + 1) & 1, 0);
+      issue_row<kSite0FromY>(io, L, gcol, g1, nok1, stage, (b + 1) & 1, 1);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
-    read_row<kSite0FromY>(a, L, stage, b & 1, 0, ok0, r0);
-    read_row<kSite0FromY>(a, L, stage, b & 1, 1, ok1, r1);
+    read_row<kSite0FromY>(io, L, stage, b & 1, 0, ok0, r0);
+    read_row<kSite0FromY>(io, L, stage, b & 1, 1, ok1, r1);
     // an edge is counted by the step that computes it for its first pixel's row
     // in [0, H) (rows outside are torus copies or do not exist)
-    const bool cc = row0 - 1 >= 0 && row0 - 1 < H;
-    const bool c0 = row0 >= 0 && row0 < H;
-    const bool c1 = row0 + 1 >= 0 && row0 + 1 < H;
-    for (int t = 0; t < posX; ++t) {
+    const bool cc = !warm && row0 - 1 >= 0 && row0 - 1 < H;
+    const bool c0 = !warm && row0 >= 0 && row0 < H;
+    const bool c1 = !warm && row0 + 1 >= 0 && row0 + 1 < H;
+    const int nt = warm ? posX : 4;
+    for (int t = 0; t < nt; ++t) {
       const int k = (order >> (4 * t)) & 0xF;
-      if (k == kI) vstep<kI>(c, L, r0, r1, c0);
-      else if (k == 1) hstep1(c, L, r0, r1, c0, c1);
-      else hstep2(c, L, r0, r1, c0, c1);
+      // 1, 2, kI: updates before kX on this pair; 0: kX; 5, 6: V1, V2 after kX
+      const int kind = t < posX ? k : (t == posX ? 0 : 4 + k);
+      Edge e0, e1;
+      if (kind == 1) gather_h1(L, r0, r1, c0, c1, e0, e1);
+      else if (kind == 2) gather_h2(L, r0, r1, c0, c1, e0, e1);
+      else if (kind == 0) gather_v<kX>(L, carry, r0, cc, e0, e1);
+      else if (kind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
+      else if (kind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
+      else gather_v<kI>(L, r0, r1, c0, e0, e1);
+      edges2(c, e0, e1);
+      if (kind == 1) scatter_h1(c, r0, r1, e0, e1);
+      else if (kind == 2) scatter_h2(c, L, r0, r1, e0, e1);
+      else if (kind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
+      else if (kind == 5) scatter_h1(c, carry, r0, e0, e1);
+      else if (kind == 6) scatter_h2(c, L, carry, r0, e0, e1);
+      else scatter_v<kI>(c, r0, r1, e0, e1);
     }
-    vstep<kX>(c, L, carry, r0, cc);
-    for (int t = posX + 1; t < 4; ++t) {
-      const int k = (order >> (4 * t)) & 0xF;
-      if (k == 1) hstep1(c, L, carry, r0, cc, c0);
-      else hstep2(c, L, carry, r0, cc, c0);
-    }
-    store_row(a, c, L, gcol, row0 - 1, carry);
-    store_row(a, c, L, gcol, row0, r0);
-    if ((b + 1) % kStepsPerUnit == 0 || b + 1 == b_hi) {
-      flush_unit(a, c.eab, unit_base + b / kStepsPerUnit);
-      c.eab = 0.0f;
+    if (!warm) {
+      store_row(io, c, L, gcol, row0 - 1, carry);
+      store_row(io, c, L, gcol, row0, r0);
+      if ((b + 1) % kStepsPerUnit == 0 || b + 1 == b_hi) {
+        flush_unit(abar_partial, c.eab, unit_base + b / kStepsPerUnit);
+        c.eab = 0.0f;
+      }
     }
     carry = r1;
   }
@@ -626,9 +675,10 @@ __device__ __forceinline__ void run_units_any(const SweepArgs& a, long long u_lo
     run_units<kSite0FromY, 3>(a, u_lo, u_hi, stage);
 }
 
+// Staging slots of this warp, followed by its argument copy.
 __device__ __forceinline__ float2* warp_stage() {
   extern __shared__ float2 stage_all[];
-  return stage_all + (threadIdx.x >> 5) * (kSlots * kSlotFloats2);
+  return stage_all + (threadIdx.x >> 5) * ((kSmemPerWarp + kIoBytes) / sizeof(float2));
 }
 
 __device__ __forceinline__ int global_warp() { return blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); }

@@ -7,6 +7,7 @@ from oracle.ep import EPOracle
 from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC
 from paper_2110_01585_gb300 import synthetic as syn
 
+from ._cases import DECONV_CASES, oracle_run, probes, y32
 from ._parity import assert_parity, cuda
 
 pytestmark = pytest.mark.gpu
@@ -16,13 +17,13 @@ def _probes(S, n, seed):
     return syn.rbmc_probes(S, n, n, seed=seed)
 
 
-def _gpu(p, sweeps, S, probes, em_every=0, cg_rtol=1e-9, **kw):
+def _gpu(p, sweeps, S, pr, em_every=0, cg_rtol=1e-9, **kw):
     torch = cuda()
     yt = torch.as_tensor(p.y.astype(np.float32), device="cuda")
     ep = EPTV(yt, p.xi, p.beta, op=OP_CONV_PERIODIC, kernel=p.kernel, rbmc_samples=S,
               cg_rtol=cg_rtol, **kw)
-    ep.set_probes(torch.as_tensor(probes[0], dtype=torch.float32, device="cuda"),
-                  torch.as_tensor(probes[1], dtype=torch.float32, device="cuda"))
+    ep.set_probes(torch.as_tensor(pr[0], dtype=torch.float32, device="cuda"),
+                  torch.as_tensor(pr[1], dtype=torch.float32, device="cuda"))
     ep.sweep(sweeps, em_every=em_every)
     mu, var = ep.posterior()
     st = ep.status()
@@ -31,68 +32,18 @@ def _gpu(p, sweeps, S, probes, em_every=0, cg_rtol=1e-9, **kw):
     return out
 
 
-def _oracle(p, sweeps, probes, em_every=0, order="prior_first"):
-    h, w = p.shape
-    o = EPOracle("deconv", p.y, p.xi, p.beta, h, w, kernel=p.kernel, site0="rbmc",
-                 probes=probes, order=order)
-    o.run(sweeps, em_every=em_every)
-    mu, var = o.posterior()
-    return mu, var, o
-
-
-def test_deconv_32_uniform9_em():
-    p = syn.deconv_problem(32, 32, kernel=syn.uniform_kernel(9), bsnr_db=40.0, beta0=1.0,
-                           seed=0, grf_length=8.0)
-    pr = _probes(8, 32 * 32, 1)
-    mu, var, ep = _gpu(p, 10, 8, pr, em_every=5)
-    mu_r, var_r, o = _oracle(p, 10, pr, em_every=5)
-    assert_parity(mu, var, mu_r, var_r, p.y)
-    ep.close()
-
-
-def test_deconv_multi_tile_ragged_uniform5():
-    """Sizes that are not powers of two use the Jacobi-preconditioned solver."""
-    p = syn.deconv_problem(48, 80, kernel=syn.uniform_kernel(5), bsnr_db=30.0, beta0=3.0,
-                           seed=2, grf_length=8.0)
-    pr = _probes(4, 48 * 80, 3)
-    mu, var, ep = _gpu(p, 6, 4, pr, em_every=3, cg_max_iter=20000)
-    mu_r, var_r, _ = _oracle(p, 6, pr, em_every=3)
-    assert_parity(mu, var, mu_r, var_r, p.y)
-    ep.close()
-
-
-def test_deconv_non_separable_kernel():
-    rng = np.random.default_rng(4)
-    k = rng.random((5, 3)) ** 2
-    k /= k.sum()
-    p = syn.deconv_problem(40, 36, kernel=k, bsnr_db=35.0, beta0=5.0, seed=5, grf_length=6.0)
-    pr = _probes(6, 40 * 36, 6)
-    mu, var, ep = _gpu(p, 5, 6, pr, cg_max_iter=20000)
-    mu_r, var_r, _ = _oracle(p, 5, pr)
-    assert_parity(mu, var, mu_r, var_r, p.y)
-    ep.close()
-
-
-def test_deconv_gaussian15():
-    p = syn.deconv_problem(64, 64, kernel=syn.gaussian_kernel(15, 2.0), bsnr_db=30.0, beta0=2.0,
-                           seed=7, grf_length=8.0)
-    pr = _probes(4, 64 * 64, 8)
-    # the first solve (after one prior pass, with capped prior sites) is badly
-    # conditioned for a 15x15 blur: several thousand iterations
-    mu, var, ep = _gpu(p, 4, 4, pr, cg_max_iter=20000)
-    mu_r, var_r, _ = _oracle(p, 4, pr)
-    assert_parity(mu, var, mu_r, var_r, p.y)
-    ep.close()
-
-
-def test_deconv_q0_first_order():
-    """Algorithm 1 as listed (likelihood site first): the first solve sees a flat
-    cavity (precision 4e-8), the worst-conditioned system of the run."""
-    p = syn.deconv_problem(32, 32, kernel=syn.uniform_kernel(3), bsnr_db=30.0, beta0=4.0,
-                           seed=9, grf_length=8.0)
-    pr = _probes(4, 32 * 32, 10)
-    mu, var, ep = _gpu(p, 5, 4, pr, order_mode=1)
-    mu_r, var_r, _ = _oracle(p, 5, pr, order="q0_first")
+@pytest.mark.parametrize("name", sorted(DECONV_CASES))
+def test_deconv_parity(name):
+    """Uniform 9x9 with EM, uniform 5x5 on a ragged 48x80 grid with EM, a
+    non-separable 5x3 kernel, a 15x15 Gaussian (the first solve after one prior
+    pass with capped prior sites needs thousands of iterations), and Algorithm 1
+    as listed (likelihood site first: the first solve sees a flat cavity of
+    precision 4e-8, the worst-conditioned system of the run)."""
+    make, (S, seed), sweeps, em_every, order, opts = DECONV_CASES[name]
+    p = make()
+    pr = probes(p, S, seed)
+    mu, var, ep = _gpu(p, sweeps, S, pr, em_every=em_every, **opts)
+    mu_r, var_r = oracle_run(p, y32(p), pr, sweeps, em_every, order)
     assert_parity(mu, var, mu_r, var_r, p.y)
     ep.close()
 
