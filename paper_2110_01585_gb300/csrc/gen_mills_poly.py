@@ -62,6 +62,13 @@ def main():
             for c in p[-2::-1]:
                 f.write("  p = fmaf(p, u, %.9ef);\n" % c)
             f.write("  return p;\n}\n\n")
+        # the same coefficients as (c, c) pairs for the packed two-lane form
+        for name, p in (("kMillsG2", pg), ("kMillsV2", pv)):
+            f.write("static __constant__ float2 %s[%d] = {\n" % (name, len(p)))
+            for c in p:
+                f.write("    {%.9ef, %.9ef},\n" % (c, c))
+            f.write("};\n\n")
+        f.write("constexpr int kMillsDegree = %d;\n\n" % DEGREE)
         f.write("}  // namespace eptv\n")
     print("wrote", out)
 

@@ -169,10 +169,11 @@ struct Lane {
 
 template <int K>
 __device__ __forceinline__ void cavity(const Px& x, float& ct, float& cn) {
-  ct = 0.0f;
-  cn = 0.0f;
+  constexpr int first = K == 0 ? 1 : 0;
+  ct = x.t[first];
+  cn = x.n[first];
 #pragma unroll
-  for (int s = 0; s < 5; ++s) {
+  for (int s = first + 1; s < 5; ++s) {
     if (s == K) continue;
     ct += x.t[s];
     cn += x.n[s];
@@ -191,50 +192,130 @@ __device__ __noinline__ Moments tilted_fast_ool(float mu, float s2, float lam) {
   return tilted_fast(mu, s2, lam);
 }
 
-// Eq. update_qk_x from the tilted moments: tau = rho / (c_j + q c_i), the variance
-// cap, then nu = tau E + (E - m) / c.
-__device__ __forceinline__ void edge_finish(Ctx& c, Edge& e, float ci, float cj, float mi, float mj,
-                                            const Moments& o) {
-  const bool cnt = e.valid && e.count;
-  float tni = o.rho * rcp_approx(cj + o.q * ci);
-  float tnj = o.rho * rcp_approx(ci + o.q * cj);
-  if (!(tni >= c.min_tau)) {
-    tni = c.min_tau;
-    c.n_capped += cnt;
-  }
-  if (!(tnj >= c.min_tau)) {
-    tnj = c.min_tau;
-    c.n_capped += cnt;
-  }
-  e.tni = tni;
-  e.tnj = tnj;
-  e.nni = tni * (mi + ci * o.d) + o.d;
-  e.nnj = tnj * (mj - cj * o.d) - o.d;
-  if (cnt) c.eab += o.eab;
+// ------------------------------------------- two edges at once, packed FP32
+//
+// The two edges of an update step run through the same arithmetic, so it is
+// written on float2 pairs (edge 0, edge 1) with the packed FP32 FMA/ADD/MUL of
+// sm_100-family GPUs: one instruction per operation for both edges.  Constant
+// pairs come from the constant bank.
+
+static __constant__ float2 kPairs[4] = {
+    {kMillsK, kMillsK}, {-1.0f, -1.0f}, {1.0f, 1.0f}, {0.398942280f, 0.398942280f}};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, kPairs[1], a); }
+__device__ __forceinline__ float2 rcp2(float2 a) {
+  return make_float2(rcp_approx(a.x), rcp_approx(a.y));
 }
 
-// The two independent edges of one update step, in straight-line code; the FP64
-// moments only when some lane of the warp needs them.
+struct Mills2 {
+  float2 h, g, v;
+};
+
+// h, g, v of the polynomial fits at b >= 0 (mills_fast without its reflection).
+__device__ __forceinline__ Mills2 mills_fit2(float2 b) {
+  const float2 r = rcp2(add2(kPairs[0], b));
+  const float2 u = mul2(sub2(kPairs[0], b), r);
+  const float2 kr = mul2(kPairs[0], r);
+  float2 G = kMillsG2[kMillsDegree], V = kMillsV2[kMillsDegree];
+#pragma unroll
+  for (int i = kMillsDegree - 1; i >= 0; --i) {
+    G = fma2(G, u, kMillsG2[i]);
+    V = fma2(V, u, kMillsV2[i]);
+  }
+  Mills2 m;
+  m.g = mul2(G, kr);
+  m.v = mul2(mul2(V, kr), kr);
+  m.h = add2(m.g, b);
+  return m;
+}
+
+struct Moments2 {
+  float2 d, q, rho, eab;
+};
+
+// tilted_fast for two edges.  Of a+ and a- (a+ + a- = 2 l >= 0) only the smaller
+// can be negative; its reflection is formed once per edge and selected in.
+__device__ __forceinline__ Moments2 tilted2(float2 mu, float2 s2, float2 lam) {
+  const float2 rs = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
+  const float2 s = mul2(s2, rs);
+  const float2 z = mul2(mu, rs);
+  const float2 l = mul2(lam, s);
+  const float2 ap = sub2(l, z), am = add2(l, z);
+  Mills2 P = mills_fit2(make_float2(fabsf(ap.x), fabsf(ap.y)));
+  Mills2 M = mills_fit2(make_float2(fabsf(am.x), fabsf(am.y)));
+  // reflection at the smaller argument a = -b: h(a) = phi(b) h(b) / (h(b) - phi(b))
+  const bool px = ap.x < am.x, py = ap.y < am.y;
+  const float2 b = make_float2(fabsf(px ? ap.x : am.x), fabsf(py ? ap.y : am.y));
+  const float2 hb = make_float2(px ? P.h.x : M.h.x, py ? P.h.y : M.h.y);
+  const float2 phi =
+      mul2(kPairs[3], make_float2(__expf(-0.5f * b.x * b.x), __expf(-0.5f * b.y * b.y)));
+  const float2 hn = mul2(mul2(phi, hb), rcp2(sub2(hb, phi)));  // h(b) - phi(b) >= 0.4
+  const float2 gn = add2(hn, b);
+  const float2 vn = sub2(kPairs[2], mul2(hn, gn));
+  if ((px ? ap.x : am.x) < 0.0f) {
+    if (px) { P.h.x = hn.x; P.g.x = gn.x; P.v.x = vn.x; } else { M.h.x = hn.x; M.g.x = gn.x; M.v.x = vn.x; }
+  }
+  if ((py ? ap.y : am.y) < 0.0f) {
+    if (py) { P.h.y = hn.y; P.g.y = gn.y; P.v.y = vn.y; } else { M.h.y = hn.y; M.g.y = gn.y; M.v.y = vn.y; }
+  }
+  const float2 inv = rcp2(add2(P.h, M.h));  // not both h vanish
+  const float2 wp = mul2(M.h, inv), wm = mul2(P.h, inv);
+  Moments2 o;
+  o.d = mul2(sub2(mul2(wp, sub2(P.h, l)), mul2(wm, sub2(M.h, l))), rs);
+  const float2 gs = add2(P.g, M.g);
+  const float2 mix = mul2(mul2(wp, wm), mul2(gs, gs));
+  o.q = add2(fma2(wp, P.v, mul2(wm, M.v)), mix);
+  o.rho = sub2(fma2(mul2(wp, P.h), P.g, mul2(mul2(wm, M.h), M.g)), mix);
+  o.eab = mul2(s, fma2(wp, P.g, mul2(wm, M.g)));
+  return o;
+}
+
+// The two independent edges of one update step; the FP64 moments only when
+// some lane of the warp needs them.  Eq. update_qk_x from the tilted moments:
+// tau = rho / (c_j + q c_i), the variance cap, then nu = tau E + (E - m) / c.
 __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
-  const float ci0 = rcp_approx(e0.ti), cj0 = rcp_approx(e0.tj);
-  const float ci1 = rcp_approx(e1.ti), cj1 = rcp_approx(e1.tj);
-  const float mi0 = e0.ni * ci0, mj0 = e0.nj * cj0;
-  const float mi1 = e1.ni * ci1, mj1 = e1.nj * cj1;
-  const float s20 = ci0 + cj0, s21 = ci1 + cj1;
+  const float2 ti = make_float2(e0.ti, e1.ti), tj = make_float2(e0.tj, e1.tj);
+  const float2 ci = rcp2(ti), cj = rcp2(tj);
+  const float2 mi = mul2(make_float2(e0.ni, e1.ni), ci);
+  const float2 mj = mul2(make_float2(e0.nj, e1.nj), cj);
+  const float2 s2 = add2(ci, cj);
+  const float2 mu = sub2(mi, mj);
   const float l2 = c.lam * c.lam;
-  const bool t0 = c.tail && e0.valid && l2 * s20 < 1e-6f;
-  const bool t1 = c.tail && e1.valid && l2 * s21 < 1e-6f;
-  Moments o0, o1;
+  const bool t0 = c.tail && e0.valid && l2 * s2.x < 1e-6f;
+  const bool t1 = c.tail && e1.valid && l2 * s2.y < 1e-6f;
+  Moments2 o;
   if (__any_sync(0xffffffffu, t0 || t1)) {
-    o0 = t0 ? tilted_fp64(e0.ti, e0.ni, e0.tj, e0.nj, c.lam_d) : tilted_fast_ool(mi0 - mj0, s20, c.lam);
-    o1 = t1 ? tilted_fp64(e1.ti, e1.ni, e1.tj, e1.nj, c.lam_d) : tilted_fast_ool(mi1 - mj1, s21, c.lam);
+    const Moments a = t0 ? tilted_fp64(e0.ti, e0.ni, e0.tj, e0.nj, c.lam_d)
+                         : tilted_fast_ool(mu.x, s2.x, c.lam);
+    const Moments b = t1 ? tilted_fp64(e1.ti, e1.ni, e1.tj, e1.nj, c.lam_d)
+                         : tilted_fast_ool(mu.y, s2.y, c.lam);
+    o.d = make_float2(a.d, b.d);
+    o.q = make_float2(a.q, b.q);
+    o.rho = make_float2(a.rho, b.rho);
+    o.eab = make_float2(a.eab, b.eab);
     c.n_fp64 += (t0 && e0.count) + (t1 && e1.count);
   } else {
-    o0 = tilted_fast(mi0 - mj0, s20, c.lam);
-    o1 = tilted_fast(mi1 - mj1, s21, c.lam);
+    o = tilted2(mu, s2, make_float2(c.lam, c.lam));
   }
-  edge_finish(c, e0, ci0, cj0, mi0, mj0, o0);
-  edge_finish(c, e1, ci1, cj1, mi1, mj1, o1);
+  float2 tni = mul2(o.rho, rcp2(fma2(o.q, ci, cj)));
+  float2 tnj = mul2(o.rho, rcp2(fma2(o.q, cj, ci)));
+  const bool k0 = e0.valid && e0.count, k1 = e1.valid && e1.count;
+  if (!(tni.x >= c.min_tau)) { tni.x = c.min_tau; c.n_capped += k0; }
+  if (!(tnj.x >= c.min_tau)) { tnj.x = c.min_tau; c.n_capped += k0; }
+  if (!(tni.y >= c.min_tau)) { tni.y = c.min_tau; c.n_capped += k1; }
+  if (!(tnj.y >= c.min_tau)) { tnj.y = c.min_tau; c.n_capped += k1; }
+  const float2 nd = mul2(o.d, kPairs[1]);
+  const float2 nni = fma2(tni, fma2(ci, o.d, mi), o.d);  // tau E + (E - m) / c
+  const float2 nnj = fma2(tnj, fma2(cj, nd, mj), nd);
+  e0.tni = tni.x; e1.tni = tni.y;
+  e0.tnj = tnj.x; e1.tnj = tnj.y;
+  e0.nni = nni.x; e1.nni = nni.y;
+  e0.nnj = nnj.x; e1.nnj = nnj.y;
+  if (k0) c.eab += o.eab.x;
+  if (k1) c.eab += o.eab.y;
 }
 
 template <int K>
@@ -338,14 +419,6 @@ constexpr size_t kSmemPerWarp = size_t(kSlots) * kSlotFloats2 * sizeof(float2);
 constexpr size_t kIoBytes = 128;  // per-warp copy of the loop's argument fields
 constexpr size_t kSmemBytes = (kSmemPerWarp + kIoBytes) * kWarpsPerBlock;
 
-__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes, bool fill) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int src_size = fill ? bytes : 0;  // 0: write zeros, read nothing
-  if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_size));
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_size));
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -397,38 +470,59 @@ __device__ __forceinline__ int image_row(const Io& io, int r, bool& ok) {
   return r;
 }
 
-// Plane q of the staged set: site 0 (y, or tau0 and nu0), then tau1..4, nu1..4.
-template <bool kSite0FromY>
-__device__ __forceinline__ const float* plane_at(const Io& io, int q, int p) {
+// One 8- or 4-byte cp.async to a shared address plus an immediate offset; a zero
+// source size writes zeros and reads nothing.
+template <int kBytes, int kOff>
+__device__ __forceinline__ void cp_async_imm(unsigned dst, const float* src, int src_size) {
+  if (kBytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0+%1], [%2], 8, %3;\n" ::"r"(dst), "n"(kOff), "l"(src),
+                 "r"(src_size));
+  else
+    asm volatile("cp.async.ca.shared.global [%0+%1], [%2], 4, %3;\n" ::"r"(dst), "n"(kOff), "l"(src),
+                 "r"(src_size));
+}
+
+// Copies of one pixel column (kBytes = 8: both pixels of the lane) of every
+// staged plane: site 0 (y, or tau0 and nu0), then tau1..4, nu1..4, one plane
+// every 64 float2 of the slot.
+template <bool kSite0FromY, int kBytes>
+__device__ __forceinline__ void issue_planes(const float* s0, const float* s1, const float* tin,
+                                             const float* nin, int n, int p, unsigned dst, int size) {
   constexpr int k0 = kSite0FromY ? 1 : 2;
-  if (q == 0) return io.s0 + p;
-  if (!kSite0FromY && q == 1) return io.s1 + p;
-  q -= k0;
-  return q < 4 ? io.tin + q * io.n + p : io.nin + (q - 4) * io.n + p;
+  cp_async_imm<kBytes, 0>(dst, s0 + p, size);
+  if (!kSite0FromY) cp_async_imm<kBytes, 512>(dst, s1 + p, size);
+  const float* t = tin + p;
+  const float* m = nin + p;
+  cp_async_imm<kBytes, (k0 + 0) * 512>(dst, t, size);
+  cp_async_imm<kBytes, (k0 + 1) * 512>(dst, t + n, size);
+  cp_async_imm<kBytes, (k0 + 2) * 512>(dst, t + 2 * n, size);
+  cp_async_imm<kBytes, (k0 + 3) * 512>(dst, t + 3 * n, size);
+  cp_async_imm<kBytes, (k0 + 4) * 512>(dst, m, size);
+  cp_async_imm<kBytes, (k0 + 5) * 512>(dst, m + n, size);
+  cp_async_imm<kBytes, (k0 + 6) * 512>(dst, m + 2 * n, size);
+  cp_async_imm<kBytes, (k0 + 7) * 512>(dst, m + 3 * n, size);
 }
 
 // Issues the copies of image row gr (already wrapped; ok = it exists) into row
 // slot r of pair slot `slot`.
 template <bool kSite0FromY>
-__device__ __forceinline__ void issue_row(const Io& io, const Lane& L, const int (&gcol)[2], int gr,
-                                          bool ok, float2* stage, int slot, int r) {
-  constexpr int kPlanes = kSite0FromY ? 9 : 10;
-  const int base = ok ? gr * io.width : 0;
-  float2* dst = stage + slot * kSlotFloats2 + r * 32 + L.lane;
-  if (io.vec2) {
+__device__ __forceinline__ void issue_row(const Io& io_ref, const Lane& L, const int (&gcol)[2],
+                                          int gr, bool ok, float2* stage, int slot, int r) {
+  const float* s0 = io_ref.s0;
+  const float* s1 = io_ref.s1;
+  const float* tin = io_ref.tin;
+  const float* nin = io_ref.nin;
+  const int n = io_ref.n;
+  const int base = ok ? gr * io_ref.width : 0;
+  const unsigned dst =
+      (unsigned)__cvta_generic_to_shared(stage + slot * kSlotFloats2 + r * 32 + L.lane);
+  if (io_ref.vec2) {
     const bool fill = ok && L.col_ok[0];
-    const int p = fill ? base + gcol[0] : 0;
-#pragma unroll
-    for (int q = 0; q < kPlanes; ++q) cp_async(dst + q * 64, plane_at<kSite0FromY>(io, q, p), 8, fill);
+    issue_planes<kSite0FromY, 8>(s0, s1, tin, nin, n, fill ? base + gcol[0] : 0, dst, fill ? 8 : 0);
   } else {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const bool fill = ok && L.col_ok[k];
-      const int p = fill ? base + gcol[k] : 0;
-#pragma unroll
-      for (int q = 0; q < kPlanes; ++q)
-        cp_async(reinterpret_cast<float*>(dst + q * 64) + k, plane_at<kSite0FromY>(io, q, p), 4, fill);
-    }
+    const bool f0 = ok && L.col_ok[0], f1 = ok && L.col_ok[1];
+    issue_planes<kSite0FromY, 4>(s0, s1, tin, nin, n, f0 ? base + gcol[0] : 0, dst, f0 ? 4 : 0);
+    issue_planes<kSite0FromY, 4>(s0, s1, tin, nin, n, f1 ? base + gcol[1] : 0, dst + 4, f1 ? 4 : 0);
   }
 }
 
@@ -468,28 +562,38 @@ __device__ __forceinline__ void read_row(const Io& io, const Lane& L, const floa
 
 // Stores a final row; gr is the unwrapped row index (rows outside [0, H) are
 // torus copies or do not exist and are not stored).
-__device__ __forceinline__ void store_row(const Io& io, Ctx& c, const Lane& L, const int (&gcol)[2],
-                                          int gr, const Row& R) {
-  if (!L.own_col || gr < 0 || gr >= io.height) return;
-  const int base = gr * io.width;
+__device__ __forceinline__ void store_row(const Io& io_ref, Ctx& c, const Lane& L,
+                                          const int (&gcol)[2], int gr, const Row& R) {
+  const int H = io_ref.height;
+  if (!L.own_col || gr < 0 || gr >= H) return;
+  const int n = io_ref.n;
+  const int base = gr * io_ref.width;
+  float* t = io_ref.tout;
+  float* m = io_ref.nout;
   float sum = 0.0f;
-  if (io.vec2) {
-    const int p = base + gcol[0];
+  if (io_ref.vec2) {
+    t += base + gcol[0];
+    m += base + gcol[0];
 #pragma unroll
     for (int s = 1; s < 5; ++s) {
-      *reinterpret_cast<float2*>(io.tout + (s - 1) * io.n + p) = make_float2(R.x[0].t[s], R.x[1].t[s]);
-      *reinterpret_cast<float2*>(io.nout + (s - 1) * io.n + p) = make_float2(R.x[0].n[s], R.x[1].n[s]);
+      *reinterpret_cast<float2*>(t) = make_float2(R.x[0].t[s], R.x[1].t[s]);
+      *reinterpret_cast<float2*>(m) = make_float2(R.x[0].n[s], R.x[1].n[s]);
+      t += n;
+      m += n;
       sum += R.x[0].t[s] + R.x[1].t[s] + R.x[0].n[s] + R.x[1].n[s];
     }
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (!L.col_ok[k]) continue;
-      const int p = base + gcol[k];
+      float* tk = t + base + gcol[k];
+      float* mk = m + base + gcol[k];
 #pragma unroll
       for (int s = 1; s < 5; ++s) {
-        io.tout[(s - 1) * io.n + p] = R.x[k].t[s];
-        io.nout[(s - 1) * io.n + p] = R.x[k].n[s];
+        *tk = R.x[k].t[s];
+        *mk = R.x[k].n[s];
+        tk += n;
+        mk += n;
         sum += R.x[k].t[s] + R.x[k].n[s];
       }
     }
