@@ -415,9 +415,12 @@ __device__ __forceinline__ void scatter_v(const Ctx& c, Row& top, Row& bot, cons
 constexpr int kSlots = 2;
 constexpr int kMaxPlanes = 10;
 constexpr int kSlotFloats2 = kMaxPlanes * 2 * 32;
+constexpr int kCarryFloats2 = 10 * 32;  // the carried row between steps: [t0..t4, n0..n4][lane]
 constexpr size_t kSmemPerWarp = size_t(kSlots) * kSlotFloats2 * sizeof(float2);
+constexpr size_t kCarryBytes = size_t(kCarryFloats2) * sizeof(float2);
 constexpr size_t kIoBytes = 128;  // per-warp copy of the loop's argument fields
-constexpr size_t kSmemBytes = (kSmemPerWarp + kIoBytes) * kWarpsPerBlock;
+constexpr size_t kWarpSmem = kSmemPerWarp + kCarryBytes + kIoBytes;
+constexpr size_t kSmemBytes = kWarpSmem * kWarpsPerBlock;
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -610,6 +613,50 @@ __device__ __forceinline__ void flush_unit(double* abar_partial, float lane_sum,
   if ((threadIdx.x & 31) == 0) abar_partial[unit] = v;
 }
 
+// One update step of a known kind: 1, 2 (V1, V2 on the pair r0, r1), 3 or 4 (the
+// in-pair vertical update kI on r0, r1), 0 (kX joining carry and r0), 5 and 6
+// (V1, V2 after kX on carry and r0).
+template <int kKind, int kX, int kI>
+__device__ __forceinline__ void do_step(Ctx& c, const Lane& L, Row& carry, Row& r0, Row& r1, bool cc,
+                                        bool c0, bool c1) {
+  Edge e0, e1;
+  if (kKind == 1) gather_h1(L, r0, r1, c0, c1, e0, e1);
+  else if (kKind == 2) gather_h2(L, r0, r1, c0, c1, e0, e1);
+  else if (kKind == 0) gather_v<kX>(L, carry, r0, cc, e0, e1);
+  else if (kKind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
+  else if (kKind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
+  else gather_v<kI>(L, r0, r1, c0, e0, e1);
+  edges2(c, e0, e1);
+  if (kKind == 1) scatter_h1(c, r0, r1, e0, e1);
+  else if (kKind == 2) scatter_h2(c, L, r0, r1, e0, e1);
+  else if (kKind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
+  else if (kKind == 5) scatter_h1(c, carry, r0, e0, e1);
+  else if (kKind == 6) scatter_h2(c, L, carry, r0, e0, e1);
+  else scatter_v<kI>(c, r0, r1, e0, e1);
+}
+
+// The carried row waits in shared memory while the next pair takes its updates
+// before kX (registers are the occupancy limit); [plane][lane] float2 layout.
+__device__ __forceinline__ void save_row(float2* dst, const Row& R) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    dst[s * 32] = make_float2(R.x[0].t[s], R.x[1].t[s]);
+    dst[(5 + s) * 32] = make_float2(R.x[0].n[s], R.x[1].n[s]);
+  }
+}
+
+__device__ __forceinline__ void load_saved_row(const float2* src, bool ok, Row& R) {
+  R.ok = ok;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const float2 t = src[s * 32], n = src[(5 + s) * 32];
+    R.x[0].t[s] = t.x;
+    R.x[1].t[s] = t.y;
+    R.x[0].n[s] = n.x;
+    R.x[1].n[s] = n.y;
+  }
+}
+
 // Steps per strip: step b finalises rows 2b - o - 1 and 2b - o (o = 0 when V4 is
 // the later vertical update of the order, 1 when V3 is); one spare step covers
 // both offsets and odd heights.
@@ -671,7 +718,8 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
   c.bad = false;
   const int order = a.order;
   const int posX = order_pos(order, kX);
-  Io* const io_smem = reinterpret_cast<Io*>(stage + kSlots * kSlotFloats2);
+  float2* const carry_smem = stage + kSlots * kSlotFloats2 + L.lane;
+  Io* const io_smem = reinterpret_cast<Io*>(stage + kSlots * kSlotFloats2 + kCarryFloats2);
   if (L.lane == 0) *io_smem = make_io(a, kSite0FromY);
   __syncwarp();
   const Io& io = *io_smem;
@@ -679,8 +727,8 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
 
   // Step b_lo - 1 only applies the updates before kX to its pair, whose second
   // row is carried into step b_lo.  Pair b lives in staging slot b & 1.
-  Row carry, r0, r1;
-  bool nok0, nok1;
+  Row r0, r1;
+  bool nok0, nok1, carry_ok = false;
   {
     const int rw = 2 * (b_lo - 1) - kOff;
     const int g0 = image_row(io, rw, nok0), g1 = image_row(io, rw + 1, nok1);
@@ -709,25 +757,38 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
     const bool cc = !warm && row0 - 1 >= 0 && row0 - 1 < H;
     const bool c0 = !warm && row0 >= 0 && row0 < H;
     const bool c1 = !warm && row0 + 1 >= 0 && row0 + 1 < H;
-    const int nt = warm ? posX : 4;
-    for (int t = 0; t < nt; ++t) {
-      const int k = (order >> (4 * t)) & 0xF;
-      // 1, 2, kI: updates before kX on this pair; 0: kX; 5, 6: V1, V2 after kX
-      const int kind = t < posX ? k : (t == posX ? 0 : 4 + k);
-      Edge e0, e1;
-      if (kind == 1) gather_h1(L, r0, r1, c0, c1, e0, e1);
-      else if (kind == 2) gather_h2(L, r0, r1, c0, c1, e0, e1);
-      else if (kind == 0) gather_v<kX>(L, carry, r0, cc, e0, e1);
-      else if (kind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
-      else if (kind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
-      else gather_v<kI>(L, r0, r1, c0, e0, e1);
-      edges2(c, e0, e1);
-      if (kind == 1) scatter_h1(c, r0, r1, e0, e1);
-      else if (kind == 2) scatter_h2(c, L, r0, r1, e0, e1);
-      else if (kind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
-      else if (kind == 5) scatter_h1(c, carry, r0, e0, e1);
-      else if (kind == 6) scatter_h2(c, L, carry, r0, e0, e1);
-      else scatter_v<kI>(c, r0, r1, e0, e1);
+    Row carry;
+    if (kX == 4 && order == 0x4321) {
+      // the default order V1, V2, V3, V4 as straight-line code
+      do_step<1, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<2, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<kI, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+      if (!warm) {
+        load_saved_row(carry_smem, carry_ok, carry);
+        do_step<0, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+      }
+    } else {
+      const int nt = warm ? posX : 4;
+      for (int t = 0; t < nt; ++t) {
+        const int k = (order >> (4 * t)) & 0xF;
+        // 1, 2, kI: updates before kX on this pair; 0: kX; 5, 6: V1, V2 after kX
+        const int kind = t < posX ? k : (t == posX ? 0 : 4 + k);
+        if (kind == 0) load_saved_row(carry_smem, carry_ok, carry);
+        Edge e0, e1;
+        if (kind == 1) gather_h1(L, r0, r1, c0, c1, e0, e1);
+        else if (kind == 2) gather_h2(L, r0, r1, c0, c1, e0, e1);
+        else if (kind == 0) gather_v<kX>(L, carry, r0, cc, e0, e1);
+        else if (kind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
+        else if (kind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
+        else gather_v<kI>(L, r0, r1, c0, e0, e1);
+        edges2(c, e0, e1);
+        if (kind == 1) scatter_h1(c, r0, r1, e0, e1);
+        else if (kind == 2) scatter_h2(c, L, r0, r1, e0, e1);
+        else if (kind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
+        else if (kind == 5) scatter_h1(c, carry, r0, e0, e1);
+        else if (kind == 6) scatter_h2(c, L, carry, r0, e0, e1);
+        else scatter_v<kI>(c, r0, r1, e0, e1);
+      }
     }
     if (!warm) {
       store_row(io, c, L, gcol, row0 - 1, carry);
@@ -737,7 +798,8 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
         c.eab = 0.0f;
       }
     }
-    carry = r1;
+    save_row(carry_smem, r1);
+    carry_ok = r1.ok;
   }
   if (c.bad) atomicOr(a.status, ST_NONFINITE);
   if (c.n_fp64) atomicAdd(&a.counters[DC_FP64], (unsigned long long)c.n_fp64);
@@ -782,7 +844,7 @@ __device__ __forceinline__ void run_units_any(const SweepArgs& a, long long u_lo
 // Staging slots of this warp, followed by its argument copy.
 __device__ __forceinline__ float2* warp_stage() {
   extern __shared__ float2 stage_all[];
-  return stage_all + (threadIdx.x >> 5) * ((kSmemPerWarp + kIoBytes) / sizeof(float2));
+  return stage_all + (threadIdx.x >> 5) * (kWarpSmem / sizeof(float2));
 }
 
 __device__ __forceinline__ int global_warp() { return blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); }
