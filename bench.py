@@ -38,6 +38,8 @@ WORKLOADS = {
                         seed=0, n_rect=40),
     "batched256": dict(kind="batch", n=256, h=None, w=None, em_every=5, beta0=1.0, S=32, seed=0),
     "cs128": dict(kind="cs", h=128, w=128, ratio=0.3, sigma=0.01, beta0=1.0, em_every=5, seed=0),
+    # learned warm start: seconds and sweeps to the posterior of converged plain EP
+    "warmstart512": dict(kind="warmstart", h=512, w=512, seed=900003, em_every=0),
 }
 
 
@@ -210,6 +212,41 @@ def run_batch(args, rank, world):
                 stats={"cg_iters": None, "n_fp64": None}, status=status, e2e=None, n_px=n_px)
 
 
+def run_warmstart(args, rank, world):
+    """Cold start against the packaged warm-start network on one held-out
+    problem of the warm-start workload: sweeps and device seconds until the
+    posterior is within the parity tolerances of converged cold-start EP."""
+    import torch
+
+    import paper_2110_01585_gb300 as pkg
+    from paper_2110_01585_gb300 import synthetic as syn
+    from paper_2110_01585_gb300.train_warmstart import sweeps_to_match
+    from paper_2110_01585_gb300.warmstart import WarmStartNet
+
+    cfg = WORKLOADS[args.workload]
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    net, meta = WarmStartNet.load(os.path.join(os.path.dirname(pkg.__file__), "data",
+                                               "warmstart_gauss15_128.npz"))
+    beta, probes = float(meta["beta"]), int(meta["probes"])
+    p = syn.warmstart_problem(cfg["h"], cfg["w"], seed=cfg["seed"] + rank, beta=beta)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as sampler:
+        r = sweeps_to_match(p, beta, probes, net=net)
+    clocks = sampler.summary()
+    n_px = cfg["h"] * cfg["w"]
+    cold, warm = r["cold"], r["warm"]
+    ok = cold["sweeps"] is not None and warm["sweeps"] is not None
+    value = n_px * warm["sweeps"] / warm["seconds"] / 1e6 if ok else 0.0
+    return {"value": value, "ms_per_step": (warm["seconds"] / warm["sweeps"] * 1e3) if ok else 0.0,
+            "n_px": n_px, "clocks": clocks, "launches": None, "roofline": None, "e2e": None,
+            "stats": {"cg_iters": None, "n_fp64": None}, "status": 0, "trace": {},
+            "to_posterior": {"tolerance": "1e-4 means, 1e-3 variances vs 250 cold sweeps",
+                             "cold_sweeps": cold["sweeps"], "warm_sweeps": warm["sweeps"],
+                             "cold_s": cold["seconds"], "warm_s": warm["seconds"],
+                             "speedup_time": (cold["seconds"] / warm["seconds"]) if ok else None,
+                             "network": "6 x conv3x3, 32 channels, FP32, trained on 256 x 128^2",
+                             "beta": beta, "rbmc_probes": probes}}
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -219,6 +256,8 @@ def run_ours(args, rank, world):
     cfg = WORKLOADS[args.workload]
     if cfg["kind"] == "batch":
         return run_batch(args, rank, world)
+    if cfg["kind"] == "warmstart":
+        return run_warmstart(args, rank, world)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     prob = _problem(cfg, rank)
@@ -332,6 +371,13 @@ def run_oracle_sample(cfg, budget_s=20.0):
         o = EPOracle("deconv", p.y, p.xi, p.beta, side, side, kernel=p.kernel, site0="rbmc_cg",
                      probes=pr)
         sample = f"{side}x{side} crop-size instance of the same generator/blur/BSNR, CG mode"
+    elif cfg["kind"] == "warmstart":
+        side = 64
+        p = syn.warmstart_problem(side, side, seed=cfg["seed"], beta=18.157)
+        pr = syn.rbmc_probes(8, side * side, side * side, seed=1)
+        o = EPOracle("deconv", p.y, p.xi, p.beta, side, side, kernel=p.kernel, site0="rbmc_cg",
+                     probes=pr)
+        sample = f"{side}x{side} instance of the warm-start workload, CG mode"
     elif cfg["kind"] == "cs":
         side = 64
         p = syn.cs_problem(side, side, ratio=cfg["ratio"], sigma=cfg["sigma"], beta0=cfg["beta0"],
@@ -373,6 +419,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="deconv512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=None,
+                    help="side of a single-image workload's image (smaller cases for profiling)")
     ap.add_argument("--batch-n", type=int, default=None,
                     help="number of problems of the batched256 workload (default 256)")
     args = ap.parse_args()
@@ -381,6 +429,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     cfg = WORKLOADS[args.workload]
+    if args.size is not None and cfg["h"] is not None:
+        cfg["h"] = cfg["w"] = int(args.size)
     config = {"workload": args.workload, "height": cfg["h"], "width": cfg["w"],
               "l2": "flushed before every timed step (256 MB write, untimed)"}
     if cfg["kind"] == "cs":
@@ -390,6 +440,9 @@ def main():
         config.update(problems=cfg["n"], sides="log-uniform 64..1024, even",
                       sigma="U[0.02, 0.2]", blur_widths=[1, 5, 9, 15], em_every=cfg["em_every"],
                       rbmc_probes=cfg["S"])
+    elif cfg["kind"] == "warmstart":
+        config.update(kernel="gaussian 15x15 std 2 periodic", bsnr_db=30.0,
+                      l2="not flushed (each sweep is timed alone)")
     elif cfg["kind"] == "deconv":
         config.update(kernel="uniform 9x9 periodic", bsnr_db=cfg["bsnr_db"], beta0=cfg["beta0"],
                       em_every=cfg["em_every"], rbmc_probes=cfg["S"])
@@ -409,7 +462,7 @@ def main():
                 "unit": "Mpixel-EP-sweeps/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": v, "unit": "Mpixel-EP-sweeps/s", "cores": 1, "kind": "oracle",
+                "cpu_baseline": {"value": v, "unit": "Mpixel-EP-sweeps/s", "cores": cpu["cores"], "kind": "oracle",
                                  "sample": cpu["sample"]},
                 "e2e": {"value": v, "unit": "Mpixel-EP-sweeps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -423,7 +476,7 @@ def main():
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and cfg["kind"] not in ("batch",):
+    if world == 1 and not args.no_cpu_baseline and cfg["kind"] not in ("batch", "warmstart"):
         cpu = run_oracle_sample(cfg, budget_s=20.0)
     line = {"metric": "Mpixel-EP-sweeps/s", "value": round(res["value"], 3), "unit": "Mpixel-EP-sweeps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -435,6 +488,8 @@ def main():
                        "fp64_edges": res["stats"]["n_fp64"], "status": res["status"]},
             "pixels_per_step": res["n_px"],
             "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in res["trace"].items() if v[1]}}
+    if "to_posterior" in res:
+        line["to_posterior"] = res["to_posterior"]
     print(json.dumps(line))
 
 

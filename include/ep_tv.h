@@ -257,6 +257,73 @@ ep_tv_status ep_tv_batch_sweep(ep_tv_batch* batch, int32_t n_sweeps, int32_t em_
 /* Synchronises and frees the batch (not the contexts).  NULL is accepted. */
 void ep_tv_batch_destroy(ep_tv_batch* batch);
 
+/* ---- Learned warm start (not in the paper) ----------------------------------
+   A small fully convolutional network predicts, from an observation, a per-pixel
+   guess of the EP posterior mean and log-variance; ep_tv_warm_start turns the
+   guess into sites before plain EP sweeps, which remain the judge of its error
+   (a context that is never warm-started is the cold-start fallback).  The calls
+   below are the network's building blocks.  Arrays are float32 in NCHW order
+   (image, channel, row, column), DEVICE pointers; every call is asynchronous on
+   cuda_stream and returns EP_TV_ERR_ARG for invalid sizes or NULL pointers. */
+
+/* y = conv3x3(x, weight) + bias on the torus (circular one-pixel padding), then a
+   ReLU if relu != 0.  x: n x cin x h x w; weight: cout x cin x 3 x 3, the taps of a
+   cross-correlation, y[o](i, j) = bias[o] + sum_c sum_{a,e} weight[o, c, a, e]
+   x[c]((i + a - 1) mod h, (j + e - 1) mod w); bias: cout floats or NULL; y: n x cout
+   x h x w, must not alias x.  1 <= cout <= 32, 1 <= n <= 65535. */
+ep_tv_status ep_tv_conv3x3_forward(int32_t n, int32_t cin, int32_t cout, int32_t height,
+                                   int32_t width, const float* x, const float* weight,
+                                   const float* bias, int32_t relu, float* y, void* cuda_stream);
+/* Bytes of DEVICE scratch ep_tv_conv3x3_backward needs for these sizes (0 if invalid). */
+size_t ep_tv_conv3x3_backward_work(int32_t n, int32_t cin, int32_t cout, int32_t height,
+                                   int32_t width);
+/* Gradients through one ep_tv_conv3x3_forward call given dy = dL/dy.  y is that
+   call's output when it applied the ReLU (dy is masked by y > 0), else NULL.
+   Overwrites dweight (cout x cin x 3 x 3), dbias (cout) and, unless it is NULL,
+   dx (n x cin x h x w; needs cin <= 32).  work: DEVICE scratch of at least
+   ep_tv_conv3x3_backward_work bytes, owned by the caller.  The weight gradient
+   is summed per 16 x 16 tile and then over tiles in a fixed order
+   (deterministic). */
+ep_tv_status ep_tv_conv3x3_backward(int32_t n, int32_t cin, int32_t cout, int32_t height,
+                                    int32_t width, const float* x, const float* weight,
+                                    const float* y, const float* dy, float* dx, float* dweight,
+                                    float* dbias, void* work, size_t work_bytes, void* cuda_stream);
+/* One Adam step (Kingma and Ba) on count parameters in place; m, v are the moment
+   buffers (start at zero), t the step number from 1. */
+ep_tv_status ep_tv_adam_step(int64_t count, float* param, const float* grad, float* m, float* v,
+                             int32_t t, float lr, float beta1, float beta2, float eps,
+                             void* cuda_stream);
+/* Training loss of the warm start against converged states of plain EP.  out is
+   the network output, n x 6 x h x w; y and mean are n x h x w (observation, EP
+   posterior mean); tau is n x 5 x h x w (the EP site precisions, site 0 first);
+   log_xi holds n floats, log of each image's noise variance.  With targets
+   t0 = mean - y and t[1 + s] = log(tau_s) + log_xi, loss = mean over images and
+   pixels of w_mean (out0 - t0)^2 + (1/5) sum_s (out[1 + s] - t[1 + s])^2.
+   Writes dL/dout (n x 6 x h x w) and the loss (DEVICE, one double). */
+ep_tv_status ep_tv_warmstart_loss(int32_t n, int32_t height, int32_t width, const float* out,
+                                  const float* y, const float* mean, const float* tau,
+                                  const float* log_xi, float w_mean, float* dout, double* loss,
+                                  void* cuda_stream);
+/* Which sites ep_tv_warm_start sets. */
+typedef enum {
+  EP_TV_WARM_ALL_SITES = 0,  /* all five sites from the prediction */
+  EP_TV_WARM_SITE0 = 1,      /* the likelihood site only; the prior sites keep their
+                                initial (capped) values, as in the cold start */
+  EP_TV_WARM_PRIOR = 2       /* the four prior sites only; the likelihood site keeps
+                                its initial value (y/xi, 1/xi) and is formed by the
+                                first sweep from the warm prior sites */
+} ep_tv_warm_mode;
+
+/* Sets sites of a context from the warm-start network's output for its
+   observation (DEVICE, 6 x N floats): the predicted posterior mean is
+   y + out[0] (y and xi of the context; not for the dense operator, EP_TV_ERR_ARG),
+   and site s gets the precision tau_s = exp(out[1 + s]) / xi (prior sites capped
+   below at 1/var_cap) and the predicted mean, nu_s = tau_s (y + out[0]).  mode
+   (ep_tv_warm_mode) selects the sites.  For denoising, site 0 is exact from the
+   start and keeps (1/xi, y/xi) (EP_TV_WARM_SITE0 then changes nothing).  Call it
+   after ep_tv_init (or ep_tv_reset) and before sweeping. */
+ep_tv_status ep_tv_warm_start(ep_tv_ctx* ctx, const float* out, int32_t mode);
+
 /* Frees the context (synchronises its stream first).  NULL is accepted. */
 void ep_tv_destroy(ep_tv_ctx* ctx);
 

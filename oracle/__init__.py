@@ -21,6 +21,9 @@ ep         Algorithm 1 (EP sweep) and Algorithm 2 (EP-EM), with the site
            updates Eq. update_q0_x / Eq. update_qk_x, the projection of the
            edge moments onto the two pixels, the recombination Eq. Q_x_final,
            the variance cap and damping of Sec. III-C.
+cnn        The convolutional network of the learned warm start (not in the
+           paper): circular 3x3 convolutions, ReLU, their gradients, the Adam
+           step and the training loss.
 
 Every floating-point quantity is float64.
 """

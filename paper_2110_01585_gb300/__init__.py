@@ -264,3 +264,17 @@ def solve_host(y: np.ndarray, xi: float, beta: float, n_sweeps: int, em_every: i
                                 var.ctypes.data_as(ctypes.c_void_p), ctypes.byref(b))
     _lib.check(code, "ep_tv_solve_host")
     return mean, var, b.value
+
+
+WARM_ALL_SITES, WARM_SITE0, WARM_PRIOR = 0, 1, 2
+
+
+def warm_start(ep: "EPTV", out, mode: int = WARM_ALL_SITES):
+    """``ep_tv_warm_start``: set sites of ``ep`` from the warm-start network's
+    output for its observation (CUDA float32 tensor, (6, H, W)); mode
+    WARM_ALL_SITES, WARM_SITE0 (likelihood site only) or WARM_PRIOR (prior sites
+    only)."""
+    out = out.contiguous()
+    _lib.check(ep._lib.ep_tv_warm_start(ep._ctx, ctypes.c_void_p(out.data_ptr()), int(mode)),
+               "ep_tv_warm_start")
+    ep._warm_keep = out

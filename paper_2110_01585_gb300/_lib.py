@@ -71,6 +71,19 @@ SIGNATURES = {
     "ep_tv_batch_create": (c_int32, [c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p)]),
     "ep_tv_batch_sweep": (c_int32, [c_void_p, c_int32, c_int32]),
     "ep_tv_batch_destroy": (None, [c_void_p]),
+    "ep_tv_conv3x3_forward": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p,
+                                        c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "ep_tv_conv3x3_backward_work": (c_size_t, [c_int32, c_int32, c_int32, c_int32, c_int32]),
+    "ep_tv_conv3x3_backward": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_size_t, c_void_p]),
+    "ep_tv_adam_step": (c_int32, [ctypes.c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                  ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  c_void_p]),
+    "ep_tv_warmstart_loss": (c_int32, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, ctypes.c_float, c_void_p, c_void_p,
+                                       c_void_p]),
+    "ep_tv_warm_start": (c_int32, [c_void_p, c_void_p, c_int32]),
     "ep_tv_destroy": (None, [c_void_p]),
     "ep_tv_status_str": (ctypes.c_char_p, [c_int32]),
 }

@@ -445,6 +445,19 @@ ep_tv_status ep_tv_reset(ep_tv_ctx* c) {
   return init_state(c);
 }
 
+ep_tv_status ep_tv_warm_start(ep_tv_ctx* c, const float* out, int32_t mode) {
+  if (!c || !out || c->op.op == EP_TV_OP_DENSE) return EP_TV_ERR_ARG;
+  if (mode != EP_TV_WARM_ALL_SITES && mode != EP_TV_WARM_SITE0 && mode != EP_TV_WARM_PRIOR)
+    return EP_TV_ERR_ARG;
+  if (c->failed) return EP_TV_ERR_STATE;
+  const bool identity = c->op.op == EP_TV_OP_IDENTITY;
+  if (identity && mode == EP_TV_WARM_SITE0) return EP_TV_OK;  // site 0 is exact already
+  launch_warm_start(c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur], out, c->y,
+                    (float)log(c->p.xi), c->n, (float)(1.0 / c->p.var_cap),
+                    identity || mode == EP_TV_WARM_PRIOR, mode == EP_TV_WARM_SITE0, c->stream);
+  return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+}
+
 ep_tv_status ep_tv_solve_host(const ep_tv_operator* op, const float* y_host,
                               const ep_tv_params* p, int32_t n_sweeps, int32_t em_every,
                               float* mean_host, float* var_host, double* beta_out) {

@@ -136,6 +136,9 @@ void launch_abar_reduce(const double* partial, int n_partial, double* dscal, dou
 
 void launch_init_sites(float* tau0, float* nu0, float* tp, float* np, const float* mu0, long long n,
                        float inv_xi, float min_tau, cudaStream_t s);
+void launch_warm_start(float* tau0, float* nu0, float* tp, float* np, const float* out,
+                       const float* y, float log_xi, long long n, float min_tau, bool keep_site0,
+                       bool site0_only, cudaStream_t s);
 void launch_posterior(const float* tau0, const float* nu0, const float* tp, const float* np,
                       long long n, float* mean, float* var, cudaStream_t s);
 

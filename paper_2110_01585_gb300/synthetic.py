@@ -155,6 +155,62 @@ def deconv_problem(h: int = 512, w: int = 512, kernel: Optional[np.ndarray] = No
     return Problem("deconv", x, y, xi, beta0, kernel=np.asarray(kernel, np.float64), seed=seed)
 
 
+def pixel_scale_image(h: int, w: int, rng: np.random.Generator, background: float = 0.5,
+                      grf_length: float = 8.0, grf_std: float = 0.05) -> np.ndarray:
+    """Piecewise-constant image whose features are sized in pixels, not relative
+    to the image, so that small and large images share their local statistics:
+    one rectangle per 64^2 pixels (sides U[4, 48]), one disc per 128^2 pixels
+    (radius U[4, 16]), intensities U[0, 1], plus a Gaussian random field of
+    length scale ``grf_length`` pixels and standard deviation ``grf_std``.  Shapes
+    wrap around the torus."""
+    img = np.full((h, w), background, dtype=np.float64)
+    n_rect = max(1, (h * w) // (64 * 64))
+    n_disc = max(1, (h * w) // (128 * 128))
+    for _ in range(n_rect):
+        r0, c0 = int(rng.integers(0, h)), int(rng.integers(0, w))
+        rh, rw = int(rng.integers(4, 49)), int(rng.integers(4, 49))
+        rows = np.arange(r0, r0 + rh) % h
+        cols = np.arange(c0, c0 + rw) % w
+        img[np.ix_(rows, cols)] = rng.uniform(0.0, 1.0)
+    for _ in range(n_disc):
+        cy, cx = rng.uniform(0, h), rng.uniform(0, w)
+        rad = rng.uniform(4.0, 16.0)
+        rr = np.arange(int(cy - rad) - 1, int(cy + rad) + 2)
+        cc = np.arange(int(cx - rad) - 1, int(cx + rad) + 2)
+        inside = (rr[:, None] + 0.0 - cy) ** 2 + (cc[None, :] + 0.0 - cx) ** 2 <= rad * rad
+        value = rng.uniform(0.0, 1.0)
+        sub = img[np.ix_(rr % h, cc % w)]
+        sub[inside] = value
+        img[np.ix_(rr % h, cc % w)] = sub
+    white = rng.standard_normal((h, w))
+    fy = np.fft.fftfreq(h)[:, None]
+    fx = np.fft.fftfreq(w)[None, :]
+    envelope = np.exp(-2.0 * (math.pi * grf_length) ** 2 * (fy ** 2 + fx ** 2))
+    field = np.real(np.fft.ifft2(np.fft.fft2(white) * envelope))
+    sd = field.std()
+    if sd > 0:
+        img += grf_std * field / sd
+    return img
+
+
+WARMSTART_BLUR_STD = 2.0
+
+
+def warmstart_problem(h: int, w: int, seed: int, bsnr_db: float = 30.0,
+                      beta: float = 1.0) -> Problem:
+    """Deconvolution workload of the learned warm start: 15 x 15 Gaussian blur of
+    standard deviation 2 pixels, BSNR 30 dB, image features sized in pixels
+    (``pixel_scale_image``) so that networks trained on small images apply to
+    large ones."""
+    rng = np.random.default_rng(seed)
+    kernel = gaussian_kernel(15, WARMSTART_BLUR_STD)
+    x = pixel_scale_image(h, w, rng)
+    hx = circular_blur(x, kernel)
+    xi = float(np.var(hx) / 10.0 ** (bsnr_db / 10.0))
+    y = hx + math.sqrt(xi) * rng.standard_normal((h, w))
+    return Problem("deconv", x, y, xi, beta, kernel=kernel, seed=seed)
+
+
 def cs_problem(h: int = 128, w: int = 128, ratio: float = 0.3, sigma: float = 0.01,
                beta0: float = 1.0, seed: int = 0, m: Optional[int] = None) -> Problem:
     """Compressive sensing with a dense Gaussian matrix, entries N(0, 1/M)."""
