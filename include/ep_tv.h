@@ -214,11 +214,11 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* ctx, int32_t kernel, double* ms, int64_
    not allocate after start-up, or runs inside an allocator or host runtime that
    owns the device memory and only hands out the buffers it was asked for.  The
    caller passes every input and output; the scratch the pass needs (one FP64
-   partial sum of E|u| per 16 x 64 tile, a status word, counters) lives in a
-   file-scope device array of 65536 + 8 doubles (512 KB) that every GPU loading
-   the library holds until the process exits.
-     height, width  image size; ceil(height/16) * ceil(width/64) must not exceed
-                    65536 (about 67 M pixels), else EP_TV_ERR_ARG.
+   partial sum of E|u| per work unit of 16 row pairs of a 60-column strip, a
+   status word, counters) lives in a file-scope device array of 65536 + 8 doubles
+   (512 KB) that every GPU loading the library holds until the process exits.
+     height, width  image size; ceil(width/60) * ceil((height/2 + 2)/16) work units
+                    (about 60 M pixels) must not exceed 65536, else EP_TV_ERR_ARG.
      p              uses damping, var_cap, periodic, precision, and xi when y is given.
      beta           DEVICE pointer to the TV parameter (one double).
      y              DEVICE, N floats: denoising, site 0 = (1/xi, y/xi); or NULL and
@@ -247,8 +247,9 @@ ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width, const ep_t
    pointers (the caller still owns and frees the contexts, after the batch). */
 typedef struct ep_tv_batch ep_tv_batch;
 ep_tv_status ep_tv_batch_create(int32_t n, ep_tv_ctx* const* ctxs, ep_tv_batch** out);
-/* n_sweeps sweeps of every context: one launch runs the prior-site pass of all
-   images (blocks mapped to images through a table), then the likelihood-site
+/* n_sweeps sweeps of every context: one persistent launch runs the prior-site
+   pass of all images (warps take contiguous ranges of the images' work units,
+   found through a table), then the likelihood-site
    updates run concurrently on one worker stream per context, each driven by a host
    thread of a pool of up to 16; with em_every > 0 every context's beta is updated
    after each em_every-th sweep.  Returns when all work is enqueued (the likelihood
