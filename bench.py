@@ -52,9 +52,37 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# ---- multi-rank host logic (one process per GPU, independent replicas)
+
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank's own problem: every replica solves a different instance."""
+    return base + 1000 * rank
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The job's time: the largest of the ranks' times."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pixels_per_rank: int, world: int, steps: int, ms_total: float) -> float:
+    """Whole-job Mpixel-EP-sweeps/s: all ranks' pixel-sweeps over the job's time."""
+    return pixels_per_rank * world * steps / (ms_total / 1e3) / 1e6
+
+
 def _problem(cfg, rank=0):
     from paper_2110_01585_gb300 import synthetic as syn
-    seed = cfg["seed"] + 1000 * rank
+    seed = replica_seed(cfg["seed"], rank)
     if cfg["kind"] == "deconv":
         k = syn.uniform_kernel(cfg["kernel"][1])
         return syn.deconv_problem(cfg["h"], cfg["w"], kernel=k, bsnr_db=cfg["bsnr_db"],
@@ -145,7 +173,7 @@ def run_batch(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     n_prob = args.batch_n or cfg["n"]
-    probs = syn.batched_problems(n_prob, seed=cfg["seed"] + 1000 * rank)
+    probs = syn.batched_problems(n_prob, seed=replica_seed(cfg["seed"], rank))
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     ctxs = []
@@ -168,6 +196,7 @@ def run_batch(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    barrier(world)
     for c in ctxs:
         c.trace(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -183,7 +212,14 @@ def run_batch(args, rank, world):
             with torch.cuda.stream(stream):
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
-    ms_total = sum(a.elapsed_time(b) for a, b in ev)
+    barrier(world)
+    # pixels per rank differ between replicas: the job rate sums the ranks' work
+    ms_total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    n_px_job = n_px
+    if world > 1:
+        t = torch.tensor([float(n_px)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        n_px_job = int(t.item())
     trace = {}
     for c in ctxs:
         for k, v in c.trace_read().items():
@@ -196,7 +232,7 @@ def run_batch(args, rank, world):
     batch.close()
     for c in ctxs:
         c.close()
-    value = n_px * args.steps / (ms_total / 1e3) / 1e6
+    value = job_throughput(n_px_job, 1, args.steps, ms_total)
     # kernel classes overlap across worker streams: shares are of summed kernel time
     tot_k = sum(v[0] for v in trace.values()) or 1.0
     name, (kms, kl, units, bpu) = max(trace.items(), key=lambda kv: kv[1][0])
@@ -285,8 +321,7 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     ep.trace(True)
@@ -301,19 +336,14 @@ def run_ours(args, rank, world):
             with torch.cuda.stream(stream):
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     trace = ep.trace_read()
     ep.trace(False)
     st = ep.stats()
     status = ep.status()
-    ms_total = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
     ms_per_step = ms_total / args.steps
-    value = n_px * world * args.steps / (ms_total / 1e3) / 1e6
+    value = job_throughput(n_px, world, args.steps, ms_total)
     launches = sum(v[1] for v in trace.values())
     dom = max(trace.items(), key=lambda kv: kv[1][0])
     name, (kms, kl, units, bpu) = dom
