@@ -192,7 +192,8 @@ typedef enum {
   EP_TV_K_CG_UPDATE = 2,     /* CG x / r update, unit = pixel of one active system */
   EP_TV_K_CG_RESIDUAL = 3,   /* initial CG residual, unit = pixel of one system */
   EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
-  EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one system */
+  EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one
+                                transformed system (pairs of stopped systems are skipped) */
   EP_TV_K_CS = 6,            /* dense-operator likelihood site (Woodbury, FP64), unit = pixel;
                                 its per-unit figure is FP64 flops, not bytes */
   EP_TV_K_COUNT = 7

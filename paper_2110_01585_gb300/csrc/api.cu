@@ -526,6 +526,8 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* c, int32_t kernel, double* ms, int64_t*
     u = (double)(cnt[DC_CG_DIR_UNITS] - c->cnt_base[DC_CG_DIR_UNITS]) * (double)c->n;
   if (kernel == EP_TV_K_CG_UPDATE)
     u = (double)(cnt[DC_CG_UPD_UNITS] - c->cnt_base[DC_CG_UPD_UNITS]) * (double)c->n;
+  if (kernel == EP_TV_K_CG_PRECOND)
+    u = (double)(cnt[DC_CG_PRE_UNITS] - c->cnt_base[DC_CG_PRE_UNITS]) * (double)c->n;
   double bpu = 0.0;
   if (kernel == EP_TV_K_PRIOR_SWEEP)
     bpu = prior_sweep_bytes_per_pixel(c->op.op == EP_TV_OP_IDENTITY);

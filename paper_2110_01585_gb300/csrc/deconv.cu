@@ -672,7 +672,17 @@ struct FftDesc {
   float2* tmp;       // pairs x H x WP (rows of the padded grid beyond H are zero)
   const float* hth;  // |h_f|^2 / xi on the HP x WP grid
   const double* dbar;
+  const float* act;  // CG scalars of the current iteration ([4 R], [4 j] = 1 if system j
+                     // is active), or NULL: transform every system
+  unsigned long long* counters;  // DC_CG_PRE_UNITS counts the systems transformed
 };
+
+// Both systems of a pair have stopped in this CG iteration: their z is not used.
+__device__ __forceinline__ bool pair_idle(const FftDesc& f, int pair) {
+  if (!f.act) return false;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  return f.act[4 * j0] == 0.f && (j1 >= f.R || f.act[4 * j1] == 0.f);
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -796,6 +806,9 @@ __device__ __forceinline__ void make_table(float2* tw, int n) {
 
 // Pack two residual planes into complex rows (zero-padded to WP) and transform them.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
+  if (pair_idle(f, blockIdx.y)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.counters)
+    atomicAdd(&f.counters[DC_CG_PRE_UNITS], 2 * blockIdx.y + 1 < f.R ? 2ull : 1ull);
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
   float2* s = sm2 + f.WP;
@@ -831,6 +844,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f,
 // Column transforms (rows beyond H are zero), the preconditioner filter and the
 // inverse column transforms; only rows below H are kept.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_cols_filter_kernel(FftDesc f) {
+  if (pair_idle(f, blockIdx.y)) return;
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
   float2* s = sm2 + f.HP;
@@ -863,6 +877,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_cols_filter_kernel(FftDesc
 // partial r.z per system.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f, const float* __restrict__ Rr,
                                                                       float* Z, double* part_rz) {
+  if (pair_idle(f, blockIdx.y)) return;
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
   float2* s = sm2 + f.WP;
@@ -1189,9 +1204,14 @@ int ilog2(int v) {
   return l;
 }
 
-// z = M^{-1} r for all systems; r.z partials into rz_buf ([R][nbz]).
-void precond_apply(LikelihoodState* L, double* rz_buf, cudaStream_t s) {
-  const FftDesc& f = L->fd;
+// z = M^{-1} r; r.z partials into rz_buf ([R][nbz]).  With act (the CG scalars of
+// the iteration that just updated r), pairs of systems that both stopped are skipped;
+// without it every system is transformed (the first application of a pass).
+void precond_apply(LikelihoodState* L, double* rz_buf, const float* act,
+                   unsigned long long* counters, cudaStream_t s) {
+  FftDesc f = L->fd;
+  f.act = act;
+  f.counters = counters;
   fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(
       f, L->Rr);
   fft_cols_filter_kernel<<<dim3(f.WP / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
@@ -1600,8 +1620,8 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     if (outer >= L->max_outer || total >= L->max_iter) break;
     if (L->fft) {
       tr->begin(EP_TV_K_CG_PRECOND, s);
-      precond_apply(L, a.part_rz, s);
-      tr->end(s, (double)L->R * N);
+      precond_apply(L, a.part_rz, nullptr, counters, s);
+      tr->end(s, -1.0);
     }
     int launched = 0, pending = -1, slot = 0;
     while (true) {
@@ -1617,8 +1637,9 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
         tr->end(s, -1.0);
         if (L->fft) {
           tr->begin(EP_TV_K_CG_PRECOND, s);
-          precond_apply(L, a.part_rz + (long long)((launched + 1) & 1) * L->R * L->nbz, s);
-          tr->end(s, (double)L->R * N);
+          precond_apply(L, a.part_rz + (long long)((launched + 1) & 1) * L->R * L->nbz, L->d_scal,
+                        counters, s);
+          tr->end(s, -1.0);
         }
         ++launched;
       }

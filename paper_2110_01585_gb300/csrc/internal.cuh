@@ -30,6 +30,7 @@ enum : int {
   DC_CG_ITERS = 2,
   DC_CG_DIR_UNITS = 3,   // active systems summed over direction launches
   DC_CG_UPD_UNITS = 4,   // active systems summed over update launches
+  DC_CG_PRE_UNITS = 5,   // systems transformed, summed over preconditioner applications
   DC_COUNT = 8,
 };
 
