@@ -584,7 +584,12 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
 }
 
 // x += alpha p, r -= alpha q, partials of the new r.Minv.r and r.r.
-__global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
+// 64 threads per 32 x 32 tile: four rows of float4 per thread keep more loads in
+// flight and make the block reduction a smaller share of the work.
+constexpr int kUpdThreads = 64;
+constexpr int kUpdRows = kTile * kTile / 4 / kUpdThreads;
+
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it) {
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
   const int buf = it & 1, nbuf = buf ^ 1;
@@ -611,33 +616,45 @@ __global__ void __launch_bounds__(kThreads) update_kernel(CgArgs a, int it) {
   const float* Q = a.Qp + (long long)j * c.N;
   float rz2 = 0.f, rr2 = 0.f;
   if ((c.W & 3) == 0 && c0 + kTile <= c.W && r0 + kTile <= c.H) {
-    // full tile, rows 16-byte aligned: one float4 of each plane per thread
-    const int tr = threadIdx.x >> 3, c4 = (threadIdx.x & 7) * 4;
-    const long long p = (long long)(r0 + tr) * c.W + c0 + c4;
-    const float4 pv = *reinterpret_cast<const float4*>(P + p);
-    const float4 qv = *reinterpret_cast<const float4*>(Q + p);
-    float4 rv = *reinterpret_cast<const float4*>(Rr + p);
-    double2 x01 = *reinterpret_cast<const double2*>(X + p);
-    double2 x23 = *reinterpret_cast<const double2*>(X + p + 2);
-    x01.x += (double)(alpha * pv.x);
-    x01.y += (double)(alpha * pv.y);
-    x23.x += (double)(alpha * pv.z);
-    x23.y += (double)(alpha * pv.w);
-    rv.x = fmaf(-alpha, qv.x, rv.x);
-    rv.y = fmaf(-alpha, qv.y, rv.y);
-    rv.z = fmaf(-alpha, qv.z, rv.z);
-    rv.w = fmaf(-alpha, qv.w, rv.w);
-    *reinterpret_cast<double2*>(X + p) = x01;
-    *reinterpret_cast<double2*>(X + p + 2) = x23;
-    *reinterpret_cast<float4*>(Rr + p) = rv;
-    rr2 = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
-    if (!a.fft) {
-      const float4 mv = *reinterpret_cast<const float4*>(a.Minv + p);
-      rz2 = rv.x * rv.x * mv.x + rv.y * rv.y * mv.y + rv.z * rv.z * mv.z + rv.w * rv.w * mv.w;
+    // full tile, rows 16-byte aligned: kUpdRows float4 of each plane per thread,
+    // all loads issued before the first store
+    const int c4 = (threadIdx.x & 7) * 4;
+    float4 pv[kUpdRows], qv[kUpdRows], rv[kUpdRows], mv[kUpdRows];
+    double2 x01[kUpdRows], x23[kUpdRows];
+#pragma unroll
+    for (int k = 0; k < kUpdRows; ++k) {
+      const int tr = (threadIdx.x >> 3) + k * (kUpdThreads >> 3);
+      const long long p = (long long)(r0 + tr) * c.W + c0 + c4;
+      pv[k] = *reinterpret_cast<const float4*>(P + p);
+      qv[k] = *reinterpret_cast<const float4*>(Q + p);
+      rv[k] = *reinterpret_cast<const float4*>(Rr + p);
+      x01[k] = *reinterpret_cast<const double2*>(X + p);
+      x23[k] = *reinterpret_cast<const double2*>(X + p + 2);
+      if (!a.fft) mv[k] = *reinterpret_cast<const float4*>(a.Minv + p);
+    }
+#pragma unroll
+    for (int k = 0; k < kUpdRows; ++k) {
+      const int tr = (threadIdx.x >> 3) + k * (kUpdThreads >> 3);
+      const long long p = (long long)(r0 + tr) * c.W + c0 + c4;
+      x01[k].x += (double)(alpha * pv[k].x);
+      x01[k].y += (double)(alpha * pv[k].y);
+      x23[k].x += (double)(alpha * pv[k].z);
+      x23[k].y += (double)(alpha * pv[k].w);
+      float4 r = rv[k];
+      r.x = fmaf(-alpha, qv[k].x, r.x);
+      r.y = fmaf(-alpha, qv[k].y, r.y);
+      r.z = fmaf(-alpha, qv[k].z, r.z);
+      r.w = fmaf(-alpha, qv[k].w, r.w);
+      *reinterpret_cast<double2*>(X + p) = x01[k];
+      *reinterpret_cast<double2*>(X + p + 2) = x23[k];
+      *reinterpret_cast<float4*>(Rr + p) = r;
+      rr2 += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+      if (!a.fft)
+        rz2 += r.x * r.x * mv[k].x + r.y * r.y * mv[k].y + r.z * r.z * mv[k].z + r.w * r.w * mv[k].w;
     }
   } else {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int tr = ty; tr < kTile; tr += kThreads / 32) {
+    for (int tr = ty; tr < kTile; tr += kUpdThreads / 32) {
       const int gr = r0 + tr, gcol = c0 + tx;
       if (gr >= c.H || gcol >= c.W) continue;
       const long long p = (long long)gr * c.W + gcol;
@@ -804,6 +821,25 @@ __device__ __forceinline__ void make_table(float2* tw, int n) {
   }
 }
 
+// s[idx] = get(idx) for idx < total, four loads in flight per thread before the
+// stores to shared memory.
+template <typename Get>
+__device__ __forceinline__ void stage_loads(float2* s, int total, Get get) {
+  for (int base = 0; base < total; base += 4 * kFftThreads) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * kFftThreads + threadIdx.x;
+      v[u] = idx < total ? get(idx) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * kFftThreads + threadIdx.x;
+      if (idx < total) s[idx] = v[u];
+    }
+  }
+}
+
 // Pack two residual planes into complex rows (zero-padded to WP) and transform them.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f, const float* __restrict__ Rr) {
   if (pair_idle(f, blockIdx.y)) return;
@@ -819,17 +855,17 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f,
   make_table(tw, f.WP);
   const float* r0p = Rr + (long long)j0 * N;
   const float* r1p = Rr + (long long)j1 * N;
-  for (int rr = 0; rr < f.rpb; ++rr) {
+  const bool two = j1 < f.R;
+  stage_loads(s, f.rpb * f.WP, [&](int idx) {
+    const int rr = idx / f.WP, cc = idx - rr * f.WP;
     const int row = row0 + rr;
-    for (int cc = threadIdx.x; cc < f.WP; cc += blockDim.x) {
-      float2 v = make_float2(0.f, 0.f);
-      if (row < f.H && cc < f.W) {
-        const long long p = (long long)row * f.W + cc;
-        v = make_float2(r0p[p], j1 < f.R ? r1p[p] : 0.f);
-      }
-      s[rr * f.WP + cc] = v;
+    float2 v = make_float2(0.f, 0.f);
+    if (row < f.H && cc < f.W) {
+      const long long p = (long long)row * f.W + cc;
+      v = make_float2(r0p[p], two ? r1p[p] : 0.f);
     }
-  }
+    return v;
+  });
   __syncthreads();
   fft_forward(s, f.WP, f.rpb, 1, f.WP, tw);
   float2* out = f.tmp + (long long)pair * f.H * f.WP;
@@ -852,10 +888,10 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_cols_filter_kernel(FftDesc
   const int c0 = blockIdx.x * f.cw;
   float2* t = f.tmp + (long long)pair * f.H * f.WP;
   make_table(tw, f.HP);
-  for (int idx = threadIdx.x; idx < f.HP * f.cw; idx += blockDim.x) {
+  stage_loads(s, f.HP * f.cw, [&](int idx) {
     const int i = idx / f.cw, c = idx - i * f.cw;
-    s[idx] = i < f.H ? t[(long long)i * f.WP + c0 + c] : make_float2(0.f, 0.f);
-  }
+    return i < f.H ? t[(long long)i * f.WP + c0 + c] : make_float2(0.f, 0.f);
+  });
   __syncthreads();
   fft_forward(s, f.HP, f.cw, f.cw, 1, tw);
   // filter, then the inverse column transform as conj(F(conj(.)))
@@ -892,11 +928,11 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f,
   const float2* tin = f.tmp + (long long)pair * f.H * f.WP;
   for (int r0 = rbeg; r0 < rend; r0 += f.rpb) {
     __syncthreads();
-    for (int rr = 0; rr < f.rpb; ++rr) {
+    stage_loads(s, f.rpb * f.WP, [&](int idx) {
+      const int rr = idx / f.WP, cc = idx - rr * f.WP;
       const int row = r0 + rr;
-      for (int cc = threadIdx.x; cc < f.WP; cc += blockDim.x)
-        s[rr * f.WP + cc] = row < rend ? cconj(tin[(long long)row * f.WP + cc]) : make_float2(0.f, 0.f);
-    }
+      return row < rend ? cconj(tin[(long long)row * f.WP + cc]) : make_float2(0.f, 0.f);
+    });
     __syncthreads();
     fft_forward(s, f.WP, f.rpb, 1, f.WP, tw);
     float rz0 = 0.f, rz1 = 0.f;
@@ -1633,7 +1669,7 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
         tr->end(s, -1.0);
         cg_scalars_kernel<<<1, 1024, 0, s>>>(a, launched, 1, L->d_scal);
         tr->begin(EP_TV_K_CG_UPDATE, s);
-        update_kernel<<<grid, kThreads, 0, s>>>(a, launched);
+        update_kernel<<<grid, kUpdThreads, 0, s>>>(a, launched);
         tr->end(s, -1.0);
         if (L->fft) {
           tr->begin(EP_TV_K_CG_PRECOND, s);
