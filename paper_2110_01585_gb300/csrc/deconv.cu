@@ -26,7 +26,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -1254,6 +1256,94 @@ void precond_apply(LikelihoodState* L, double* rz_buf, const float* act,
   fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z, rz_buf);
 }
 
+// ---- launch-shape tuning of the FFT preconditioner
+//
+// Rows per block of the two row passes (rpb) and columns per block of the column
+// pass (cw) trade shared memory, occupancy and the length of each block's work;
+// the best pair depends on the padded size and the number of systems.  Measured
+// once per (device, HP, WP, H, R) with CUDA events on the context's stream and
+// cached for every later context of that shape.  Neither changes any result: a
+// transform is computed the same way in any block shape, and the r.z partial sums
+// are grouped by nbz, which is not tuned.
+struct FftShape {
+  int rpb, cw;
+};
+std::mutex g_tune_mu;
+std::map<std::array<int, 5>, FftShape> g_tune;
+
+float time_precond(LikelihoodState* L, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  const int reps = 3;
+  precond_apply(L, L->part + (size_t)L->R * L->nbmax, nullptr, nullptr, s);  // warm
+  cudaEventRecord(e0, s);
+  for (int i = 0; i < reps; ++i)
+    precond_apply(L, L->part + (size_t)L->R * L->nbmax, nullptr, nullptr, s);
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+    return -1.f;
+  return ms;
+}
+
+void tune_fft_shape(LikelihoodState* L, cudaStream_t s) {
+  const char* env = getenv("EPTV_FFT_TUNE");
+  if (env && env[0] == '0') return;
+  FftDesc& f = L->fd;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::array<int, 5> key{dev, f.HP, f.WP, f.H, f.R};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      f.rpb = it->second.rpb;
+      f.cw = it->second.cw;
+      L->smem_rows = sizeof(float2) * ((size_t)f.WP + (size_t)f.rpb * f.WP);
+      L->smem_cols = sizeof(float2) * ((size_t)f.HP + (size_t)f.HP * f.cw);
+      return;
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  // candidates: powers of two up to the shapes the plan allows (the defaults)
+  const int rpb_max = f.rpb, cw_max = f.cw;
+  auto set = [&](int rpb, int cw) {
+    f.rpb = rpb;
+    f.cw = cw;
+    L->smem_rows = sizeof(float2) * ((size_t)f.WP + (size_t)rpb * f.WP);
+    L->smem_cols = sizeof(float2) * ((size_t)f.HP + (size_t)f.HP * cw);
+  };
+  FftShape best{rpb_max, cw_max};
+  float best_ms = time_precond(L, s, e0, e1);
+  bool ok = best_ms >= 0.f;
+  for (int cw = 1; ok && cw < cw_max; cw *= 2) {
+    set(best.rpb, cw);
+    const float ms = time_precond(L, s, e0, e1);
+    if (ms < 0.f) ok = false;
+    else if (ms < best_ms) { best_ms = ms; best.cw = cw; }
+  }
+  for (int rpb = 1; ok && rpb < rpb_max; rpb *= 2) {
+    set(rpb, best.cw);
+    const float ms = time_precond(L, s, e0, e1);
+    if (ms < 0.f) ok = false;
+    else if (ms < best_ms) { best_ms = ms; best.rpb = rpb; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) {  // keep the plan's shapes
+    cudaGetLastError();
+    best = FftShape{rpb_max, cw_max};
+  }
+  set(best.rpb, best.cw);
+  if (L->debug)
+    fprintf(stderr, "[eptv fft] HP %d WP %d H %d R %d: rpb %d (of %d) cw %d (of %d), %.3f ms / 3\n",
+            f.HP, f.WP, f.H, f.R, best.rpb, rpb_max, best.cw, cw_max, best_ms);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+}
+
 // E1 = H^T eps1 / sqrt(xi) from E1 holding eps1 (in place through Rr as scratch).
 ep_tv_status finish_probes(LikelihoodState* L, cudaStream_t s) {
   const long long N = L->c.N;
@@ -1546,6 +1636,11 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   if (st != EP_TV_OK) {
     likelihood_destroy(L);
     return st;
+  }
+  if (L->fft) tune_fft_shape(L, s);
+  if (cudaGetLastError() != cudaSuccess) {
+    likelihood_destroy(L);
+    return EP_TV_ERR_CUDA;
   }
   *out = L;
   return EP_TV_OK;
