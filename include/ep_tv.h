@@ -259,6 +259,16 @@ ep_tv_status ep_tv_batch_sweep(ep_tv_batch* batch, int32_t n_sweeps, int32_t em_
 /* Synchronises and frees the batch (not the contexts).  NULL is accepted. */
 void ep_tv_batch_destroy(ep_tv_batch* batch);
 
+/* CUDA graphs (not in the paper).  Contexts without a likelihood solver
+   (denoising) and batches of them, on a stream other than the legacy default
+   stream, with tracing off and the default update order, run ep_tv_sweep /
+   ep_tv_batch_sweep calls of at least two periods of lcm(2, em_every) sweeps by
+   replaying a graph of one period, captured on first use (thread-local capture
+   mode) and cached per buffer parity; the remaining sweeps are launched
+   directly.  Results are identical to direct launches.  Returns how many of the
+   context's sweeps ran from graph replays (-1 for NULL). */
+int64_t ep_tv_graph_sweeps(const ep_tv_ctx* ctx);
+
 /* ---- Learned warm start (not in the paper) ----------------------------------
    A small fully convolutional network predicts, from an observation, a per-pixel
    guess of the EP posterior mean and log-variance; ep_tv_warm_start turns the

@@ -178,6 +178,10 @@ class EPTV:
         return {"passes": a.value, "iterations": b.value, "relres_mean": rm.value,
                 "relres_probe_max": rp.value}
 
+    def graph_sweeps(self) -> int:
+        """Sweeps of this context that ran from captured-graph replays."""
+        return int(self._lib.ep_tv_graph_sweeps(self._ctx))
+
     def trace(self, on: bool = True):
         """Enable (and reset) or disable per-kernel CUDA-event tracing."""
         _lib.check(self._lib.ep_tv_trace_enable(self._ctx, int(bool(on))), "ep_tv_trace_enable")

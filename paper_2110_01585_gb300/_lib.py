@@ -71,6 +71,7 @@ SIGNATURES = {
     "ep_tv_batch_create": (c_int32, [c_int32, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p)]),
     "ep_tv_batch_sweep": (c_int32, [c_void_p, c_int32, c_int32]),
     "ep_tv_batch_destroy": (None, [c_void_p]),
+    "ep_tv_graph_sweeps": (ctypes.c_int64, [c_void_p]),
     "ep_tv_conv3x3_forward": (c_int32, [c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "ep_tv_conv3x3_backward_work": (c_size_t, [c_int32, c_int32, c_int32, c_int32, c_int32]),

@@ -44,6 +44,12 @@ struct ep_tv_ctx {
   unsigned long long cnt_base[DC_COUNT] = {};  // counters when tracing was enabled
   bool failed = false;
   long long sweeps = 0;
+  // Sweeps of a context without a likelihood solver replayed from a captured
+  // graph: one per starting buffer parity, for the EM period it was captured with.
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_em[2] = {-1, -1};
+  int graph_len[2] = {0, 0};
+  long long graph_sweeps = 0;  // sweeps run from graph replays (this context or its batch)
 };
 
 namespace {
@@ -88,8 +94,18 @@ ep_tv_status check_params(const ep_tv_operator* op, const ep_tv_params* p) {
   return EP_TV_OK;
 }
 
+void drop_graphs(ep_tv_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    if (c->graph[b]) cudaGraphExecDestroy(c->graph[b]);
+    c->graph[b] = nullptr;
+    c->graph_em[b] = -1;
+    c->graph_len[b] = 0;
+  }
+}
+
 void free_ctx(ep_tv_ctx* c) {
   if (!c) return;
+  drop_graphs(c);
   if (c->lik) likelihood_destroy(c->lik);
   cudaFree(c->tau0);
   cudaFree(c->nu0);
@@ -161,6 +177,44 @@ SweepArgs sweep_args(ep_tv_ctx* c, int order) {
   a.status = c->status;
   a.counters = c->counters;
   return a;
+}
+
+// Graph of `period` sweeps (default order) of a context without a likelihood
+// solver, starting from buffer parity c->cur; captured on first use and cached.
+cudaGraphExec_t graph_for(ep_tv_ctx* c, int period, int em_every) {
+  const int b = c->cur;
+  if (c->graph[b] && c->graph_em[b] == em_every && c->graph_len[b] == period) return c->graph[b];
+  if (c->graph[b]) {
+    cudaGraphExecDestroy(c->graph[b]);
+    c->graph[b] = nullptr;
+  }
+  prior_sweep_prewarm();  // occupancy queries and attributes outside the capture
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  int cur = c->cur;
+  for (int t = 0; t < period; ++t) {
+    SweepArgs a = sweep_args(c, 0x4321);
+    a.tin = c->ptau[cur];
+    a.nin = c->pnu[cur];
+    a.tout = c->ptau[cur ^ 1];
+    a.nout = c->pnu[cur ^ 1];
+    launch_prior_sweep(a, true, c->stream);
+    cur ^= 1;
+    if (em_every > 0 && (t + 1) % em_every == 0)
+      launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
+  }
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  c->graph[b] = exec;
+  c->graph_em[b] = em_every;
+  c->graph_len[b] = period;
+  return exec;
 }
 
 }  // namespace
@@ -277,7 +331,25 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
       }
     }
   }
-  for (int t = 0; t < n_sweeps; ++t) {
+  int t0 = 0;
+  if (!k_order && !c->lik && !c->tracer.on && c->stream != nullptr) {
+    // Denoising: a sweep is the prior-site launch (and an E|u| reduction with EM),
+    // the same launches every period of lcm(2, em_every) sweeps; replay them from
+    // a graph captured once.
+    const int period = em_every > 0 ? (em_every % 2 == 0 ? em_every : 2 * em_every) : 2;
+    const int reps = n_sweeps / period;
+    if (reps >= 2) {
+      cudaGraphExec_t g = graph_for(c, period, em_every);
+      if (g) {
+        for (int r = 0; r < reps; ++r)
+          if (cudaGraphLaunch(g, c->stream) != cudaSuccess) return EP_TV_ERR_CUDA;
+        c->sweeps += (long long)reps * period;
+        c->graph_sweeps += (long long)reps * period;
+        t0 = reps * period;
+      }
+    }
+  }
+  for (int t = t0; t < n_sweeps; ++t) {
     int order = 0;
     for (int u = 0; u < 4; ++u) {
       int k = k_order ? k_order[4 * t + u] : u + 1;
@@ -568,9 +640,85 @@ struct ep_tv_batch {
   int next_job = 0, jobs_total = 0, jobs_done = 0;
   bool stop = false;
   ep_tv_status job_err = EP_TV_OK;
+  // Batches without likelihood solvers: sweeps replayed from a captured graph of
+  // one persistent launch per sweep over two fixed image tables (one per parity).
+  BatchItem* g_items[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph = nullptr;
+  int graph_em = -1, graph_len = 0;
+  std::vector<int> graph_cur;            // buffer parity of every context at capture
 };
 
 namespace {
+
+// Image table of a sweep with every context's prior buffers at parity cur ^ flip.
+void fill_items(ep_tv_batch* b, BatchItem* h, int flip) {
+  long long unit = 0;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    ep_tv_ctx* c = b->ctx[i];
+    h[i].a = sweep_args(c, 0x4321);
+    if (flip) {
+      h[i].a.tin = c->ptau[c->cur ^ 1];
+      h[i].a.nin = c->pnu[c->cur ^ 1];
+      h[i].a.tout = c->ptau[c->cur];
+      h[i].a.nout = c->pnu[c->cur];
+    }
+    prior_sweep_prepare(h[i].a);
+    h[i].site0_from_y = c->op.op == EP_TV_OP_IDENTITY;
+    h[i].units = prior_sweep_blocks(c->height, c->width);
+    h[i].unit_begin = unit;
+    unit += h[i].units;
+  }
+}
+
+// Graph of `period` batch sweeps from the contexts' current parities (captured on
+// first use, recaptured when the parities or the EM period differ).
+cudaGraphExec_t batch_graph(ep_tv_batch* b, int period, int em_every) {
+  std::vector<int> cur;
+  for (ep_tv_ctx* c : b->ctx) cur.push_back(c->cur);
+  if (b->graph && b->graph_em == em_every && b->graph_len == period && b->graph_cur == cur)
+    return b->graph;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  const size_t n = b->ctx.size();
+  for (int i = 0; i < 2; ++i)
+    if (!b->g_items[i] && cudaMalloc(&b->g_items[i], sizeof(BatchItem) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  std::vector<BatchItem> h(n);
+  for (int f = 0; f < 2; ++f) {
+    fill_items(b, h.data(), f);
+    if (cudaMemcpy(b->g_items[f], h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  prior_sweep_prewarm();
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  for (int t = 0; t < period; ++t) {
+    launch_prior_sweep_batch(b->g_items[t & 1], (int)n, b->total_units, b->stream);
+    if (em_every > 0 && (t + 1) % em_every == 0)
+      for (ep_tv_ctx* c : b->ctx)
+        launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, b->stream);
+  }
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  b->graph = exec;
+  b->graph_em = em_every;
+  b->graph_len = period;
+  b->graph_cur = cur;
+  return exec;
+}
 
 void batch_worker(ep_tv_batch* b) {
   cudaSetDevice(b->device);
@@ -610,6 +758,8 @@ void batch_free(ep_tv_batch* b) {
     if (b->h_items[i]) cudaFreeHost(b->h_items[i]);
     if (b->items_ev[i]) cudaEventDestroy(b->items_ev[i]);
   }
+  for (int i = 0; i < 2; ++i) cudaFree(b->g_items[i]);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto s : b->wstream) cudaStreamDestroy(s);
   for (auto e : b->wdone) cudaEventDestroy(e);
   if (b->prior_done) cudaEventDestroy(b->prior_done);
@@ -669,22 +819,34 @@ ep_tv_status ep_tv_batch_create(int32_t n, ep_tv_ctx* const* ctxs, ep_tv_batch**
 ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_every) {
   if (!b || n_sweeps < 0 || em_every < 0) return EP_TV_ERR_ARG;
   const int n = (int)b->ctx.size();
-  for (ep_tv_ctx* c : b->ctx)
+  bool tracing = false;
+  for (ep_tv_ctx* c : b->ctx) {
     if (c->failed) return EP_TV_ERR_STATE;
-  for (int t = 0; t < n_sweeps; ++t) {
+    tracing |= c->tracer.on;
+  }
+  int t0 = 0;
+  if (b->lik.empty() && !tracing && b->stream != nullptr) {
+    // denoising only: replay one persistent launch per sweep (and the EM
+    // reductions) from a captured graph, lcm(2, em_every) sweeps per replay
+    const int period = em_every > 0 ? (em_every % 2 == 0 ? em_every : 2 * em_every) : 2;
+    const int reps = n_sweeps / period;
+    if (reps >= 2) {
+      cudaGraphExec_t g = batch_graph(b, period, em_every);
+      if (g) {
+        for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(g, b->stream));
+        for (ep_tv_ctx* c : b->ctx) {
+          c->sweeps += (long long)reps * period;
+          c->graph_sweeps += (long long)reps * period;
+        }
+        t0 = reps * period;
+      }
+    }
+  }
+  for (int t = t0; t < n_sweeps; ++t) {
     // image table of this sweep (prior buffers alternate per context)
     CK(cudaEventSynchronize(b->items_ev[b->slot]));
     BatchItem* h = b->h_items[b->slot];
-    long long unit = 0;
-    for (int i = 0; i < n; ++i) {
-      ep_tv_ctx* c = b->ctx[i];
-      h[i].a = sweep_args(c, 0x4321);
-      prior_sweep_prepare(h[i].a);
-      h[i].site0_from_y = c->op.op == EP_TV_OP_IDENTITY;
-      h[i].units = prior_sweep_blocks(c->height, c->width);
-      h[i].unit_begin = unit;
-      unit += h[i].units;
-    }
+    fill_items(b, h, 0);
     CK(cudaMemcpyAsync(b->d_items[b->slot], h, sizeof(BatchItem) * n, cudaMemcpyHostToDevice,
                        b->stream));
     CK(cudaEventRecord(b->items_ev[b->slot], b->stream));
@@ -719,6 +881,8 @@ ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_ever
   }
   return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
 }
+
+int64_t ep_tv_graph_sweeps(const ep_tv_ctx* c) { return c ? c->graph_sweeps : -1; }
 
 void ep_tv_batch_destroy(ep_tv_batch* b) {
   if (!b) return;

@@ -124,6 +124,9 @@ struct BatchItem {
 void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s);
 // Algorithmic DRAM bytes per pixel of one prior-site pass.
 double prior_sweep_bytes_per_pixel(bool site0_from_y);
+// Runs the per-device set-up of the prior-pass launchers (occupancy queries and
+// attributes) so that a later launch inside a stream capture makes no such calls.
+void prior_sweep_prewarm();
 // Fills the fields of `a` that the launch derives (vector access).
 void prior_sweep_prepare(SweepArgs& a);
 // Work units (and E|u| partial sums) of one image's prior-site pass.

@@ -970,6 +970,14 @@ int prior_sweep_blocks(int height, int width) {
   return strips_of(width) * units_per_strip(height);
 }
 
+void prior_sweep_prewarm() {
+  resident_warps(prior_sweep_kernel<true, 4>, 0);
+  resident_warps(prior_sweep_kernel<true, 3>, 1);
+  resident_warps(prior_sweep_kernel<false, 4>, 2);
+  resident_warps(prior_sweep_kernel<false, 3>, 3);
+  resident_warps(prior_sweep_batch_kernel, 4);
+}
+
 void launch_prior_sweep_batch(const BatchItem* items, int n_items, long long total_units,
                               cudaStream_t s) {
   int n_warps, blocks;
