@@ -12,20 +12,22 @@ from ._parity import assert_parity, cuda
 pytestmark = pytest.mark.gpu
 
 
-def _run(side, m, sweeps, em_every, seed):
+def _run(side, m, sweeps, em_every, seed, width=None, periodic=1, order="prior_first"):
     torch = cuda()
-    p = syn.cs_problem(side, side, m=m, seed=seed, beta0=2.0)
+    h, w = side, (width or side)
+    p = syn.cs_problem(h, w, m=m, seed=seed, beta0=2.0)
     # both sides see the same float32 data
     A32 = p.A.astype(np.float32)
     y32 = p.y.astype(np.float32)
     At = torch.as_tensor(A32, device="cuda")
     yt = torch.as_tensor(y32, device="cuda")
-    with EPTV(yt, p.xi, p.beta, op=OP_DENSE, dense=At, height=side, width=side) as ep:
+    with EPTV(yt, p.xi, p.beta, op=OP_DENSE, dense=At, height=h, width=w, periodic=periodic,
+              order_mode=1 if order == "q0_first" else 0) as ep:
         ep.sweep(sweeps, em_every=em_every)
         mu, var = (t.cpu().numpy() for t in ep.posterior())
         assert ep.status() == 0
-    o = EPOracle("cs", y32.astype(np.float64), p.xi, p.beta, side, side,
-                 A=A32.astype(np.float64), site0="woodbury")
+    o = EPOracle("cs", y32.astype(np.float64), p.xi, p.beta, h, w,
+                 A=A32.astype(np.float64), site0="woodbury", periodic=bool(periodic), order=order)
     o.run(sweeps, em_every=em_every)
     mu_r, var_r = o.posterior()
     return mu, var, mu_r, var_r, p
@@ -37,3 +39,10 @@ def test_cs_matches_oracle(side, m, sweeps, em):
     # y is not an image here; scale the mean tolerance by the range of the back-projection
     ref = p.A.T @ p.y
     assert_parity(mu, var, mu_r, var_r, ref)
+
+
+def test_cs_free_boundary_odd_size_q0_first():
+    """A 21 x 34 image with the free boundary (odd height), Algorithm 1's listed
+    order (likelihood site first) and EM."""
+    mu, var, mu_r, var_r, p = _run(21, 214, 6, 3, seed=5, width=34, periodic=0, order="q0_first")
+    assert_parity(mu, var, mu_r, var_r, p.A.T @ p.y)
