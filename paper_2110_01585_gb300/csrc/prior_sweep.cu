@@ -77,52 +77,11 @@ __device__ __forceinline__ int wrap(int v, int n) {
 // g and v for a >= 0 come from the polynomial fits of mills_poly.cuh (about
 // 3e-7 relative), so no erfcx is evaluated; for a = -b < 0 the reflection
 // Q(-b) = 1 - Q(b) of the upper tail Q gives h(a) = phi(b) h(b) / (h(b) - phi(b)).
-
-struct Mills {
-  float h, g, v;
-};
-
-__device__ __forceinline__ Mills mills_fast(float a) {
-  const float b = fabsf(a);
-  const float r = rcp_approx(kMillsK + b);
-  const float u = (kMillsK - b) * r;
-  const float kr = kMillsK * r;
-  Mills m;
-  m.g = mills_G(u) * kr;
-  m.v = mills_V(u) * kr * kr;
-  m.h = m.g + b;
-  if (a < 0.0f) {
-    const float phi = 0.398942280f * __expf(-0.5f * b * b);
-    const float h = phi * m.h * rcp_approx(m.h - phi);  // h(b) - phi(b) >= 0.4
-    m.h = h;
-    m.g = h + b;
-    m.v = 1.0f - h * m.g;
-  }
-  return m;
-}
+// tilted2 below evaluates these in an equivalent sorted form.
 
 struct Moments {
   float d, q, rho, eab;
 };
-
-__device__ __forceinline__ Moments tilted_fast(float mu, float s2, float lam) {
-  const float rs = rsqrtf(s2);
-  const float s = s2 * rs;
-  const float z = mu * rs;
-  const float l = lam * s;
-  const Mills p = mills_fast(l - z);
-  const Mills m = mills_fast(l + z);
-  const float inv = rcp_approx(p.h + m.h);  // a+ + a- = 2 l >= 0: not both h vanish
-  const float wp = m.h * inv, wm = p.h * inv;
-  Moments o;
-  o.d = (wp * (p.h - l) - wm * (m.h - l)) * rs;
-  const float gs = p.g + m.g;
-  const float mix = wp * wm * gs * gs;
-  o.q = wp * p.v + wm * m.v + mix;
-  o.rho = wp * p.h * p.g + wm * m.h * m.g - mix;
-  o.eab = s * (wp * p.g + wm * m.g);
-  return o;
-}
 
 // The same moments in FP64 from the cavity natural parameters (rare; kept out of
 // line so that the streaming loop stays small).
@@ -153,10 +112,10 @@ struct Row {
 struct Ctx {
   float lam, min_tau, damp, keep;
   double lam_d;
-  bool tail;
+  float tail_s2;  // lam s < 1e-3, i.e. s^2 < 1e-6 / lam^2, takes the FP64 moments (-1: never)
   float eab;  // E|u| of the counted edges of this lane since the last flush
   unsigned n_fp64, n_capped;
-  bool bad;
+  float2 fin;  // sum of the stored site values: non-finite iff one of them is
 };
 
 // Geometry of one lane: which of its pixels exist and which it owns.
@@ -188,10 +147,6 @@ struct Edge {
   float tni, nni, tnj, nnj;
 };
 
-__device__ __noinline__ Moments tilted_fast_ool(float mu, float s2, float lam) {
-  return tilted_fast(mu, s2, lam);
-}
-
 // ------------------------------------------- two edges at once, packed FP32
 //
 // The two edges of an update step run through the same arithmetic, so it is
@@ -199,8 +154,11 @@ __device__ __noinline__ Moments tilted_fast_ool(float mu, float s2, float lam) {
 // sm_100-family GPUs: one instruction per operation for both edges.  Constant
 // pairs come from the constant bank.
 
-static __constant__ float2 kPairs[4] = {
-    {kMillsK, kMillsK}, {-1.0f, -1.0f}, {1.0f, 1.0f}, {0.398942280f, 0.398942280f}};
+static __constant__ float2 kPairs[5] = {{kMillsK, kMillsK},
+                                        {-1.0f, -1.0f},
+                                        {1.0f, 1.0f},
+                                        {0.398942280f, 0.398942280f},   // 1 / sqrt(2 pi)
+                                        {-0.721347520f, -0.721347520f}};  // -log2(e) / 2
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -208,6 +166,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, kPairs[1], a); }
 __device__ __forceinline__ float2 rcp2(float2 a) {
   return make_float2(rcp_approx(a.x), rcp_approx(a.y));
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 struct Mills2 {
@@ -236,45 +199,48 @@ struct Moments2 {
   float2 d, q, rho, eab;
 };
 
-// tilted_fast for two edges.  Of a+ and a- (a+ + a- = 2 l >= 0) only the smaller
-// can be negative; its reflection is formed once per edge and selected in.
+// tilted_fast for two edges, with the two halves taken in sorted order: for
+// az = |z| the truncation points are hi = l + az >= l >= 0 and lo = l - az, and
+// only lo can be negative (then its h, g, v come from the reflection).  With
+// w_lo = h_hi / (h_lo + h_hi), w_hi = h_lo / (h_lo + h_hi) the moments become
+//   d   = -sign(z) lam (h_hi - h_lo) / (h_hi + h_lo)
+//   q   = w_lo v_lo + w_hi v_hi + w_lo w_hi (g_lo + g_hi)^2
+//   rho = 2 l (g_lo + g_hi) h_lo h_hi / (h_lo + h_hi)^2
+//   eab = s (w_lo g_lo + w_hi g_hi)
+// (the rho form uses h - g = a on each half and lo + hi = 2 l: a product of
+// positive terms, free of cancellation).
 __device__ __forceinline__ Moments2 tilted2(float2 mu, float2 s2, float2 lam) {
   const float2 rs = make_float2(rsqrtf(s2.x), rsqrtf(s2.y));
   const float2 s = mul2(s2, rs);
   const float2 z = mul2(mu, rs);
+  const float2 az = make_float2(fabsf(z.x), fabsf(z.y));
   const float2 l = mul2(lam, s);
-  const float2 ap = sub2(l, z), am = add2(l, z);
-  Mills2 P = mills_fit2(make_float2(fabsf(ap.x), fabsf(ap.y)));
-  Mills2 M = mills_fit2(make_float2(fabsf(am.x), fabsf(am.y)));
-  // reflection at the smaller argument a = -b: h(a) = phi(b) h(b) / (h(b) - phi(b))
-  const bool px = ap.x < am.x, py = ap.y < am.y;
-  const float2 b = make_float2(fabsf(px ? ap.x : am.x), fabsf(py ? ap.y : am.y));
-  const float2 hb = make_float2(px ? P.h.x : M.h.x, py ? P.h.y : M.h.y);
-  const float2 phi =
-      mul2(kPairs[3], make_float2(__expf(-0.5f * b.x * b.x), __expf(-0.5f * b.y * b.y)));
-  const float2 hn = mul2(mul2(phi, hb), rcp2(sub2(hb, phi)));  // h(b) - phi(b) >= 0.4
+  const float2 hi = add2(l, az), lo = sub2(l, az);
+  const float2 b = make_float2(fabsf(lo.x), fabsf(lo.y));
+  const Mills2 H = mills_fit2(hi);
+  Mills2 L = mills_fit2(b);
+  // reflection at lo = -b < 0: h(lo) = phi(b) h(b) / (h(b) - phi(b)), h(b) - phi(b) >= 0.4
+  const float2 e = mul2(mul2(b, b), kPairs[4]);
+  const float2 phi = mul2(kPairs[3], make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+  const float2 hn = mul2(mul2(phi, L.h), rcp2(sub2(L.h, phi)));
   const float2 gn = add2(hn, b);
   const float2 vn = sub2(kPairs[2], mul2(hn, gn));
-  if ((px ? ap.x : am.x) < 0.0f) {
-    if (px) { P.h.x = hn.x; P.g.x = gn.x; P.v.x = vn.x; } else { M.h.x = hn.x; M.g.x = gn.x; M.v.x = vn.x; }
-  }
-  if ((py ? ap.y : am.y) < 0.0f) {
-    if (py) { P.h.y = hn.y; P.g.y = gn.y; P.v.y = vn.y; } else { M.h.y = hn.y; M.g.y = gn.y; M.v.y = vn.y; }
-  }
-  const float2 inv = rcp2(add2(P.h, M.h));  // not both h vanish
-  const float2 wp = mul2(M.h, inv), wm = mul2(P.h, inv);
+  if (lo.x < 0.0f) { L.h.x = hn.x; L.g.x = gn.x; L.v.x = vn.x; }
+  if (lo.y < 0.0f) { L.h.y = hn.y; L.g.y = gn.y; L.v.y = vn.y; }
+  const float2 inv = rcp2(add2(H.h, L.h));  // not both h vanish
+  const float2 wl = mul2(H.h, inv), wh = mul2(L.h, inv);
   Moments2 o;
-  o.d = mul2(sub2(mul2(wp, sub2(P.h, l)), mul2(wm, sub2(M.h, l))), rs);
-  const float2 gs = add2(P.g, M.g);
-  const float2 mix = mul2(mul2(wp, wm), mul2(gs, gs));
-  o.q = add2(fma2(wp, P.v, mul2(wm, M.v)), mix);
-  o.rho = sub2(fma2(mul2(wp, P.h), P.g, mul2(mul2(wm, M.h), M.g)), mix);
-  o.eab = mul2(s, fma2(wp, P.g, mul2(wm, M.g)));
+  const float2 dm = mul2(mul2(sub2(H.h, L.h), inv), lam);
+  o.d = make_float2(copysignf(dm.x, -z.x), copysignf(dm.y, -z.y));
+  const float2 gs = add2(L.g, H.g);
+  o.q = add2(fma2(wl, L.v, mul2(wh, H.v)), mul2(mul2(wl, wh), mul2(gs, gs)));
+  o.rho = mul2(mul2(gs, mul2(wl, L.h)), mul2(add2(l, l), inv));
+  o.eab = mul2(s, fma2(wl, L.g, mul2(wh, H.g)));
   return o;
 }
 
-// The two independent edges of one update step; the FP64 moments only when
-// some lane of the warp needs them.  Eq. update_qk_x from the tilted moments:
+// The two independent edges of one update step; the FP64 moments replace the
+// packed ones for the edges that need them.  Eq. update_qk_x from the tilted moments:
 // tau = rho / (c_j + q c_i), the variance cap, then nu = tau E + (E - m) / c.
 __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
   const float2 ti = make_float2(e0.ti, e1.ti), tj = make_float2(e0.tj, e1.tj);
@@ -283,22 +249,20 @@ __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
   const float2 mj = mul2(make_float2(e0.nj, e1.nj), cj);
   const float2 s2 = add2(ci, cj);
   const float2 mu = sub2(mi, mj);
-  const float l2 = c.lam * c.lam;
-  const bool t0 = c.tail && e0.valid && l2 * s2.x < 1e-6f;
-  const bool t1 = c.tail && e1.valid && l2 * s2.y < 1e-6f;
-  Moments2 o;
-  if (__any_sync(0xffffffffu, t0 || t1)) {
-    const Moments a = t0 ? tilted_fp64(e0.ti, e0.ni, e0.tj, e0.nj, c.lam_d)
-                         : tilted_fast_ool(mu.x, s2.x, c.lam);
-    const Moments b = t1 ? tilted_fp64(e1.ti, e1.ni, e1.tj, e1.nj, c.lam_d)
-                         : tilted_fast_ool(mu.y, s2.y, c.lam);
-    o.d = make_float2(a.d, b.d);
-    o.q = make_float2(a.q, b.q);
-    o.rho = make_float2(a.rho, b.rho);
-    o.eab = make_float2(a.eab, b.eab);
+  const bool t0 = e0.valid && s2.x < c.tail_s2;
+  const bool t1 = e1.valid && s2.y < c.tail_s2;
+  Moments2 o = tilted2(mu, s2, make_float2(c.lam, c.lam));
+  if (t0 || t1) {
+    // one call site for both edges keeps the rare path small
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+      if (!(k ? t1 : t0)) continue;
+      const Moments a = tilted_fp64(k ? e1.ti : e0.ti, k ? e1.ni : e0.ni, k ? e1.tj : e0.tj,
+                                    k ? e1.nj : e0.nj, c.lam_d);
+      if (k) { o.d.y = a.d; o.q.y = a.q; o.rho.y = a.rho; o.eab.y = a.eab; }
+      else   { o.d.x = a.d; o.q.x = a.q; o.rho.x = a.rho; o.eab.x = a.eab; }
+    }
     c.n_fp64 += (t0 && e0.count) + (t1 && e1.count);
-  } else {
-    o = tilted2(mu, s2, make_float2(c.lam, c.lam));
   }
   float2 tni = mul2(o.rho, rcp2(fma2(o.q, ci, cj)));
   float2 tnj = mul2(o.rho, rcp2(fma2(o.q, cj, ci)));
@@ -573,19 +537,21 @@ __device__ __forceinline__ void store_row(const Io& io_ref, Ctx& c, const Lane& 
   const int base = gr * io_ref.width;
   float* t = io_ref.tout;
   float* m = io_ref.nout;
-  float sum = 0.0f;
   if (io_ref.vec2) {
     t += base + gcol[0];
     m += base + gcol[0];
 #pragma unroll
     for (int s = 1; s < 5; ++s) {
-      *reinterpret_cast<float2*>(t) = make_float2(R.x[0].t[s], R.x[1].t[s]);
-      *reinterpret_cast<float2*>(m) = make_float2(R.x[0].n[s], R.x[1].n[s]);
+      const float2 tv = make_float2(R.x[0].t[s], R.x[1].t[s]);
+      const float2 nv = make_float2(R.x[0].n[s], R.x[1].n[s]);
+      *reinterpret_cast<float2*>(t) = tv;
+      *reinterpret_cast<float2*>(m) = nv;
       t += n;
       m += n;
-      sum += R.x[0].t[s] + R.x[1].t[s] + R.x[0].n[s] + R.x[1].n[s];
+      c.fin = add2(c.fin, add2(tv, nv));
     }
   } else {
+    float sum = 0.0f;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (!L.col_ok[k]) continue;
@@ -600,9 +566,8 @@ __device__ __forceinline__ void store_row(const Io& io_ref, Ctx& c, const Lane& 
         sum += R.x[k].t[s] + R.x[k].n[s];
       }
     }
+    c.fin.x += sum;
   }
-  // a NaN or infinity in any stored site value makes the sum non-finite
-  c.bad |= !isfinite(sum);
 }
 
 // Warp sum of the lanes' E|u| in FP64 (fixed tree), stored in the unit's slot.
@@ -708,14 +673,14 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
   Ctx c;
   c.lam = (float)(*a.beta);
   c.lam_d = *a.beta;
-  c.tail = a.fp64_tail && c.lam > 0.0f;
+  c.tail_s2 = (a.fp64_tail && c.lam > 0.0f) ? 1e-6f / (c.lam * c.lam) : -1.0f;
   c.min_tau = a.min_tau;
   c.damp = a.damping;
   c.keep = 1.0f - a.damping;
   c.eab = 0.0f;
   c.n_fp64 = 0;
   c.n_capped = 0;
-  c.bad = false;
+  c.fin = make_float2(0.0f, 0.0f);
   const int order = a.order;
   const int posX = order_pos(order, kX);
   float2* const carry_smem = stage + kSlots * kSlotFloats2 + L.lane;
@@ -765,7 +730,10 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
       do_step<kI, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
       if (!warm) {
         load_saved_row(carry_smem, carry_ok, carry);
+        save_row(carry_smem, r1);  // r1 is final for this step: frees its registers
         do_step<0, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+      } else {
+        save_row(carry_smem, r1);
       }
     } else {
       const int nt = warm ? posX : 4;
@@ -773,7 +741,10 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
         const int k = (order >> (4 * t)) & 0xF;
         // 1, 2, kI: updates before kX on this pair; 0: kX; 5, 6: V1, V2 after kX
         const int kind = t < posX ? k : (t == posX ? 0 : 4 + k);
-        if (kind == 0) load_saved_row(carry_smem, carry_ok, carry);
+        if (kind == 0) {  // r1 takes no update from kX on
+          load_saved_row(carry_smem, carry_ok, carry);
+          save_row(carry_smem, r1);
+        }
         Edge e0, e1;
         if (kind == 1) gather_h1(L, r0, r1, c0, c1, e0, e1);
         else if (kind == 2) gather_h2(L, r0, r1, c0, c1, e0, e1);
@@ -789,6 +760,7 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
         else if (kind == 6) scatter_h2(c, L, carry, r0, e0, e1);
         else scatter_v<kI>(c, r0, r1, e0, e1);
       }
+      if (warm) save_row(carry_smem, r1);
     }
     if (!warm) {
       store_row(io, c, L, gcol, row0 - 1, carry);
@@ -798,10 +770,9 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
         c.eab = 0.0f;
       }
     }
-    save_row(carry_smem, r1);
     carry_ok = r1.ok;
   }
-  if (c.bad) atomicOr(a.status, ST_NONFINITE);
+  if (!isfinite(c.fin.x + c.fin.y)) atomicOr(a.status, ST_NONFINITE);
   if (c.n_fp64) atomicAdd(&a.counters[DC_FP64], (unsigned long long)c.n_fp64);
   if (c.n_capped) atomicAdd(&a.counters[DC_CAPPED], (unsigned long long)c.n_capped);
 }
