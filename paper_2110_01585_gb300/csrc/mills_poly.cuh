@@ -1,86 +1,44 @@
 // Generated by gen_mills_poly.py; do not edit.
 // g(b) = G(u) K / (b + K), v(b) = V(u) (K / (b + K))^2, u = (K - b) / (K + b), b >= 0;
-// coefficients of u^0 .. u^14.
+// coefficients of u^0 .. u^12 (literals, so that the packed FMAs take them as
+// immediates instead of constant-bank loads).
 #pragma once
 
 namespace eptv {
 
 constexpr float kMillsK = 2.0f;
+constexpr int kMillsDegree = 12;
 
-__device__ __forceinline__ float mills_G(float u) {
-  float p = 1.779735618e-04f;
-  p = fmaf(p, u, 6.985943445e-05f);
-  p = fmaf(p, u, -1.159832800e-03f);
-  p = fmaf(p, u, 3.476753057e-04f);
-  p = fmaf(p, u, 3.041465779e-03f);
-  p = fmaf(p, u, -3.527105914e-03f);
-  p = fmaf(p, u, -2.492271357e-03f);
-  p = fmaf(p, u, 1.078331225e-02f);
-  p = fmaf(p, u, -9.144003327e-03f);
-  p = fmaf(p, u, -1.472682652e-02f);
-  p = fmaf(p, u, 4.442855075e-02f);
-  p = fmaf(p, u, -1.180622736e-02f);
-  p = fmaf(p, u, -1.323406673e-01f);
-  p = fmaf(p, u, 1.678016007e-01f);
-  p = fmaf(p, u, 7.464310650e-01f);
-  return p;
-}
-
-__device__ __forceinline__ float mills_V(float u) {
-  float p = 4.269059762e-04f;
-  p = fmaf(p, u, 1.280884476e-03f);
-  p = fmaf(p, u, -4.134165730e-03f);
-  p = fmaf(p, u, -3.511105471e-03f);
-  p = fmaf(p, u, 1.489520605e-02f);
-  p = fmaf(p, u, -3.988641760e-03f);
-  p = fmaf(p, u, -2.474652902e-02f);
-  p = fmaf(p, u, 3.401531326e-02f);
-  p = fmaf(p, u, 4.992823019e-03f);
-  p = fmaf(p, u, -7.183591634e-02f);
-  p = fmaf(p, u, 7.436602430e-02f);
-  p = fmaf(p, u, 6.526947198e-02f);
-  p = fmaf(p, u, -2.162265483e-01f);
-  p = fmaf(p, u, 3.546015767e-02f);
-  p = fmaf(p, u, 4.571163883e-01f);
-  return p;
-}
-
-static __constant__ float2 kMillsG2[15] = {
-    {7.464310650e-01f, 7.464310650e-01f},
-    {1.678016007e-01f, 1.678016007e-01f},
-    {-1.323406673e-01f, -1.323406673e-01f},
-    {-1.180622736e-02f, -1.180622736e-02f},
-    {4.442855075e-02f, 4.442855075e-02f},
-    {-1.472682652e-02f, -1.472682652e-02f},
-    {-9.144003327e-03f, -9.144003327e-03f},
-    {1.078331225e-02f, 1.078331225e-02f},
-    {-2.492271357e-03f, -2.492271357e-03f},
-    {-3.527105914e-03f, -3.527105914e-03f},
-    {3.041465779e-03f, 3.041465779e-03f},
-    {3.476753057e-04f, 3.476753057e-04f},
-    {-1.159832800e-03f, -1.159832800e-03f},
-    {6.985943445e-05f, 6.985943445e-05f},
-    {1.779735618e-04f, 1.779735618e-04f},
+__device__ constexpr float kMillsG[13] = {
+    7.464310867e-01f,
+    1.678013790e-01f,
+    -1.323427964e-01f,
+    -1.180001915e-02f,
+    4.446261600e-02f,
+    -1.477649222e-02f,
+    -9.348394839e-03f,
+    1.095359462e-02f,
+    -1.908295607e-03f,
+    -3.810909866e-03f,
+    2.184968013e-03f,
+    5.747184676e-04f,
+    -5.369253335e-04f,
 };
 
-static __constant__ float2 kMillsV2[15] = {
-    {4.571163883e-01f, 4.571163883e-01f},
-    {3.546015767e-02f, 3.546015767e-02f},
-    {-2.162265483e-01f, -2.162265483e-01f},
-    {6.526947198e-02f, 6.526947198e-02f},
-    {7.436602430e-02f, 7.436602430e-02f},
-    {-7.183591634e-02f, -7.183591634e-02f},
-    {4.992823019e-03f, 4.992823019e-03f},
-    {3.401531326e-02f, 3.401531326e-02f},
-    {-2.474652902e-02f, -2.474652902e-02f},
-    {-3.988641760e-03f, -3.988641760e-03f},
-    {1.489520605e-02f, 1.489520605e-02f},
-    {-3.511105471e-03f, -3.511105471e-03f},
-    {-4.134165730e-03f, -4.134165730e-03f},
-    {1.280884476e-03f, 1.280884476e-03f},
-    {4.269059762e-04f, 4.269059762e-04f},
+__device__ constexpr float kMillsV[13] = {
+    4.571164404e-01f,
+    3.545609236e-02f,
+    -2.162316553e-01f,
+    6.538330058e-02f,
+    7.444773677e-02f,
+    -7.274654515e-02f,
+    4.502548187e-03f,
+    3.713746917e-02f,
+    -2.334574379e-02f,
+    -9.192234943e-03f,
+    1.284072104e-02f,
+    6.517690757e-04f,
+    -2.639994813e-03f,
 };
-
-constexpr int kMillsDegree = 14;
 
 }  // namespace eptv

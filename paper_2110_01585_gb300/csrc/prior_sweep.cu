@@ -74,8 +74,8 @@ __device__ __forceinline__ int wrap(int v, int n) {
 //   q   = Sbar / s^2        = w+ v+ + w- v- + w+ w- (g+ + g-)^2
 //   rho = 1 - q             = w+ h+ g+ + w- h- g- - w+ w- (g+ + g-)^2
 //   eab = E|u|              = s (w+ g+ + w- g-)
-// g and v for a >= 0 come from the polynomial fits of mills_poly.cuh (about
-// 3e-7 relative), so no erfcx is evaluated; for a = -b < 0 the reflection
+// g and v for a >= 0 come from the degree-12 polynomial fits of mills_poly.cuh
+// (g within 5e-8, v within 1e-6 relative), so no erfcx is evaluated; for a = -b < 0 the reflection
 // Q(-b) = 1 - Q(b) of the upper tail Q gives h(a) = phi(b) h(b) / (h(b) - phi(b)).
 // tilted2 below evaluates these in an equivalent sorted form.
 
@@ -182,11 +182,12 @@ __device__ __forceinline__ Mills2 mills_fit2(float2 b) {
   const float2 r = rcp2(add2(kPairs[0], b));
   const float2 u = mul2(sub2(kPairs[0], b), r);
   const float2 kr = mul2(kPairs[0], r);
-  float2 G = kMillsG2[kMillsDegree], V = kMillsV2[kMillsDegree];
+  float2 G = make_float2(kMillsG[kMillsDegree], kMillsG[kMillsDegree]);
+  float2 V = make_float2(kMillsV[kMillsDegree], kMillsV[kMillsDegree]);
 #pragma unroll
   for (int i = kMillsDegree - 1; i >= 0; --i) {
-    G = fma2(G, u, kMillsG2[i]);
-    V = fma2(V, u, kMillsV2[i]);
+    G = fma2(G, u, make_float2(kMillsG[i], kMillsG[i]));
+    V = fma2(V, u, make_float2(kMillsV[i], kMillsV[i]));
   }
   Mills2 m;
   m.g = mul2(G, kr);
@@ -249,8 +250,8 @@ __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
   const float2 mj = mul2(make_float2(e0.nj, e1.nj), cj);
   const float2 s2 = add2(ci, cj);
   const float2 mu = sub2(mi, mj);
-  const bool t0 = e0.valid && s2.x < c.tail_s2;
-  const bool t1 = e1.valid && s2.y < c.tail_s2;
+  const bool t0 = s2.x < c.tail_s2;  // an invalid edge here costs time only
+  const bool t1 = s2.y < c.tail_s2;
   Moments2 o = tilted2(mu, s2, make_float2(c.lam, c.lam));
   if (t0 || t1) {
     // one call site for both edges keeps the rare path small
@@ -262,15 +263,18 @@ __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
       if (k) { o.d.y = a.d; o.q.y = a.q; o.rho.y = a.rho; o.eab.y = a.eab; }
       else   { o.d.x = a.d; o.q.x = a.q; o.rho.x = a.rho; o.eab.x = a.eab; }
     }
-    c.n_fp64 += (t0 && e0.count) + (t1 && e1.count);
+    c.n_fp64 += (t0 && e0.valid && e0.count) + (t1 && e1.valid && e1.count);
   }
   float2 tni = mul2(o.rho, rcp2(fma2(o.q, ci, cj)));
   float2 tnj = mul2(o.rho, rcp2(fma2(o.q, cj, ci)));
   const bool k0 = e0.valid && e0.count, k1 = e1.valid && e1.count;
-  if (!(tni.x >= c.min_tau)) { tni.x = c.min_tau; c.n_capped += k0; }
-  if (!(tnj.x >= c.min_tau)) { tnj.x = c.min_tau; c.n_capped += k0; }
-  if (!(tni.y >= c.min_tau)) { tni.y = c.min_tau; c.n_capped += k1; }
-  if (!(tnj.y >= c.min_tau)) { tnj.y = c.min_tau; c.n_capped += k1; }
+  if (!(tni.x >= c.min_tau && tnj.x >= c.min_tau && tni.y >= c.min_tau && tnj.y >= c.min_tau)) {
+    // rare: some new precision is below the cap (or not a number)
+    if (!(tni.x >= c.min_tau)) { tni.x = c.min_tau; c.n_capped += k0; }
+    if (!(tnj.x >= c.min_tau)) { tnj.x = c.min_tau; c.n_capped += k0; }
+    if (!(tni.y >= c.min_tau)) { tni.y = c.min_tau; c.n_capped += k1; }
+    if (!(tnj.y >= c.min_tau)) { tnj.y = c.min_tau; c.n_capped += k1; }
+  }
   const float2 nd = mul2(o.d, kPairs[1]);
   const float2 nni = fma2(tni, fma2(ci, o.d, mi), o.d);  // tau E + (E - m) / c
   const float2 nnj = fma2(tnj, fma2(cj, nd, mj), nd);
