@@ -962,8 +962,214 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f,
              j1 < f.R ? part_rz + (long long)j1 * f.nbz + blockIdx.x : nullptr, nullptr);
 }
 
+// ---- register-resident 512-point transforms
+//
+// When a transform length is 512 each transform is held by one warp: lane l
+// keeps x[32 m + l], m = 0..15, and the transform runs as three radix-8 steps,
+// 512 = 8 x 8 x 8, with the index splits n = 64 r + t, t = 8 s + u and
+// k = k1 + 8 k3 + 64 k4 (w_n = exp(-2 pi i / n)):
+//   B_t[k1]              = w512^(t k1) sum_r x[64 r + t] w8^(r k1)
+//   C_u[k1, k3]          = w64^(u k3)  sum_s B_(8 s + u)[k1] w8^(s k3)
+//   X[k1 + 8 k3 + 64 k4] = sum_u C_u[k1, k3] w8^(u k4)
+// The two regroupings pass through a per-warp scratch of kXs float2 in shared
+// memory, padded so that the accesses of a half-warp fall in distinct banks;
+// the output X[32 m + l] lands in lane l, the layout of the input, so a forward
+// transform, a pointwise filter and another transform chain in registers.
+constexpr int kF = 512;
+constexpr int kXs = 578;        // scratch / staged-column pitch in float2
+constexpr int kF512Warps = 8;   // warps per block of the 512-point kernels
+
+// Which passes take the 512-point kernels (the others take the Stockham ones).
+inline bool fft512_rows(const FftDesc& f) { return f.WP == kF; }
+inline bool fft512_cols(const FftDesc& f) { return f.HP == kF && f.WP >= kF512Warps; }
+
+__device__ __forceinline__ void fft512_warp(float2 (&v)[16], float2* xs, const float2* tw) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = l + 32 * h;
+    float2 a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = v[2 * r + h];
+    dft_reg<8>(a);
+    xs[t * 9] = a[0];
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) xs[t * 9 + k1] = cmul(a[k1], tw[(t * k1) & (kF - 1)]);
+  }
+  __syncwarp();
+  const int k1 = l & 7;
+  float2 b[2][8];
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int u = (l >> 3) + 4 * g;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) b[g][s] = xs[(8 * s + u) * 9 + k1];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int u = (l >> 3) + 4 * g;
+    dft_reg<8>(b[g]);
+    xs[u * 72 + k1] = b[g][0];
+#pragma unroll
+    for (int k3 = 1; k3 < 8; ++k3)
+      xs[u * 72 + k1 + 8 * k3] = cmul(b[g][k3], tw[(8 * u * k3) & (kF - 1)]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = l + 32 * h;  // j = k1 + 8 k3
+    float2 c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = xs[u * 72 + j];
+    dft_reg<8>(c);
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) v[2 * k4 + h] = c[k4];
+  }
+  __syncwarp();  // the scratch is free again
+}
+
+// fft_rows_fwd_kernel for WP = 512: one warp per row, rows [blockIdx.x rpb, +rpb).
+__global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDesc f,
+                                                                         const float* __restrict__ Rr,
+                                                                         int rpb) {
+  if (pair_idle(f, blockIdx.y)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.counters)
+    atomicAdd(&f.counters[DC_CG_PRE_UNITS], 2 * blockIdx.y + 1 < f.R ? 2ull : 1ull);
+  __shared__ float2 tw[kF];
+  __shared__ float2 scratch[kF512Warps][kXs];
+  make_table(tw, kF);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const bool two = j1 < f.R;
+  const long long N = (long long)f.H * f.W;
+  const float* r0p = Rr + (long long)j0 * N;
+  const float* r1p = Rr + (long long)j1 * N;
+  float2* out = f.tmp + (long long)pair * f.H * kF;
+  const int rend = min(f.H, (blockIdx.x + 1) * rpb);
+  for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
+    const long long p0 = (long long)row * f.W;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int c = 32 * m + l;
+      v[m] = make_float2(0.f, 0.f);
+      if (c < f.W) v[m] = make_float2(r0p[p0 + c], two ? r1p[p0 + c] : 0.f);
+    }
+    fft512_warp(v, scratch[w], tw);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) out[(long long)row * kF + 32 * m + l] = v[m];
+  }
+}
+
+// fft_cols_filter_kernel for HP = 512: the block takes columns c0 .. c0 + 7 of a
+// pair, stages the 512 x 8 tile in shared memory (64-byte row segments from
+// global memory; rows at and beyond H are zero), and each warp transforms one
+// column in registers, filters it with hthT (the filter stored column-major,
+// [c][i]), transforms again and leaves it in its slot for the block's store.
+__global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(FftDesc f,
+                                                                            const float* __restrict__ hthT) {
+  if (pair_idle(f, blockIdx.y)) return;
+  __shared__ float2 tw[kF];
+  __shared__ float2 cols[kF512Warps][kXs];
+  make_table(tw, kF);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int c0 = blockIdx.x * kF512Warps;
+  float2* t = f.tmp + (long long)blockIdx.y * f.H * f.WP;
+  const int cc = threadIdx.x & 7, ro = threadIdx.x >> 3;  // 32 rows x 8 columns per block step
+  for (int i0 = 0; i0 < kF; i0 += 128) {
+    float2 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u + ro;
+      x[u] = i < f.H ? t[(long long)i * f.WP + c0 + cc] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cols[cc][i0 + 32 * u + ro] = x[u];
+  }
+  __syncthreads();
+  float2* xs = cols[w];
+  float2 v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = xs[32 * m + l];
+  __syncwarp();
+  fft512_warp(v, xs, tw);
+  // filter, then the inverse transform as conj(F(conj(.)))
+  const float dbar = (float)(*f.dbar);
+  const float* g = hthT + (long long)(c0 + w) * kF;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const float gi = __frcp_rn(g[32 * m + l] + dbar);
+    v[m] = make_float2(v[m].x * gi, -v[m].y * gi);
+  }
+  fft512_warp(v, xs, tw);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) xs[32 * m + l] = cconj(v[m]);
+  __syncthreads();
+  for (int i0 = 0; i0 < kF; i0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u + ro;
+      if (i < f.H) t[(long long)i * f.WP + c0 + cc] = cols[cc][i];
+    }
+  }
+}
+
+// fft_rows_inv_kernel for WP = 512: one warp per row of the block's range
+// [blockIdx.x rows_per, +rows_per), rows_per = ceil(H / nbz).
+__global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDesc f,
+                                                                         const float* __restrict__ Rr,
+                                                                         float* Z, double* part_rz) {
+  if (pair_idle(f, blockIdx.y)) return;
+  __shared__ float2 tw[kF];
+  __shared__ float2 scratch[kF512Warps][kXs];
+  make_table(tw, kF);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const bool two = j1 < f.R;
+  const long long N = (long long)f.H * f.W;
+  const float scale = 1.0f / ((float)f.HP * (float)kF);
+  const int rows_per = (f.H + f.nbz - 1) / f.nbz;
+  const int rend = min(f.H, (blockIdx.x + 1) * rows_per);
+  const float2* tin = f.tmp + (long long)pair * f.H * kF;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int row = blockIdx.x * rows_per + w; row < rend; row += kF512Warps) {
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = cconj(tin[(long long)row * kF + 32 * m + l]);
+    fft512_warp(v, scratch[w], tw);
+    const long long p0 = (long long)row * f.W;
+    float rz0 = 0.f, rz1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int c = 32 * m + l;
+      if (c < f.W) {
+        const long long p = p0 + c;
+        const float z0 = v[m].x * scale;
+        Z[(long long)j0 * N + p] = z0;
+        rz0 = fmaf(Rr[(long long)j0 * N + p], z0, rz0);
+        if (two) {
+          const float z1 = -v[m].y * scale;
+          Z[(long long)j1 * N + p] = z1;
+          rz1 = fmaf(Rr[(long long)j1 * N + p], z1, rz1);
+        }
+      }
+    }
+    acc0 += (double)rz0;
+    acc1 += (double)rz1;
+  }
+  block_sum3(acc0, acc1, 0.0, part_rz + (long long)j0 * f.nbz + blockIdx.x,
+             two ? part_rz + (long long)j1 * f.nbz + blockIdx.x : nullptr, nullptr);
+}
+
 // |h_f|^2 / xi on the H x W frequency grid (phases reduced exactly in integers).
-__global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int kw, float inv_xi) {
+// transposed: out[fc * H + fr] (column-major, the layout of the 512-point column pass).
+__global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int kw, float inv_xi,
+                           int transposed) {
   const long long N = (long long)H * W;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
        p += (long long)gridDim.x * blockDim.x) {
@@ -981,7 +1187,7 @@ __global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int
         im += (double)k[a * kw + b] * sn;
       }
     }
-    out[p] = (float)((re * re + im * im) * inv_xi);
+    out[transposed ? (long long)fc * H + fr : p] = (float)((re * re + im * im) * inv_xi);
   }
 }
 
@@ -1250,10 +1456,22 @@ void precond_apply(LikelihoodState* L, double* rz_buf, const float* act,
   FftDesc f = L->fd;
   f.act = act;
   f.counters = counters;
-  fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(
-      f, L->Rr);
-  fft_cols_filter_kernel<<<dim3(f.WP / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
-  fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z, rz_buf);
+  constexpr int kRows512 = 4 * kF512Warps;  // rows per block of the 512-point forward row pass
+  if (fft512_rows(f))
+    fft512_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs), 32 * kF512Warps, 0, s>>>(
+        f, L->Rr, kRows512);
+  else
+    fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(
+        f, L->Rr);
+  if (fft512_cols(f))
+    fft512_cols_filter_kernel<<<dim3(f.WP / kF512Warps, f.pairs), 32 * kF512Warps, 0, s>>>(f, f.hth);
+  else
+    fft_cols_filter_kernel<<<dim3(f.WP / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
+  if (fft512_rows(f))
+    fft512_rows_inv_kernel<<<dim3(f.nbz, f.pairs), 32 * kF512Warps, 0, s>>>(f, L->Rr, L->Z, rz_buf);
+  else
+    fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z,
+                                                                                rz_buf);
 }
 
 // ---- launch-shape tuning of the FFT preconditioner
@@ -1288,6 +1506,7 @@ void tune_fft_shape(LikelihoodState* L, cudaStream_t s) {
   const char* env = getenv("EPTV_FFT_TUNE");
   if (env && env[0] == '0') return;
   FftDesc& f = L->fd;
+  if (fft512_rows(f) && fft512_cols(f)) return;  // the tuned shapes are not used
   int dev = 0;
   cudaGetDevice(&dev);
   const std::array<int, 5> key{dev, f.HP, f.WP, f.H, f.R};
@@ -1506,7 +1725,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     const int cap = kFftMaxItems * kFftThreads;
     f.rpb = std::max(1, std::min({HP, 4096 / WP, cap * rmin(WP) / WP}));
     f.cw = std::max(1, std::min({WP, 16, cap * rmin(HP) / HP}));
-    f.nbz = std::min(c.H, 64);
+    // r.z partials: one per block of the inverse row pass (32 rows each for 512-point rows)
+    f.nbz = WP == kF ? (c.H + 31) / 32 : std::min(c.H, 64);
     L->nbz = f.nbz;
     L->smem_rows = sizeof(float2) * ((size_t)WP + (size_t)f.rpb * WP);
     L->smem_cols = sizeof(float2) * ((size_t)HP + (size_t)HP * f.cw);
@@ -1617,8 +1837,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     L->fd.tmp = L->ftmp;
     L->fd.hth = L->hth;
     L->fd.dbar = L->dbar;
-    hth_kernel<<<grid1d((long long)L->fd.HP * L->fd.WP), 256, 0, s>>>(L->hth, L->fd.HP, L->fd.WP,
-                                                                      L->d_k, kh, kw, L->inv_xi);
+    hth_kernel<<<grid1d((long long)L->fd.HP * L->fd.WP), 256, 0, s>>>(
+        L->hth, L->fd.HP, L->fd.WP, L->d_k, kh, kw, L->inv_xi, fft512_cols(L->fd) ? 1 : 0);
   }
   // H^T y / xi
   conv_t_kernel<<<dim3(grid1d(N), 1), 256, 0, s>>>(cfg.y, L->Hty, c.H, c.W, L->d_k, kh, kw,
