@@ -691,6 +691,7 @@ struct FftDesc {
   float2* tmp;       // pairs x H x WP (rows of the padded grid beyond H are zero)
   const float* hth;  // |h_f|^2 / xi on the HP x WP grid
   const double* dbar;
+  const float2* tw512;  // exp(-2 pi i m / 512), m < 512 (the 512-point kernels)
   const float* act;  // CG scalars of the current iteration ([4 R], [4 j] = 1 if system j
                      // is active), or NULL: transform every system
   unsigned long long* counters;  // DC_CG_PRE_UNITS counts the systems transformed
@@ -979,6 +980,15 @@ constexpr int kF = 512;
 constexpr int kXs = 578;        // scratch / staged-column pitch in float2
 constexpr int kF512Warps = 8;   // warps per block of the 512-point kernels
 
+__global__ void tw512_kernel(float2* tw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < kF) {
+    float sn, cs;
+    sincospif(-2.0f * (float)m / (float)kF, &sn, &cs);
+    tw[m] = make_float2(cs, sn);
+  }
+}
+
 // Which passes take the 512-point kernels (the others take the Stockham ones).
 inline bool fft512_rows(const FftDesc& f) { return f.WP == kF; }
 inline bool fft512_cols(const FftDesc& f) { return f.HP == kF && f.WP >= kF512Warps; }
@@ -1038,7 +1048,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
     atomicAdd(&f.counters[DC_CG_PRE_UNITS], 2 * blockIdx.y + 1 < f.R ? 2ull : 1ull);
   __shared__ float2 tw[kF];
   __shared__ float2 scratch[kF512Warps][kXs];
-  make_table(tw, kF);
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) tw[m] = f.tw512[m];
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int pair = blockIdx.y;
@@ -1074,20 +1084,20 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
   if (pair_idle(f, blockIdx.y)) return;
   __shared__ float2 tw[kF];
   __shared__ float2 cols[kF512Warps][kXs];
-  make_table(tw, kF);
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) tw[m] = f.tw512[m];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int c0 = blockIdx.x * kF512Warps;
   float2* t = f.tmp + (long long)blockIdx.y * f.H * f.WP;
   const int cc = threadIdx.x & 7, ro = threadIdx.x >> 3;  // 32 rows x 8 columns per block step
-  for (int i0 = 0; i0 < kF; i0 += 128) {
-    float2 x[4];
+  {
+    float2 x[16];  // all of the thread's tile loads in flight at once
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + 32 * u + ro;
+    for (int u = 0; u < 16; ++u) {
+      const int i = 32 * u + ro;
       x[u] = i < f.H ? t[(long long)i * f.WP + c0 + cc] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) cols[cc][i0 + 32 * u + ro] = x[u];
+    for (int u = 0; u < 16; ++u) cols[cc][32 * u + ro] = x[u];
   }
   __syncthreads();
   float2* xs = cols[w];
@@ -1108,12 +1118,10 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
 #pragma unroll
   for (int m = 0; m < 16; ++m) xs[32 * m + l] = cconj(v[m]);
   __syncthreads();
-  for (int i0 = 0; i0 < kF; i0 += 128) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + 32 * u + ro;
-      if (i < f.H) t[(long long)i * f.WP + c0 + cc] = cols[cc][i];
-    }
+  for (int u = 0; u < 16; ++u) {
+    const int i = 32 * u + ro;
+    if (i < f.H) t[(long long)i * f.WP + c0 + cc] = cols[cc][i];
   }
 }
 
@@ -1125,7 +1133,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDes
   if (pair_idle(f, blockIdx.y)) return;
   __shared__ float2 tw[kF];
   __shared__ float2 scratch[kF512Warps][kXs];
-  make_table(tw, kF);
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) tw[m] = f.tw512[m];
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int pair = blockIdx.y;
@@ -1138,11 +1146,19 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDes
   const float2* tin = f.tmp + (long long)pair * f.H * kF;
   double acc0 = 0.0, acc1 = 0.0;
   for (int row = blockIdx.x * rows_per + w; row < rend; row += kF512Warps) {
-    float2 v[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = cconj(tin[(long long)row * kF + 32 * m + l]);
-    fft512_warp(v, scratch[w], tw);
     const long long p0 = (long long)row * f.W;
+    float2 v[16], rr[16];  // rr: the residuals of both systems, loaded before the transform
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      v[m] = cconj(tin[(long long)row * kF + 32 * m + l]);
+      const int c = 32 * m + l;
+      rr[m] = make_float2(0.f, 0.f);
+      if (c < f.W) {
+        rr[m].x = Rr[(long long)j0 * N + p0 + c];
+        if (two) rr[m].y = Rr[(long long)j1 * N + p0 + c];
+      }
+    }
+    fft512_warp(v, scratch[w], tw);
     float rz0 = 0.f, rz1 = 0.f;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -1151,11 +1167,11 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDes
         const long long p = p0 + c;
         const float z0 = v[m].x * scale;
         Z[(long long)j0 * N + p] = z0;
-        rz0 = fmaf(Rr[(long long)j0 * N + p], z0, rz0);
+        rz0 = fmaf(rr[m].x, z0, rz0);
         if (two) {
           const float z1 = -v[m].y * scale;
           Z[(long long)j1 * N + p] = z1;
-          rz1 = fmaf(Rr[(long long)j1 * N + p], z1, rz1);
+          rz1 = fmaf(rr[m].y, z1, rz1);
         }
       }
     }
@@ -1384,6 +1400,7 @@ struct LikelihoodState {
   float2* ftmp = nullptr;
   float* Z = nullptr;
   float* hth = nullptr;
+  float2* tw512 = nullptr;
   double* dpart = nullptr;
   double* dbar = nullptr;
   int prep_blocks = 0;
@@ -1456,7 +1473,7 @@ void precond_apply(LikelihoodState* L, double* rz_buf, const float* act,
   FftDesc f = L->fd;
   f.act = act;
   f.counters = counters;
-  constexpr int kRows512 = 4 * kF512Warps;  // rows per block of the 512-point forward row pass
+  constexpr int kRows512 = kF512Warps;  // one row per warp: more blocks in flight hide load latency
   if (fft512_rows(f))
     fft512_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs), 32 * kF512Warps, 0, s>>>(
         f, L->Rr, kRows512);
@@ -1725,8 +1742,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     const int cap = kFftMaxItems * kFftThreads;
     f.rpb = std::max(1, std::min({HP, 4096 / WP, cap * rmin(WP) / WP}));
     f.cw = std::max(1, std::min({WP, 16, cap * rmin(HP) / HP}));
-    // r.z partials: one per block of the inverse row pass (32 rows each for 512-point rows)
-    f.nbz = WP == kF ? (c.H + 31) / 32 : std::min(c.H, 64);
+    // r.z partials: one per block of the inverse row pass (8 rows each for 512-point rows)
+    f.nbz = WP == kF ? (c.H + 7) / 8 : std::min(c.H, 64);
     L->nbz = f.nbz;
     L->smem_rows = sizeof(float2) * ((size_t)WP + (size_t)f.rpb * WP);
     L->smem_cols = sizeof(float2) * ((size_t)HP + (size_t)HP * f.cw);
@@ -1770,7 +1787,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             (!L->fft ||
              (cudaMalloc(&L->ftmp, sizeof(float2) * ((L->R + 1) / 2) * c.H * L->fd.WP) == cudaSuccess &&
               cudaMalloc(&L->Z, sizeof(float) * RN) == cudaSuccess &&
-              cudaMalloc(&L->hth, sizeof(float) * L->fd.HP * L->fd.WP) == cudaSuccess)) &&
+              cudaMalloc(&L->hth, sizeof(float) * L->fd.HP * L->fd.WP) == cudaSuccess &&
+              cudaMalloc(&L->tw512, sizeof(float2) * kF) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&L->d_relres, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_prev_rr, sizeof(double) * L->R) == cudaSuccess &&
@@ -1836,6 +1854,8 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
   if (L->fft) {
     L->fd.tmp = L->ftmp;
     L->fd.hth = L->hth;
+    L->fd.tw512 = L->tw512;
+    tw512_kernel<<<(kF + 255) / 256, 256, 0, s>>>(L->tw512);
     L->fd.dbar = L->dbar;
     hth_kernel<<<grid1d((long long)L->fd.HP * L->fd.WP), 256, 0, s>>>(
         L->hth, L->fd.HP, L->fd.WP, L->d_k, kh, kw, L->inv_xi, fft512_cols(L->fd) ? 1 : 0);
@@ -1890,6 +1910,7 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->dpart);
   cudaFree(L->dbar);
   cudaFree(L->ftmp);
+  cudaFree(L->tw512);
   cudaFree(L->Z);
   cudaFree(L->hth);
   cudaFree(L->d_active);
