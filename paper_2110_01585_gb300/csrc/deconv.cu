@@ -63,6 +63,9 @@ struct ConvDesc {
 };
 
 __device__ __forceinline__ int wrapi(int v, int n) {
+  if (v >= 0 && v < n) return v;  // the common cases without a division
+  if (v < 0 && v >= -n) return v + n;
+  if (v >= n && v < 2 * n) return v - n;
   v %= n;
   return v < 0 ? v + n : v;
 }
@@ -558,6 +561,25 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
   column_table(ctab, c0 - c.hc, RW, c.W);
   __syncthreads();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (a.fft && (c.W & 3) == 0 && (c.hc & 3) == 0 && RW <= 64 && c0 >= c.hc &&
+      c0 + kTile + c.hc <= c.W) {
+    // no column wraps: float4 rows, 16 threads per region row
+    const int q = threadIdx.x & 15;
+    if (4 * q < RW) {
+      for (int rr_ = threadIdx.x >> 4; rr_ < RH; rr_ += kThreads / 16) {
+        const long long p = (long long)wrapi(r0 - c.hr + rr_, c.H) * c.W + c0 - c.hc + 4 * q;
+        float4 v = *reinterpret_cast<const float4*>(z + p);
+        if (it > 0) {
+          const float4 po = *reinterpret_cast<const float4*>(Pold + p);
+          v.x = fmaf(beta, po.x, v.x);
+          v.y = fmaf(beta, po.y, v.y);
+          v.z = fmaf(beta, po.z, v.z);
+          v.w = fmaf(beta, po.w, v.w);
+        }
+        *reinterpret_cast<float4*>(sm.v + rr_ * RW + 4 * q) = v;
+      }
+    }
+  } else
   for (int rr_ = ty; rr_ < RH; rr_ += kThreads / 32) {
     const long long rowp = (long long)wrapi(r0 - c.hr + rr_, c.H) * c.W;
     for (int cc = tx; cc < RW; cc += 32) {
