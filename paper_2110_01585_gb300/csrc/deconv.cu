@@ -1123,6 +1123,10 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
   }
   __syncthreads();
   float2* xs = cols[w];
+  const float* g = hthT + (long long)(c0 + w) * kF;
+  float gv[16];  // the filter column, loaded before the transform
+#pragma unroll
+  for (int m = 0; m < 16; ++m) gv[m] = g[32 * m + l];
   float2 v[16];
 #pragma unroll
   for (int m = 0; m < 16; ++m) v[m] = xs[32 * m + l];
@@ -1130,10 +1134,9 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
   fft512_warp(v, xs, tw);
   // filter, then the inverse transform as conj(F(conj(.)))
   const float dbar = (float)(*f.dbar);
-  const float* g = hthT + (long long)(c0 + w) * kF;
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
-    const float gi = __frcp_rn(g[32 * m + l] + dbar);
+    const float gi = __frcp_rn(gv[m] + dbar);
     v[m] = make_float2(v[m].x * gi, -v[m].y * gi);
   }
   fft512_warp(v, xs, tw);
