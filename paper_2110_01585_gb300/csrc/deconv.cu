@@ -1239,7 +1239,8 @@ __global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int
 __global__ void cg_scalars_kernel(CgArgs a, int it, int stage, float* scal) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int buf = it & 1;
-  for (int j = warp; j < a.R; j += blockDim.x / 32) {
+  const int wpb = blockDim.x / 32;
+  for (int j = blockIdx.x * wpb + warp; j < a.R; j += gridDim.x * wpb) {
     double s0 = 0.0, s1 = 0.0;
     if (stage == 0) {
       for (int i = lane; i < a.nb; i += 32) s0 += a.part_rr[((long long)buf * a.R + j) * a.nb + i];
@@ -2024,11 +2025,11 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     while (true) {
       const int n = std::min(kChunk, L->max_iter - total - launched);
       for (int t = 0; t < n; ++t) {
-        cg_scalars_kernel<<<1, 1024, 0, s>>>(a, launched, 0, L->d_scal);
+        cg_scalars_kernel<<<L->R, 32, 0, s>>>(a, launched, 0, L->d_scal);  // one warp per system
         tr->begin(EP_TV_K_CG_DIRECTION, s);
         direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
         tr->end(s, -1.0);
-        cg_scalars_kernel<<<1, 1024, 0, s>>>(a, launched, 1, L->d_scal);
+        cg_scalars_kernel<<<L->R, 32, 0, s>>>(a, launched, 1, L->d_scal);
         tr->begin(EP_TV_K_CG_UPDATE, s);
         update_kernel<<<grid, kUpdThreads, 0, s>>>(a, launched);
         tr->end(s, -1.0);
