@@ -349,6 +349,67 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   return fast_two_sum(p, fmaf(a.lo, b, e));
 }
 
+// The separable part of residual_kernel with a compile-time K x K kernel: the
+// same float-float H x and FP32 H^T sums in the same order, with the region
+// sizes, index divisions and tap loops resolved at compile time.
+template <int K>
+__device__ __forceinline__ void residual_sep_fixed(const ConvDesc& c, const float* taph,
+                                                   const float* tapl, const float* xh,
+                                                   const float* xl, float* ph, float* pl, float* vs,
+                                                   float* tmpf, float* outb, const float* yp, int r0,
+                                                   int c0) {
+  constexpr int hh = K / 2, hw = K / 2;
+  constexpr int RH = kTile + 2 * (K - 1), RW = RH;
+  constexpr int MH = kTile + 2 * hh, MW = MH;
+  float uh[K], ul[K], vh[K], vl[K];
+#pragma unroll
+  for (int b = 0; b < K; ++b) {
+    uh[b] = taph[b];
+    ul[b] = tapl[b];
+    vh[b] = taph[K + b];
+    vl[b] = tapl[K + b];
+  }
+  for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
+    const int rr = idx / MW, mc = idx - rr * MW;
+    const int base = rr * RW + mc + 2 * hw;
+    ff acc = {0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < K; ++b) acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, vh[b], vl[b]);
+    ph[idx] = acc.hi;
+    pl[idx] = acc.lo;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
+    const int mr = idx / MW, mc = idx - mr * MW;
+    const int base = (mr + 2 * hh) * MW + mc;
+    ff acc = {0.f, 0.f};
+#pragma unroll
+    for (int aa = 0; aa < K; ++aa)
+      acc = ff_fma(acc, ff{ph[base - aa * MW], pl[base - aa * MW]}, uh[aa], ul[aa]);
+    const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
+    const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
+    vs[idx] = v.hi + v.lo;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
+    const int mr = idx / kTile, tc = idx - mr * kTile;
+    const float* row = vs + mr * MW + tc;
+    float acc = 0.f;
+#pragma unroll
+    for (int b = 0; b < K; ++b) acc = fmaf(vh[b], row[b], acc);
+    tmpf[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+    const int tr = idx / kTile, tc = idx - tr * kTile;
+    const float* col = tmpf + tr * kTile + tc;
+    float acc = 0.f;
+#pragma unroll
+    for (int aa = 0; aa < K; ++aa) acc = fmaf(uh[aa], col[aa * kTile], acc);
+    outb[idx] = acc;
+  }
+}
+
 // True residual of every system (blockIdx.z),
 //   r = H^T (y' - H x) / xi + (n' - d x),
 // y' = y, n' = n for the mean system and y' = sqrt(xi) eps1_s, n' = sqrt(d) eps2_s for
@@ -396,75 +457,79 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   }
   __syncthreads();
   const float* yp = j == 0 ? a.Y0 : a.Y1 + (long long)(j - 1) * c.N;
-  // v = y' - H x on the (kh/2, kw/2)-halo region: (H x)(r,c) = sum k[a,b] x(r-a+hh, c-b+hw)
-  if (c.separable) {
-    const float* uh = taph;
-    const float* ul = tapl;
-    const float* vh = taph + c.kh;
-    const float* vl = tapl + c.kh;
-    for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
-      const int rr = idx / MW, mc = idx - rr * MW;
-      const int base = rr * RW + mc + 2 * hw;
-      ff acc = {0.f, 0.f};
-      for (int b = 0; b < c.kw; ++b) acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, vh[b], vl[b]);
-      ph[idx] = acc.hi;
-      pl[idx] = acc.lo;
+  if (c.separable && c.kh == 9 && c.kw == 9) {
+    residual_sep_fixed<9>(c, taph, tapl, xh, xl, ph, pl, vs, tmpf, outb, yp, r0, c0);
+  } else {
+    // v = y' - H x on the (kh/2, kw/2)-halo region: (H x)(r,c) = sum k[a,b] x(r-a+hh, c-b+hw)
+    if (c.separable) {
+      const float* uh = taph;
+      const float* ul = tapl;
+      const float* vh = taph + c.kh;
+      const float* vl = tapl + c.kh;
+      for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
+        const int rr = idx / MW, mc = idx - rr * MW;
+        const int base = rr * RW + mc + 2 * hw;
+        ff acc = {0.f, 0.f};
+        for (int b = 0; b < c.kw; ++b) acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, vh[b], vl[b]);
+        ph[idx] = acc.hi;
+        pl[idx] = acc.lo;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
+        const int mr = idx / MW, mc = idx - mr * MW;
+        const int base = (mr + 2 * hh) * MW + mc;
+        ff acc = {0.f, 0.f};
+        for (int aa = 0; aa < c.kh; ++aa)
+          acc = ff_fma(acc, ff{ph[base - aa * MW], pl[base - aa * MW]}, uh[aa], ul[aa]);
+        const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
+        const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
+        vs[idx] = v.hi + v.lo;
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
+        const int mr = idx / MW, mc = idx - mr * MW;
+        ff acc = {0.f, 0.f};
+        for (int aa = 0; aa < c.kh; ++aa) {
+          const int base = (mr + 2 * hh - aa) * RW + mc + 2 * hw;
+          for (int b = 0; b < c.kw; ++b)
+            acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, taph[aa * c.kw + b], tapl[aa * c.kw + b]);
+        }
+        const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
+        const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
+        vs[idx] = v.hi + v.lo;
+      }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
-      const int mr = idx / MW, mc = idx - mr * MW;
-      const int base = (mr + 2 * hh) * MW + mc;
-      ff acc = {0.f, 0.f};
-      for (int aa = 0; aa < c.kh; ++aa)
-        acc = ff_fma(acc, ff{ph[base - aa * MW], pl[base - aa * MW]}, uh[aa], ul[aa]);
-      const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-      const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
-      vs[idx] = v.hi + v.lo;
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
-      const int mr = idx / MW, mc = idx - mr * MW;
-      ff acc = {0.f, 0.f};
-      for (int aa = 0; aa < c.kh; ++aa) {
-        const int base = (mr + 2 * hh - aa) * RW + mc + 2 * hw;
-        for (int b = 0; b < c.kw; ++b)
-          acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, taph[aa * c.kw + b], tapl[aa * c.kw + b]);
+    // H^T v on the tile in FP32: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
+    if (c.separable) {
+      const float* u = taph;
+      const float* v = taph + c.kh;
+      for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
+        const int mr = idx / kTile, tc = idx - mr * kTile;
+        const float* row = vs + mr * MW + tc;
+        float acc = 0.f;
+        for (int b = 0; b < c.kw; ++b) acc = fmaf(v[b], row[b], acc);
+        tmpf[idx] = acc;
       }
-      const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-      const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
-      vs[idx] = v.hi + v.lo;
-    }
-  }
-  __syncthreads();
-  // H^T v on the tile in FP32: (H^T v)(r, c) = sum k[a, b] v(r + a - hh, c + b - hw)
-  if (c.separable) {
-    const float* u = taph;
-    const float* v = taph + c.kh;
-    for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
-      const int mr = idx / kTile, tc = idx - mr * kTile;
-      const float* row = vs + mr * MW + tc;
-      float acc = 0.f;
-      for (int b = 0; b < c.kw; ++b) acc = fmaf(v[b], row[b], acc);
-      tmpf[idx] = acc;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-      const int tr = idx / kTile, tc = idx - tr * kTile;
-      const float* col = tmpf + tr * kTile + tc;
-      float acc = 0.f;
-      for (int aa = 0; aa < c.kh; ++aa) acc = fmaf(u[aa], col[aa * kTile], acc);
-      outb[idx] = acc;
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-      const int tr = idx / kTile, tc = idx - tr * kTile;
-      float acc = 0.f;
-      for (int aa = 0; aa < c.kh; ++aa) {
-        const float* vrow = vs + (tr + aa) * MW + tc;
-        const float* krow = taph + aa * c.kw;
-        for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], vrow[b], acc);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+        const int tr = idx / kTile, tc = idx - tr * kTile;
+        const float* col = tmpf + tr * kTile + tc;
+        float acc = 0.f;
+        for (int aa = 0; aa < c.kh; ++aa) acc = fmaf(u[aa], col[aa * kTile], acc);
+        outb[idx] = acc;
       }
-      outb[idx] = acc;
+    } else {
+      for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+        const int tr = idx / kTile, tc = idx - tr * kTile;
+        float acc = 0.f;
+        for (int aa = 0; aa < c.kh; ++aa) {
+          const float* vrow = vs + (tr + aa) * MW + tc;
+          const float* krow = taph + aa * c.kw;
+          for (int b = 0; b < c.kw; ++b) acc = fmaf(krow[b], vrow[b], acc);
+        }
+        outb[idx] = acc;
+      }
     }
   }
   __syncthreads();
