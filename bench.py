@@ -143,7 +143,10 @@ def _kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_01585_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+        path = os.path.join(csrc, f)
+        if not os.path.isfile(path) or f.endswith(".pyc"):
+            continue  # e.g. a __pycache__ left by running the generator script
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
