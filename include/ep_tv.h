@@ -272,7 +272,7 @@ int64_t ep_tv_graph_sweeps(const ep_tv_ctx* ctx);
 /* ---- Learned warm start (not in the paper) ----------------------------------
    A small fully convolutional network predicts, from an observation, a per-pixel
    guess of the EP posterior mean and log-variance; ep_tv_warm_start turns the
-   guess into sites before plain EP sweeps, which remain the judge of its error
+   guess into sites before plain EP sweeps, which then correct its error
    (a context that is never warm-started is the cold-start fallback).  The calls
    below are the network's building blocks.  Arrays are float32 in NCHW order
    (image, channel, row, column), DEVICE pointers; every call is asynchronous on

@@ -1,7 +1,7 @@
 // Learned warm start: the building blocks of a small fully convolutional network
 // (3x3 convolutions on the torus with bias and ReLU, their backward pass, the
 // Adam step, the training loss) and nothing else.  The paper has no
-// counterpart; its EP sweeps remain the judge of the network's output.
+// counterpart; its EP sweeps correct whatever the network's output gets wrong.
 //
 // Arrays are float32 NCHW.  The convolution is a direct one on CUDA cores: a
 // block computes a 16 x 16 pixel tile of one image for all (up to 32) output

@@ -3,7 +3,7 @@
 A small fully convolutional network maps an observation to a per-pixel guess of
 the converged EP state: the posterior mean and the precision of each of the five
 sites.  ``ep_tv_warm_start`` sets the sites from it, and plain EP sweeps take
-over from there (and judge the guess: a context that is not warm-started is the
+over from there (and correct the guess: a context that is not warm-started is the
 cold-start fallback).  Predicting the site precisions, not only the posterior,
 starts EP near the fixed point the cold start reaches.
 
