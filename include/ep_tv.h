@@ -29,8 +29,8 @@
  *   - Argument errors are returned synchronously and change nothing.  Errors found
  *     on the device (non-finite site values, solver failure) are latched in a
  *     device status word and returned by the next call that synchronises
- *     (ep_tv_em_beta with an output pointer, ep_tv_posterior_host, ep_tv_status_check,
- *     ep_tv_state_export); after that the context refuses further sweeps with
+ *     (ep_tv_em_beta with an output pointer, ep_tv_status_check, ep_tv_state_export,
+ *     ep_tv_solve_host); after that the context refuses further sweeps with
  *     EP_TV_ERR_STATE until ep_tv_reset.  No call aborts the process.
  *   - A context is not thread-safe; distinct contexts are independent.
  */
@@ -218,9 +218,11 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* ctx, int32_t kernel, double* ms, int64_
    partial sum of E|u| per work unit of 16 row pairs of a 60-column strip, a
    status word, counters) lives in a file-scope device array of 65536 + 8 doubles
    (512 KB) that every GPU loading the library holds until the process exits.
-     height, width  image size; ceil(width/60) * ceil((height/2 + 2)/16) work units
-                    (about 60 M pixels) must not exceed 65536, else EP_TV_ERR_ARG.
-     p              uses damping, var_cap, periodic, precision, and xi when y is given.
+     height, width  image size; its ceil(width / 60) * ceil(((height + 1) / 2 + 1) / 16)
+                    work units (about 126 M pixels at most) must not exceed 65536, and
+                    height * width must not exceed 2^31, else EP_TV_ERR_ARG.
+     p              uses damping, var_cap, periodic, precision (0 or 1), and xi when y
+                    is given.
      beta           DEVICE pointer to the TV parameter (one double).
      y              DEVICE, N floats: denoising, site 0 = (1/xi, y/xi); or NULL and
      tau0, nu0      DEVICE, N floats each: the likelihood site.
@@ -234,7 +236,9 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* ctx, int32_t kernel, double* ms, int64_
    All calls on a device share the scratch array and it keeps the last call's
    contents: calls that overlap on the GPU race and must be serialised by the
    caller.  The first call on a device looks up the array's device address with
-   that device current; make it before any stream capture begins.  Asynchronous. */
+   that device current and keeps it; make it before any stream capture begins,
+   and do not call this entry point again after cudaDeviceReset on that device
+   (the kept address belongs to the reset context).  Asynchronous. */
 ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width, const ep_tv_params* p,
                                        const double* beta, const float* y, const float* tau0,
                                        const float* nu0, const float* tau_in, const float* nu_in,

@@ -5,7 +5,7 @@
 // budgets), allocators that own the whole device and hand out only the buffers
 // they were asked for, or plug-ins whose host does not let them touch the
 // device allocator.  They pass in every input and output buffer; the only
-// scratch this pass needs (one FP64 partial sum of E|u| per tile, a status
+// scratch this pass needs (one FP64 partial sum of E|u| per work unit, a status
 // word and counters) lives in the file-scope array below, of fixed size.
 //
 // Every GPU that loads the library holds this array until the process exits.
@@ -13,7 +13,8 @@
 // calls that overlap on the GPU (different streams, or host threads) race on
 // it; serialise them.  The first call on a device looks up the array's device
 // address with that device current; make that first call before any stream
-// capture begins.
+// capture begins, and do not use the entry point across cudaDeviceReset: the
+// cached address belongs to the context it was looked up in.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -24,11 +25,13 @@
 namespace eptv {
 namespace {
 
-constexpr int kNoAllocMaxBlocks = 65536;  // tiles of 16 x 64 pixels: ~67 M pixels
+// One work unit is 16 row pairs of a 60-column strip, so 65536 units hold images
+// of up to about 65536 * 32 * 60 = 126 M pixels.
+constexpr int kNoAllocMaxBlocks = 65536;
 constexpr int kNoAllocDoubles = kNoAllocMaxBlocks + 8;
 constexpr int kMaxDevices = 64;
 
-// [0, kNoAllocMaxBlocks): per-tile partial sums of E|u|
+// [0, kNoAllocMaxBlocks): per-unit partial sums of E|u|
 // [kNoAllocMaxBlocks + DS_*]: FP64 scalars written by the reduction
 // [kNoAllocMaxBlocks + 4, +8): status word and counters (bytes reinterpreted)
 static __device__ __align__(256) double g_scratch[kNoAllocDoubles];
@@ -70,14 +73,20 @@ extern "C" ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width,
                                                   uint32_t* flags_out, void* cuda_stream) {
   if (!p || !beta || !tau_in || !nu_in || !tau_out || !nu_out || !abar_out) return EP_TV_ERR_ARG;
   if (height < 1 || width < 1) return EP_TV_ERR_ARG;
+  if ((long long)height * width > (1ll << 31)) return EP_TV_ERR_ARG;
   if (!y && (!tau0 || !nu0)) return EP_TV_ERR_ARG;
+  if (p->precision != 0 && p->precision != 1) return EP_TV_ERR_ARG;
   if (p->periodic != 0 && p->periodic != 1) return EP_TV_ERR_ARG;
   if (p->periodic && ((height % 2) || (width % 2))) return EP_TV_ERR_ARG;
   if (!(p->damping > 0.0 && p->damping <= 1.0) || !(p->var_cap > 0.0)) return EP_TV_ERR_ARG;
   if (y && !(p->xi > 0.0)) return EP_TV_ERR_ARG;
   if (tau_in == tau_out || nu_in == nu_out) return EP_TV_ERR_ARG;
+  // Work units in 64-bit: ceil(width / 60) * ceil(((height + 1) / 2 + 1) / 16), the
+  // count prior_sweep_blocks returns, without its int overflow for huge sizes.
+  const long long units = ((long long)width + 59) / 60 * ((((long long)height + 1) / 2 + 1 + 15) / 16);
+  if (units > kNoAllocMaxBlocks) return EP_TV_ERR_ARG;  // image larger than the fixed scratch
   const int nblk = prior_sweep_blocks(height, width);
-  if (nblk > kNoAllocMaxBlocks) return EP_TV_ERR_ARG;  // image larger than the fixed scratch
+  if (nblk != units) return EP_TV_ERR_ARG;
   int order = 0x4321;
   if (k_order) {
     int seen = 0;
