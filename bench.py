@@ -164,6 +164,27 @@ def _ncu_traffic(kernel_name):
     return None
 
 
+# The conjugate-gradient iteration of the deconvolution likelihood site moves at
+# least 32 bytes per pixel per right-hand side: read p, x, r and Q p, write x, r
+# and p (FP32 planes; the method's work, whatever the implementation stores).
+CG_BYTES_PER_PIXEL_RHS = 32.0
+
+
+def cg_iteration_roofline(trace, peak, peak_src):
+    """Whole-iteration roofline of the CG: 32 B per active system-pixel of each
+    iteration over the device time of the direction, update and preconditioner
+    kernels.  Active system-pixels are the update kernel's units."""
+    need = ("cg_direction", "cg_update", "cg_precond")
+    if not all(k in trace and trace[k][1] for k in need):
+        return None
+    ms = sum(trace[k][0] for k in need)
+    units = trace["cg_update"][2]
+    achieved = units * CG_BYTES_PER_PIXEL_RHS / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"bytes_per_pixel_rhs": CG_BYTES_PER_PIXEL_RHS, "system_pixel_iterations": units,
+            "ms": round(ms, 3), "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / peak, 4)}
+
+
 def run_batch(args, rank, world):
     """256 uneven problems (denoising and deconvolution) advanced by ep_tv_batch_sweep."""
     import numpy as np
@@ -361,9 +382,13 @@ def run_ours(args, rank, world):
     roofline = {"bound": bound, "kernel": name, "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_src, "unit": unit, "frac": round(achieved / peak, 4),
                 "traffic": traffic_per_launch,
+                "algorithmic_bytes_per_unit": bpu,
                 "algorithmic_bytes_per_launch": units * bpu / kl if kl else None,
                 "avg_launch_us": kms / kl * 1e3 if kl else None,
                 "share_of_step": round(kms / ms_total, 4) if ms_total else None}
+    cgi = cg_iteration_roofline(trace, peak, peak_src)
+    if cgi is not None:
+        roofline["cg_iteration"] = cgi
     ep.close()
 
     # end to end through the host-buffer API: copies in, all sweeps, posterior out

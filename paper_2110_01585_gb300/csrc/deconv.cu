@@ -7,10 +7,13 @@
 // Monte Carlo for it; the estimator here (fixed probes, so the EP map stays
 // deterministic across sweeps) is
 //   z_s = Q^{-1} w_s,  w_s = H^T eps1_s / sqrt(xi) + sqrt(d) eps2_s   (cov w_s = Q)
-//   Var_i = 1/Q_ii + (1/S) sum_s ((w_s)_i - Q_ii z_{s,i})^2 / Q_ii^2,
-// where (w_s)_i - Q_ii z_{s,i} = sum_{j != i} Q_ij z_{s,j} at the solution.
-// The 1 + S systems share Q and are solved together by Jacobi-preconditioned
-// conjugate gradients in FP32 with FP64 dot products, warm-started from the
+//   Var_i = 1/Q_ii + (1/S) sum_s (sum_{j != i} Q_ij z_{s,j})^2 / Q_ii^2,
+// with the off-diagonal sum taken from an explicit matvec of the computed z_s
+// (rb_offdiag_kernel), so that the estimate does not depend on how closely the
+// probe solves met their tolerance.
+// The 1 + S systems share Q and are solved together by conjugate gradients with
+// a circulant (FFT) preconditioner, in FP32 with FP64 dot products inside an
+// iterative refinement on a float-float true residual, warm-started from the
 // previous sweep's solutions.  Then Eq. update_q0_x with cap and damping.
 //
 // Q p is a periodic stencil: H^T H is the autocorrelation of the kernel,
@@ -1358,25 +1361,70 @@ __global__ void check_kernel(const double* part_rr, const double* thr, const dou
   if (threadIdx.x == 0) *active = cnt;
 }
 
+// Rao-Blackwellised terms of the probes, by an explicit matvec of each computed
+// sample: with Q z = H^T H z / xi + d z and (H^T H)_ii = g0 = sum k^2, the
+// off-diagonal part of row i is
+//   o_s(i) = sum_{j != i} Q_ij z_{s,j} = (H^T H z_s)_i / xi - (g0 / xi) z_{s,i}
+// (the d z terms cancel).  Block z = group g of kRbGroup probes; the block's
+// tile sums o_s(i)^2 over its probes in order and writes acc[g][i].
+constexpr int kRbGroup = 8;
+
+__global__ void __launch_bounds__(kThreads) rb_offdiag_kernel(CgArgs a, float* acc) {
+  extern __shared__ float smem[];
+  const ConvDesc& c = a.c;
+  const int g = blockIdx.z;
+  const int s_lo = g * kRbGroup, s_hi = min(a.S, s_lo + kRbGroup);
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  StencilSmem sm = carve(c, smem);
+  __shared__ float outb[kTile * kTile];
+  __shared__ int ctab[kTile + 2 * kMaxHalf];
+  stage_taps(c, sm.taps);
+  const int RH = kTile + 2 * c.hr, RW = kTile + 2 * c.hc;
+  column_table(ctab, c0 - c.hc, RW, c.W);
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  constexpr int kRowsPerThread = kTile / (kThreads / 32);
+  float sq[kRowsPerThread];
+#pragma unroll
+  for (int u = 0; u < kRowsPerThread; ++u) sq[u] = 0.f;
+  for (int s = s_lo; s < s_hi; ++s) {
+    const double* z = a.X + (long long)(s + 1) * c.N;
+    for (int rr = ty; rr < RH; rr += kThreads / 32) {
+      const long long rowp = (long long)wrapi(r0 - c.hr + rr, c.H) * c.W;
+      for (int cc = tx; cc < RW; cc += 32) sm.v[rr * RW + cc] = (float)z[rowp + ctab[cc]];
+    }
+    __syncthreads();
+    hth_tile(c, sm, outb);
+#pragma unroll
+    for (int u = 0; u < kRowsPerThread; ++u) {
+      const int tr = ty + u * (kThreads / 32);
+      const float zi = sm.v[(tr + c.hr) * RW + tx + c.hc];
+      const float o = outb[tr * kTile + tx] * c.inv_xi - c.g0_xi * zi;
+      sq[u] = fmaf(o, o, sq[u]);
+    }
+    __syncthreads();  // the next probe overwrites the staged region
+  }
+#pragma unroll
+  for (int u = 0; u < kRowsPerThread; ++u) {
+    const int gr = r0 + ty + u * (kThreads / 32), gcol = c0 + tx;
+    if (gr < c.H && gcol < c.W) acc[(long long)g * c.N + (long long)gr * c.W + gcol] = sq[u];
+  }
+}
+
 // Eq. update_q0_x from E = X[0] and the RBMC variance, with cap and damping.
-__global__ void site0_kernel(CgArgs a, float* tau0, float* nu0, float min_tau, float damping,
-                             unsigned* status, unsigned long long* counters) {
+// acc: the n_groups planes of rb_offdiag_kernel, summed in group order.
+__global__ void site0_kernel(CgArgs a, const float* acc, int n_groups, float* tau0, float* nu0,
+                             float min_tau, float damping, unsigned* status,
+                             unsigned long long* counters) {
   const long long N = a.c.N;
   unsigned capped = 0;
   bool bad = false;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
        p += (long long)gridDim.x * blockDim.x) {
     const float minv = a.Minv[p];
-    const float qii = a.c.g0_xi + a.D[p];
-    const float sd = sqrtf(a.D[p]);
-    float acc = 0.f;
-    for (int s = 0; s < a.S; ++s) {
-      const long long o = (long long)s * N + p;
-      const float w = a.E1[o] + sd * a.E2[o];
-      const float off = w - qii * (float)a.X[(long long)(s + 1) * N + p];
-      acc = fmaf(off, off, acc);
-    }
-    const float var = minv + minv * minv * acc / (float)a.S;
+    float sq = 0.f;
+    for (int g = 0; g < n_groups; ++g) sq += acc[(long long)g * N + p];
+    const float var = minv + minv * minv * sq / (float)a.S;
     const float E = (float)a.X[p];
     const float d = a.D[p];
     float tn = 1.0f / var - d;
@@ -2133,21 +2181,28 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
   if (ran_out) set_status_kernel<<<1, 1, 0, s>>>(status, ST_CG_NOCONV);
   store_iters_kernel<<<1, 1, 0, s>>>(counters, (unsigned long long)iters);
   tr->begin(EP_TV_K_SITE0, s);
-  site0_kernel<<<grid1d(N), 256, 0, s>>>(a, tau, nu, L->min_tau, L->damping, status, counters);
+  // Q p is free once the solves have finished: it holds the RB sums
+  const int groups = (L->S + kRbGroup - 1) / kRbGroup;
+  rb_offdiag_kernel<<<dim3(c.tiles_x, c.tiles_y, groups), kThreads, L->smem, s>>>(a, L->Qp);
+  site0_kernel<<<grid1d(N), 256, 0, s>>>(a, L->Qp, groups, tau, nu, L->min_tau, L->damping, status,
+                                         counters);
   tr->end(s, (double)N);
   return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
 }
 
+// What each kernel class must move at least once per unit (the method's data,
+// not the implementation's intermediates), for the roofline.
 double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
   if (L->cs) return kernel == EP_TV_K_CS ? cs_flops(L->cs) : 0.0;
+  const double groups = (double)((L->S + kRbGroup - 1) / kRbGroup);
   switch (kernel) {
-    case EP_TV_K_CG_DIRECTION: return 16.0;  // read r, p; write p, q (per system pixel)
-    case EP_TV_K_CG_UPDATE: return 24.0;     // read x, r, p, q; write x, r
-    case EP_TV_K_CG_RESIDUAL: return 12.0;   // read x and the rhs source; write r
-    case EP_TV_K_CG_PRECOND: return 28.0;    // rows: r in, half-complex out; columns: complex
-                                             // in/out; rows: complex, r in, z out (per system)
-    case EP_TV_K_SITE0:                      // read X (R planes), E1, E2, D, Ncav, Minv,
-      return 4.0 * (L->R + 2 * L->S + 5) + 8.0;  // tau0, nu0; write tau0, nu0
+    case EP_TV_K_CG_DIRECTION: return 16.0;  // read z, p; write p, Q p (per active system pixel)
+    case EP_TV_K_CG_UPDATE: return 32.0;     // read x (FP64), r, p, Q p; write x (FP64), r
+    case EP_TV_K_CG_RESIDUAL: return 24.0;   // read x (FP64), y', the probe planes; write r
+    case EP_TV_K_CG_PRECOND: return 8.0;     // r in, z out (per transformed system pixel)
+    case EP_TV_K_SITE0:                      // read the S probe solutions (FP64), write and
+      return 8.0 * L->S + 8.0 * groups       // read the RB sums, read x_0 (FP64), d, n, Minv,
+             + 36.0;                         // tau0, nu0; write tau0, nu0 (per pixel)
   }
   return 0.0;
 }
