@@ -189,14 +189,16 @@ ep_tv_status ep_tv_solve_host(const ep_tv_operator* op, const float* y_host,
 typedef enum {
   EP_TV_K_PRIOR_SWEEP = 0,   /* fused V_1..V_4 prior-site pass, unit = pixel */
   EP_TV_K_CG_DIRECTION = 1,  /* CG direction + H^T H stencil, unit = pixel of one active system */
-  EP_TV_K_CG_UPDATE = 2,     /* CG x / r update, unit = pixel of one active system */
+  EP_TV_K_CG_UPDATE = 2,     /* CG correction / residual update, unit = pixel of one active system */
   EP_TV_K_CG_RESIDUAL = 3,   /* initial CG residual, unit = pixel of one system */
   EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
   EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one
                                 transformed system (pairs of stopped systems are skipped) */
   EP_TV_K_CS = 6,            /* dense-operator likelihood site (Woodbury, FP64), unit = pixel;
                                 its per-unit figure is FP64 flops, not bytes */
-  EP_TV_K_COUNT = 7
+  EP_TV_K_CG_COMMIT = 7,     /* adds a refinement pass's FP32 correction to the FP64 solution,
+                                unit = pixel of one system that iterated in the pass */
+  EP_TV_K_COUNT = 8
 } ep_tv_kernel;
 
 /* Tracing: with on != 0, every launch of the kernel classes above is bracketed

@@ -20,7 +20,7 @@ STATUS_NAMES = {
 
 OP_IDENTITY, OP_CONV_PERIODIC, OP_DENSE = 0, 1, 2
 KERNELS = {0: "prior_sweep", 1: "cg_direction", 2: "cg_update", 3: "cg_residual", 4: "site0",
-           5: "cg_precond", 6: "cs_woodbury"}
+           5: "cg_precond", 6: "cs_woodbury", 7: "cg_commit"}
 
 # Every function declared in include/ep_tv.h, with its ctypes signature.
 c_void_p, c_int32, c_double, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t

@@ -239,6 +239,34 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c3, double
   __syncthreads();
 }
 
+// Last-block reduction.  Every block of a group has written its partial sum (by
+// thread 0, before the block barrier at the end of block_sum3); each then counts
+// itself in with an atomic, and the block that arrives last returns true and
+// resets the counter for the next launch.  That block sums the group's partials
+// in index order (group_sum), so the result does not depend on which block it is.
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned n_blocks) {
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partial is visible before it is counted
+    last = atomicAdd(counter, 1u) == n_blocks - 1;
+    if (last) atomicExch(counter, 0u);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Sum of n partials in a fixed order, by the first warp of a block (all 32 lanes
+// get the result).  Loads bypass L1: the partials were written by other SMs.
+__device__ __forceinline__ double group_sum(const double* part, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += __ldcg(part + i);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
 struct CgArgs {
   ConvDesc c;
   int R;                 // right-hand sides (1 + S)
@@ -261,12 +289,17 @@ struct CgArgs {
   const double* thr;     // [R] inner-loop convergence threshold on r.r
   const double* rr0;     // [R] r.r at the start of the refinement pass
   float* Z;              // R planes, preconditioned residual (FFT preconditioner)
+  float* Ec;             // R planes, FP32 correction summed over one refinement pass
   double* part_pq;       // [R][nb]
-  double* part_rz;       // [2][R][nbz]
-  double* part_rr;       // [2][R][nb]
+  double* part_rz;       // [R][nbz]
+  double* part_rr;       // [R][nb]
   double* part_bb;       // [R][nb]
   double rtol2;
-  const float* scal;     // [R][4]: active flag, beta, alpha (from cg_scalars_kernel)
+  float* scal;           // [R][4]: active flag, beta; each written by the last block
+                         // of the kernel whose partial sums it needs
+  double* rzs;           // [R] r.z of the current iteration
+  unsigned* arrive;      // [R] block-arrival counters of the update kernel
+  const int* act0;       // [R] 1 if the system iterates in the current refinement pass
   int nb;                // tile blocks per system
   int nbz;               // blocks per system producing r.z partials
   int fft;               // 1: z = M^{-1} r by the circulant preconditioner, else Jacobi
@@ -567,10 +600,13 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
 
 // Per system after a true residual: done if r.r <= rtol^2 b.b (threshold +inf),
 // otherwise the inner loop runs until r.r <= max(eta^2 r.r, (rtol/2)^2 b.b).
-__global__ void thresholds_kernel(const double* part_rr, const double* part_bb, int R, int nb,
+// Also starts the pass's CG scalars: active flag (and act0) = not done, beta = 0,
+// and for Jacobi r.z from the residual kernel's r.Minv.r partials.
+__global__ void thresholds_kernel(const double* part_rr, const double* part_bb,
+                                  const double* part_rz, int fft, int R, int nb,
                                   double rtol2_mean, double rtol2_probe, double eta2, double* thr,
                                   double* relres, double* prev_rr, double* rr0, int first,
-                                  int* active) {
+                                  int* active, float* scal, int* act0, double* rzs) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -600,7 +636,17 @@ __global__ void thresholds_kernel(const double* part_rr, const double* part_bb, 
       rr0[j] = rr;
       relres[j] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
       thr[j] = done ? INFINITY : fmax(eta2 * rr, 0.25 * rtol2 * bb);
+      scal[4 * j] = done ? 0.f : 1.f;
+      scal[4 * j + 1] = 0.f;
+      act0[j] = done ? 0 : 1;
       if (!done) atomicAdd(&cnt, 1);
+    }
+    if (!fft) {
+      double rz = 0;
+      for (int i = lane; i < nb; i += 32) rz += part_rz[(long long)j * nb + i];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) rz += __shfl_down_sync(0xffffffffu, rz, off);
+      if (lane == 0) rzs[j] = rz;
     }
   }
   __syncthreads();
@@ -675,7 +721,12 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(CgArgs a, int it) {
              nullptr);
 }
 
-// x += alpha p, r -= alpha q, partials of the new r.Minv.r and r.r.
+// e += alpha p, r -= alpha q (e: the FP32 correction of this refinement pass,
+// added to the FP64 solution by commit_kernel when the pass ends), partials of
+// the new r.r (and r.Minv.r for Jacobi).  alpha = r.z / p.q: every block sums the
+// direction kernel's p.q partials of its system itself, in the same order, while
+// its tile loads are in flight.  The last block of a system then sets its active
+// flag for the next iteration (and, for Jacobi, beta and r.z).
 // 64 threads per 32 x 32 tile: four rows of float4 per thread keep more loads in
 // flight and make the block reduction a smaller share of the work.
 constexpr int kUpdThreads = 64;
@@ -684,35 +735,30 @@ constexpr int kUpdRows = kTile * kTile / 4 / kUpdThreads;
 __global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it) {
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
-  const int buf = it & 1, nbuf = buf ^ 1;
-  const long long o_cur = ((long long)buf * a.R + j) * a.nb;
-  const long long o_nxt = ((long long)nbuf * a.R + j) * a.nb;
-  const long long oz_cur = ((long long)buf * a.R + j) * a.nbz;
-  const long long oz_nxt = ((long long)nbuf * a.R + j) * a.nbz;
+  if (a.scal[4 * j] == 0.f) return;  // this system has stopped
   const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
-  if (a.scal[4 * j] == 0.f) {
-    // converged: carry this block's partials forward so the state stays converged
-    if (threadIdx.x == 0) {
-      a.part_rr[o_nxt + blk] = a.part_rr[o_cur + blk];
-      if (!a.fft) a.part_rz[oz_nxt + blk] = a.part_rz[oz_cur + blk];
+  if (blk == 0 && threadIdx.x == 0) atomicAdd(&a.counters[DC_CG_UPD_UNITS], 1ull);
+  __shared__ float alpha_s;
+  auto form_alpha = [&]() {
+    if (threadIdx.x < 32) {
+      const double pqs = group_sum(a.part_pq + (long long)j * a.nb, a.nb);
+      if (threadIdx.x == 0) alpha_s = (float)(a.rzs[j] / pqs);
     }
-    return;
-  }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-    atomicAdd(&a.counters[DC_CG_UPD_UNITS], 1ull);
-  const float alpha = a.scal[4 * j + 2];
+    __syncthreads();
+    return alpha_s;
+  };
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
-  double* X = a.X + (long long)j * c.N;
+  float* Ec = a.Ec + (long long)j * c.N;
   float* Rr = a.Rr + (long long)j * c.N;
   const float* P = ((it & 1) ? a.P2 : a.P) + (long long)j * c.N;
   const float* Q = a.Qp + (long long)j * c.N;
+  const bool first = it == 0;  // the correction starts at zero: not read
   float rz2 = 0.f, rr2 = 0.f;
   if ((c.W & 3) == 0 && c0 + kTile <= c.W && r0 + kTile <= c.H) {
     // full tile, rows 16-byte aligned: kUpdRows float4 of each plane per thread,
     // all loads issued before the first store
     const int c4 = (threadIdx.x & 7) * 4;
-    float4 pv[kUpdRows], qv[kUpdRows], rv[kUpdRows], mv[kUpdRows];
-    double2 x01[kUpdRows], x23[kUpdRows];
+    float4 pv[kUpdRows], qv[kUpdRows], rv[kUpdRows], ev[kUpdRows], mv[kUpdRows];
 #pragma unroll
     for (int k = 0; k < kUpdRows; ++k) {
       const int tr = (threadIdx.x >> 3) + k * (kUpdThreads >> 3);
@@ -720,45 +766,70 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it) {
       pv[k] = *reinterpret_cast<const float4*>(P + p);
       qv[k] = *reinterpret_cast<const float4*>(Q + p);
       rv[k] = *reinterpret_cast<const float4*>(Rr + p);
-      x01[k] = *reinterpret_cast<const double2*>(X + p);
-      x23[k] = *reinterpret_cast<const double2*>(X + p + 2);
+      ev[k] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(Ec + p);
       if (!a.fft) mv[k] = *reinterpret_cast<const float4*>(a.Minv + p);
     }
+    const float alpha = form_alpha();
 #pragma unroll
     for (int k = 0; k < kUpdRows; ++k) {
       const int tr = (threadIdx.x >> 3) + k * (kUpdThreads >> 3);
       const long long p = (long long)(r0 + tr) * c.W + c0 + c4;
-      x01[k].x += (double)(alpha * pv[k].x);
-      x01[k].y += (double)(alpha * pv[k].y);
-      x23[k].x += (double)(alpha * pv[k].z);
-      x23[k].y += (double)(alpha * pv[k].w);
-      float4 r = rv[k];
+      float4 e = ev[k], r = rv[k];
+      e.x = fmaf(alpha, pv[k].x, e.x);
+      e.y = fmaf(alpha, pv[k].y, e.y);
+      e.z = fmaf(alpha, pv[k].z, e.z);
+      e.w = fmaf(alpha, pv[k].w, e.w);
       r.x = fmaf(-alpha, qv[k].x, r.x);
       r.y = fmaf(-alpha, qv[k].y, r.y);
       r.z = fmaf(-alpha, qv[k].z, r.z);
       r.w = fmaf(-alpha, qv[k].w, r.w);
-      *reinterpret_cast<double2*>(X + p) = x01[k];
-      *reinterpret_cast<double2*>(X + p + 2) = x23[k];
+      *reinterpret_cast<float4*>(Ec + p) = e;
       *reinterpret_cast<float4*>(Rr + p) = r;
       rr2 += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
       if (!a.fft)
         rz2 += r.x * r.x * mv[k].x + r.y * r.y * mv[k].y + r.z * r.z * mv[k].z + r.w * r.w * mv[k].w;
     }
   } else {
+    const float alpha = form_alpha();
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int tr = ty; tr < kTile; tr += kUpdThreads / 32) {
       const int gr = r0 + tr, gcol = c0 + tx;
       if (gr >= c.H || gcol >= c.W) continue;
       const long long p = (long long)gr * c.W + gcol;
-      X[p] += (double)(alpha * P[p]);
+      Ec[p] = fmaf(alpha, P[p], first ? 0.f : Ec[p]);
       const float r = fmaf(-alpha, Q[p], Rr[p]);
       Rr[p] = r;
       if (!a.fft) rz2 = fmaf(r * r, a.Minv[p], rz2);
       rr2 = fmaf(r, r, rr2);
     }
   }
-  block_sum3((double)rz2, (double)rr2, 0.0, a.fft ? nullptr : a.part_rz + oz_nxt + blk,
-             a.part_rr + o_nxt + blk, nullptr);
+  block_sum3((double)rz2, (double)rr2, 0.0, a.fft ? nullptr : a.part_rz + (long long)j * a.nbz + blk,
+             a.part_rr + (long long)j * a.nb + blk, nullptr);
+  if (arrive_last(a.arrive + j, (unsigned)a.nb) && threadIdx.x < 32) {
+    const double rr = group_sum(a.part_rr + (long long)j * a.nb, a.nb);
+    const double rzn = a.fft ? 0.0 : group_sum(a.part_rz + (long long)j * a.nbz, a.nbz);
+    if (threadIdx.x == 0) {
+      // stop at the pass target, or when the recurrence residual has grown
+      // fourfold over the pass (FP32 CG losing its way on a badly conditioned
+      // system): the next pass restarts from the true residual
+      a.scal[4 * j] = (rr <= a.thr[j] || rr > 16.0 * a.rr0[j]) ? 0.f : 1.f;
+      if (!a.fft) {
+        a.scal[4 * j + 1] = (float)(rzn / a.rzs[j]);
+        a.rzs[j] = rzn;
+      }
+    }
+  }
+}
+
+// x += e for every system that iterated in the pass that just ended.
+__global__ void commit_kernel(double* X, const float* Ec, const int* act0, long long N) {
+  const int j = blockIdx.y;
+  if (!act0[j]) return;
+  double* x = X + (long long)j * N;
+  const float* e = Ec + (long long)j * N;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x)
+    x[p] += (double)e[p];
 }
 
 
@@ -784,8 +855,29 @@ struct FftDesc {
   const float2* tw512;  // exp(-2 pi i m / 512), m < 512 (the 512-point kernels)
   const float* act;  // CG scalars of the current iteration ([4 R], [4 j] = 1 if system j
                      // is active), or NULL: transform every system
+  float* scal_w;     // the same array, written: beta of the active systems
+  double* rzs;       // [R] r.z, or NULL: leave the CG scalars alone (shape tuning)
+  unsigned* arrive;  // [pairs] block-arrival counters of the inverse row pass
+  int first;         // 1: first application of a refinement pass (beta = 0)
   unsigned long long* counters;  // DC_CG_PRE_UNITS counts the systems transformed
 };
+
+// The last block of a pair's inverse row pass sums the r.z partials of its two
+// systems and sets, for each system still active, beta = r.z(new) / r.z(old)
+// (0 in the first application of a refinement pass) and r.z = r.z(new).
+__device__ __forceinline__ void rz_tail(const FftDesc& f, int pair, const double* part_rz) {
+  if (!f.rzs) return;
+  if (!arrive_last(f.arrive + pair, gridDim.x) || threadIdx.x >= 32) return;
+  for (int u = 0; u < 2; ++u) {
+    const int j = 2 * pair + u;
+    if (j >= f.R) break;
+    const double rz = group_sum(part_rz + (long long)j * f.nbz, f.nbz);
+    if (threadIdx.x == 0 && f.act[4 * j] != 0.f) {
+      f.scal_w[4 * j + 1] = f.first ? 0.f : (float)(rz / f.rzs[j]);
+      f.rzs[j] = rz;
+    }
+  }
+}
 
 // Both systems of a pair have stopped in this CG iteration: their z is not used.
 __device__ __forceinline__ bool pair_idle(const FftDesc& f, int pair) {
@@ -1051,6 +1143,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f,
   __syncthreads();
   block_sum3(acc0, acc1, 0.0, part_rz + (long long)j0 * f.nbz + blockIdx.x,
              j1 < f.R ? part_rz + (long long)j1 * f.nbz + blockIdx.x : nullptr, nullptr);
+  rz_tail(f, pair, part_rz);
 }
 
 // ---- register-resident 512-point transforms
@@ -1273,6 +1366,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDes
   }
   block_sum3(acc0, acc1, 0.0, part_rz + (long long)j0 * f.nbz + blockIdx.x,
              two ? part_rz + (long long)j1 * f.nbz + blockIdx.x : nullptr, nullptr);
+  rz_tail(f, pair, part_rz);
 }
 
 // |h_f|^2 / xi on the H x W frequency grid (phases reduced exactly in integers).
@@ -1300,65 +1394,20 @@ __global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int
   }
 }
 
-// Per-system CG scalars from the block partials, one warp per system, in a fixed
-// order.  stage 0 (before the direction kernel of iteration it): active flag
-// (r.r above the system's threshold) and beta = rz(it) / rz(it - 1); stage 1
-// (before the update kernel): alpha = rz(it) / p.q.
-__global__ void cg_scalars_kernel(CgArgs a, int it, int stage, float* scal) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int buf = it & 1;
-  const int wpb = blockDim.x / 32;
-  for (int j = blockIdx.x * wpb + warp; j < a.R; j += gridDim.x * wpb) {
-    double s0 = 0.0, s1 = 0.0;
-    if (stage == 0) {
-      for (int i = lane; i < a.nb; i += 32) s0 += a.part_rr[((long long)buf * a.R + j) * a.nb + i];
-      if (it > 0)
-        for (int i = lane; i < a.nbz; i += 32) {
-          s1 += a.part_rz[((long long)buf * a.R + j) * a.nbz + i];
-        }
-    } else {
-      for (int i = lane; i < a.nbz; i += 32) s0 += a.part_rz[((long long)buf * a.R + j) * a.nbz + i];
-      for (int i = lane; i < a.nb; i += 32) s1 += a.part_pq[(long long)j * a.nb + i];
-    }
-    double s2 = 0.0;
-    if (stage == 0 && it > 0)
-      for (int i = lane; i < a.nbz; i += 32) s2 += a.part_rz[((long long)(buf ^ 1) * a.R + j) * a.nbz + i];
+// Number of systems still active after the last update (their flags).
+__global__ void check_kernel(const float* scal, int R, int* active) {
+  int cnt = 0;
+  for (int j = threadIdx.x; j < R; j += blockDim.x) cnt += scal[4 * j] != 0.f;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      s0 += __shfl_down_sync(0xffffffffu, s0, off);
-      s1 += __shfl_down_sync(0xffffffffu, s1, off);
-      s2 += __shfl_down_sync(0xffffffffu, s2, off);
-    }
-    if (lane == 0) {
-      if (stage == 0) {
-        // stop at the pass target, or when the recurrence residual has grown
-        // fourfold over the pass (FP32 CG losing its way on a badly conditioned
-        // system): the next pass restarts from the true residual
-        scal[4 * j] = (s0 <= a.thr[j] || s0 > 16.0 * a.rr0[j]) ? 0.f : 1.f;
-        scal[4 * j + 1] = it > 0 ? (float)(s1 / s2) : 0.f;
-      } else {
-        scal[4 * j + 2] = (float)(s0 / s1);
-      }
-    }
-  }
-}
-
-// Number of systems still above tolerance, from the partials in buffer `buf`.
-__global__ void check_kernel(const double* part_rr, const double* thr, const double* rr0, int R,
-                             int nb, int buf, int* active) {
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
+  for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+  __shared__ int wsum[32];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = warp; j < R; j += blockDim.x / 32) {
-    double rr = 0;
-    for (int i = lane; i < nb; i += 32) rr += part_rr[((long long)buf * R + j) * nb + i];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, off);
-    if (lane == 0 && !(rr <= thr[j]) && rr <= 16.0 * rr0[j]) atomicAdd(&cnt, 1);
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+    *active = t;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *active = cnt;
 }
 
 // Rao-Blackwellised terms of the probes, by an explicit matvec of each computed
@@ -1551,7 +1600,11 @@ struct LikelihoodState {
   size_t smem = 0;
   size_t smem_res = 0;
   int last_iters = 0;
-  float* d_scal = nullptr;      // [R][4] CG scalars
+  float* d_scal = nullptr;      // [R][4] CG scalars: active flag, beta
+  double* d_rzs = nullptr;      // [R] r.z of the current iteration
+  unsigned* d_arrive = nullptr; // [R + pairs] block-arrival counters (start and stay zero)
+  int* d_act0 = nullptr;        // [R] systems that iterate in the current pass
+  float* Ec = nullptr;          // R planes: FP32 correction of the current pass
   double* d_relres = nullptr;  // [R] sqrt(r.r / b.b) after the last true residual
   double* d_prev_rr = nullptr; // [R] r.r of the previous refinement pass
   double* d_rr0 = nullptr;     // [R] r.r at the start of the current pass
@@ -1584,12 +1637,16 @@ CgArgs cg_args(LikelihoodState* L) {
   a.thr = L->thr;
   a.rr0 = L->d_rr0;
   a.scal = L->d_scal;
+  a.rzs = L->d_rzs;
+  a.arrive = L->d_arrive;
+  a.act0 = L->d_act0;
   a.Z = L->Z;
+  a.Ec = L->Ec;
   const long long rn = (long long)L->R * L->nbmax;
   a.part_pq = L->part;
   a.part_rz = L->part + rn;
-  a.part_rr = L->part + 3 * rn;
-  a.part_bb = L->part + 5 * rn;
+  a.part_rr = L->part + 2 * rn;
+  a.part_bb = L->part + 3 * rn;
   a.rtol2 = L->rtol2;
   a.nb = L->nb;
   a.nbz = L->nbz;
@@ -1604,13 +1661,19 @@ int ilog2(int v) {
   return l;
 }
 
-// z = M^{-1} r; r.z partials into rz_buf ([R][nbz]).  With act (the CG scalars of
-// the iteration that just updated r), pairs of systems that both stopped are skipped;
-// without it every system is transformed (the first application of a pass).
-void precond_apply(LikelihoodState* L, double* rz_buf, const float* act,
+// z = M^{-1} r; r.z partials into rz_buf ([R][nbz]).  With cg (the solver's own
+// call), pairs of systems that have both stopped are skipped and the inverse row
+// pass sets beta and r.z of the active systems (first: the first application of a
+// refinement pass, beta = 0); without it every system is transformed and the CG
+// scalars are left alone (launch-shape tuning).
+void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
                    unsigned long long* counters, cudaStream_t s) {
   FftDesc f = L->fd;
-  f.act = act;
+  f.act = cg ? L->d_scal : nullptr;
+  f.scal_w = cg ? L->d_scal : nullptr;
+  f.rzs = cg ? L->d_rzs : nullptr;
+  f.arrive = L->d_arrive + L->R;
+  f.first = first;
   f.counters = counters;
   constexpr int kRows512 = kF512Warps;  // one row per warp: more blocks in flight hide load latency
   if (fft512_rows(f))
@@ -1647,10 +1710,10 @@ std::map<std::array<int, 5>, FftShape> g_tune;
 
 float time_precond(LikelihoodState* L, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   const int reps = 3;
-  precond_apply(L, L->part + (size_t)L->R * L->nbmax, nullptr, nullptr, s);  // warm
+  precond_apply(L, L->part + (size_t)L->R * L->nbmax, false, 0, nullptr, s);  // warm
   cudaEventRecord(e0, s);
   for (int i = 0; i < reps; ++i)
-    precond_apply(L, L->part + (size_t)L->R * L->nbmax, nullptr, nullptr, s);
+    precond_apply(L, L->part + (size_t)L->R * L->nbmax, false, 0, nullptr, s);
   cudaEventRecord(e1, s);
   float ms = 0.f;
   if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
@@ -1920,7 +1983,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->P, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->P2, sizeof(float) * RN) == cudaSuccess &&
             cudaMalloc(&L->Qp, sizeof(float) * RN) == cudaSuccess &&
-            cudaMalloc(&L->part, sizeof(double) * 6 * L->R * L->nbmax) == cudaSuccess &&
+            cudaMalloc(&L->part, sizeof(double) * 4 * L->R * L->nbmax) == cudaSuccess &&
             cudaMalloc(&L->dpart, sizeof(double) * L->prep_blocks) == cudaSuccess &&
             cudaMalloc(&L->dbar, sizeof(double)) == cudaSuccess &&
             (!L->fft ||
@@ -1933,6 +1996,10 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->d_prev_rr, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_rr0, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_scal, sizeof(float) * 4 * L->R) == cudaSuccess &&
+            cudaMalloc(&L->d_rzs, sizeof(double) * L->R) == cudaSuccess &&
+            cudaMalloc(&L->d_arrive, sizeof(unsigned) * (L->R + (L->R + 1) / 2)) == cudaSuccess &&
+            cudaMalloc(&L->d_act0, sizeof(int) * L->R) == cudaSuccess &&
+            cudaMalloc(&L->Ec, sizeof(float) * RN) == cudaSuccess &&
             cudaHostAlloc(&L->h_relres, sizeof(double) * L->R, cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
             cudaEventCreateWithFlags(&L->ev[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -1941,6 +2008,12 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     cudaGetLastError();
     likelihood_destroy(L);
     return EP_TV_ERR_NOMEM;
+  }
+  // the block-arrival counters start at zero; every last block resets its own
+  if (cudaMemsetAsync(L->d_arrive, 0, sizeof(unsigned) * (L->R + (L->R + 1) / 2), s) !=
+      cudaSuccess) {
+    likelihood_destroy(L);
+    return EP_TV_ERR_CUDA;
   }
   c.k = L->d_k;
   c.gr = L->d_g;
@@ -2057,6 +2130,10 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->d_prev_rr);
   cudaFree(L->d_rr0);
   cudaFree(L->d_scal);
+  cudaFree(L->d_rzs);
+  cudaFree(L->d_arrive);
+  cudaFree(L->d_act0);
+  cudaFree(L->Ec);
   if (L->h_relres) cudaFreeHost(L->h_relres);
   if (L->h_active) cudaFreeHost(L->h_active);
   if (L->ev[0]) cudaEventDestroy(L->ev[0]);
@@ -2105,9 +2182,10 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     tr->begin(EP_TV_K_CG_RESIDUAL, s);
     residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
     tr->end(s, (double)L->R * N);
-    thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, L->R, L->nb, L->rtol2_true,
-                                         L->rtol2_probe, eta2, L->thr, L->d_relres, L->d_prev_rr,
-                                         L->d_rr0, outer == 0, L->d_active);
+    thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, a.part_rz, a.fft, L->R, L->nb,
+                                         L->rtol2_true, L->rtol2_probe, eta2, L->thr, L->d_relres,
+                                         L->d_prev_rr, L->d_rr0, outer == 0, L->d_active, L->d_scal,
+                                         L->d_act0, L->d_rzs);
     if (cudaMemcpyAsync(L->h_active, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(L->h_relres, L->d_relres, sizeof(double) * L->R, cudaMemcpyDeviceToHost,
@@ -2129,33 +2207,35 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
       break;
     }
     if (outer >= L->max_outer || total >= L->max_iter) break;
+    const int started = L->h_active[0];  // systems that iterate in this pass
     if (L->fft) {
+      // z = M^{-1} r of the true residual: r.z of every active system, beta = 0
       tr->begin(EP_TV_K_CG_PRECOND, s);
-      precond_apply(L, a.part_rz, nullptr, counters, s);
+      precond_apply(L, a.part_rz, true, 1, counters, s);
       tr->end(s, -1.0);
     }
+    // Iterations run in chunks; the CG scalars (alpha, beta, active flags) are
+    // formed on the device by the last block of each reduction, so a chunk needs
+    // no host round trip.  The host reads the active count of a chunk while the
+    // next one is already queued, and stops once it reaches zero.
     int launched = 0, pending = -1, slot = 0;
     while (true) {
       const int n = std::min(kChunk, L->max_iter - total - launched);
       for (int t = 0; t < n; ++t) {
-        cg_scalars_kernel<<<L->R, 32, 0, s>>>(a, launched, 0, L->d_scal);  // one warp per system
         tr->begin(EP_TV_K_CG_DIRECTION, s);
         direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
         tr->end(s, -1.0);
-        cg_scalars_kernel<<<L->R, 32, 0, s>>>(a, launched, 1, L->d_scal);
         tr->begin(EP_TV_K_CG_UPDATE, s);
         update_kernel<<<grid, kUpdThreads, 0, s>>>(a, launched);
         tr->end(s, -1.0);
         if (L->fft) {
           tr->begin(EP_TV_K_CG_PRECOND, s);
-          precond_apply(L, a.part_rz + (long long)((launched + 1) & 1) * L->R * L->nbz, L->d_scal,
-                        counters, s);
+          precond_apply(L, a.part_rz, true, 0, counters, s);
           tr->end(s, -1.0);
         }
         ++launched;
       }
-      check_kernel<<<1, 1024, 0, s>>>(a.part_rr, L->thr, L->d_rr0, L->R, L->nb, launched & 1,
-                                      L->d_active);
+      check_kernel<<<1, 64, 0, s>>>(L->d_scal, L->R, L->d_active);
       if (cudaMemcpyAsync(L->h_active + slot, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
               cudaSuccess ||
           cudaEventRecord(L->ev[slot], s) != cudaSuccess)
@@ -2171,8 +2251,12 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
         break;
       }
     }
-    // the solution and the partials of every launched iteration are final; count
-    // the iterations up to the poll that found all systems converged
+    // the corrections of every launched iteration are final: add them to the FP64
+    // solutions of the systems that iterated, then count the iterations up to the
+    // poll that found all systems stopped
+    tr->begin(EP_TV_K_CG_COMMIT, s);
+    commit_kernel<<<dim3(std::min(grid1d(N), 1024), L->R), 256, 0, s>>>(L->X, L->Ec, L->d_act0, N);
+    tr->end(s, (double)started * N);
     total += launched;
   }
   iters = total;
@@ -2197,9 +2281,11 @@ double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
   const double groups = (double)((L->S + kRbGroup - 1) / kRbGroup);
   switch (kernel) {
     case EP_TV_K_CG_DIRECTION: return 16.0;  // read z, p; write p, Q p (per active system pixel)
-    case EP_TV_K_CG_UPDATE: return 32.0;     // read x (FP64), r, p, Q p; write x (FP64), r
+    case EP_TV_K_CG_UPDATE: return 24.0;     // read e, r, p, Q p; write e, r (FP32 correction)
     case EP_TV_K_CG_RESIDUAL: return 24.0;   // read x (FP64), y', the probe planes; write r
     case EP_TV_K_CG_PRECOND: return 8.0;     // r in, z out (per transformed system pixel)
+    case EP_TV_K_CG_COMMIT: return 20.0;     // read x (FP64) and e, write x (per committed
+                                             // system pixel)
     case EP_TV_K_SITE0:                      // read the S probe solutions (FP64), write and
       return 8.0 * L->S + 8.0 * groups       // read the RB sums, read x_0 (FP64), d, n, Minv,
              + 36.0;                         // tau0, nu0; write tau0, nu0 (per pixel)

@@ -46,3 +46,33 @@ def test_cs_free_boundary_odd_size_q0_first():
     order (likelihood site first) and EM."""
     mu, var, mu_r, var_r, p = _run(21, 214, 6, 3, seed=5, width=34, periodic=0, order="q0_first")
     assert_parity(mu, var, mu_r, var_r, p.A.T @ p.y)
+
+
+def test_cs_config_128_full_size():
+    """The compressive-sensing configuration at its stated size: 128 x 128 image
+    (N = 16384), M = floor(0.3 N) = 4915 Gaussian rows of variance 1/M, noise
+    sigma 0.01, beta0 = 1 (Sec. V-C), six sweeps with EM after the third and
+    sixth.  The oracle forms the Woodbury site in FP64 with one 4915 x 4915
+    Cholesky factorisation per sweep (Sec. III-C)."""
+    torch = cuda()
+    h = w = 128
+    p = syn.cs_problem(h, w, ratio=0.3, sigma=0.01, beta0=1.0, seed=0)
+    assert p.A.shape == (4915, 16384)
+    A32 = p.A.astype(np.float32)
+    y32 = p.y.astype(np.float32)
+    At = torch.as_tensor(A32, device="cuda")
+    yt = torch.as_tensor(y32, device="cuda")
+    with EPTV(yt, p.xi, p.beta, op=OP_DENSE, dense=At, height=h, width=w) as ep:
+        ep.sweep(6, em_every=3)
+        mu, var = (t.cpu().numpy() for t in ep.posterior())
+        beta_gpu, _ = ep.em_beta()
+        assert ep.status() == 0
+    del At
+    o = EPOracle("cs", y32.astype(np.float64), p.xi, p.beta, h, w, A=A32.astype(np.float64),
+                 site0="woodbury")
+    o.run(6, em_every=3)
+    mu_r, var_r = o.posterior()
+    assert_parity(mu, var, mu_r, var_r, p.A.T @ p.y)
+    # beta of the last EM step (N / a_u of the sixth sweep, recomputed on both sides)
+    beta_ref = o.em_update()
+    assert abs(beta_gpu / beta_ref - 1.0) < 1e-4, (beta_gpu, beta_ref)
