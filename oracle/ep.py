@@ -47,6 +47,26 @@ from .partition import edges
 from .tilted import laplace_tilted
 
 
+def _fft_qmul(hth, inv_c, xi, h, w, v):
+    """Q v = H^T H v / xi + diag(1/c) v with the periodic blur applied through the
+    FFT (H^T H is circulant with eigenvalues |h_f|^2 = hth)."""
+    v2 = np.asarray(v).reshape(h, w)
+    return np.real(np.fft.ifft2(hth * np.fft.fft2(v2))).reshape(-1) / xi + inv_c * v2.reshape(-1)
+
+
+def _fft_cg_solve(job):
+    """Q x = b by conjugate gradients to a relative residual of 1e-11 (a module
+    function so that a process pool can run it)."""
+    from scipy.sparse.linalg import LinearOperator, cg
+    hth, inv_c, xi, h, w, b = job
+    Q = LinearOperator((h * w, h * w), matvec=lambda v: _fft_qmul(hth, inv_c, xi, h, w, v),
+                       dtype=np.float64)
+    x, info = cg(Q, b, rtol=1e-11, atol=0.0, maxiter=20000)
+    if info != 0:
+        raise RuntimeError("oracle CG did not converge")
+    return x
+
+
 class EPOracle:
     """Algorithm 1 / Algorithm 2 in FP64.
 
@@ -69,6 +89,9 @@ class EPOracle:
         (periodic convolution is diagonal in the Fourier basis); for images too
         large for dense factorisation (deconv).
     probes : (eps1 (S, M), eps2 (S, N)) standard normals for "rbmc".
+    pool : optional executor (e.g. a spawn-context process pool) on which
+        "rbmc_cg" runs the 1 + S independent solves of one site-0 update; each
+        solve is the same computation as without it, so results do not change.
     """
 
     def __init__(self, kind: str, y: np.ndarray, xi: float, lam: float,
@@ -76,7 +99,7 @@ class EPOracle:
                  A: Optional[np.ndarray] = None, damping: float = 0.5,
                  var_cap: float = 1e8, periodic: bool = True,
                  order: str = "prior_first", site0: str = "exact",
-                 probes=None):
+                 probes=None, pool=None):
         if kind not in ("denoise", "deconv", "cs"):
             raise ValueError(kind)
         self.kind = kind
@@ -93,6 +116,7 @@ class EPOracle:
         self.order = order
         self.site0 = site0
         self.probes = probes
+        self.pool = pool
         self.edge_lists = [edges(self.height, self.width, k, self.periodic) for k in (1, 2, 3, 4)]
         self.abar = 0.0          # sum of E|u| over the edges of the last sweep
         self.n_sweeps = 0
@@ -223,7 +247,6 @@ class EPOracle:
 
     def _rbmc_cg(self, c, m):
         """Site-0 moments with CG solves; same estimator as :meth:`_rbmc_var`."""
-        from scipy.sparse.linalg import LinearOperator, cg
         h, w = self.height, self.width
         kh, kw = self.kernel.shape
         pad = np.zeros((h, w))
@@ -232,30 +255,21 @@ class EPOracle:
         hth = np.abs(hf) ** 2
         inv_c = 1.0 / c
 
-        def qmul(v):
-            v2 = np.asarray(v).reshape(h, w)
-            return (np.real(np.fft.ifft2(hth * np.fft.fft2(v2))).reshape(-1) / self.xi + inv_c * v2.reshape(-1))
-
-        Q = LinearOperator((self.n, self.n), matvec=qmul, dtype=np.float64)
-
-        def solve(b):
-            x, info = cg(Q, b, rtol=1e-11, atol=0.0, maxiter=20000)
-            if info != 0:
-                raise RuntimeError("oracle CG did not converge")
-            return x
-
         def ht(v):
             return np.real(np.fft.ifft2(np.conj(hf) * np.fft.fft2(v.reshape(h, w)))).reshape(-1)
 
-        E = solve(ht(self.y) / self.xi + m / c)
         eps1, eps2 = self.probes
         S = eps1.shape[0]
+        rhs = [ht(self.y) / self.xi + m / c]
+        rhs += [ht(eps1[s]) / math.sqrt(self.xi) + eps2[s] / np.sqrt(c) for s in range(S)]
+        jobs = [(hth, inv_c, self.xi, h, w, b) for b in rhs]
+        sols = list(self.pool.map(_fft_cg_solve, jobs)) if self.pool else [_fft_cg_solve(j) for j in jobs]
+        E = sols[0]
         qdiag = np.sum(self.kernel ** 2) / self.xi + inv_c
         acc = np.zeros(self.n)
         for s in range(S):
-            wv = ht(eps1[s]) / math.sqrt(self.xi) + eps2[s] / np.sqrt(c)
-            z = solve(wv)
-            off = qmul(z) - qdiag * z
+            z = sols[1 + s]
+            off = _fft_qmul(hth, inv_c, self.xi, h, w, z) - qdiag * z
             acc += (off / qdiag) ** 2
         return E, 1.0 / qdiag + acc / S
 

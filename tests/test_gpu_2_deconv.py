@@ -169,3 +169,40 @@ def test_full_size_512_residual_and_site0_samples():
         n_exp = 0.5 * n_new + 0.5 * nu0[0, rr, cc]
         assert abs(tau1[0, rr, cc] / t_exp - 1) < 1e-4
         assert abs(nu1[0, rr, cc] - n_exp) <= 1e-4 * abs(t_exp) * (abs(E) + 0.1)
+
+
+def test_config2_512_against_oracle_samples():
+    """The deconvolution configuration at its stated size: 512 x 512, 9 x 9
+    uniform periodic blur, BSNR 40 dB, 32 RBMC probes, beta0 = 1, six sweeps with
+    the EM update after the fifth.  The FP64 oracle (every solve by CG to 1e-11)
+    takes about 20 minutes for this on 8 cores, so its result is stored by
+    tests/golden/make_deconv512.py (which calls only the oracle and the input
+    generators) at 8192 sampled pixels, with the image-wide sums of the mean and
+    the variance and the EM output."""
+    import os
+
+    from .golden import make_deconv512 as g
+
+    ref = np.load(os.path.join(os.path.dirname(g.__file__), "deconv512_oracle.npz"))
+    p, y32_, eps1, eps2 = g.inputs()
+    # the same inputs as the stored run
+    np.testing.assert_allclose(g.checksums(y32_, eps1, eps2), ref["checksums"], rtol=1e-12)
+    torch = cuda()
+    _, _, ep = _gpu(p, 0, g.S, (eps1, eps2))
+    em = int(ref["em_every"])
+    assert int(ref["sweeps"]) == em + 1
+    ep.sweep(em, em_every=em)
+    # ep_tv_em_beta recomputes N / a_u from the same (fifth) sweep: the beta the
+    # in-sweep EM step just set, and the a_u it used
+    beta, abar = ep.em_beta()
+    ep.sweep(1)
+    mu_t, var_t = ep.posterior()
+    mu, var = (t.cpu().numpy().reshape(-1).astype(np.float64) for t in (mu_t, var_t))
+    assert ep.status() == 0
+    ep.close()
+    assert abs(abar / float(ref["abar"]) - 1.0) < 1e-5, (abar, float(ref["abar"]))
+    assert abs(beta / float(ref["beta"]) - 1.0) < 1e-5, (beta, float(ref["beta"]))
+    idx = ref["idx"]
+    assert_parity(mu[idx], var[idx], ref["mean"], ref["var"], p.y)
+    assert abs(mu.sum() / float(ref["mean_sum"]) - 1.0) < 1e-5
+    assert abs(var.sum() / float(ref["var_sum"]) - 1.0) < 1e-4
