@@ -10,9 +10,11 @@ and nothing here imports the CUDA path.
 
 Modules
 -------
-tilted     Moments of the Laplace-tilted Gaussian of one edge difference
-           (Sec. III-C, Eq. marginal_tilted_un; the paper omits the closed
-           forms, they are derived in the module docstring).
+tilted     Moments of the tilted law of one edge difference (Sec. III-C,
+           Eq. marginal_tilted_un) for the three priors of Sec. II-B: the
+           Laplace factor of l1-TV (the paper omits the closed forms; they are
+           derived in the module docstring) and the two-Gaussian factors of
+           MoG2-TV and BG-TV.
 partition  The four matchings V1..V4 of the 4-neighbour graph (Sec. II-B,
            Eq. prior1 and the caption of Fig. 1).
 operators  The degradation operators H (identity, periodic convolution, dense

@@ -44,7 +44,7 @@ import scipy.linalg
 
 from . import operators
 from .partition import edges
-from .tilted import laplace_tilted
+from .tilted import gaussian_mixture_tilted, laplace_tilted
 
 
 def _fft_qmul(hth, inv_c, xi, h, w, v):
@@ -89,6 +89,11 @@ class EPOracle:
         (periodic convolution is diagonal in the Fourier basis); for images too
         large for dense factorisation (deconv).
     probes : (eps1 (S, M), eps2 (S, N)) standard normals for "rbmc".
+    prior : the edge factor phi of Sec. II-B: "l1" (Eq. L1_TV, parameter lam),
+        "mog2" (Eq. MoG2_TV_prior, theta = (omega, s1^2, s2^2)) or "bg"
+        (Eq. BG_TV, theta = (omega, s^2)).  The EM update (Sec. IV) is defined
+        for "l1" only.
+    theta : the mixture parameters for "mog2" / "bg".
     pool : optional executor (e.g. a spawn-context process pool) on which
         "rbmc_cg" runs the 1 + S independent solves of one site-0 update; each
         solve is the same computation as without it, so results do not change.
@@ -99,9 +104,18 @@ class EPOracle:
                  A: Optional[np.ndarray] = None, damping: float = 0.5,
                  var_cap: float = 1e8, periodic: bool = True,
                  order: str = "prior_first", site0: str = "exact",
-                 probes=None, pool=None):
+                 probes=None, pool=None, prior: str = "l1", theta=None):
         if kind not in ("denoise", "deconv", "cs"):
             raise ValueError(kind)
+        if prior not in ("l1", "mog2", "bg"):
+            raise ValueError(prior)
+        self.prior = prior
+        if prior == "mog2":
+            omega, v1, v2 = (float(t) for t in theta)
+            self.mixture = (omega, v1, v2)
+        elif prior == "bg":
+            omega, v1 = (float(t) for t in theta)
+            self.mixture = (omega, v1, 0.0)
         self.kind = kind
         self.height, self.width = int(height), int(width)
         self.n = self.height * self.width
@@ -179,7 +193,11 @@ class EPOracle:
         # Eq. marginal_tilted_un
         mu_u = mi - mj
         s2 = ci + cj
-        m_bar, S_bar, eabs = laplace_tilted(mu_u, s2, self.lam)
+        if self.prior == "l1":
+            m_bar, S_bar, eabs = laplace_tilted(mu_u, s2, self.lam)
+        else:
+            m_bar, S_bar = gaussian_mixture_tilted(mu_u, s2, *self.mixture)
+            eabs = np.zeros_like(m_bar)  # no EM for the mixture priors (Sec. IV)
         # projection of the edge moments onto (x_i, x_j) (Sec. III-C)
         Ei = mi + (m_bar - mu_u) / s2 * ci
         Ej = mj - (m_bar - mu_u) / s2 * cj
@@ -308,6 +326,8 @@ class EPOracle:
 
     def em_update(self) -> float:
         """M-step of Algorithm 2 with Option 3: lam = N / a_u of the last sweep."""
+        if self.prior != "l1":
+            raise ValueError("EM is defined for the l1-TV prior only (Sec. IV)")
         self.lam = self.n / self.abar
         return self.lam
 

@@ -117,3 +117,36 @@ def laplace_tilted(mu, s2, lam):
     var = w_plus * var_plus + w_minus * var_minus + w_plus * w_minus * (e_plus - e_minus) ** 2
     eabs = w_plus * e_plus - w_minus * e_minus
     return mean, var, eabs
+
+
+def gaussian_mixture_tilted(mu, s2, omega, v1, v2):
+    """Mean and variance of P(u) ~ N(u; mu, s2) phi(u) for the two-Gaussian
+    priors of Sec. II-B (oracle, FP64).
+
+    MoG2-TV (Eq. MoG2_TV_prior): phi(u) = omega N(u; 0, v1) + (1 - omega) N(u; 0, v2).
+    BG-TV (Eq. BG_TV) is the limit v2 -> 0, where the second component is the
+    point mass delta(u); pass v2 = 0.
+
+    Each product of Gaussians is a scaled Gaussian,
+        N(u; 0, v) N(u; mu, s2) = N(mu; 0, v + s2) N(u; mu v / (v + s2), v s2 / (v + s2)),
+    so P is a two-component Gaussian mixture with weights proportional to
+    omega N(mu; 0, v1 + s2) and (1 - omega) N(mu; 0, v2 + s2) (for v2 = 0 the
+    second component is a point mass at 0 with weight (1 - omega) N(mu; 0, s2)).
+    Its mean is sum_k W_k m_k and its variance sum_k W_k (c_k + m_k^2) - mean^2.
+    """
+    mu = np.asarray(mu, dtype=np.float64)
+    s2 = np.asarray(s2, dtype=np.float64)
+    e1, e2 = v1 + s2, v2 + s2
+    # weights from the log densities (normalising constants of each component)
+    with np.errstate(divide="ignore"):  # omega = 0 or 1: that component has no weight
+        l1 = np.log(omega) - 0.5 * np.log(2 * math.pi * e1) - mu ** 2 / (2 * e1)
+        l2 = np.log(1.0 - omega) - 0.5 * np.log(2 * math.pi * e2) - mu ** 2 / (2 * e2)
+    lmax = np.maximum(l1, l2)
+    w1 = np.exp(l1 - lmax)
+    w2 = np.exp(l2 - lmax)
+    w1, w2 = w1 / (w1 + w2), w2 / (w1 + w2)
+    m1, m2 = mu * v1 / e1, mu * v2 / e2
+    c1, c2 = v1 * s2 / e1, v2 * s2 / e2
+    mean = w1 * m1 + w2 * m2
+    var = w1 * (c1 + m1 ** 2) + w2 * (c2 + m2 ** 2) - mean ** 2
+    return mean, var

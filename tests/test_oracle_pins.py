@@ -184,6 +184,141 @@ def test_one_by_two_image_is_exact(y, xi, lam):
     assert abs(lam_new - 2.0 / eabs) <= 1e-8 * lam_new
 
 
+# ---------------------------------------------------------------- mixture priors
+def _mixture_quad(mu, s2, omega, v1, v2):
+    """Mean and variance of N(u; mu, s2) [omega N(u; 0, v1) + (1 - omega) N(u; 0, v2)]
+    by mpmath quadrature of the raw integrand (v2 = 0: the second component is
+    delta(u), whose mass (1 - omega) N(0; mu, s2) sits at u = 0).  Each Gaussian
+    component's integrals run over u = c + r t, t in (-inf, inf), with c and r
+    the centre and width of the product of its two Gaussians: only the placement
+    of the quadrature nodes depends on them, the integrand is the raw product.
+    The variance is integrated as a central moment, so it does not cancel.  All
+    integrands are divided by one common constant (the largest component
+    density at its node t = 0): mpmath's tolerance is absolute, and these
+    densities can be as small as 1e-55."""
+    sd = mp.sqrt(s2)
+    comps = [(omega, v1)] + ([(1 - omega, v2)] if v2 > 0 else [])
+    grid = [-mp.inf, -12, -6, -3, -1, 0, 1, 3, 6, 12, mp.inf]
+
+    def raw(k, t):
+        wk, vk = comps[k]
+        c = mp.mpf(mu) * vk / (vk + s2)
+        r = mp.sqrt(mp.mpf(vk) * s2 / (vk + s2))
+        u = c + r * t
+        return u, wk * mp.npdf(u, 0, mp.sqrt(vk)) * mp.npdf(u, mu, sd) * r
+
+    scale = max(raw(k, 0)[1] for k in range(len(comps)))
+
+    def integral(k, g):
+        def integrand(t):
+            u, fu = raw(k, t)
+            return g(u) * fu / scale
+        return mp.quad(integrand, grid)
+
+    point = 0 if v2 > 0 else (1 - omega) * mp.npdf(0, mu, sd) / scale
+    z = sum(integral(k, lambda u: 1) for k in range(len(comps))) + point
+    m = sum(integral(k, lambda u: u) for k in range(len(comps))) / z
+    v = (sum(integral(k, lambda u: (u - m) ** 2) for k in range(len(comps))) + point * m ** 2) / z
+    return float(m), float(v)
+
+
+@pytest.mark.parametrize("theta", [(0.3, 0.5, 0.001), (0.8, 4.0, 0.1), (0.05, 0.2, 0.0),
+                                   (0.6, 1.0, 0.0)])
+def test_mixture_tilted_moments_match_quadrature(theta):
+    """The tilted moments of the MoG2-TV (Eq. MoG2_TV_prior) and BG-TV (Eq. BG_TV,
+    v2 = 0) edge factors against quadrature, from edges inside the small-gradient
+    component to edges far in the tail, to 1e-10 relative (the mean relative to
+    the larger of its size and the tilted standard deviation)."""
+    from oracle.tilted import gaussian_mixture_tilted
+    mp.mp.dps = 30
+    for mu in (-3.0, -0.2, 0.0, 1.0, 7.0):
+        for s2 in (1e-4, 0.01, 30.0):
+            mq, vq = _mixture_quad(mu, s2, *theta)
+            mo, vo = gaussian_mixture_tilted(mu, s2, *theta)
+            assert abs(mo - mq) <= 1e-10 * max(abs(mq), math.sqrt(vq)), (mu, s2, mo, mq)
+            assert abs(vo - vq) <= 1e-10 * vq, (mu, s2, vo, vq)
+
+
+def test_mixture_prior_with_one_gaussian_component_has_exact_means():
+    """With omega = 1 the MoG2-TV factor is the Gaussian N(x_i - x_j; 0, v1), the
+    posterior is Gaussian, and the EP fixed point has its exact means (the
+    variances of a diagonal approximation on a loopy graph are not exact)."""
+    h, w = 4, 6
+    rng = np.random.default_rng(1)
+    y = rng.random((h, w))
+    xi, v1 = 0.05, 0.02
+    o = EPOracle("denoise", y, xi, 0.0, h, w, prior="mog2", theta=(1.0, v1, 1.0))
+    o.run(300)
+    mu, var = o.posterior()
+    n = h * w
+    prec = np.eye(n) / xi
+    for k in (1, 2, 3, 4):
+        for a, b in zip(*edges(h, w, k, True)):
+            d = np.zeros(n)
+            d[a], d[b] = 1.0, -1.0
+            prec += np.outer(d, d) / v1
+    exact = np.linalg.solve(prec, y.reshape(-1) / xi)
+    np.testing.assert_allclose(mu.reshape(-1), exact, rtol=0, atol=1e-12)
+    assert np.all(var.reshape(-1) < np.diag(np.linalg.inv(prec)))
+
+
+def _exact_pair_mixture(y, xi, omega, v1, v2, empty_tau):
+    """Exact marginal means and variances of p(x1, x2) ~ N(y1; x1, xi) N(y2; x2, xi)
+    exp(-empty_tau (x1^2 + x2^2) / 2) phi(x1 - x2) for phi = omega N(.; 0, v1) +
+    (1 - omega) N(.; 0, v2), or (1 - omega) delta(.) when v2 = 0.  Each component
+    gives a Gaussian posterior in closed form (for the delta: the line x1 = x2),
+    weighted by its evidence."""
+    y = np.asarray(y, float)
+    b = y / xi
+    lap = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    comps = []
+    for wk, vk in ((omega, v1), (1.0 - omega, v2)):
+        if vk > 0:
+            a = np.diag([1 / xi + empty_tau] * 2) + lap / vk
+            m = np.linalg.solve(a, b)
+            logz = (math.log(wk) - 0.5 * math.log(2 * math.pi * vk) - 0.5 * math.log(np.linalg.det(a))
+                    + 0.5 * b @ m + math.log(2 * math.pi))
+            comps.append((logz, m, np.diag(np.linalg.inv(a))))
+        else:
+            a = 2 / xi + 2 * empty_tau
+            bs = b.sum()
+            logz = math.log(wk) - 0.5 * math.log(a) + 0.5 * bs * bs / a + 0.5 * math.log(2 * math.pi)
+            comps.append((logz, np.full(2, bs / a), np.full(2, 1 / a)))
+    lz = np.array([c[0] for c in comps])
+    wts = np.exp(lz - lz.max())
+    wts /= wts.sum()
+    mean = sum(wts[k] * comps[k][1] for k in range(2))
+    var = sum(wts[k] * (comps[k][2] + comps[k][1] ** 2) for k in range(2)) - mean ** 2
+    return mean, var
+
+
+@pytest.mark.parametrize("prior,theta", [("mog2", (0.3, 1.0, 1e-3)), ("mog2", (0.7, 0.5, 0.02)),
+                                         ("bg", (0.4, 0.5)), ("bg", (0.8, 2.0))])
+@pytest.mark.parametrize("y,xi", [((0.3, 0.7), 0.01), ((0.9, -0.2), 0.04), ((0.5, 0.52), 0.01)])
+def test_one_by_two_image_mixture_priors(prior, theta, y, xi):
+    """P2 for the MoG2-TV and BG-TV priors (Sec. II-B): with a single edge the
+    tilted distribution is the exact posterior, so the EP means are exact.  Where
+    the exact marginal variance is below the cavity (likelihood) variance the
+    variances are exact too; where the posterior is so bimodal that it is above
+    it, the new edge site has a negative variance and the cap of Sec. III-C sets
+    its precision to 1/var_cap, leaving the posterior variance of the likelihood
+    and the four capped sites."""
+    o = EPOracle("denoise", np.array([y]), xi, 0.0, 1, 2, periodic=False, prior=prior, theta=theta)
+    o.run(200)
+    mu, var = (a.ravel() for a in o.posterior())
+    v2 = theta[2] if prior == "mog2" else 0.0
+    cap = 1.0 / o.var_cap
+    mean, v = _exact_pair_mixture(y, xi, theta[0], theta[1], v2, 3.0 * cap)
+    np.testing.assert_allclose(mu, mean, rtol=0, atol=1e-12)
+    cavity_var = 1.0 / (1.0 / xi + 3.0 * cap)
+    if np.all(v < cavity_var):
+        assert np.all(o.tau[1] > 2 * cap)
+        np.testing.assert_allclose(var, v, rtol=1e-10)
+    else:
+        np.testing.assert_array_equal(o.tau[1], cap)
+        np.testing.assert_allclose(var, 1.0 / (1.0 / xi + 4.0 * cap), rtol=1e-12)
+
+
 # ---------------------------------------------------------------- 2x2 loop
 def _exact_2x2(y, xi, lam, empty_tau, n=1201, half=9.0):
     """Exact marginal means, variances and E sum|x_i - x_j| of the 2x2 free-boundary
