@@ -78,9 +78,17 @@ typedef struct {
                             valid and unchanged for the life of the context. */
 } ep_tv_operator;
 
+/* Edge factor phi(x_i - x_j; theta) of the prior (Sec. II-B). */
+typedef enum {
+  EP_TV_PRIOR_L1 = 0,    /* l1-TV, Eq. L1_TV: exp(-beta |u|) (beta is the paper's lambda) */
+  EP_TV_PRIOR_MOG2 = 1,  /* MoG2-TV, Eq. MoG2_TV_prior:
+                            omega N(u; 0, s1_sq) + (1 - omega) N(u; 0, s2_sq) */
+  EP_TV_PRIOR_BG = 2     /* BG-TV, Eq. BG_TV: omega N(u; 0, s1_sq) + (1 - omega) delta(u) */
+} ep_tv_prior;
+
 typedef struct {
   double xi;             /* noise variance xi > 0 (Eq. likelihood) */
-  double beta;           /* TV parameter (the paper's lambda) >= 0; EM start value */
+  double beta;           /* TV parameter (the paper's lambda) >= 0; EM start value (l1-TV) */
   double damping;        /* weight in (0, 1] on the freshly updated site when mixing
                             natural parameters: new = d * updated + (1 - d) * old */
   double var_cap;        /* site variances are capped at var_cap (the paper suggests
@@ -103,11 +111,19 @@ typedef struct {
   int32_t precision;     /* 0: FP32 with FP64 for edges whose tilted moments lose
                             FP32 accuracy; 1: FP32 only */
   uint64_t seed;         /* seed of the library's own probe generator */
+  int32_t prior;         /* ep_tv_prior (default EP_TV_PRIOR_L1) */
+  double omega;          /* MoG2 / BG: mixture weight of the N(0, s1_sq) component, in (0, 1) */
+  double s1_sq;          /* MoG2 / BG: variance of the first Gaussian component, > 0 */
+  double s2_sq;          /* MoG2: variance of the second component, > 0 (BG: unused) */
 } ep_tv_params;
 
 /* Fills *p with defaults: damping 0.5, var_cap 1e8, periodic 1, order_mode 0,
-   rbmc_samples 32, cg_max_iter 1000, cg_rtol 1e-9, precision 0, seed 1234.
-   xi and beta are set to 0 and must be provided. */
+   rbmc_samples 32, cg_max_iter 1000, cg_rtol 1e-9, precision 0, seed 1234,
+   prior EP_TV_PRIOR_L1.  xi and beta (or, for the mixture priors, omega, s1_sq
+   and s2_sq) are set to 0 and must be provided.  The mixture priors are not
+   log-concave: their edge updates can ask for negative site variances, which the
+   variance cap of Sec. III-C replaces.  The EM update of beta (Sec. IV) exists
+   for l1-TV only. */
 ep_tv_status ep_tv_default_params(ep_tv_params* p);
 
 /* Creates a context and initialises the sites as Algorithm 1 does:
@@ -135,7 +151,9 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* ctx, int32_t n_sweeps, const int8_t* k_order
 /* EM M-step (Algorithm 2, Option 3): beta <- N / a_u, with a_u the sum over all
    edges of E_{P_k}|u_n| taken during the last sweep, reduced in FP64 in a fixed
    order.  Enqueued on the stream.  If beta_out or abar_out is non-NULL the call
-   synchronises the stream and writes the new beta / a_u there (HOST doubles). */
+   synchronises the stream and writes the new beta / a_u there (HOST doubles).
+   l1-TV prior only (EP_TV_ERR_UNSUPPORTED otherwise; ep_tv_sweep likewise
+   refuses em_every > 0 for the mixture priors with EP_TV_ERR_ARG). */
 ep_tv_status ep_tv_em_beta(ep_tv_ctx* ctx, double* beta_out, double* abar_out);
 
 /* Sets beta (no EM). */
@@ -223,8 +241,8 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* ctx, int32_t kernel, double* ms, int64_
      height, width  image size; its ceil(width / 60) * ceil(((height + 1) / 2 + 1) / 16)
                     work units (about 126 M pixels at most) must not exceed 65536, and
                     height * width must not exceed 2^31, else EP_TV_ERR_ARG.
-     p              uses damping, var_cap, periodic, precision (0 or 1), and xi when y
-                    is given.
+     p              uses damping, var_cap, periodic, precision (0 or 1), the prior and
+                    its omega, s1_sq, s2_sq, and xi when y is given.
      beta           DEVICE pointer to the TV parameter (one double).
      y              DEVICE, N floats: denoising, site 0 = (1/xi, y/xi); or NULL and
      tau0, nu0      DEVICE, N floats each: the likelihood site.

@@ -134,6 +134,7 @@ class EPOracle:
         self.edge_lists = [edges(self.height, self.width, k, self.periodic) for k in (1, 2, 3, 4)]
         self.abar = 0.0          # sum of E|u| over the edges of the last sweep
         self.n_sweeps = 0
+        self.n_capped = 0        # site updates whose precision the cap replaced
         self.init()
 
     # ------------------------------------------------------------------ state
@@ -171,6 +172,7 @@ class EPOracle:
         """Eq. update_qk_x / Eq. update_q0_x with the variance cap, natural form."""
         tau_new = 1.0 / Var - 1.0 / c
         capped = tau_new < 1.0 / self.var_cap
+        self.n_capped += int(np.count_nonzero(capped))
         tau_new = np.where(capped, 1.0 / self.var_cap, tau_new)
         sigma_site = 1.0 / tau_new
         # mu_site = Sigma_site [(Sigma_site^-1 + Sigma_cav^-1) E - Sigma_cav^-1 m]

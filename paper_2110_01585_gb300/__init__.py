@@ -15,9 +15,10 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import OP_CONV_PERIODIC, OP_DENSE, OP_IDENTITY, EPTVError
+from ._lib import OP_CONV_PERIODIC, OP_DENSE, OP_IDENTITY, PRIOR_BG, PRIOR_L1, PRIOR_MOG2, EPTVError
 
 __all__ = ["EPTV", "Batch", "solve_host", "EPTVError", "OP_IDENTITY", "OP_CONV_PERIODIC", "OP_DENSE",
+           "PRIOR_L1", "PRIOR_MOG2", "PRIOR_BG",
            "default_params"]
 
 

@@ -19,6 +19,7 @@ STATUS_NAMES = {
 }
 
 OP_IDENTITY, OP_CONV_PERIODIC, OP_DENSE = 0, 1, 2
+PRIOR_L1, PRIOR_MOG2, PRIOR_BG = 0, 1, 2
 KERNELS = {0: "prior_sweep", 1: "cg_direction", 2: "cg_update", 3: "cg_residual", 4: "site0",
            5: "cg_precond", 6: "cs_woodbury", 7: "cg_commit"}
 
@@ -37,7 +38,9 @@ class Params(ctypes.Structure):
                 ("var_cap", ctypes.c_double), ("periodic", ctypes.c_int32),
                 ("order_mode", ctypes.c_int32), ("rbmc_samples", ctypes.c_int32),
                 ("cg_max_iter", ctypes.c_int32), ("cg_rtol", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("prior", ctypes.c_int32), ("omega", ctypes.c_double), ("s1_sq", ctypes.c_double),
+                ("s2_sq", ctypes.c_double)]
 
 
 SIGNATURES = {

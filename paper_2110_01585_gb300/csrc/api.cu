@@ -62,6 +62,35 @@ namespace {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+}  // namespace
+
+namespace eptv {
+// The edge factor's parameters (Sec. II-B): beta for l1-TV (checked by the
+// callers), omega in (0, 1) and positive component variances for the mixtures.
+bool prior_params_ok(const ep_tv_params* p) {
+  switch (p->prior) {
+    case EP_TV_PRIOR_L1: return true;
+    case EP_TV_PRIOR_MOG2:
+      return p->omega > 0.0 && p->omega < 1.0 && finite_pos(p->s1_sq) && finite_pos(p->s2_sq);
+    case EP_TV_PRIOR_BG: return p->omega > 0.0 && p->omega < 1.0 && finite_pos(p->s1_sq);
+  }
+  return false;
+}
+
+void set_prior_args(SweepArgs& a, const ep_tv_params* p) {
+  a.prior = p->prior;
+  a.mix_logit = 0.f;
+  a.mix_v1 = a.mix_v2 = 0.f;
+  if (p->prior != EP_TV_PRIOR_L1) {
+    a.mix_logit = (float)std::log((1.0 - p->omega) / p->omega);
+    a.mix_v1 = (float)p->s1_sq;
+    a.mix_v2 = p->prior == EP_TV_PRIOR_MOG2 ? (float)p->s2_sq : 0.f;
+  }
+}
+}  // namespace eptv
+
+namespace {
+
 ep_tv_status check_params(const ep_tv_operator* op, const ep_tv_params* p) {
   if (!op || !p) return EP_TV_ERR_ARG;
   if (op->height < 1 || op->width < 1) return EP_TV_ERR_ARG;
@@ -74,6 +103,7 @@ ep_tv_status check_params(const ep_tv_operator* op, const ep_tv_params* p) {
   if (p->periodic && ((op->height % 2) || (op->width % 2))) return EP_TV_ERR_ARG;
   if (p->order_mode != 0 && p->order_mode != 1) return EP_TV_ERR_ARG;
   if (p->precision != 0 && p->precision != 1) return EP_TV_ERR_ARG;
+  if (!prior_params_ok(p)) return EP_TV_ERR_ARG;
   const long long n = (long long)op->height * op->width;
   switch (op->op) {
     case EP_TV_OP_IDENTITY:
@@ -173,6 +203,7 @@ SweepArgs sweep_args(ep_tv_ctx* c, int order) {
   a.beta = c->dscal + DS_BETA;
   a.order = order;
   a.fp64_tail = c->p.precision == 0;
+  set_prior_args(a, &c->p);
   a.abar_partial = c->abar_partial;
   a.status = c->status;
   a.counters = c->counters;
@@ -233,6 +264,7 @@ ep_tv_status ep_tv_default_params(ep_tv_params* p) {
   p->cg_rtol = 1e-9;
   p->precision = 0;
   p->seed = 1234;
+  p->prior = EP_TV_PRIOR_L1;
   return EP_TV_OK;
 }
 
@@ -320,6 +352,7 @@ ep_tv_status ep_tv_set_probes(ep_tv_ctx* c, const float* eps1, const float* eps2
 ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
                          int32_t em_every) {
   if (!c || n_sweeps < 0 || em_every < 0) return EP_TV_ERR_ARG;
+  if (em_every > 0 && c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_ARG;  // EM: l1-TV only
   if (c->failed) return EP_TV_ERR_STATE;
   if (k_order) {
     for (int t = 0; t < n_sweeps; ++t) {
@@ -380,6 +413,7 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
 
 ep_tv_status ep_tv_em_beta(ep_tv_ctx* c, double* beta_out, double* abar_out) {
   if (!c) return EP_TV_ERR_ARG;
+  if (c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_UNSUPPORTED;  // Sec. IV: l1-TV only
   if (c->failed) return EP_TV_ERR_STATE;
   if (c->sweeps == 0) return EP_TV_ERR_ARG;
   launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
@@ -818,6 +852,9 @@ ep_tv_status ep_tv_batch_create(int32_t n, ep_tv_ctx* const* ctxs, ep_tv_batch**
 
 ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_every) {
   if (!b || n_sweeps < 0 || em_every < 0) return EP_TV_ERR_ARG;
+  if (em_every > 0)
+    for (ep_tv_ctx* c : b->ctx)
+      if (c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_ARG;  // EM: l1-TV only
   const int n = (int)b->ctx.size();
   bool tracing = false;
   for (ep_tv_ctx* c : b->ctx) {

@@ -106,6 +106,9 @@ struct SweepArgs {
   const double* beta;         // device scalar
   int order;                  // four 4-bit k values, first update in the low nibble
   int fp64_tail;              // 1: recompute poorly conditioned edges in FP64
+  int prior;                  // ep_tv_prior
+  float mix_logit;            // MoG2 / BG: log((1 - omega) / omega)
+  float mix_v1, mix_v2;       // MoG2 / BG: component variances (BG: v2 = 0, the point mass)
   double* abar_partial;       // one FP64 partial sum of E|u| per work unit
   int vec2;                   // set by prior_sweep_prepare: float2 loads and stores allowed
   unsigned* status;
@@ -119,6 +122,10 @@ struct BatchItem {
   long long units;        // work units of this image
   long long unit_begin;   // first unit of this image in the launch
 };
+
+// Whether the prior fields of p are valid, and their copy into the sweep arguments.
+bool prior_params_ok(const ep_tv_params* p);
+void set_prior_args(SweepArgs& a, const ep_tv_params* p);
 
 // Prior-site sweep over V_1..V_4 for one image; site 0 implicit (identity) or stored.
 void launch_prior_sweep(const SweepArgs& a, bool site0_from_y, cudaStream_t s);

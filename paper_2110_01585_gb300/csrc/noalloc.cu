@@ -76,6 +76,7 @@ extern "C" ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width,
   if ((long long)height * width > (1ll << 31)) return EP_TV_ERR_ARG;
   if (!y && (!tau0 || !nu0)) return EP_TV_ERR_ARG;
   if (p->precision != 0 && p->precision != 1) return EP_TV_ERR_ARG;
+  if (!prior_params_ok(p)) return EP_TV_ERR_ARG;
   if (p->periodic != 0 && p->periodic != 1) return EP_TV_ERR_ARG;
   if (p->periodic && ((height % 2) || (width % 2))) return EP_TV_ERR_ARG;
   if (!(p->damping > 0.0 && p->damping <= 1.0) || !(p->var_cap > 0.0)) return EP_TV_ERR_ARG;
@@ -126,6 +127,7 @@ extern "C" ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width,
   a.beta = beta;
   a.order = order;
   a.fp64_tail = p->precision == 0;
+  set_prior_args(a, p);
   a.abar_partial = scratch;
   a.status = status;
   a.counters = counters;

@@ -112,6 +112,7 @@ struct Row {
 };
 
 struct Ctx {
+  float mlog, v1, v2;   // mixture priors: log((1 - omega) / omega), component variances
   float lam, min_tau, damp, keep;
   double lam_d;
   float tail_s2;  // lam s < 1e-3, i.e. s^2 < 1e-6 / lam^2, takes the FP64 moments (-1: never)
@@ -242,9 +243,39 @@ __device__ __forceinline__ Moments2 tilted2(float2 mu, float2 s2, float2 lam) {
   return o;
 }
 
+// Tilted moments of the two-Gaussian edge factors of Sec. II-B (Eq. MoG2_TV_prior,
+// and Eq. BG_TV as v2 = 0):
+//   P(u) ~ N(u; mu, s2) [omega N(u; 0, v1) + (1 - omega) N(u; 0, v2)]
+//        = W1 N(u; m1, c1) + W2 N(u; m2, c2),  m_k = mu v_k / e_k,  c_k = v_k s2 / e_k,
+// e_k = v_k + s2, W1 : W2 = omega N(mu; 0, e1) : (1 - omega) N(mu; 0, e2), i.e.
+// W2 = 1 / (1 + exp(-t)) with t = log((1 - omega) / omega) + log(e1 / e2) / 2
+// - mu^2 (v1 - v2) / (2 e1 e2).  In the units of the edge update:
+//   d   = (ubar - mu) / s2 = -mu (W1 / e1 + W2 / e2)
+//   q   = Sbar / s2 = W1 v1 / e1 + W2 v2 / e2 + W1 W2 (m1 - m2)^2 / s2
+//   rho = 1 - q = s2 (W1 / e1 + W2 / e2 - W1 W2 mu^2 (v1 - v2)^2 / (e1 e2)^2)
+// using m1 - m2 = mu s2 (v1 - v2) / (e1 e2).  rho < 0 (more spread than the
+// cavity) happens for these priors, which are not log-concave; the edge update
+// then caps the new site.  No EM statistic (eab = 0): EM is for l1-TV only.
+__device__ __forceinline__ void mixture_moments(float mu, float s2, float mlog, float v1, float v2,
+                                                float& d, float& q, float& rho) {
+  const float e1 = v1 + s2, e2 = v2 + s2;
+  const float r1 = 1.0f / e1, r2 = 1.0f / e2;
+  const float dv = v1 - v2;
+  const float t = mlog + 0.5f * logf(e1 * r2) - 0.5f * mu * mu * dv * r1 * r2;
+  const float w2 = 1.0f / (1.0f + expf(-t)), w1 = 1.0f / (1.0f + expf(t));
+  const float a = w1 * r1 + w2 * r2;
+  const float sep = w1 * w2 * mu * mu * dv * dv * (r1 * r2) * (r1 * r2);
+  d = -mu * a;
+  q = w1 * v1 * r1 + w2 * v2 * r2 + s2 * sep;
+  rho = s2 * (a - sep);
+}
+
 // The two independent edges of one update step; the FP64 moments replace the
 // packed ones for the edges that need them.  Eq. update_qk_x from the tilted moments:
 // tau = rho / (c_j + q c_i), the variance cap, then nu = tau E + (E - m) / c.
+// kMix: the mixture priors (a separate instantiation, so that the l1-TV code
+// keeps its own register allocation).
+template <bool kMix>
 __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
   const float2 ti = make_float2(e0.ti, e1.ti), tj = make_float2(e0.tj, e1.tj);
   const float2 ci = rcp2(ti), cj = rcp2(tj);
@@ -252,20 +283,28 @@ __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
   const float2 mj = mul2(make_float2(e0.nj, e1.nj), cj);
   const float2 s2 = add2(ci, cj);
   const float2 mu = sub2(mi, mj);
-  const bool t0 = s2.x < c.tail_s2;  // an invalid edge here costs time only
-  const bool t1 = s2.y < c.tail_s2;
-  Moments2 o = tilted2(mu, s2, make_float2(c.lam, c.lam));
-  if (t0 || t1) {
-    // one call site for both edges keeps the rare path small
+  Moments2 o;
+  if (kMix) {
+    // closed forms in FP32
+    mixture_moments(mu.x, s2.x, c.mlog, c.v1, c.v2, o.d.x, o.q.x, o.rho.x);
+    mixture_moments(mu.y, s2.y, c.mlog, c.v1, c.v2, o.d.y, o.q.y, o.rho.y);
+    o.eab = make_float2(0.0f, 0.0f);
+  } else {
+    const bool t0 = s2.x < c.tail_s2;  // an invalid edge here costs time only
+    const bool t1 = s2.y < c.tail_s2;
+    o = tilted2(mu, s2, make_float2(c.lam, c.lam));
+    if (t0 || t1) {
+      // one call site for both edges keeps the rare path small
 #pragma unroll 1
-    for (int k = 0; k < 2; ++k) {
-      if (!(k ? t1 : t0)) continue;
-      const Moments a = tilted_fp64(k ? e1.ti : e0.ti, k ? e1.ni : e0.ni, k ? e1.tj : e0.tj,
-                                    k ? e1.nj : e0.nj, c.lam_d);
-      if (k) { o.d.y = a.d; o.q.y = a.q; o.rho.y = a.rho; o.eab.y = a.eab; }
-      else   { o.d.x = a.d; o.q.x = a.q; o.rho.x = a.rho; o.eab.x = a.eab; }
+      for (int k = 0; k < 2; ++k) {
+        if (!(k ? t1 : t0)) continue;
+        const Moments a = tilted_fp64(k ? e1.ti : e0.ti, k ? e1.ni : e0.ni, k ? e1.tj : e0.tj,
+                                      k ? e1.nj : e0.nj, c.lam_d);
+        if (k) { o.d.y = a.d; o.q.y = a.q; o.rho.y = a.rho; o.eab.y = a.eab; }
+        else   { o.d.x = a.d; o.q.x = a.q; o.rho.x = a.rho; o.eab.x = a.eab; }
+      }
+      c.n_fp64 += (t0 && e0.valid && e0.count) + (t1 && e1.valid && e1.count);
     }
-    c.n_fp64 += (t0 && e0.valid && e0.count) + (t1 && e1.valid && e1.count);
   }
   float2 tni = mul2(o.rho, rcp2(fma2(o.q, ci, cj)));
   float2 tnj = mul2(o.rho, rcp2(fma2(o.q, cj, ci)));
@@ -587,7 +626,7 @@ __device__ __forceinline__ void flush_unit(double* abar_partial, float lane_sum,
 // One update step of a known kind: 1, 2 (V1, V2 on the pair r0, r1), 3 or 4 (the
 // in-pair vertical update kI on r0, r1), 0 (kX joining carry and r0), 5 and 6
 // (V1, V2 after kX on carry and r0).
-template <int kKind, int kX, int kI>
+template <int kKind, int kX, int kI, bool kMix>
 __device__ __forceinline__ void do_step(Ctx& c, const Lane& L, Row& carry, Row& r0, Row& r1, bool cc,
                                         bool c0, bool c1) {
   Edge e0, e1;
@@ -597,7 +636,7 @@ __device__ __forceinline__ void do_step(Ctx& c, const Lane& L, Row& carry, Row& 
   else if (kKind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
   else if (kKind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
   else gather_v<kI>(L, r0, r1, c0, e0, e1);
-  edges2(c, e0, e1);
+  edges2<kMix>(c, e0, e1);
   if (kKind == 1) scatter_h1(c, r0, r1, e0, e1);
   else if (kKind == 2) scatter_h2(c, L, r0, r1, e0, e1);
   else if (kKind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
@@ -652,7 +691,7 @@ __device__ __forceinline__ int order_pos(int order, int k) {
 // before kX to it, joins its first row to the carried last row of the previous
 // pair by kX, applies the updates ordered after kX (horizontal ones only) to
 // those two rows, which are then final, and carries its second row on.
-template <bool kSite0FromY, int kX>
+template <bool kSite0FromY, int kX, bool kMix>
 __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, int b_hi,
                                        long long unit_base, float2* stage) {
   constexpr int kI = 7 - kX;
@@ -677,6 +716,9 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
   L.own_col = L.lane >= 1 && L.lane <= 30 && gc0 < W;
 
   Ctx c;
+  c.mlog = a.mix_logit;
+  c.v1 = a.mix_v1;
+  c.v2 = a.mix_v2;
   c.lam = (float)(*a.beta);
   c.lam_d = *a.beta;
   c.tail_s2 = (a.fp64_tail && c.lam > 0.0f) ? 1e-6f / (c.lam * c.lam) : -1.0f;
@@ -731,13 +773,13 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
     Row carry;
     if (kX == 4 && order == 0x4321) {
       // the default order V1, V2, V3, V4 as straight-line code
-      do_step<1, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
-      do_step<2, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
-      do_step<kI, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<1, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<2, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<kI, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
       if (!warm) {
         load_saved_row(carry_smem, carry_ok, carry);
         save_row(carry_smem, r1);  // r1 is final for this step: frees its registers
-        do_step<0, kX, kI>(c, L, carry, r0, r1, cc, c0, c1);
+        do_step<0, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
       } else {
         save_row(carry_smem, r1);
       }
@@ -758,7 +800,7 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
         else if (kind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
         else if (kind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
         else gather_v<kI>(L, r0, r1, c0, e0, e1);
-        edges2(c, e0, e1);
+        edges2<kMix>(c, e0, e1);
         if (kind == 1) scatter_h1(c, r0, r1, e0, e1);
         else if (kind == 2) scatter_h2(c, L, r0, r1, e0, e1);
         else if (kind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
@@ -793,7 +835,7 @@ __host__ __device__ __forceinline__ int later_vertical(int order) {
 }
 
 // Units [u_lo, u_hi) of one image (strip-major: unit = strip * units_per_strip + block).
-template <bool kSite0FromY, int kX>
+template <bool kSite0FromY, int kX, bool kMix>
 __device__ void run_units(const SweepArgs& a, long long u_lo, long long u_hi, float2* stage) {
   const int ups = units_per_strip(a.height);
   const int nsteps = steps_of(a.height);
@@ -803,19 +845,19 @@ __device__ void run_units(const SweepArgs& a, long long u_lo, long long u_hi, fl
     const long long strip_end = (long long)(strip + 1) * ups;
     const long long e = u_hi < strip_end ? u_hi : strip_end;
     const int k_lo = (int)(u - (long long)strip * ups), k_hi = (int)(e - (long long)strip * ups);
-    run_strip<kSite0FromY, kX>(a, strip, k_lo * kStepsPerUnit, min(k_hi * kStepsPerUnit, nsteps),
+    run_strip<kSite0FromY, kX, kMix>(a, strip, k_lo * kStepsPerUnit, min(k_hi * kStepsPerUnit, nsteps),
                                (long long)strip * ups, stage);
     u = e;
   }
 }
 
-template <bool kSite0FromY>
+template <bool kSite0FromY, bool kMix>
 __device__ __forceinline__ void run_units_any(const SweepArgs& a, long long u_lo, long long u_hi,
                                               float2* stage) {
   if (later_vertical(a.order) == 4)
-    run_units<kSite0FromY, 4>(a, u_lo, u_hi, stage);
+    run_units<kSite0FromY, 4, kMix>(a, u_lo, u_hi, stage);
   else
-    run_units<kSite0FromY, 3>(a, u_lo, u_hi, stage);
+    run_units<kSite0FromY, 3, kMix>(a, u_lo, u_hi, stage);
 }
 
 // Staging slots of this warp, followed by its argument copy.
@@ -829,7 +871,7 @@ __device__ __forceinline__ int global_warp() { return blockIdx.x * kWarpsPerBloc
 // One image: warp w takes strip w % S and the w / S-th of n_seg contiguous
 // ranges of that strip's units, so that the warps on neighbouring strips walk
 // the same rows at the same time (the strips' halo columns meet in L2).
-template <bool kSite0FromY, int kX>
+template <bool kSite0FromY, int kX, bool kMix>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_kernel(SweepArgs a, int n_seg) {
   const int S = strips_of(a.width);
   const int w = global_warp();
@@ -837,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_kernel(Sweep
   const int strip = w % S, seg = w / S;
   const long long ups = units_per_strip(a.height);
   const long long lo = ups * seg / n_seg, hi = ups * (seg + 1) / n_seg;
-  if (lo < hi) run_units<kSite0FromY, kX>(a, strip * ups + lo, strip * ups + hi, warp_stage());
+  if (lo < hi) run_units<kSite0FromY, kX, kMix>(a, strip * ups + lo, strip * ups + hi, warp_stage());
 }
 
 // Many images in one launch; units of image i start at items[i].unit_begin and
@@ -860,10 +902,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_batch_kernel
     const long long end = b.unit_begin + b.units;
     const long long e = hi < end ? hi : end;
     if (e > u) {
-      if (b.site0_from_y)
-        run_units_any<true>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
-      else
-        run_units_any<false>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+      const bool mix = b.a.prior != EP_TV_PRIOR_L1;
+      if (b.site0_from_y) {
+        if (mix) run_units_any<true, true>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+        else run_units_any<true, false>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+      } else {
+        if (mix) run_units_any<false, true>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+        else run_units_any<false, false>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+      }
       u = e;
     }
     ++it;
@@ -892,7 +938,7 @@ template <typename Kern>
 int resident_warps(Kern kernel, int slot) {
   constexpr int kMaxDev = 64;
   static std::mutex mu;
-  static int cache[kMaxDev][5] = {};
+  static int cache[kMaxDev][9] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152 * 8;
   std::lock_guard<std::mutex> lock(mu);
@@ -918,16 +964,16 @@ void launch_units(long long total, int resident, int& n_warps, int& blocks) {
   blocks = (n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
 }
 
-template <bool kSite0FromY, int kX>
+template <bool kSite0FromY, int kX, bool kMix>
 void launch_single(const SweepArgs& a, int slot, cudaStream_t s) {
   const int S = strips_of(a.width);
   const int ups = units_per_strip(a.height);
-  const int resident = resident_warps(prior_sweep_kernel<kSite0FromY, kX>, slot);
+  const int resident = resident_warps(prior_sweep_kernel<kSite0FromY, kX, kMix>, slot);
   int n_seg = resident / S;
   if (n_seg < 1) n_seg = 1;
   if (n_seg > ups) n_seg = ups;
   const int blocks = (S * n_seg + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  prior_sweep_kernel<kSite0FromY, kX><<<blocks, kThreads, kSmemBytes, s>>>(a, n_seg);
+  prior_sweep_kernel<kSite0FromY, kX, kMix><<<blocks, kThreads, kSmemBytes, s>>>(a, n_seg);
 }
 
 }  // namespace
@@ -948,11 +994,15 @@ int prior_sweep_blocks(int height, int width) {
 }
 
 void prior_sweep_prewarm() {
-  resident_warps(prior_sweep_kernel<true, 4>, 0);
-  resident_warps(prior_sweep_kernel<true, 3>, 1);
-  resident_warps(prior_sweep_kernel<false, 4>, 2);
-  resident_warps(prior_sweep_kernel<false, 3>, 3);
+  resident_warps(prior_sweep_kernel<true, 4, false>, 0);
+  resident_warps(prior_sweep_kernel<true, 3, false>, 1);
+  resident_warps(prior_sweep_kernel<false, 4, false>, 2);
+  resident_warps(prior_sweep_kernel<false, 3, false>, 3);
   resident_warps(prior_sweep_batch_kernel, 4);
+  resident_warps(prior_sweep_kernel<true, 4, true>, 5);
+  resident_warps(prior_sweep_kernel<true, 3, true>, 6);
+  resident_warps(prior_sweep_kernel<false, 4, true>, 7);
+  resident_warps(prior_sweep_kernel<false, 3, true>, 8);
 }
 
 void launch_prior_sweep_batch(const BatchItem* items, int n_items, long long total_units,
@@ -966,10 +1016,16 @@ void launch_prior_sweep(const SweepArgs& args, bool site0_from_y, cudaStream_t s
   SweepArgs a = args;
   prior_sweep_prepare(a);
   const bool x4 = later_vertical(a.order) == 4;
-  if (site0_from_y) {
-    if (x4) launch_single<true, 4>(a, 0, s); else launch_single<true, 3>(a, 1, s);
+  if (a.prior != EP_TV_PRIOR_L1) {
+    if (site0_from_y) {
+      if (x4) launch_single<true, 4, true>(a, 5, s); else launch_single<true, 3, true>(a, 6, s);
+    } else {
+      if (x4) launch_single<false, 4, true>(a, 7, s); else launch_single<false, 3, true>(a, 8, s);
+    }
+  } else if (site0_from_y) {
+    if (x4) launch_single<true, 4, false>(a, 0, s); else launch_single<true, 3, false>(a, 1, s);
   } else {
-    if (x4) launch_single<false, 4>(a, 2, s); else launch_single<false, 3>(a, 3, s);
+    if (x4) launch_single<false, 4, false>(a, 2, s); else launch_single<false, 3, false>(a, 3, s);
   }
 }
 

@@ -44,6 +44,7 @@ def test_default_params(lib):
     assert lib.ep_tv_default_params(ctypes.byref(p)) == 0
     assert p.damping == 0.5 and p.var_cap == 1e8 and p.periodic == 1
     assert p.rbmc_samples == 32 and p.order_mode == 0 and p.precision == 0
+    assert p.prior == _lib.PRIOR_L1
     assert lib.ep_tv_default_params(None) == 1
 
 
@@ -65,6 +66,13 @@ def _op(h=8, w=8, op=0, m=None):
     lambda o, p: setattr(o, "op", 9),
     lambda o, p: (setattr(o, "op", 1)),            # convolution without a kernel
     lambda o, p: setattr(p, "order_mode", 3),
+    lambda o, p: setattr(p, "prior", 3),
+    # mixture priors (Sec. II-B): omega in (0, 1), positive component variances
+    lambda o, p: (setattr(p, "prior", 1), setattr(p, "omega", 0.5), setattr(p, "s1_sq", 1.0)),
+    lambda o, p: (setattr(p, "prior", 1), setattr(p, "omega", 1.0), setattr(p, "s1_sq", 1.0),
+                  setattr(p, "s2_sq", 0.1)),
+    lambda o, p: (setattr(p, "prior", 2), setattr(p, "omega", 0.0), setattr(p, "s1_sq", 1.0)),
+    lambda o, p: (setattr(p, "prior", 2), setattr(p, "omega", 0.5), setattr(p, "s1_sq", -1.0)),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, mutate):
     o = _op()

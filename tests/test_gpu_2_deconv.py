@@ -206,3 +206,28 @@ def test_config2_512_against_oracle_samples():
     assert_parity(mu[idx], var[idx], ref["mean"], ref["var"], p.y)
     assert abs(mu.sum() / float(ref["mean_sum"]) - 1.0) < 1e-5
     assert abs(var.sum() / float(ref["var_sum"]) - 1.0) < 1e-4
+
+
+def test_deconv_mog2_prior_parity_and_no_em():
+    """The MoG2-TV prior with the deconvolution likelihood site (Sec. II-B with
+    Eq. tilted_P_1) against the oracle with the same probes, on an instance where
+    thousands of site updates hit the variance cap; EM is refused for the mixture
+    priors (Sec. IV defines it for l1-TV only)."""
+    from paper_2110_01585_gb300 import PRIOR_MOG2, EPTVError
+
+    from ._cases import MOG2_DECONV, mog2_deconv_problem, mog2_oracle_run
+    c = MOG2_DECONV
+    p = mog2_deconv_problem()
+    pr = probes(p, c["S"], c["probe_seed"])
+    theta = c["theta"]
+    mu, var, ep = _gpu(p, c["sweeps"], c["S"], pr, prior=PRIOR_MOG2, omega=theta[0],
+                       s1_sq=theta[1], s2_sq=theta[2])
+    capped = ep.stats()["n_capped"]
+    with pytest.raises(EPTVError):
+        ep.sweep(1, em_every=1)
+    with pytest.raises(EPTVError):
+        ep.em_beta()
+    ep.close()
+    mu_r, var_r, capped_r = mog2_oracle_run(p, y32(p), pr)
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    assert abs(capped - capped_r) <= max(4, 0.01 * capped_r), (capped, capped_r)
