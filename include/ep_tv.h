@@ -115,11 +115,16 @@ typedef struct {
   double omega;          /* MoG2 / BG: mixture weight of the N(0, s1_sq) component, in (0, 1) */
   double s1_sq;          /* MoG2 / BG: variance of the first Gaussian component, > 0 */
   double s2_sq;          /* MoG2: variance of the second component, > 0 (BG: unused) */
+  int32_t em_option;     /* l1-TV: the approximation of a_0 (Eq. a_0) of the EM update
+                            (Sec. IV): 1 = a_x (Eq. ax), E|x_i - x_j| under Q(x) after
+                            the sweep; 2 = a_u (Eq. au), E|u_n| under the Gaussian Q(u_n)
+                            matched during the sweep; 3 = abar_u (Eq. 3rd_alternative_a0,
+                            default), E|u_n| under the tilted P_k(u_n) */
 } ep_tv_params;
 
 /* Fills *p with defaults: damping 0.5, var_cap 1e8, periodic 1, order_mode 0,
    rbmc_samples 32, cg_max_iter 1000, cg_rtol 1e-9, precision 0, seed 1234,
-   prior EP_TV_PRIOR_L1.  xi and beta (or, for the mixture priors, omega, s1_sq
+   prior EP_TV_PRIOR_L1, em_option 3.  xi and beta (or, for the mixture priors, omega, s1_sq
    and s2_sq) are set to 0 and must be provided.  The mixture priors are not
    log-concave: their edge updates can ask for negative site variances, which the
    variance cap of Sec. III-C replaces.  The EM update of beta (Sec. IV) exists
@@ -148,13 +153,25 @@ ep_tv_status ep_tv_set_probes(ep_tv_ctx* ctx, const float* eps1, const float* ep
 ep_tv_status ep_tv_sweep(ep_tv_ctx* ctx, int32_t n_sweeps, const int8_t* k_order,
                          int32_t em_every);
 
-/* EM M-step (Algorithm 2, Option 3): beta <- N / a_u, with a_u the sum over all
-   edges of E_{P_k}|u_n| taken during the last sweep, reduced in FP64 in a fixed
-   order.  Enqueued on the stream.  If beta_out or abar_out is non-NULL the call
+/* EM M-step (Algorithm 2): beta <- N / a, with a the statistic chosen by
+   params.em_option (default Option 3: a_u, the sum over all edges of E_{P_k}|u_n|
+   taken during the last sweep), reduced in FP64 in a fixed order.  Enqueued on the stream.  If beta_out or abar_out is non-NULL the call
    synchronises the stream and writes the new beta / a_u there (HOST doubles).
    l1-TV prior only (EP_TV_ERR_UNSUPPORTED otherwise; ep_tv_sweep likewise
    refuses em_every > 0 for the mixture priors with EP_TV_ERR_ARG). */
 ep_tv_status ep_tv_em_beta(ep_tv_ctx* ctx, double* beta_out, double* abar_out);
+
+/* EP-EM (Algorithm 2) with the EP of Algorithm 1 run to convergence inside every
+   EM iteration.  For each of n_em iterations: sweeps until the largest change of a
+   posterior mean in one sweep is at most tol times the largest |posterior mean|
+   (the reading of the paper's StopRule), or max_sweeps sweeps; then the EM update
+   of beta with the statistic of params.em_option.  beta_out: HOST, n_em doubles,
+   beta after each iteration; sweeps_out: HOST, n_em int32 (sweeps of each inner
+   run), or NULL.  Synchronises after every sweep to read the change.  l1-TV only
+   (EP_TV_ERR_UNSUPPORTED otherwise).  The fast variant of Sec. IV (a fixed, small
+   number of sweeps per EM iteration) is ep_tv_sweep with em_every. */
+ep_tv_status ep_tv_ep_em(ep_tv_ctx* ctx, int32_t n_em, int32_t max_sweeps, double tol,
+                         double* beta_out, int32_t* sweeps_out);
 
 /* Sets beta (no EM). */
 ep_tv_status ep_tv_set_beta(ep_tv_ctx* ctx, double beta);

@@ -29,7 +29,9 @@ paper leaves open are:
 * EM (Sec. IV, Algorithm 2, Option 3, Eq. 3rd_alternative_a0): the statistic
   a_u is the sum over the four V_k of E_{P_k}|u_n| over all edges, taken at the
   tilted distributions of the last sweep, and lam = N / a_u with N the number
-  of pixels.
+  of pixels.  Options 1 (Eq. ax: E|x_i - x_j| under the diagonal Q(x) after the
+  sweep) and 2 (Eq. au: E|u_n| under the Gaussian Q(u_n) whose moments were
+  matched to P_k(u_n) during the sweep) replace a_u by those sums.
 * initialisation (Algorithm 1): mu_{x,0} = y, Sigma_{x,0} = xi I, the other
   sites have zero mean and variance var_cap.  For compressive sensing y has
   length M < N; the oracle uses mu_{x,0} = H^T y.
@@ -44,7 +46,7 @@ import scipy.linalg
 
 from . import operators
 from .partition import edges
-from .tilted import gaussian_mixture_tilted, laplace_tilted
+from .tilted import folded_normal_mean, gaussian_mixture_tilted, laplace_tilted
 
 
 def _fft_qmul(hth, inv_c, xi, h, w, v):
@@ -133,6 +135,8 @@ class EPOracle:
         self.pool = pool
         self.edge_lists = [edges(self.height, self.width, k, self.periodic) for k in (1, 2, 3, 4)]
         self.abar = 0.0          # sum of E|u| over the edges of the last sweep
+        self.abar_q = 0.0        # the same under the matched Gaussians Q(u_n) (Option 2)
+        self._abar_q_sweep = 0.0
         self.n_sweeps = 0
         self.n_capped = 0        # site updates whose precision the cap replaced
         self.init()
@@ -209,6 +213,8 @@ class EPOracle:
         tau_j, nu_j = self._new_site(Ej, Vj, cj, mj)
         self._damp(k, first, tau_i, nu_i)
         self._damp(k, second, tau_j, nu_j)
+        if self.prior == "l1":
+            self._abar_q_sweep += float(np.sum(folded_normal_mean(m_bar, S_bar)))
         return float(np.sum(eabs))
 
     def tilted_p0(self, c: np.ndarray, m: np.ndarray):
@@ -316,6 +322,7 @@ class EPOracle:
         if sorted(order) != [1, 2, 3, 4]:
             raise ValueError("k_order must be a permutation of 1..4")
         abar = 0.0
+        self._abar_q_sweep = 0.0
         if self.order == "q0_first":
             self.site0_update()
         for k in order:
@@ -323,22 +330,59 @@ class EPOracle:
         if self.order == "prior_first":
             self.site0_update()
         self.abar = abar
+        self.abar_q = self._abar_q_sweep
         self.n_sweeps += 1
         return abar
 
-    def em_update(self) -> float:
-        """M-step of Algorithm 2 with Option 3: lam = N / a_u of the last sweep."""
+    def em_statistic(self, option: int = 3) -> float:
+        """The approximation of a_0 (Eq. a_0) used by the M-step (Sec. IV):
+        option 1 = a_x (Eq. ax), 2 = a_u (Eq. au), 3 = abar_u (Eq. 3rd_alternative_a0)."""
+        if option == 3:
+            return self.abar
+        if option == 2:
+            return self.abar_q
+        if option == 1:
+            mu, var = (a.reshape(-1) for a in self.posterior())
+            total = 0.0
+            for first, second in self.edge_lists:
+                total += float(np.sum(folded_normal_mean(mu[first] - mu[second],
+                                                         var[first] + var[second])))
+            return total
+        raise ValueError(option)
+
+    def em_update(self, option: int = 3) -> float:
+        """M-step of Algorithm 2: lam = N / a with a from em_statistic(option)."""
         if self.prior != "l1":
             raise ValueError("EM is defined for the l1-TV prior only (Sec. IV)")
-        self.lam = self.n / self.abar
+        self.lam = self.n / self.em_statistic(option)
         return self.lam
 
-    def run(self, n_sweeps: int, em_every: int = 0, k_orders=None):
+    def run(self, n_sweeps: int, em_every: int = 0, k_orders=None, em_option: int = 3):
         """n_sweeps sweeps; with em_every > 0, lam is updated after every
         em_every-th sweep.  Returns the list of lam values after each update."""
         lams = []
         for t in range(n_sweeps):
             self.sweep(None if k_orders is None else k_orders[t])
             if em_every and (t + 1) % em_every == 0:
-                lams.append(self.em_update())
+                lams.append(self.em_update(em_option))
         return lams
+
+    def ep_em(self, n_em: int, max_sweeps: int, tol: float, em_option: int = 3):
+        """Algorithm 2 with Algorithm 1 run to convergence inside every EM
+        iteration (the StopRule is read as: the largest change of a posterior
+        mean in one sweep is at most tol times the largest |posterior mean|, or
+        max_sweeps sweeps), then the M-step.  Returns the lam after each
+        iteration and the sweeps of each inner run."""
+        lams, sweeps = [], []
+        for _ in range(n_em):
+            prev, _ = self.posterior()
+            for s in range(max_sweeps):
+                self.sweep()
+                cur, _ = self.posterior()
+                done = float(np.max(np.abs(cur - prev))) <= tol * float(np.max(np.abs(cur)))
+                prev = cur
+                if done:
+                    break
+            sweeps.append(s + 1)
+            lams.append(self.em_update(em_option))
+        return lams, sweeps

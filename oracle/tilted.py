@@ -150,3 +150,11 @@ def gaussian_mixture_tilted(mu, s2, omega, v1, v2):
     mean = w1 * m1 + w2 * m2
     var = w1 * (c1 + m1 ** 2) + w2 * (c2 + m2 ** 2) - mean ** 2
     return mean, var
+
+
+def folded_normal_mean(m, s2):
+    """E|u| for u ~ N(m, s2): s sqrt(2/pi) exp(-m^2 / (2 s2)) + m erf(m / (s sqrt 2))."""
+    from scipy.special import erf
+    m = np.asarray(m, dtype=np.float64)
+    s = np.sqrt(np.asarray(s2, dtype=np.float64))
+    return s * SQRT_2_OVER_PI * np.exp(-m * m / (2.0 * s * s)) + m * erf(m / (s * SQRT2))

@@ -135,6 +135,15 @@ class EPTV:
         _lib.check(self._lib.ep_tv_em_beta(self._ctx, ctypes.byref(b), ctypes.byref(a)), "ep_tv_em_beta")
         return b.value, a.value
 
+    def ep_em(self, n_em: int, max_sweeps: int = 200, tol: float = 1e-5):
+        """Algorithm 2 with EP run to convergence inside every EM iteration;
+        returns (beta after each iteration, sweeps of each inner run)."""
+        betas = (ctypes.c_double * n_em)()
+        sweeps = (ctypes.c_int32 * n_em)()
+        _lib.check(self._lib.ep_tv_ep_em(self._ctx, int(n_em), int(max_sweeps), float(tol), betas,
+                                         sweeps), "ep_tv_ep_em")
+        return list(betas), list(sweeps)
+
     def set_beta(self, beta: float):
         _lib.check(self._lib.ep_tv_set_beta(self._ctx, float(beta)), "ep_tv_set_beta")
 

@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("cg_max_iter", ctypes.c_int32), ("cg_rtol", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("prior", ctypes.c_int32), ("omega", ctypes.c_double), ("s1_sq", ctypes.c_double),
-                ("s2_sq", ctypes.c_double)]
+                ("s2_sq", ctypes.c_double), ("em_option", ctypes.c_int32)]
 
 
 SIGNATURES = {
@@ -51,6 +51,8 @@ SIGNATURES = {
     "ep_tv_sweep": (c_int32, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_int8), c_int32]),
     "ep_tv_em_beta": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "ep_tv_set_beta": (c_int32, [c_void_p, c_double]),
+    "ep_tv_ep_em": (c_int32, [c_void_p, c_int32, c_int32, c_double, ctypes.POINTER(c_double),
+                              ctypes.POINTER(c_int32)]),
     "ep_tv_posterior": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ep_tv_get_sites": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ep_tv_status_check": (c_int32, [c_void_p]),

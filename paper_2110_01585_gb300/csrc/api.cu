@@ -50,6 +50,10 @@ struct ep_tv_ctx {
   int graph_em[2] = {-1, -1};
   int graph_len[2] = {0, 0};
   long long graph_sweeps = 0;  // sweeps run from graph replays (this context or its batch)
+  // EP-EM convergence checks (allocated on the first ep_tv_ep_em call)
+  float* mu_prev = nullptr;     // [N] posterior mean after the previous sweep
+  unsigned* d_change = nullptr; // max |change|, max |mean| (float bits)
+  unsigned* h_change = nullptr; // pinned copy
 };
 
 namespace {
@@ -68,6 +72,7 @@ namespace eptv {
 // The edge factor's parameters (Sec. II-B): beta for l1-TV (checked by the
 // callers), omega in (0, 1) and positive component variances for the mixtures.
 bool prior_params_ok(const ep_tv_params* p) {
+  if (p->em_option < 1 || p->em_option > 3) return false;
   switch (p->prior) {
     case EP_TV_PRIOR_L1: return true;
     case EP_TV_PRIOR_MOG2:
@@ -79,6 +84,7 @@ bool prior_params_ok(const ep_tv_params* p) {
 
 void set_prior_args(SweepArgs& a, const ep_tv_params* p) {
   a.prior = p->prior;
+  a.em_option = p->em_option;
   a.mix_logit = 0.f;
   a.mix_v1 = a.mix_v2 = 0.f;
   if (p->prior != EP_TV_PRIOR_L1) {
@@ -149,6 +155,9 @@ void free_ctx(ep_tv_ctx* c) {
   cudaFree(c->abar_partial);
   cudaFree(c->status);
   cudaFree(c->counters);
+  cudaFree(c->mu_prev);
+  cudaFree(c->d_change);
+  if (c->h_change) cudaFreeHost(c->h_change);
   delete c;
 }
 
@@ -182,6 +191,17 @@ ep_tv_status latched(ep_tv_ctx* c) {
   if (st & ST_TIMEOUT) return EP_TV_ERR_TIMEOUT;
   if (st & ST_CG_NOCONV) return EP_TV_ERR_CG_NOCONV;
   return EP_TV_OK;
+}
+
+// The EM update (Sec. IV, Algorithm 2) on the device: the statistic that
+// params.em_option selects, reduced in a fixed order, then beta = N / a.  Option 1
+// (Eq. ax) is formed here from the sites (tp, np: the prior buffers holding the
+// sweep's result); Options 2 and 3 were accumulated by the prior pass.
+void launch_em(ep_tv_ctx* c, const float* tp, const float* np, cudaStream_t s) {
+  if (c->p.em_option == 1)
+    launch_ax(c->tau0, c->nu0, tp, np, c->height, c->width, c->p.periodic, c->abar_partial,
+              c->n_partial, s);
+  launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, s);
 }
 
 SweepArgs sweep_args(ep_tv_ctx* c, int order) {
@@ -234,8 +254,7 @@ cudaGraphExec_t graph_for(ep_tv_ctx* c, int period, int em_every) {
     a.nout = c->pnu[cur ^ 1];
     launch_prior_sweep(a, true, c->stream);
     cur ^= 1;
-    if (em_every > 0 && (t + 1) % em_every == 0)
-      launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
+    if (em_every > 0 && (t + 1) % em_every == 0) launch_em(c, c->ptau[cur], c->pnu[cur], c->stream);
   }
   const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   cudaGraphExec_t exec = nullptr;
@@ -265,6 +284,7 @@ ep_tv_status ep_tv_default_params(ep_tv_params* p) {
   p->precision = 0;
   p->seed = 1234;
   p->prior = EP_TV_PRIOR_L1;
+  p->em_option = 3;
   return EP_TV_OK;
 }
 
@@ -403,9 +423,7 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
       if (st != EP_TV_OK) return st;
     }
     ++c->sweeps;
-    if (em_every > 0 && (t + 1) % em_every == 0) {
-      launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
-    }
+    if (em_every > 0 && (t + 1) % em_every == 0) launch_em(c, c->ptau[c->cur], c->pnu[c->cur], c->stream);
   }
   if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
   return EP_TV_OK;
@@ -416,7 +434,7 @@ ep_tv_status ep_tv_em_beta(ep_tv_ctx* c, double* beta_out, double* abar_out) {
   if (c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_UNSUPPORTED;  // Sec. IV: l1-TV only
   if (c->failed) return EP_TV_ERR_STATE;
   if (c->sweeps == 0) return EP_TV_ERR_ARG;
-  launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, c->stream);
+  launch_em(c, c->ptau[c->cur], c->pnu[c->cur], c->stream);
   if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
   if (beta_out || abar_out) {
     double ds[DS_COUNT];
@@ -425,6 +443,54 @@ ep_tv_status ep_tv_em_beta(ep_tv_ctx* c, double* beta_out, double* abar_out) {
     if (st != EP_TV_OK) return st;
     if (beta_out) *beta_out = ds[DS_BETA];
     if (abar_out) *abar_out = ds[DS_ABAR];
+  }
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_ep_em(ep_tv_ctx* c, int32_t n_em, int32_t max_sweeps, double tol,
+                         double* beta_out, int32_t* sweeps_out) {
+  if (!c || n_em < 1 || max_sweeps < 1 || !(tol >= 0.0) || !beta_out) return EP_TV_ERR_ARG;
+  if (c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_UNSUPPORTED;
+  if (c->failed) return EP_TV_ERR_STATE;
+  cudaStream_t s = c->stream;
+  if (!c->mu_prev) {
+    if (cudaMalloc(&c->mu_prev, sizeof(float) * c->n) != cudaSuccess ||
+        cudaMalloc(&c->d_change, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaHostAlloc(&c->h_change, 2 * sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return EP_TV_ERR_NOMEM;
+    }
+  }
+  auto change = [&]() -> ep_tv_status {
+    CK(cudaMemsetAsync(c->d_change, 0, 2 * sizeof(unsigned), s));
+    launch_mean_change(c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur], c->n, c->mu_prev,
+                       c->d_change, s);
+    return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+  };
+  for (int t = 0; t < n_em; ++t) {
+    ep_tv_status st = change();  // the posterior before this iteration's EP run
+    if (st != EP_TV_OK) return st;
+    int sw = 0;
+    while (sw < max_sweeps) {
+      st = ep_tv_sweep(c, 1, nullptr, 0);
+      if (st != EP_TV_OK) return st;
+      ++sw;
+      st = change();
+      if (st != EP_TV_OK) return st;
+      CK(cudaMemcpyAsync(c->h_change, c->d_change, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      float dmax, mmax;
+      memcpy(&dmax, c->h_change, sizeof(float));
+      memcpy(&mmax, c->h_change + 1, sizeof(float));
+      if (dmax <= (float)tol * mmax) break;
+    }
+    launch_em(c, c->ptau[c->cur], c->pnu[c->cur], s);
+    double beta = 0.0;
+    CK(cudaMemcpyAsync(&beta, c->dscal + DS_BETA, sizeof(double), cudaMemcpyDeviceToHost, s));
+    st = latched(c);
+    if (st != EP_TV_OK) return st;
+    beta_out[t] = beta;
+    if (sweeps_out) sweeps_out[t] = sw;
   }
   return EP_TV_OK;
 }
@@ -739,8 +805,10 @@ cudaGraphExec_t batch_graph(ep_tv_batch* b, int period, int em_every) {
   for (int t = 0; t < period; ++t) {
     launch_prior_sweep_batch(b->g_items[t & 1], (int)n, b->total_units, b->stream);
     if (em_every > 0 && (t + 1) % em_every == 0)
-      for (ep_tv_ctx* c : b->ctx)
-        launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, b->stream);
+      for (ep_tv_ctx* c : b->ctx) {
+        const int cur = c->cur ^ ((t + 1) & 1);  // the contexts' parity after sweep t
+        launch_em(c, c->ptau[cur], c->pnu[cur], b->stream);
+      }
   }
   const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
   cudaGraphExec_t exec = nullptr;
@@ -913,8 +981,7 @@ ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_ever
       for (size_t k = 0; k < b->lik.size(); ++k) CK(cudaStreamWaitEvent(b->stream, b->wdone[k], 0));
     }
     if (em_every > 0 && (t + 1) % em_every == 0)
-      for (ep_tv_ctx* c : b->ctx)
-        launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, b->stream);
+      for (ep_tv_ctx* c : b->ctx) launch_em(c, c->ptau[c->cur], c->pnu[c->cur], b->stream);
   }
   return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
 }

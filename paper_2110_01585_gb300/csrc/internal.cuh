@@ -107,6 +107,7 @@ struct SweepArgs {
   int order;                  // four 4-bit k values, first update in the low nibble
   int fp64_tail;              // 1: recompute poorly conditioned edges in FP64
   int prior;                  // ep_tv_prior
+  int em_option;              // 1, 2 or 3: which EM statistic the pass accumulates (2: Eq. au)
   float mix_logit;            // MoG2 / BG: log((1 - omega) / omega)
   float mix_v1, mix_v2;       // MoG2 / BG: component variances (BG: v2 = 0, the point mass)
   double* abar_partial;       // one FP64 partial sum of E|u| per work unit
@@ -150,6 +151,12 @@ void launch_init_sites(float* tau0, float* nu0, float* tp, float* np, const floa
 void launch_warm_start(float* tau0, float* nu0, float* tp, float* np, const float* out,
                        const float* y, float log_xi, long long n, float min_tau, bool keep_site0,
                        bool site0_only, cudaStream_t s);
+// Option 1 of the EM statistic (a_x) into n_partial FP64 block partials.
+void launch_ax(const float* tau0, const float* nu0, const float* tp, const float* np, int height,
+               int width, int periodic, double* partial, int n_partial, cudaStream_t s);
+// Posterior mean into prev, max |change| and max |mean| as float bits into out[0..1].
+void launch_mean_change(const float* tau0, const float* nu0, const float* tp, const float* np,
+                        long long n, float* prev, unsigned* out, cudaStream_t s);
 void launch_posterior(const float* tau0, const float* nu0, const float* tp, const float* np,
                       long long n, float* mean, float* var, cudaStream_t s);
 

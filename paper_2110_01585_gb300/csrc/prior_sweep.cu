@@ -273,10 +273,22 @@ __device__ __forceinline__ void mixture_moments(float mu, float s2, float mlog, 
 // The two independent edges of one update step; the FP64 moments replace the
 // packed ones for the edges that need them.  Eq. update_qk_x from the tilted moments:
 // tau = rho / (c_j + q c_i), the variance cap, then nu = tau E + (E - m) / c.
-// kMix: the mixture priors (a separate instantiation, so that the l1-TV code
-// keeps its own register allocation).
-template <bool kMix>
+// kEdge (a separate instantiation each, so that the default code keeps its own
+// register allocation): kEdgeL1, l1-TV with the EM statistic E_{P_k}|u| of
+// Option 3 (Eq. 3rd_alternative_a0); kEdgeL1Q, l1-TV with E|u| under the
+// matched Gaussian Q(u_n) = N(ubar, Sbar) of Option 2 (Eq. au); kEdgeMix, the
+// mixture priors (no EM statistic).
+enum : int { kEdgeL1 = 0, kEdgeL1Q = 1, kEdgeMix = 2 };
+
+// E|u| for u ~ N(m, v): sqrt(v) sqrt(2/pi) exp(-m^2 / (2 v)) + m erf(m / sqrt(2 v)).
+__device__ __forceinline__ float folded_mean(float m, float v) {
+  const float r = rsqrtf(v);
+  return v * r * 0.797884561f * expf(-0.5f * m * m / v) + m * erff(0.707106781f * m * r);
+}
+
+template <int kEdge>
 __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
+  constexpr bool kMix = kEdge == kEdgeMix;
   const float2 ti = make_float2(e0.ti, e1.ti), tj = make_float2(e0.tj, e1.tj);
   const float2 ci = rcp2(ti), cj = rcp2(tj);
   const float2 mi = mul2(make_float2(e0.ni, e1.ni), ci);
@@ -304,6 +316,11 @@ __device__ __forceinline__ void edges2(Ctx& c, Edge& e0, Edge& e1) {
         else   { o.d.x = a.d; o.q.x = a.q; o.rho.x = a.rho; o.eab.x = a.eab; }
       }
       c.n_fp64 += (t0 && e0.valid && e0.count) + (t1 && e1.valid && e1.count);
+    }
+    if (kEdge == kEdgeL1Q) {
+      // Option 2: E|u| under N(ubar, Sbar), ubar = mu + s^2 d, Sbar = q s^2
+      o.eab.x = folded_mean(fmaf(s2.x, o.d.x, mu.x), o.q.x * s2.x);
+      o.eab.y = folded_mean(fmaf(s2.y, o.d.y, mu.y), o.q.y * s2.y);
     }
   }
   float2 tni = mul2(o.rho, rcp2(fma2(o.q, ci, cj)));
@@ -626,7 +643,7 @@ __device__ __forceinline__ void flush_unit(double* abar_partial, float lane_sum,
 // One update step of a known kind: 1, 2 (V1, V2 on the pair r0, r1), 3 or 4 (the
 // in-pair vertical update kI on r0, r1), 0 (kX joining carry and r0), 5 and 6
 // (V1, V2 after kX on carry and r0).
-template <int kKind, int kX, int kI, bool kMix>
+template <int kKind, int kX, int kI, int kEdge>
 __device__ __forceinline__ void do_step(Ctx& c, const Lane& L, Row& carry, Row& r0, Row& r1, bool cc,
                                         bool c0, bool c1) {
   Edge e0, e1;
@@ -636,7 +653,7 @@ __device__ __forceinline__ void do_step(Ctx& c, const Lane& L, Row& carry, Row& 
   else if (kKind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
   else if (kKind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
   else gather_v<kI>(L, r0, r1, c0, e0, e1);
-  edges2<kMix>(c, e0, e1);
+  edges2<kEdge>(c, e0, e1);
   if (kKind == 1) scatter_h1(c, r0, r1, e0, e1);
   else if (kKind == 2) scatter_h2(c, L, r0, r1, e0, e1);
   else if (kKind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
@@ -691,7 +708,7 @@ __device__ __forceinline__ int order_pos(int order, int k) {
 // before kX to it, joins its first row to the carried last row of the previous
 // pair by kX, applies the updates ordered after kX (horizontal ones only) to
 // those two rows, which are then final, and carries its second row on.
-template <bool kSite0FromY, int kX, bool kMix>
+template <bool kSite0FromY, int kX, int kEdge>
 __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, int b_hi,
                                        long long unit_base, float2* stage) {
   constexpr int kI = 7 - kX;
@@ -773,13 +790,13 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
     Row carry;
     if (kX == 4 && order == 0x4321) {
       // the default order V1, V2, V3, V4 as straight-line code
-      do_step<1, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
-      do_step<2, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
-      do_step<kI, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<1, kX, kI, kEdge>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<2, kX, kI, kEdge>(c, L, carry, r0, r1, cc, c0, c1);
+      do_step<kI, kX, kI, kEdge>(c, L, carry, r0, r1, cc, c0, c1);
       if (!warm) {
         load_saved_row(carry_smem, carry_ok, carry);
         save_row(carry_smem, r1);  // r1 is final for this step: frees its registers
-        do_step<0, kX, kI, kMix>(c, L, carry, r0, r1, cc, c0, c1);
+        do_step<0, kX, kI, kEdge>(c, L, carry, r0, r1, cc, c0, c1);
       } else {
         save_row(carry_smem, r1);
       }
@@ -800,7 +817,7 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
         else if (kind == 5) gather_h1(L, carry, r0, cc, c0, e0, e1);
         else if (kind == 6) gather_h2(L, carry, r0, cc, c0, e0, e1);
         else gather_v<kI>(L, r0, r1, c0, e0, e1);
-        edges2<kMix>(c, e0, e1);
+        edges2<kEdge>(c, e0, e1);
         if (kind == 1) scatter_h1(c, r0, r1, e0, e1);
         else if (kind == 2) scatter_h2(c, L, r0, r1, e0, e1);
         else if (kind == 0) scatter_v<kX>(c, carry, r0, e0, e1);
@@ -835,7 +852,7 @@ __host__ __device__ __forceinline__ int later_vertical(int order) {
 }
 
 // Units [u_lo, u_hi) of one image (strip-major: unit = strip * units_per_strip + block).
-template <bool kSite0FromY, int kX, bool kMix>
+template <bool kSite0FromY, int kX, int kEdge>
 __device__ void run_units(const SweepArgs& a, long long u_lo, long long u_hi, float2* stage) {
   const int ups = units_per_strip(a.height);
   const int nsteps = steps_of(a.height);
@@ -845,19 +862,24 @@ __device__ void run_units(const SweepArgs& a, long long u_lo, long long u_hi, fl
     const long long strip_end = (long long)(strip + 1) * ups;
     const long long e = u_hi < strip_end ? u_hi : strip_end;
     const int k_lo = (int)(u - (long long)strip * ups), k_hi = (int)(e - (long long)strip * ups);
-    run_strip<kSite0FromY, kX, kMix>(a, strip, k_lo * kStepsPerUnit, min(k_hi * kStepsPerUnit, nsteps),
+    run_strip<kSite0FromY, kX, kEdge>(a, strip, k_lo * kStepsPerUnit, min(k_hi * kStepsPerUnit, nsteps),
                                (long long)strip * ups, stage);
     u = e;
   }
 }
 
-template <bool kSite0FromY, bool kMix>
+template <bool kSite0FromY, int kEdge>
 __device__ __forceinline__ void run_units_any(const SweepArgs& a, long long u_lo, long long u_hi,
                                               float2* stage) {
   if (later_vertical(a.order) == 4)
-    run_units<kSite0FromY, 4, kMix>(a, u_lo, u_hi, stage);
+    run_units<kSite0FromY, 4, kEdge>(a, u_lo, u_hi, stage);
   else
-    run_units<kSite0FromY, 3, kMix>(a, u_lo, u_hi, stage);
+    run_units<kSite0FromY, 3, kEdge>(a, u_lo, u_hi, stage);
+}
+
+// The edge variant of an image's arguments.
+__host__ __device__ __forceinline__ int edge_kind(const SweepArgs& a) {
+  return a.prior != EP_TV_PRIOR_L1 ? kEdgeMix : (a.em_option == 2 ? kEdgeL1Q : kEdgeL1);
 }
 
 // Staging slots of this warp, followed by its argument copy.
@@ -871,7 +893,7 @@ __device__ __forceinline__ int global_warp() { return blockIdx.x * kWarpsPerBloc
 // One image: warp w takes strip w % S and the w / S-th of n_seg contiguous
 // ranges of that strip's units, so that the warps on neighbouring strips walk
 // the same rows at the same time (the strips' halo columns meet in L2).
-template <bool kSite0FromY, int kX, bool kMix>
+template <bool kSite0FromY, int kX, int kEdge>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_kernel(SweepArgs a, int n_seg) {
   const int S = strips_of(a.width);
   const int w = global_warp();
@@ -879,7 +901,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_kernel(Sweep
   const int strip = w % S, seg = w / S;
   const long long ups = units_per_strip(a.height);
   const long long lo = ups * seg / n_seg, hi = ups * (seg + 1) / n_seg;
-  if (lo < hi) run_units<kSite0FromY, kX, kMix>(a, strip * ups + lo, strip * ups + hi, warp_stage());
+  if (lo < hi) run_units<kSite0FromY, kX, kEdge>(a, strip * ups + lo, strip * ups + hi, warp_stage());
 }
 
 // Many images in one launch; units of image i start at items[i].unit_begin and
@@ -902,13 +924,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) prior_sweep_batch_kernel
     const long long end = b.unit_begin + b.units;
     const long long e = hi < end ? hi : end;
     if (e > u) {
-      const bool mix = b.a.prior != EP_TV_PRIOR_L1;
+      const int kind = edge_kind(b.a);
+      const long long ulo = u - b.unit_begin, uhi = e - b.unit_begin;
       if (b.site0_from_y) {
-        if (mix) run_units_any<true, true>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
-        else run_units_any<true, false>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+        if (kind == kEdgeMix) run_units_any<true, kEdgeMix>(b.a, ulo, uhi, warp_stage());
+        else if (kind == kEdgeL1Q) run_units_any<true, kEdgeL1Q>(b.a, ulo, uhi, warp_stage());
+        else run_units_any<true, kEdgeL1>(b.a, ulo, uhi, warp_stage());
       } else {
-        if (mix) run_units_any<false, true>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
-        else run_units_any<false, false>(b.a, u - b.unit_begin, e - b.unit_begin, warp_stage());
+        if (kind == kEdgeMix) run_units_any<false, kEdgeMix>(b.a, ulo, uhi, warp_stage());
+        else if (kind == kEdgeL1Q) run_units_any<false, kEdgeL1Q>(b.a, ulo, uhi, warp_stage());
+        else run_units_any<false, kEdgeL1>(b.a, ulo, uhi, warp_stage());
       }
       u = e;
     }
@@ -938,7 +963,7 @@ template <typename Kern>
 int resident_warps(Kern kernel, int slot) {
   constexpr int kMaxDev = 64;
   static std::mutex mu;
-  static int cache[kMaxDev][9] = {};
+  static int cache[kMaxDev][13] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152 * 8;
   std::lock_guard<std::mutex> lock(mu);
@@ -964,16 +989,27 @@ void launch_units(long long total, int resident, int& n_warps, int& blocks) {
   blocks = (n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
 }
 
-template <bool kSite0FromY, int kX, bool kMix>
-void launch_single(const SweepArgs& a, int slot, cudaStream_t s) {
+template <bool kSite0FromY, int kX, int kEdge>
+void launch_single(const SweepArgs& a, cudaStream_t s) {
+  // occupancy cache slot of this instantiation: 0..3 and 5..12 (4 is the batch kernel's)
+  const int slot = kEdge * 4 + (kSite0FromY ? 0 : 2) + (kX == 4 ? 0 : 1) + (kEdge ? 1 : 0);
   const int S = strips_of(a.width);
   const int ups = units_per_strip(a.height);
-  const int resident = resident_warps(prior_sweep_kernel<kSite0FromY, kX, kMix>, slot);
+  const int resident = resident_warps(prior_sweep_kernel<kSite0FromY, kX, kEdge>, slot);
   int n_seg = resident / S;
   if (n_seg < 1) n_seg = 1;
   if (n_seg > ups) n_seg = ups;
   const int blocks = (S * n_seg + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  prior_sweep_kernel<kSite0FromY, kX, kMix><<<blocks, kThreads, kSmemBytes, s>>>(a, n_seg);
+  prior_sweep_kernel<kSite0FromY, kX, kEdge><<<blocks, kThreads, kSmemBytes, s>>>(a, n_seg);
+}
+
+template <int kEdge>
+void launch_edge(const SweepArgs& a, bool site0_from_y, bool x4, cudaStream_t s) {
+  if (site0_from_y) {
+    if (x4) launch_single<true, 4, kEdge>(a, s); else launch_single<true, 3, kEdge>(a, s);
+  } else {
+    if (x4) launch_single<false, 4, kEdge>(a, s); else launch_single<false, 3, kEdge>(a, s);
+  }
 }
 
 }  // namespace
@@ -994,15 +1030,19 @@ int prior_sweep_blocks(int height, int width) {
 }
 
 void prior_sweep_prewarm() {
-  resident_warps(prior_sweep_kernel<true, 4, false>, 0);
-  resident_warps(prior_sweep_kernel<true, 3, false>, 1);
-  resident_warps(prior_sweep_kernel<false, 4, false>, 2);
-  resident_warps(prior_sweep_kernel<false, 3, false>, 3);
+  resident_warps(prior_sweep_kernel<true, 4, kEdgeL1>, 0);
+  resident_warps(prior_sweep_kernel<true, 3, kEdgeL1>, 1);
+  resident_warps(prior_sweep_kernel<false, 4, kEdgeL1>, 2);
+  resident_warps(prior_sweep_kernel<false, 3, kEdgeL1>, 3);
   resident_warps(prior_sweep_batch_kernel, 4);
-  resident_warps(prior_sweep_kernel<true, 4, true>, 5);
-  resident_warps(prior_sweep_kernel<true, 3, true>, 6);
-  resident_warps(prior_sweep_kernel<false, 4, true>, 7);
-  resident_warps(prior_sweep_kernel<false, 3, true>, 8);
+  resident_warps(prior_sweep_kernel<true, 4, kEdgeL1Q>, 5);
+  resident_warps(prior_sweep_kernel<true, 3, kEdgeL1Q>, 6);
+  resident_warps(prior_sweep_kernel<false, 4, kEdgeL1Q>, 7);
+  resident_warps(prior_sweep_kernel<false, 3, kEdgeL1Q>, 8);
+  resident_warps(prior_sweep_kernel<true, 4, kEdgeMix>, 9);
+  resident_warps(prior_sweep_kernel<true, 3, kEdgeMix>, 10);
+  resident_warps(prior_sweep_kernel<false, 4, kEdgeMix>, 11);
+  resident_warps(prior_sweep_kernel<false, 3, kEdgeMix>, 12);
 }
 
 void launch_prior_sweep_batch(const BatchItem* items, int n_items, long long total_units,
@@ -1016,16 +1056,10 @@ void launch_prior_sweep(const SweepArgs& args, bool site0_from_y, cudaStream_t s
   SweepArgs a = args;
   prior_sweep_prepare(a);
   const bool x4 = later_vertical(a.order) == 4;
-  if (a.prior != EP_TV_PRIOR_L1) {
-    if (site0_from_y) {
-      if (x4) launch_single<true, 4, true>(a, 5, s); else launch_single<true, 3, true>(a, 6, s);
-    } else {
-      if (x4) launch_single<false, 4, true>(a, 7, s); else launch_single<false, 3, true>(a, 8, s);
-    }
-  } else if (site0_from_y) {
-    if (x4) launch_single<true, 4, false>(a, 0, s); else launch_single<true, 3, false>(a, 1, s);
-  } else {
-    if (x4) launch_single<false, 4, false>(a, 2, s); else launch_single<false, 3, false>(a, 3, s);
+  switch (edge_kind(a)) {
+    case kEdgeMix: launch_edge<kEdgeMix>(a, site0_from_y, x4, s); break;
+    case kEdgeL1Q: launch_edge<kEdgeL1Q>(a, site0_from_y, x4, s); break;
+    default: launch_edge<kEdgeL1>(a, site0_from_y, x4, s); break;
   }
 }
 

@@ -224,3 +224,71 @@ def test_mixture_priors_match_oracle(prior, theta, sweeps, h, w, periodic):
     assert_parity(mu, var, mu_r, var_r, p.y)
     assert o.n_capped > 0
     assert abs(capped - o.n_capped) <= max(4, 0.01 * o.n_capped), (capped, o.n_capped)
+
+
+@pytest.mark.parametrize("option", [1, 2, 3])
+def test_em_options_match_beta_trajectory(option):
+    """The three approximations of a_0 (Sec. IV): Option 1 (Eq. ax, E|x_i - x_j|
+    under Q(x)), Option 2 (Eq. au, E|u_n| under the matched Gaussian Q(u_n)) and
+    Option 3 (Eq. 3rd_alternative_a0, the tilted P_k(u_n)), each driving the EM
+    update every sweep from beta0 = 1 (the fast EP-EM of Sec. V), against the
+    oracle's beta trajectory and final posterior."""
+    p = syn.denoise_problem(64, 96, sigma=0.1, beta=1.0, seed=8)
+    torch = cuda()
+    yt = torch.as_tensor(p.y.astype(np.float32), device="cuda")
+    o = EPOracle("denoise", p.y, p.xi, 1.0, 64, 96)
+    with EPTV(yt, p.xi, 1.0, em_option=option) as ep:
+        for t in range(12):
+            ep.sweep(1)
+            beta, a = ep.em_beta()
+            o.sweep()
+            a_r = o.em_statistic(option)
+            beta_r = o.em_update(option)
+            assert abs(a / a_r - 1) < 2e-5, (t, a, a_r)
+            assert abs(beta / beta_r - 1) < 2e-5, (t, beta, beta_r)
+        mu, var = (x.cpu().numpy() for x in ep.posterior())
+        # the same through the device-side EM of ep_tv_sweep
+        with EPTV(yt, p.xi, 1.0, em_option=option) as ep2:
+            ep2.sweep(12, em_every=1)
+            beta2, _ = ep2.em_beta()
+            assert abs(beta2 / beta_r - 1) < 2e-5
+    mu_r, var_r = o.posterior()
+    assert_parity(mu, var, mu_r, var_r, p.y)
+
+
+def test_full_ep_em_matches_oracle():
+    """Algorithm 2 with the EP of Algorithm 1 run to convergence inside every EM
+    iteration (sweeps until the largest change of a posterior mean is below
+    1e-5 of the largest mean), from beta0 = 1: beta after each iteration and the
+    length of each inner run against the oracle."""
+    p = syn.denoise_problem(48, 64, sigma=0.1, beta=1.0, seed=12)
+    torch = cuda()
+    yt = torch.as_tensor(p.y.astype(np.float32), device="cuda")
+    with EPTV(yt, p.xi, 1.0) as ep:
+        betas, sweeps = ep.ep_em(5, max_sweeps=300, tol=1e-5)
+        mu, var = (x.cpu().numpy() for x in ep.posterior())
+    o = EPOracle("denoise", p.y, p.xi, 1.0, 48, 64)
+    betas_r, sweeps_r = o.ep_em(5, max_sweeps=300, tol=1e-5)
+    assert all(s < 300 for s in sweeps_r)
+    # the stop decision is taken in FP32 on the GPU: a run may end one sweep apart
+    assert all(abs(a - b) <= 1 for a, b in zip(sweeps, sweeps_r)), (sweeps, sweeps_r)
+    np.testing.assert_allclose(betas, betas_r, rtol=2e-4)
+    mu_r, var_r = o.posterior()
+    assert_parity(mu, var, mu_r, var_r, p.y, rtol_mean=3e-4, rtol_var=3e-3)
+
+
+@pytest.mark.parametrize("sigma", [0.05, 0.1, 0.2])
+def test_lambda_study_option3_nearest_mse_optimum(sigma):
+    """Sec. IV (Fig. 3): of the three approximations of a_0, Option 3
+    (Eq. 3rd_alternative_a0) gives the EM estimate of beta nearest (in log) the
+    MSE-optimal value and the lowest MSE of the three, here on seeded synthetic
+    64 x 64 denoising problems at three noise levels."""
+    from paper_2110_01585_gb300.lambda_study import study
+    p = syn.denoise_problem(64, 64, sigma=sigma, beta=1.0, seed=7)
+    grid = np.exp(np.linspace(np.log(1.0), np.log(400.0), 25))
+    beta_opt, mse_opt, _, opts = study(p, grid)
+    dist = {k: abs(np.log(opts[k][0] / beta_opt)) for k in opts}
+    assert dist[3] <= dist[1] and dist[3] <= dist[2], (beta_opt, opts)
+    assert opts[3][1] <= opts[1][1] and opts[3][1] <= opts[2][1], opts
+    # every EP-EM estimate is worse than the grid optimum
+    assert all(v[1] >= mse_opt * (1 - 1e-6) for v in opts.values())

@@ -148,7 +148,7 @@ def _exact_pair_moments(y, xi, lam, empty_tau):
     nodes, weights = np.polynomial.legendre.leggauss(600)
     v_lo, v_hi = y[0] + y[1] - 16 * sd, y[0] + y[1] + 16 * sd
     u_span = abs(y[0] - y[1]) + 16 * sd
-    acc = np.zeros(6)
+    acc = np.zeros(7)
     for u_lo, u_hi in ((-u_span, 0.0), (0.0, u_span)):
         u = 0.5 * (u_hi - u_lo) * nodes + 0.5 * (u_hi + u_lo)
         wu = 0.5 * (u_hi - u_lo) * weights
@@ -161,10 +161,10 @@ def _exact_pair_moments(y, xi, lam, empty_tau):
                 - lam * np.abs(x1 - x2) - empty_tau * (x1 ** 2 + x2 ** 2) / 2)
         p = np.exp(logp) * W
         acc += [p.sum(), (p * x1).sum(), (p * x2).sum(), (p * x1 ** 2).sum(),
-                (p * x2 ** 2).sum(), (p * np.abs(x1 - x2)).sum()]
+                (p * x2 ** 2).sum(), (p * np.abs(x1 - x2)).sum(), (p * (x1 - x2) ** 2).sum()]
     z = acc[0]
     m1, m2 = acc[1] / z, acc[2] / z
-    return m1, m2, acc[3] / z - m1 ** 2, acc[4] / z - m2 ** 2, acc[5] / z
+    return m1, m2, acc[3] / z - m1 ** 2, acc[4] / z - m2 ** 2, acc[5] / z, acc[6] / z
 
 
 @pytest.mark.parametrize("y,xi,lam", [((0.3, 0.7), 0.01, 20.0), ((0.9, -0.2), 0.04, 3.0),
@@ -176,7 +176,7 @@ def test_one_by_two_image_is_exact(y, xi, lam):
     o.run(80)
     mu, var = o.posterior()
     # sites 2, 3, 4 have no edge here and keep precision 1/var_cap each
-    m1, m2, v1, v2, eabs = _exact_pair_moments(y, xi, lam, 3.0 / o.var_cap)
+    m1, m2, v1, v2, eabs, _ = _exact_pair_moments(y, xi, lam, 3.0 / o.var_cap)
     np.testing.assert_allclose(mu.ravel(), [m1, m2], rtol=1e-8)
     np.testing.assert_allclose(var.ravel(), [v1, v2], rtol=1e-8)
     # EM (Algorithm 2, Option 3): a_u = E|x1 - x2| under the exact posterior
@@ -373,6 +373,51 @@ def test_two_by_two_loop_against_exact_posterior(y, xi, lam):
     assert np.max(np.abs(mu - mean) / np.sqrt(v)) <= 0.03
     assert np.max(np.abs(var / v - 1.0)) <= 0.12
     assert abs(o.abar / eabs - 1.0) <= 0.08
+
+
+def test_folded_normal_mean_matches_quadrature():
+    from oracle.tilted import folded_normal_mean
+    mp.mp.dps = 30
+    for m in (-4.0, -0.3, 0.0, 0.01, 2.5):
+        for s2 in (1e-6, 0.04, 9.0):
+            sd = mp.sqrt(s2)
+            q = mp.quad(lambda u: abs(u) * mp.npdf(u, m, sd), [-mp.inf, min(0, m), max(0, m), mp.inf])
+            assert abs(folded_normal_mean(m, s2) - float(q)) <= 1e-12 * max(float(q), 1e-300)
+
+
+@pytest.mark.parametrize("y,xi,lam", [((0.3, 0.7), 0.01, 20.0), ((0.9, -0.2), 0.04, 3.0)])
+def test_em_option2_on_one_by_two_image(y, xi, lam):
+    """Eq. au (Option 2): on a 1 x 2 image the tilted law of u = x1 - x2 is the
+    exact posterior of u, so Q(u) carries its exact mean and variance and a_u is
+    the folded-normal mean of N(E u, Var u) from the exact posterior."""
+    from oracle.tilted import folded_normal_mean
+    o = EPOracle("denoise", np.array([y]), xi, lam, 1, 2, periodic=False)
+    o.run(80)
+    m1, m2, _, _, _, eu2 = _exact_pair_moments(y, xi, lam, 3.0 / o.var_cap)
+    mu_u = m1 - m2
+    assert abs(o.em_statistic(2) / folded_normal_mean(mu_u, eu2 - mu_u ** 2) - 1.0) <= 1e-8
+
+
+def test_em_options_agree_at_lambda_zero():
+    """With lam = 0 every prior site stays at the cap, Q(x) has mean y and
+    variance 1 / (1/xi + 4/var_cap), and the tilted laws of the edges are the
+    Gaussians of their cavities: Options 1, 2 and 3 (Eq. ax, Eq. au,
+    Eq. 3rd_alternative_a0) all give sum over edges of E|N(y_i - y_j, c_i + c_j)|,
+    with c the cavity variance 1 / (1/xi + 3/var_cap)."""
+    from oracle.tilted import folded_normal_mean
+    h, w = 6, 8
+    y = np.random.default_rng(3).random((h, w))
+    xi = 0.02
+    o = EPOracle("denoise", y, xi, 0.0, h, w)
+    o.run(3)
+    yf = y.reshape(-1)
+    c = 1.0 / (1.0 / xi + 3.0 / o.var_cap)
+    post = 1.0 / (1.0 / xi + 4.0 / o.var_cap)
+    ref_tilted = sum(float(np.sum(folded_normal_mean(yf[f] - yf[g], 2 * c))) for f, g in o.edge_lists)
+    ref_q = sum(float(np.sum(folded_normal_mean(yf[f] - yf[g], 2 * post))) for f, g in o.edge_lists)
+    assert abs(o.em_statistic(3) / ref_tilted - 1) <= 1e-10
+    assert abs(o.em_statistic(2) / ref_tilted - 1) <= 1e-10
+    assert abs(o.em_statistic(1) / ref_q - 1) <= 1e-10
 
 
 # ---------------------------------------------------------------- lam -> 0
