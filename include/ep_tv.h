@@ -139,6 +139,41 @@ ep_tv_status ep_tv_default_params(ep_tv_params* p);
 ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
                         void* cuda_stream, ep_tv_ctx** out);
 
+/* ---- Row blocks of a sharded image (not in the paper) -----------------------
+   One image split by rows over several processes or GPUs, denoising only.  A
+   sweep (Algorithm 1) moves information across at most one row per vertical
+   update (V3, V4), i.e. two rows per sweep, so a block that also holds the two
+   rows above and below its own rows (its halo) computes the sweep of its own
+   rows exactly as the whole image would, bit for bit.  After every sweep each
+   block sends its two first and two last own rows of the prior sites to its
+   neighbours' halos (ep_tv_block_halo_out / _in; the caller moves the buffers,
+   e.g. with NCCL), and the EM statistic is the sum over blocks of each block's
+   own edges (ep_tv_em_beta on a block returns it in abar_out and leaves beta
+   alone; the caller sets beta = N / sum with ep_tv_set_beta). */
+typedef struct {
+  int32_t global_height;  /* rows of the whole image */
+  int32_t row0;           /* first own row, even */
+  int32_t rows;           /* own rows, >= 2 and < global_height (even on the torus) */
+} ep_tv_block;
+
+/* Creates the context of one row block.  op: EP_TV_OP_IDENTITY with width W and
+   height = rows + halo above + halo below, the halos being 2 rows where the whole
+   image has rows there (always on the torus, p->periodic = 1, which makes the
+   columns wrap and the block's halo rows the torus neighbours of its own rows;
+   on the free boundary none above row 0 or below the last row).  y: DEVICE, the
+   observation of those rows, top halo first.  The block's own rows start at row
+   2 of the context (0 if it has no top halo).  Other arguments as ep_tv_init;
+   ep_tv_sweep refuses em_every > 0 on a block. */
+ep_tv_status ep_tv_init_block(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
+                              const ep_tv_block* blk, void* cuda_stream, ep_tv_ctx** out);
+/* Copies the block's first (side 0) or last (side 1) two own rows of the eight
+   prior-site planes (tau_1..4, nu_1..4, each 2 x W, in that order) into buf
+   (DEVICE, 16 W floats).  Asynchronous on the context's stream. */
+ep_tv_status ep_tv_block_halo_out(ep_tv_ctx* ctx, int32_t side, float* buf);
+/* Writes buf (as ep_tv_block_halo_out fills it, from the neighbour) into the
+   block's halo rows above (side 0) or below (side 1).  Asynchronous. */
+ep_tv_status ep_tv_block_halo_in(ep_tv_ctx* ctx, int32_t side, const float* buf);
+
 /* Replaces the library-drawn probe vectors of the RBMC estimator (CONV_PERIODIC)
    by caller-drawn standard normals.  eps1: DEVICE, S x M; eps2: DEVICE, S x N;
    both copied.  The probes stay fixed across sweeps (common random numbers). */

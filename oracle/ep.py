@@ -96,6 +96,10 @@ class EPOracle:
         (Eq. BG_TV, theta = (omega, s^2)).  The EM update (Sec. IV) is defined
         for "l1" only.
     theta : the mixture parameters for "mog2" / "bg".
+    periodic_rows : whether the rows wrap (default: periodic); a band of rows cut
+        from a torus has wrapping columns and non-wrapping rows.
+    count_rows : (lo, hi) or None; the EM statistics take only the edges whose
+        first pixel's row is in [lo, hi) (one band's share of a whole image).
     pool : optional executor (e.g. a spawn-context process pool) on which
         "rbmc_cg" runs the 1 + S independent solves of one site-0 update; each
         solve is the same computation as without it, so results do not change.
@@ -106,7 +110,8 @@ class EPOracle:
                  A: Optional[np.ndarray] = None, damping: float = 0.5,
                  var_cap: float = 1e8, periodic: bool = True,
                  order: str = "prior_first", site0: str = "exact",
-                 probes=None, pool=None, prior: str = "l1", theta=None):
+                 probes=None, pool=None, prior: str = "l1", theta=None,
+                 periodic_rows=None, count_rows=None):
         if kind not in ("denoise", "deconv", "cs"):
             raise ValueError(kind)
         if prior not in ("l1", "mog2", "bg"):
@@ -133,7 +138,10 @@ class EPOracle:
         self.site0 = site0
         self.probes = probes
         self.pool = pool
-        self.edge_lists = [edges(self.height, self.width, k, self.periodic) for k in (1, 2, 3, 4)]
+        self.periodic_rows = self.periodic if periodic_rows is None else bool(periodic_rows)
+        self.edge_lists = [edges(self.height, self.width, k, self.periodic, self.periodic_rows)
+                           for k in (1, 2, 3, 4)]
+        self.count_rows = count_rows
         self.abar = 0.0          # sum of E|u| over the edges of the last sweep
         self.abar_q = 0.0        # the same under the matched Gaussians Q(u_n) (Option 2)
         self._abar_q_sweep = 0.0
@@ -213,9 +221,17 @@ class EPOracle:
         tau_j, nu_j = self._new_site(Ej, Vj, cj, mj)
         self._damp(k, first, tau_i, nu_i)
         self._damp(k, second, tau_j, nu_j)
+        counted = self._counted(first)
         if self.prior == "l1":
-            self._abar_q_sweep += float(np.sum(folded_normal_mean(m_bar, S_bar)))
-        return float(np.sum(eabs))
+            self._abar_q_sweep += float(np.sum(folded_normal_mean(m_bar, S_bar)[counted]))
+        return float(np.sum(eabs[counted]))
+
+    def _counted(self, first):
+        """Edges whose first pixel's row is in count_rows (all edges by default)."""
+        if self.count_rows is None:
+            return slice(None)
+        rows = first // self.width
+        return (rows >= self.count_rows[0]) & (rows < self.count_rows[1])
 
     def tilted_p0(self, c: np.ndarray, m: np.ndarray):
         """Mean and marginal variances of P_0 (Eq. tilted_P_1) for cavity (c, m)."""
@@ -345,8 +361,8 @@ class EPOracle:
             mu, var = (a.reshape(-1) for a in self.posterior())
             total = 0.0
             for first, second in self.edge_lists:
-                total += float(np.sum(folded_normal_mean(mu[first] - mu[second],
-                                                         var[first] + var[second])))
+                f = folded_normal_mean(mu[first] - mu[second], var[first] + var[second])
+                total += float(np.sum(f[self._counted(first)]))
             return total
         raise ValueError(option)
 

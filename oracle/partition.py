@@ -14,7 +14,8 @@ The reading used here:
 
 With ``periodic=False`` the wrap-around edges of V2 and V4 are dropped (and
 odd sizes are allowed); pixels with no edge in V_k keep site k at its initial
-value.  Pixel p = r * W + c (row-major).  The edge difference is
+value.  ``periodic_rows`` (default: ``periodic``) decides the wrap of V4 alone,
+so that a band of rows cut from a torus keeps its wrapping columns.  Pixel p = r * W + c (row-major).  The edge difference is
 u = x_first - x_second, i.e. left minus right and top minus bottom.
 """
 from __future__ import annotations
@@ -22,9 +23,10 @@ from __future__ import annotations
 import numpy as np
 
 
-def edges(height: int, width: int, k: int, periodic: bool = True):
+def edges(height: int, width: int, k: int, periodic: bool = True, periodic_rows=None):
     """Return (first, second) flat pixel indices of the edges of V_k, k in 1..4."""
-    if periodic and (height % 2 or width % 2):
+    periodic_rows = periodic if periodic_rows is None else periodic_rows
+    if (periodic and width % 2) or (periodic_rows and height % 2):
         raise ValueError("periodic boundary needs even height and width")
     first, second = [], []
     for r in range(height):
@@ -48,7 +50,7 @@ def edges(height: int, width: int, k: int, periodic: bool = True):
             elif k == 4 and r % 2 == 1:
                 rn = r + 1
                 if rn == height:
-                    if not periodic:
+                    if not periodic_rows:
                         continue
                     rn = 0
                 if rn == r:

@@ -33,6 +33,10 @@ class Operator(ctypes.Structure):
                 ("kh", ctypes.c_int32), ("kw", ctypes.c_int32), ("dense", ctypes.c_void_p)]
 
 
+class Block(ctypes.Structure):
+    _fields_ = [("global_height", ctypes.c_int32), ("row0", ctypes.c_int32), ("rows", ctypes.c_int32)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("xi", ctypes.c_double), ("beta", ctypes.c_double), ("damping", ctypes.c_double),
                 ("var_cap", ctypes.c_double), ("periodic", ctypes.c_int32),
@@ -48,6 +52,10 @@ SIGNATURES = {
     "ep_tv_init": (c_int32, [ctypes.POINTER(Operator), c_void_p, ctypes.POINTER(Params), c_void_p,
                              ctypes.POINTER(c_void_p)]),
     "ep_tv_set_probes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "ep_tv_init_block": (c_int32, [ctypes.POINTER(Operator), c_void_p, ctypes.POINTER(Params),
+                                   ctypes.POINTER(Block), c_void_p, ctypes.POINTER(c_void_p)]),
+    "ep_tv_block_halo_out": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "ep_tv_block_halo_in": (c_int32, [c_void_p, c_int32, c_void_p]),
     "ep_tv_sweep": (c_int32, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_int8), c_int32]),
     "ep_tv_em_beta": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "ep_tv_set_beta": (c_int32, [c_void_p, c_double]),

@@ -50,6 +50,8 @@ struct ep_tv_ctx {
   int graph_em[2] = {-1, -1};
   int graph_len[2] = {0, 0};
   long long graph_sweeps = 0;  // sweeps run from graph replays (this context or its batch)
+  // Row block of a sharded image (ep_tv_init_block); rows = 0 for a whole image.
+  int blk_rows = 0, blk_top = 0, blk_bottom = 0;  // own rows, halo rows above and below
   // EP-EM convergence checks (allocated on the first ep_tv_ep_em call)
   float* mu_prev = nullptr;     // [N] posterior mean after the previous sweep
   unsigned* d_change = nullptr; // max |change|, max |mean| (float bits)
@@ -204,6 +206,13 @@ void launch_em(ep_tv_ctx* c, const float* tp, const float* np, cudaStream_t s) {
   launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 1, s);
 }
 
+// Option 1 for a row block: the edges whose first pixel is one of its own rows.
+void launch_ax_rows(ep_tv_ctx* c) {
+  launch_ax_block(c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur], c->height, c->width,
+                  c->p.periodic, c->blk_top, c->blk_top + c->blk_rows, c->abar_partial, c->n_partial,
+                  c->stream);
+}
+
 SweepArgs sweep_args(ep_tv_ctx* c, int order) {
   SweepArgs a;
   a.tau0 = c->tau0;
@@ -218,6 +227,9 @@ SweepArgs sweep_args(ep_tv_ctx* c, int order) {
   a.width = c->width;
   a.n = c->n;
   a.periodic = c->p.periodic;
+  a.periodic_rows = c->blk_rows ? 0 : c->p.periodic;
+  a.count_lo = c->blk_rows ? c->blk_top : 0;
+  a.count_hi = c->blk_rows ? c->blk_top + c->blk_rows : c->height;
   a.damping = (float)c->p.damping;
   a.min_tau = (float)(1.0 / c->p.var_cap);
   a.beta = c->dscal + DS_BETA;
@@ -362,6 +374,61 @@ ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_pa
   return EP_TV_OK;
 }
 
+ep_tv_status ep_tv_init_block(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
+                              const ep_tv_block* blk, void* cuda_stream, ep_tv_ctx** out) {
+  if (!out) return EP_TV_ERR_ARG;
+  *out = nullptr;
+  if (!op || !p || !blk || op->op != EP_TV_OP_IDENTITY) return EP_TV_ERR_ARG;
+  const int H = blk->global_height;
+  if (H < 4 || blk->row0 < 0 || (blk->row0 % 2) || blk->rows < 2 || blk->row0 + blk->rows > H ||
+      blk->rows >= H)
+    return EP_TV_ERR_ARG;
+  if (p->periodic && (H % 2 || blk->rows % 2)) return EP_TV_ERR_ARG;
+  const int top = (p->periodic || blk->row0 > 0) ? 2 : 0;
+  const int bottom = (p->periodic || blk->row0 + blk->rows < H) ? 2 : 0;
+  if (op->height != blk->rows + top + bottom) return EP_TV_ERR_ARG;
+  // the block itself is an image whose rows do not wrap; its halo rows carry the
+  // neighbours' state, so the parity of the matchings V3 and V4 is kept (row0 even)
+  ep_tv_params q = *p;
+  ep_tv_operator o = *op;
+  const int periodic_cols = p->periodic;
+  q.periodic = 0;  // the argument checks of a free-boundary image (odd widths allowed)
+  if (periodic_cols && (op->width % 2)) return EP_TV_ERR_ARG;
+  ep_tv_status st = ep_tv_init(&o, y, &q, cuda_stream, out);
+  if (st != EP_TV_OK) return st;
+  ep_tv_ctx* c = *out;
+  c->p.periodic = periodic_cols;
+  c->blk_rows = blk->rows;
+  c->blk_top = top;
+  c->blk_bottom = bottom;
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_block_halo_out(ep_tv_ctx* c, int32_t side, float* buf) {
+  if (!c || !c->blk_rows || !buf || (side != 0 && side != 1)) return EP_TV_ERR_ARG;
+  const int r = side == 0 ? c->blk_top : c->blk_top + c->blk_rows - 2;
+  const size_t row = (size_t)c->width, plane = (size_t)c->n;
+  for (int k = 0; k < 8; ++k) {
+    const float* src = (k < 4 ? c->ptau[c->cur] + k * plane : c->pnu[c->cur] + (k - 4) * plane) + r * row;
+    CK(cudaMemcpyAsync(buf + k * 2 * row, src, sizeof(float) * 2 * row, cudaMemcpyDeviceToDevice,
+                       c->stream));
+  }
+  return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_block_halo_in(ep_tv_ctx* c, int32_t side, const float* buf) {
+  if (!c || !c->blk_rows || !buf || (side != 0 && side != 1)) return EP_TV_ERR_ARG;
+  if ((side == 0 && !c->blk_top) || (side == 1 && !c->blk_bottom)) return EP_TV_ERR_ARG;
+  const int r = side == 0 ? 0 : c->blk_top + c->blk_rows;
+  const size_t row = (size_t)c->width, plane = (size_t)c->n;
+  for (int k = 0; k < 8; ++k) {
+    float* dst = (k < 4 ? c->ptau[c->cur] + k * plane : c->pnu[c->cur] + (k - 4) * plane) + r * row;
+    CK(cudaMemcpyAsync(dst, buf + k * 2 * row, sizeof(float) * 2 * row, cudaMemcpyDeviceToDevice,
+                       c->stream));
+  }
+  return EP_TV_OK;
+}
+
 ep_tv_status ep_tv_set_probes(ep_tv_ctx* c, const float* eps1, const float* eps2,
                               int32_t n_samples) {
   if (!c || !eps1 || !eps2 || n_samples < 1) return EP_TV_ERR_ARG;
@@ -372,6 +439,7 @@ ep_tv_status ep_tv_set_probes(ep_tv_ctx* c, const float* eps1, const float* eps2
 ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
                          int32_t em_every) {
   if (!c || n_sweeps < 0 || em_every < 0) return EP_TV_ERR_ARG;
+  if (em_every > 0 && c->blk_rows) return EP_TV_ERR_ARG;  // blocks: EM needs all blocks' a_u
   if (em_every > 0 && c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_ARG;  // EM: l1-TV only
   if (c->failed) return EP_TV_ERR_STATE;
   if (k_order) {
@@ -434,7 +502,14 @@ ep_tv_status ep_tv_em_beta(ep_tv_ctx* c, double* beta_out, double* abar_out) {
   if (c->p.prior != EP_TV_PRIOR_L1) return EP_TV_ERR_UNSUPPORTED;  // Sec. IV: l1-TV only
   if (c->failed) return EP_TV_ERR_STATE;
   if (c->sweeps == 0) return EP_TV_ERR_ARG;
-  launch_em(c, c->ptau[c->cur], c->pnu[c->cur], c->stream);
+  if (c->blk_rows) {
+    // a row block reports the a_u of its own edges; beta is set by the caller
+    if (c->p.em_option == 1)
+      launch_ax_rows(c);
+    launch_abar_reduce(c->abar_partial, c->n_partial, c->dscal, (double)c->n, 0, c->stream);
+  } else {
+    launch_em(c, c->ptau[c->cur], c->pnu[c->cur], c->stream);
+  }
   if (cudaGetLastError() != cudaSuccess) return EP_TV_ERR_CUDA;
   if (beta_out || abar_out) {
     double ds[DS_COUNT];

@@ -54,11 +54,16 @@ __device__ __forceinline__ double folded_mean_edge(float mi, float vi, float mj,
   return s * 0.79788456080286536 * exp(-0.5 * m * m / v) + m * erf(m / (1.4142135623730951 * s));
 }
 
+// Rows [row_lo, row_hi) take their right and lower edges; periodic_rows: the
+// last row's lower edge wraps to row 0 (a row block of a sharded image: no wrap,
+// its lower halo rows are in the block).
 __global__ void ax_kernel(const float* tau0, const float* nu0, const float* tp, const float* np,
-                          int height, int width, int periodic, double* partial) {
+                          int height, int width, int periodic, int periodic_rows, int row_lo,
+                          int row_hi, double* partial) {
   const long long n = (long long)height * width;
+  const long long p_lo = (long long)row_lo * width, p_hi = (long long)row_hi * width;
   double acc = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+  for (long long p = p_lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < p_hi;
        p += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(p / width), c = (int)(p - (long long)r * width);
     float m, v, mq, vq;
@@ -68,7 +73,7 @@ __global__ void ax_kernel(const float* tau0, const float* nu0, const float* tp, 
       moments_at(tau0, nu0, tp, np, n, q, mq, vq);
       acc += folded_mean_edge(m, v, mq, vq);
     }
-    if (r + 1 < height || (periodic && height > 1)) {
+    if (r + 1 < height || (periodic_rows && height > 1)) {
       const long long q = (long long)(r + 1 < height ? r + 1 : 0) * width + c;
       moments_at(tau0, nu0, tp, np, n, q, mq, vq);
       acc += folded_mean_edge(m, v, mq, vq);
@@ -186,7 +191,15 @@ void launch_posterior(const float* tau0, const float* nu0, const float* tp, cons
 
 void launch_ax(const float* tau0, const float* nu0, const float* tp, const float* np, int height,
                int width, int periodic, double* partial, int n_partial, cudaStream_t s) {
-  ax_kernel<<<n_partial, kEwThreads, 0, s>>>(tau0, nu0, tp, np, height, width, periodic, partial);
+  ax_kernel<<<n_partial, kEwThreads, 0, s>>>(tau0, nu0, tp, np, height, width, periodic, periodic,
+                                             0, height, partial);
+}
+
+void launch_ax_block(const float* tau0, const float* nu0, const float* tp, const float* np,
+                     int height, int width, int periodic, int row_lo, int row_hi, double* partial,
+                     int n_partial, cudaStream_t s) {
+  ax_kernel<<<n_partial, kEwThreads, 0, s>>>(tau0, nu0, tp, np, height, width, periodic, 0, row_lo,
+                                             row_hi, partial);
 }
 
 void launch_mean_change(const float* tau0, const float* nu0, const float* tp, const float* np,

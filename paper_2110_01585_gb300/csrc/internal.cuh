@@ -100,7 +100,10 @@ struct SweepArgs {
   float inv_xi;               // 1 / xi as float (identity operator)
   int height, width;
   long long n;
-  int periodic;
+  int periodic;               // columns wrap (and rows, unless periodic_rows says otherwise)
+  int periodic_rows;          // rows wrap (a row block of a sharded image: 0)
+  int count_lo, count_hi;     // E|u| and the counters take the edges whose first pixel's
+                              // row is in [count_lo, count_hi) (whole image: [0, height))
   float damping;
   float min_tau;              // 1 / var_cap
   const double* beta;         // device scalar
@@ -154,6 +157,10 @@ void launch_warm_start(float* tau0, float* nu0, float* tp, float* np, const floa
 // Option 1 of the EM statistic (a_x) into n_partial FP64 block partials.
 void launch_ax(const float* tau0, const float* nu0, const float* tp, const float* np, int height,
                int width, int periodic, double* partial, int n_partial, cudaStream_t s);
+// The same over the edges whose first pixel's row is in [row_lo, row_hi), rows not wrapping.
+void launch_ax_block(const float* tau0, const float* nu0, const float* tp, const float* np,
+                     int height, int width, int periodic, int row_lo, int row_hi, double* partial,
+                     int n_partial, cudaStream_t s);
 // Posterior mean into prev, max |change| and max |mean| as float bits into out[0..1].
 void launch_mean_change(const float* tau0, const float* nu0, const float* tp, const float* np,
                         long long n, float* prev, unsigned* out, cudaStream_t s);

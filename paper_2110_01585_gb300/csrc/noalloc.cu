@@ -122,6 +122,9 @@ extern "C" ep_tv_status ep_tv_prior_sweep_noalloc(int32_t height, int32_t width,
   a.width = width;
   a.n = (long long)height * width;
   a.periodic = p->periodic;
+  a.periodic_rows = p->periodic;
+  a.count_lo = 0;
+  a.count_hi = height;
   a.damping = (float)p->damping;
   a.min_tau = (float)(1.0 / p->var_cap);
   a.beta = beta;

@@ -463,7 +463,7 @@ struct __align__(16) Io {
   float* nout;
   int n;             // plane stride (pixels; images are below 2^31 pixels)
   int height, width;
-  bool periodic, vec2;
+  bool periodic, vec2;  // periodic: the rows wrap (columns: SweepArgs::periodic)
   float inv_xi;
 };
 
@@ -480,7 +480,7 @@ __device__ __forceinline__ Io make_io(const SweepArgs& a, bool site0_from_y) {
   io.n = (int)a.n;
   io.height = a.height;
   io.width = a.width;
-  io.periodic = a.periodic != 0;
+  io.periodic = a.periodic_rows != 0;
   io.vec2 = a.vec2 != 0;
   io.inv_xi = a.inv_xi;
   return io;
@@ -783,10 +783,12 @@ __device__ __noinline__ void run_strip(const SweepArgs& a, int strip, int b_lo, 
     read_row<kSite0FromY>(io, L, stage, b & 1, 0, ok0, r0);
     read_row<kSite0FromY>(io, L, stage, b & 1, 1, ok1, r1);
     // an edge is counted by the step that computes it for its first pixel's row
-    // in [0, H) (rows outside are torus copies or do not exist)
-    const bool cc = !warm && row0 - 1 >= 0 && row0 - 1 < H;
-    const bool c0 = !warm && row0 >= 0 && row0 < H;
-    const bool c1 = !warm && row0 + 1 >= 0 && row0 + 1 < H;
+    // in [count_lo, count_hi) (rows outside are torus copies, do not exist, or
+    // belong to another block of a sharded image)
+    const int clo = a.count_lo, chi = a.count_hi;
+    const bool cc = !warm && row0 - 1 >= clo && row0 - 1 < chi;
+    const bool c0 = !warm && row0 >= clo && row0 < chi;
+    const bool c1 = !warm && row0 + 1 >= clo && row0 + 1 < chi;
     Row carry;
     if (kX == 4 && order == 0x4321) {
       // the default order V1, V2, V3, V4 as straight-line code
