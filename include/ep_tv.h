@@ -139,6 +139,18 @@ ep_tv_status ep_tv_default_params(ep_tv_params* p);
 ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
                         void* cuda_stream, ep_tv_ctx** out);
 
+/* Like ep_tv_init, with a diagonal noise covariance: y_m ~ N(h_m x, xi_m), one
+   variance per measurement, which the likelihood site takes in place of xi I
+   (Sec. III-C, last sentence of the discussion of Eq. tilted_P_1).  xi: DEVICE,
+   op->m floats, each finite and > 0 (EP_TV_ERR_ARG otherwise), copied; p->xi is
+   ignored.  Denoising: site 0 is (1/xi_p, y_p/xi_p), still exact.  Dense
+   operator: K = diag(xi) + A C A^T in the Woodbury site, and the initial site 0
+   of Algorithm 1 takes the mean of xi as its variance.  The periodic convolution
+   is not supported with a noise plane (EP_TV_ERR_UNSUPPORTED).  Synchronises
+   once (the variances are checked on the host). */
+ep_tv_status ep_tv_init_noise(const ep_tv_operator* op, const float* y, const float* xi,
+                              const ep_tv_params* p, void* cuda_stream, ep_tv_ctx** out);
+
 /* ---- Row blocks of a sharded image (not in the paper) -----------------------
    One image split by rows over several processes or GPUs, denoising only.  A
    sweep (Algorithm 1) moves information across at most one row per vertical

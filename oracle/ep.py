@@ -76,7 +76,12 @@ class EPOracle:
     ----------
     kind : "denoise", "deconv" or "cs"
     y : observation, (H, W) for denoise/deconv, (M,) for cs
-    xi : noise variance (Eq. likelihood)
+    xi : noise variance (Eq. likelihood): a scalar (i.i.d. noise), or one variance
+        per measurement (length M) for a diagonal noise covariance, which the
+        likelihood site takes in place of xi I (Sec. III-C, last sentence of the
+        discussion of Eq. tilted_P_1).  The initial site 0 (Algorithm 1) then has
+        variance xi_p per pixel when M = N, and the mean of xi for compressive
+        sensing.
     lam : TV parameter lambda (Eq. L1_TV)
     height, width : image size
     kernel : blur kernel for "deconv"
@@ -127,7 +132,9 @@ class EPOracle:
         self.height, self.width = int(height), int(width)
         self.n = self.height * self.width
         self.y = np.asarray(y, dtype=np.float64).reshape(-1)
-        self.xi = float(xi)
+        xi_arr = np.asarray(xi, dtype=np.float64).reshape(-1)
+        self.xi_vec = xi_arr if xi_arr.size > 1 else None  # per measurement, or None
+        self.xi = float(xi_arr.mean())
         self.lam = float(lam)
         self.kernel = None if kernel is None else np.asarray(kernel, np.float64)
         self.A = None if A is None else np.asarray(A, np.float64)
@@ -159,8 +166,9 @@ class EPOracle:
             mu0 = self.A.T @ self.y
         else:
             mu0 = self.y.copy()
-        self.tau[0] = 1.0 / self.xi
-        self.nu[0] = mu0 / self.xi
+        xi0 = self.xi if (self.xi_vec is None or self.kind == "cs") else self.xi_vec
+        self.tau[0] = 1.0 / xi0
+        self.nu[0] = mu0 / xi0
         self.tau[1:] = 1.0 / self.var_cap
         self.nu[1:] = 0.0
 
@@ -235,16 +243,19 @@ class EPOracle:
 
     def tilted_p0(self, c: np.ndarray, m: np.ndarray):
         """Mean and marginal variances of P_0 (Eq. tilted_P_1) for cavity (c, m)."""
+        xi = self.xi if self.xi_vec is None else self.xi_vec  # per measurement
         if self.kind == "denoise":
-            var = 1.0 / (1.0 / self.xi + 1.0 / c)
-            return var * (self.y / self.xi + m / c), var
+            var = 1.0 / (1.0 / xi + 1.0 / c)
+            return var * (self.y / xi + m / c), var
         if self.site0 == "rbmc_cg":
+            if self.xi_vec is not None:
+                raise ValueError("the FFT-based solves assume i.i.d. noise")
             return self._rbmc_cg(c, m)
-        H, Hty = self._operator()
+        H, _ = self._operator()
         if self.site0 == "woodbury":
             return self._woodbury(H, c, m)
-        Q = H.T @ H / self.xi + np.diag(1.0 / c)
-        b = Hty / self.xi + m / c
+        Q = H.T @ (H / np.reshape(xi, (-1, 1))) + np.diag(1.0 / c)
+        b = H.T @ (self.y / xi) + m / c
         cho = scipy.linalg.cho_factor(Q, lower=True)
         E = scipy.linalg.cho_solve(cho, b)
         if self.site0 == "exact":
@@ -270,8 +281,8 @@ class EPOracle:
         """Rao-Blackwellised Monte Carlo estimate of diag(Q^{-1}).
 
         Samples z_s ~ N(0, Q^{-1}) are drawn by perturbation: z_s solves
-        Q z_s = H^T eps1_s / sqrt(xi) + eps2_s / sqrt(c), whose right-hand side has
-        covariance H^T H / xi + diag(1/c) = Q.  For each pixel, x_i given the
+        Q z_s = H^T (eps1_s / sqrt(xi)) + eps2_s / sqrt(c), whose right-hand side has
+        covariance H^T diag(1/xi) H + diag(1/c) = Q.  For each pixel, x_i given the
         other pixels is Gaussian with variance 1/Q_ii and mean
         -(1/Q_ii) sum_{j != i} Q_ij z_j, so
         Var_i = 1/Q_ii + (1/S) sum_s ((sum_{j != i} Q_ij z_{s,j}) / Q_ii)^2.
@@ -281,7 +292,8 @@ class EPOracle:
         qdiag = np.diag(Q).copy()
         acc = np.zeros(self.n)
         for s in range(S):
-            w = H.T @ eps1[s] / math.sqrt(self.xi) + eps2[s] / np.sqrt(c)
+            xi = self.xi if self.xi_vec is None else self.xi_vec
+            w = H.T @ (eps1[s] / np.sqrt(xi)) + eps2[s] / np.sqrt(c)
             z = scipy.linalg.cho_solve(cho, w)
             off = Q @ z - qdiag * z
             acc += (off / qdiag) ** 2
@@ -317,7 +329,8 @@ class EPOracle:
 
     def _woodbury(self, H, c, m):
         """Cov_P0 = C - C H^T (xi I + H C H^T)^{-1} H C with C = diag(c)."""
-        K = self.xi * np.eye(H.shape[0]) + (H * c[None, :]) @ H.T
+        xi = self.xi if self.xi_vec is None else self.xi_vec
+        K = np.diag(np.broadcast_to(xi, (H.shape[0],)).astype(np.float64)) + (H * c[None, :]) @ H.T
         cho = scipy.linalg.cho_factor(K, lower=True)
         KinvH = scipy.linalg.cho_solve(cho, H)
         var = c - c * c * np.einsum("mi,mi->i", H, KinvH)

@@ -59,12 +59,14 @@ class EPTV:
     y: CUDA float32 tensor, (H, W) for identity/convolution, (M,) for dense.
     kernel: host array (kh, kw) for the periodic convolution.
     dense: CUDA float32 tensor (M, N) for compressive sensing; kept alive here.
+    xi_plane: CUDA float32 tensor of M noise variances (a diagonal noise
+        covariance, ep_tv_init_noise); xi is then ignored.
     stream: torch.cuda.Stream (default: the current stream).
     Remaining keyword arguments set fields of ``ep_tv_params``.
     """
 
     def __init__(self, y, xi: float, beta: float, op: int = OP_IDENTITY, height: int = None,
-                 width: int = None, kernel=None, dense=None, stream=None, **params):
+                 width: int = None, kernel=None, dense=None, stream=None, xi_plane=None, **params):
         torch = _torch()
         self._lib = _lib.load()
         if not (isinstance(y, torch.Tensor) and y.is_cuda and y.dtype == torch.float32):
@@ -83,10 +85,18 @@ class EPTV:
         self.params = default_params(xi=float(xi), beta=float(beta), **params)
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            code = self._lib.ep_tv_init(ctypes.byref(o), ctypes.c_void_p(y.data_ptr()),
-                                        ctypes.byref(self.params),
-                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
-        _lib.check(code, "ep_tv_init")
+            if xi_plane is None:
+                code = self._lib.ep_tv_init(ctypes.byref(o), ctypes.c_void_p(y.data_ptr()),
+                                            ctypes.byref(self.params),
+                                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+            else:
+                self._xi_keep = xi_plane.contiguous()
+                code = self._lib.ep_tv_init_noise(ctypes.byref(o), ctypes.c_void_p(y.data_ptr()),
+                                                  ctypes.c_void_p(self._xi_keep.data_ptr()),
+                                                  ctypes.byref(self.params),
+                                                  ctypes.c_void_p(self.stream.cuda_stream),
+                                                  ctypes.byref(ctx))
+        _lib.check(code, "ep_tv_init" if xi_plane is None else "ep_tv_init_noise")
         self._ctx = ctx
 
     # -- lifecycle

@@ -52,6 +52,8 @@ SIGNATURES = {
     "ep_tv_init": (c_int32, [ctypes.POINTER(Operator), c_void_p, ctypes.POINTER(Params), c_void_p,
                              ctypes.POINTER(c_void_p)]),
     "ep_tv_set_probes": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "ep_tv_init_noise": (c_int32, [ctypes.POINTER(Operator), c_void_p, c_void_p, ctypes.POINTER(Params),
+                                   c_void_p, ctypes.POINTER(c_void_p)]),
     "ep_tv_init_block": (c_int32, [ctypes.POINTER(Operator), c_void_p, ctypes.POINTER(Params),
                                    ctypes.POINTER(Block), c_void_p, ctypes.POINTER(c_void_p)]),
     "ep_tv_block_halo_out": (c_int32, [c_void_p, c_int32, c_void_p]),

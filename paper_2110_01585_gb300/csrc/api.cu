@@ -50,6 +50,7 @@ struct ep_tv_ctx {
   int graph_em[2] = {-1, -1};
   int graph_len[2] = {0, 0};
   long long graph_sweeps = 0;  // sweeps run from graph replays (this context or its batch)
+  float* xi_plane = nullptr;  // [M] noise variances of a diagonal noise covariance, or NULL
   // Row block of a sharded image (ep_tv_init_block); rows = 0 for a whole image.
   int blk_rows = 0, blk_top = 0, blk_bottom = 0;  // own rows, halo rows above and below
   // EP-EM convergence checks (allocated on the first ep_tv_ep_em call)
@@ -158,6 +159,7 @@ void free_ctx(ep_tv_ctx* c) {
   cudaFree(c->status);
   cudaFree(c->counters);
   cudaFree(c->mu_prev);
+  cudaFree(c->xi_plane);
   cudaFree(c->d_change);
   if (c->h_change) cudaFreeHost(c->h_change);
   delete c;
@@ -169,6 +171,8 @@ ep_tv_status init_state(ep_tv_ctx* c) {
   c->cur = 0;
   launch_init_sites(c->tau0, c->nu0, c->ptau[0], c->pnu[0], c->mu0, c->n, inv_xi, min_tau,
                     c->stream);
+  if (c->xi_plane && c->op.op == EP_TV_OP_IDENTITY)
+    launch_site0_noise(c->tau0, c->nu0, c->y, c->xi_plane, c->n, c->stream);
   double ds[DS_COUNT] = {c->p.beta, 0.0, 0.0, 0.0};
   CK(cudaMemcpyAsync(c->dscal, ds, sizeof(ds), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
@@ -194,6 +198,10 @@ ep_tv_status latched(ep_tv_ctx* c) {
   if (st & ST_CG_NOCONV) return EP_TV_ERR_CG_NOCONV;
   return EP_TV_OK;
 }
+
+// Denoising contexts with i.i.d. noise form site 0 from y inside the prior pass;
+// with a noise plane (and for the other operators) the site is stored.
+bool site0_from_y(const ep_tv_ctx* c) { return c->op.op == EP_TV_OP_IDENTITY && !c->xi_plane; }
 
 // The EM update (Sec. IV, Algorithm 2) on the device: the statistic that
 // params.em_option selects, reduced in a fixed order, then beta = N / a.  Option 1
@@ -264,7 +272,7 @@ cudaGraphExec_t graph_for(ep_tv_ctx* c, int period, int em_every) {
     a.nin = c->pnu[cur];
     a.tout = c->ptau[cur ^ 1];
     a.nout = c->pnu[cur ^ 1];
-    launch_prior_sweep(a, true, c->stream);
+    launch_prior_sweep(a, site0_from_y(c), c->stream);
     cur ^= 1;
     if (em_every > 0 && (t + 1) % em_every == 0) launch_em(c, c->ptau[cur], c->pnu[cur], c->stream);
   }
@@ -372,6 +380,44 @@ ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_pa
   }
   *out = c;
   return EP_TV_OK;
+}
+
+ep_tv_status ep_tv_init_noise(const ep_tv_operator* op, const float* y, const float* xi,
+                              const ep_tv_params* p, void* cuda_stream, ep_tv_ctx** out) {
+  if (!out) return EP_TV_ERR_ARG;
+  *out = nullptr;
+  if (!op || !p || !xi || !y) return EP_TV_ERR_ARG;
+  if (op->op == EP_TV_OP_CONV_PERIODIC) return EP_TV_ERR_UNSUPPORTED;
+  if (op->m < 1) return EP_TV_ERR_ARG;
+  std::vector<float> h((size_t)op->m);
+  CK(cudaMemcpy(h.data(), xi, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+  double sum = 0.0;
+  for (float v : h) {
+    if (!(std::isfinite(v) && v > 0.0f)) return EP_TV_ERR_ARG;
+    sum += v;
+  }
+  ep_tv_params q = *p;
+  q.xi = sum / (double)h.size();  // the scalar the initial site of Algorithm 1 takes for CS
+  ep_tv_status st = ep_tv_init(op, y, &q, cuda_stream, out);
+  if (st != EP_TV_OK) return st;
+  ep_tv_ctx* c = *out;
+  if (cudaMalloc(&c->xi_plane, sizeof(float) * op->m) != cudaSuccess) {
+    cudaGetLastError();
+    ep_tv_destroy(c);
+    *out = nullptr;
+    return EP_TV_ERR_NOMEM;
+  }
+  st = cudaMemcpyAsync(c->xi_plane, xi, sizeof(float) * op->m, cudaMemcpyDeviceToDevice, c->stream) ==
+               cudaSuccess
+           ? EP_TV_OK
+           : EP_TV_ERR_CUDA;
+  if (st == EP_TV_OK && c->lik) st = likelihood_set_noise(c->lik, c->xi_plane, c->stream);
+  if (st == EP_TV_OK) st = init_state(c);
+  if (st != EP_TV_OK) {
+    ep_tv_destroy(c);
+    *out = nullptr;
+  }
+  return st;
 }
 
 ep_tv_status ep_tv_init_block(const ep_tv_operator* op, const float* y, const ep_tv_params* p,
@@ -482,7 +528,7 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
       if (st != EP_TV_OK) return st;
     }
     c->tracer.begin(EP_TV_K_PRIOR_SWEEP, c->stream);
-    launch_prior_sweep(sweep_args(c, order), c->op.op == EP_TV_OP_IDENTITY, c->stream);
+    launch_prior_sweep(sweep_args(c, order), site0_from_y(c), c->stream);
     c->tracer.end(c->stream, (double)c->n);
     c->cur ^= 1;
     if (c->lik && c->p.order_mode == 0) {
@@ -777,7 +823,7 @@ ep_tv_status ep_tv_trace_read(ep_tv_ctx* c, int32_t kernel, double* ms, int64_t*
     u = (double)(cnt[DC_CG_PRE_UNITS] - c->cnt_base[DC_CG_PRE_UNITS]) * (double)c->n;
   double bpu = 0.0;
   if (kernel == EP_TV_K_PRIOR_SWEEP)
-    bpu = prior_sweep_bytes_per_pixel(c->op.op == EP_TV_OP_IDENTITY);
+    bpu = prior_sweep_bytes_per_pixel(site0_from_y(c));
   else if (c->lik)
     bpu = likelihood_bytes_per_unit(c->lik, kernel);
   if (kernel == EP_TV_K_CS && c->n > 0) bpu /= (double)c->n;  // FP64 flops per pixel
@@ -838,7 +884,7 @@ void fill_items(ep_tv_batch* b, BatchItem* h, int flip) {
       h[i].a.nout = c->pnu[c->cur];
     }
     prior_sweep_prepare(h[i].a);
-    h[i].site0_from_y = c->op.op == EP_TV_OP_IDENTITY;
+    h[i].site0_from_y = site0_from_y(c);
     h[i].units = prior_sweep_blocks(c->height, c->width);
     h[i].unit_begin = unit;
     unit += h[i].units;

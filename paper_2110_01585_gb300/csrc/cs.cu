@@ -119,14 +119,20 @@ __global__ void to_f64_kernel(const float* A, double* out, long long total) {
     out[e] = (double)A[e];
 }
 
-// K = 0, then the diagonal gets xi (the GEMM adds G G^T with beta = 1).
-__global__ void init_k_kernel(double* K, int M, double xi) {
+// K = 0, then the diagonal gets the noise covariance: xi, or xi_v[i] for a
+// diagonal (non-i.i.d.) noise covariance (the GEMM adds G G^T with beta = 1).
+__global__ void init_k_kernel(double* K, int M, double xi, const double* xi_v) {
   const long long total = (long long)M * M;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / M), j = (int)(e - (long long)i * M);
-    K[e] = i == j ? xi : 0.0;
+    K[e] = i == j ? (xi_v ? xi_v[i] : xi) : 0.0;
   }
+}
+
+__global__ void f32_to_f64_kernel(const float* in, double* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
 }
 
 // In-place Cholesky of the diagonal block K[k0:k0+b, k0:k0+b] (b <= 64), one block
@@ -320,6 +326,7 @@ struct CsState {
   double* w = nullptr;
   double* g = nullptr;
   double* t = nullptr;        // M
+  double* xi_v = nullptr;     // M noise variances (diagonal noise covariance), or NULL
 };
 
 namespace {
@@ -334,6 +341,7 @@ void cs_free(CsState* S) {
   cudaFree(S->w);
   cudaFree(S->g);
   cudaFree(S->t);
+  cudaFree(S->xi_v);
   delete S;
 }
 
@@ -381,6 +389,15 @@ void cs_destroy(CsState* S) {
   if (S) cs_free(S);
 }
 
+ep_tv_status cs_set_noise(CsState* S, const float* xi_m, cudaStream_t s) {
+  if (!S->xi_v && cudaMalloc(&S->xi_v, sizeof(double) * S->M) != cudaSuccess) {
+    cudaGetLastError();
+    return EP_TV_ERR_NOMEM;
+  }
+  f32_to_f64_kernel<<<(S->M + 255) / 256, 256, 0, s>>>(xi_m, S->xi_v, S->M);
+  return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+}
+
 ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, const float* np,
                        unsigned* status, unsigned long long* counters, Tracer* tr, cudaStream_t s) {
   const int M = S->M, N = S->N;
@@ -389,7 +406,7 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
   cs_cavity_kernel<<<g1d(N), 256, 0, s>>>(tp, np, N, S->c, S->sqc, S->m);
   // K = xi I + (A C^{1/2})(A C^{1/2})^T, lower triangle
   scale_cols_kernel<<<g1d(MN), 256, 0, s>>>(S->A, S->sqc, S->G, M, N);
-  init_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->xi);
+  init_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->xi, S->xi_v);
   gemm(true, M, M, N, S->G, N, S->G, N, S->K, M, 1.0, 1.0, true, s);
   // blocked right-looking Cholesky K = L L^T (lower)
   for (int k0 = 0; k0 < M; k0 += kNb) {

@@ -2176,6 +2176,11 @@ ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s) {
   return EP_TV_OK;
 }
 
+ep_tv_status likelihood_set_noise(LikelihoodState* L, const float* xi_m, cudaStream_t s) {
+  if (!L->cs) return EP_TV_ERR_UNSUPPORTED;
+  return cs_set_noise(L->cs, xi_m, s);
+}
+
 ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const float* eps2,
                                    int n_samples, cudaStream_t s) {
   if (L->cs || n_samples != L->S) return EP_TV_ERR_ARG;

@@ -123,6 +123,18 @@ __global__ void mean_change_kernel(const float* __restrict__ tau0, const float* 
   }
 }
 
+// Denoising with a diagonal noise covariance: site 0 = (1 / xi_p, y_p / xi_p),
+// the exact likelihood site (Eq. tilted_P_1 with H = I).
+__global__ void site0_noise_kernel(float* tau0, float* nu0, const float* y, const float* xi,
+                                   long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const float t = 1.0f / xi[p];
+    tau0[p] = t;
+    nu0[p] = y[p] * t;
+  }
+}
+
 // mean = (sum_s nu_s) / (sum_s tau_s), var = 1 / (sum_s tau_s)
 __global__ void posterior_kernel(const float* __restrict__ tau0, const float* __restrict__ nu0,
                                  const float* __restrict__ tp, const float* __restrict__ np,
@@ -206,6 +218,11 @@ void launch_mean_change(const float* tau0, const float* nu0, const float* tp, co
                         long long n, float* prev, unsigned* out, cudaStream_t s) {
   mean_change_kernel<<<ew_blocks(n) < 1024 ? ew_blocks(n) : 1024, kEwThreads, 0, s>>>(tau0, nu0, tp,
                                                                                       np, n, prev, out);
+}
+
+void launch_site0_noise(float* tau0, float* nu0, const float* y, const float* xi, long long n,
+                        cudaStream_t s) {
+  site0_noise_kernel<<<ew_blocks(n), kEwThreads, 0, s>>>(tau0, nu0, y, xi, n);
 }
 
 }  // namespace eptv

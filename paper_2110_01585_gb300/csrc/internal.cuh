@@ -164,6 +164,9 @@ void launch_ax_block(const float* tau0, const float* nu0, const float* tp, const
 // Posterior mean into prev, max |change| and max |mean| as float bits into out[0..1].
 void launch_mean_change(const float* tau0, const float* nu0, const float* tp, const float* np,
                         long long n, float* prev, unsigned* out, cudaStream_t s);
+// Site 0 of denoising with per-pixel noise variances xi: (1 / xi, y / xi).
+void launch_site0_noise(float* tau0, float* nu0, const float* y, const float* xi, long long n,
+                        cudaStream_t s);
 void launch_posterior(const float* tau0, const float* nu0, const float* tp, const float* np,
                       long long n, float* mean, float* var, cudaStream_t s);
 

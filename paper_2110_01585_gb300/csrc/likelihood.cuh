@@ -30,6 +30,8 @@ void likelihood_destroy(LikelihoodState* L);
 ep_tv_status likelihood_reset(LikelihoodState* L, cudaStream_t s);
 ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const float* eps2,
                                    int n_samples, cudaStream_t s);
+// Diagonal noise covariance (dense operator; EP_TV_ERR_UNSUPPORTED otherwise).
+ep_tv_status likelihood_set_noise(LikelihoodState* L, const float* xi_m, cudaStream_t s);
 // One q_{x,0} update: cavity from sites 1..4, tilted moments of P_0
 // (Eq. tilted_P_1), site update (Eq. update_q0_x) with cap and damping.
 // tau0, nu0: likelihood site (updated in place); tp, np: prior sites, [4][N].
@@ -51,6 +53,8 @@ ep_tv_status likelihood_state_import(LikelihoodState* L, const void* host, cudaS
 struct CsState;
 ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** out, float* mu0);
 void cs_destroy(CsState* S);
+// Diagonal noise covariance: K = diag(xi_m) + A C A^T (xi_m DEVICE, M floats, copied).
+ep_tv_status cs_set_noise(CsState* S, const float* xi_m, cudaStream_t s);
 ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, const float* np,
                        unsigned* status, unsigned long long* counters, Tracer* tr, cudaStream_t s);
 double cs_flops(const CsState* S);  // FP64 flops of one update

@@ -292,3 +292,26 @@ def test_lambda_study_option3_nearest_mse_optimum(sigma):
     assert opts[3][1] <= opts[1][1] and opts[3][1] <= opts[2][1], opts
     # every EP-EM estimate is worse than the grid optimum
     assert all(v[1] >= mse_opt * (1 - 1e-6) for v in opts.values())
+
+
+def test_diagonal_noise_denoising_matches_oracle():
+    """Denoising with one noise variance per pixel (a diagonal noise covariance,
+    Sec. III-C): variances spread over a factor of 20, EM every 5 sweeps."""
+    torch = cuda()
+    h, w = 64, 80
+    p = syn.denoise_problem(h, w, sigma=0.1, beta=5.0, seed=44)
+    xi = 0.004 * np.exp(np.random.default_rng(45).uniform(0.0, 3.0, h * w))
+    y = p.x + np.sqrt(xi.reshape(h, w)) * np.random.default_rng(46).standard_normal((h, w))
+    xi32 = xi.astype(np.float32)
+    yt = torch.as_tensor(y.astype(np.float32), device="cuda")
+    with EPTV(yt, 0.0, p.beta, xi_plane=torch.as_tensor(xi32, device="cuda")) as ep:
+        ep.sweep(20, em_every=5)
+        mu, var = (t.cpu().numpy() for t in ep.posterior())
+        beta, _ = ep.em_beta()
+        assert ep.status() == 0
+    o = EPOracle("denoise", y.astype(np.float32).astype(np.float64), xi32.astype(np.float64), p.beta,
+                 h, w)
+    o.run(20, em_every=5)
+    mu_r, var_r = o.posterior()
+    assert_parity(mu, var, mu_r, var_r, y)
+    assert abs(beta / o.em_update() - 1) < 1e-4

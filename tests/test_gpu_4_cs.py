@@ -76,3 +76,26 @@ def test_cs_config_128_full_size():
     # beta of the last EM step (N / a_u of the sixth sweep, recomputed on both sides)
     beta_ref = o.em_update()
     assert abs(beta_gpu / beta_ref - 1.0) < 1e-4, (beta_gpu, beta_ref)
+
+
+def test_cs_diagonal_noise_matches_oracle():
+    """Compressive sensing with one noise variance per measurement: the Woodbury
+    site with K = diag(xi) + A C A^T (Sec. III-C)."""
+    torch = cuda()
+    h = w = 32
+    p = syn.cs_problem(h, w, m=307, seed=32, beta0=2.0)
+    m = p.A.shape[0]
+    xi = 1e-4 * np.exp(np.random.default_rng(33).uniform(0.0, 3.0, m))
+    y = p.A @ p.x.reshape(-1) + np.sqrt(xi) * np.random.default_rng(34).standard_normal(m)
+    A32, y32, xi32 = p.A.astype(np.float32), y.astype(np.float32), xi.astype(np.float32)
+    At = torch.as_tensor(A32, device="cuda")
+    with EPTV(torch.as_tensor(y32, device="cuda"), 0.0, p.beta, op=OP_DENSE, dense=At, height=h,
+              width=w, xi_plane=torch.as_tensor(xi32, device="cuda")) as ep:
+        ep.sweep(8, em_every=4)
+        mu, var = (t.cpu().numpy() for t in ep.posterior())
+        assert ep.status() == 0
+    o = EPOracle("cs", y32.astype(np.float64), xi32.astype(np.float64), p.beta, h, w,
+                 A=A32.astype(np.float64), site0="woodbury")
+    o.run(8, em_every=4)
+    mu_r, var_r = o.posterior()
+    assert_parity(mu, var, mu_r, var_r, p.A.T @ y)

@@ -420,6 +420,67 @@ def test_em_options_agree_at_lambda_zero():
     assert abs(o.em_statistic(1) / ref_q - 1) <= 1e-10
 
 
+# ---------------------------------------------------------------- non-i.i.d. noise
+def _noise_plane(n, seed):
+    """Noise variances spread over a factor of 20 (seeded)."""
+    return 0.005 * np.exp(np.random.default_rng(seed).uniform(0.0, 3.0, n))
+
+
+def test_diagonal_noise_lambda_zero_closed_forms():
+    """Sec. III-C: a diagonal noise covariance enters Eq. tilted_P_1 in place of
+    xi I.  With lam = 0 the prior sites stay at the cap: the EP variances are those
+    of the Gaussian posterior with precision H^T diag(1/xi) H + 4/var_cap (per
+    pixel for denoising, the diagonal of the dense inverse for deconvolution),
+    and the mean tends to the weighted least-squares solution (y for denoising,
+    H^{-1} y for an invertible blur, whatever the weights)."""
+    h, w = 6, 8
+    n = h * w
+    xi = _noise_plane(n, 1)
+    y = np.random.default_rng(2).random((h, w))
+    o = EPOracle("denoise", y, xi, 0.0, h, w)
+    o.run(30)
+    mu, var = (a.reshape(-1) for a in o.posterior())
+    ridge = 4.0 / o.var_cap
+    np.testing.assert_allclose(var, 1.0 / (1.0 / xi + ridge), rtol=1e-13)
+    np.testing.assert_allclose(mu, y.reshape(-1), rtol=1e-9, atol=1e-12)
+    k = np.array([[0.02, 0.05, 0.01], [0.04, 0.7, 0.08], [0.03, 0.06, 0.01]])
+    o = EPOracle("deconv", y, xi, 0.0, h, w, kernel=k, site0="exact")
+    o.run(40)
+    mu, var = (a.reshape(-1) for a in o.posterior())
+    H = operators.conv_matrix(h, w, k)
+    cov = np.linalg.inv(H.T @ np.diag(1.0 / xi) @ H + ridge * np.eye(n))
+    np.testing.assert_allclose(var, np.diag(cov), rtol=1e-10)
+    np.testing.assert_allclose(mu, np.linalg.solve(H, y.reshape(-1)), rtol=0, atol=1e-6)
+
+
+def test_diagonal_noise_woodbury_equals_dense_inverse():
+    """Compressive sensing with a diagonal noise covariance: the Woodbury form
+    (K = diag(xi) + H C H^T) equals the dense inverse of Eq. tilted_P_1."""
+    rng = np.random.default_rng(6)
+    n, m = 256, 77
+    H = rng.standard_normal((m, n)) / math.sqrt(m)
+    xi = _noise_plane(m, 7)
+    c = rng.uniform(0.5, 2.0, n)
+    mv = rng.standard_normal(n)
+    o = EPOracle("cs", rng.standard_normal(m), xi, 1.0, 16, 16, A=H, site0="woodbury")
+    E, V = o._woodbury(H, c, mv)
+    Q = H.T @ np.diag(1.0 / xi) @ H + np.diag(1.0 / c)
+    cov = np.linalg.inv(Q)
+    np.testing.assert_allclose(V, np.diag(cov), rtol=1e-10)
+    np.testing.assert_allclose(E, cov @ (H.T @ (o.y / xi) + mv / c), rtol=1e-9, atol=1e-10)
+
+
+def test_constant_noise_plane_equals_scalar_noise():
+    h, w = 8, 8
+    p = syn.denoise_problem(h, w, sigma=0.1, beta=10.0, seed=3)
+    a = EPOracle("denoise", p.y, p.xi, p.beta, h, w)
+    b = EPOracle("denoise", p.y, np.full(h * w, p.xi), p.beta, h, w)
+    a.run(5)
+    b.run(5)
+    for x, z in zip(a.posterior(), b.posterior()):
+        np.testing.assert_allclose(x, z, rtol=1e-14)
+
+
 # ---------------------------------------------------------------- lam -> 0
 def test_lambda_zero_denoise_closed_form():
     """P3: with lam = 0 every prior site sits at the cap, mu = y and
