@@ -353,8 +353,12 @@ void ep_tv_batch_destroy(ep_tv_batch* batch);
    ep_tv_batch_sweep calls of at least two periods of lcm(2, em_every) sweeps by
    replaying a graph of one period, captured on first use (thread-local capture
    mode) and cached per buffer parity; the remaining sweeps are launched
-   directly.  Results are identical to direct launches.  Returns how many of the
-   context's sweeps ran from graph replays (-1 for NULL). */
+   directly.  The deconvolution site runs every update, with tracing off and on
+   such a stream, as one graph whose refinement passes and CG iterations are
+   conditional WHILE nodes driven by device-side counters (no host round trip
+   inside an update), captured on first use per prior-site buffer; with tracing
+   on it runs the host-driven loop.  Results are identical to direct launches.
+   Returns how many of the context's sweeps ran from graph replays (-1 for NULL). */
 int64_t ep_tv_graph_sweeps(const ep_tv_ctx* ctx);
 
 /* ---- Learned warm start (not in the paper) ----------------------------------

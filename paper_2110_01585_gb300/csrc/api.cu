@@ -536,6 +536,7 @@ ep_tv_status ep_tv_sweep(ep_tv_ctx* c, int32_t n_sweeps, const int8_t* k_order,
                                           c->status, c->counters, &c->tracer, c->stream);
       if (st != EP_TV_OK) return st;
     }
+    if (c->lik && likelihood_graph_last(c->lik)) ++c->graph_sweeps;
     ++c->sweeps;
     if (em_every > 0 && (t + 1) % em_every == 0) launch_em(c, c->ptau[c->cur], c->pnu[c->cur], c->stream);
   }

@@ -300,6 +300,8 @@ struct CgArgs {
   double* rzs;           // [R] r.z of the current iteration
   unsigned* arrive;      // [R] block-arrival counters of the update kernel
   const int* act0;       // [R] 1 if the system iterates in the current refinement pass
+  const int* it_dev;     // iteration index in device memory (graph replays), or NULL: the
+                         // kernels' it argument
   int nb;                // tile blocks per system
   int nbz;               // blocks per system producing r.z partials
   int fft;               // 1: z = M^{-1} r by the circulant preconditioner, else Jacobi
@@ -605,8 +607,11 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
 __global__ void thresholds_kernel(const double* part_rr, const double* part_bb,
                                   const double* part_rz, int fft, int R, int nb,
                                   double rtol2_mean, double rtol2_probe, double eta2, double* thr,
-                                  double* relres, double* prev_rr, double* rr0, int first,
-                                  int* active, float* scal, int* act0, double* rzs) {
+                                  double* relres, double* prev_rr, double* rr0, int first_arg,
+                                  const int* outer_dev, int* active, float* scal, int* act0,
+                                  double* rzs) {
+  // the first true residual of this update (graph replays: passes started = 0)
+  const int first = outer_dev ? (*outer_dev == 0) : first_arg;
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -654,10 +659,11 @@ __global__ void thresholds_kernel(const double* part_rr, const double* part_bb,
 }
 
 // Direction and product: p = Minv r + beta p, q = Q p, partial p.q.
-__global__ void __launch_bounds__(kThreads, 5) direction_kernel(CgArgs a, int it) {
+__global__ void __launch_bounds__(kThreads, 5) direction_kernel(CgArgs a, int it_arg) {
   extern __shared__ float smem[];
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
+  const int it = a.it_dev ? *a.it_dev : it_arg;
   if (a.scal[4 * j] == 0.f) return;  // this system has converged
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&a.counters[DC_CG_DIR_UNITS], 1ull);
@@ -760,9 +766,10 @@ __global__ void __launch_bounds__(kThreads, 5) direction_kernel(CgArgs a, int it
 constexpr int kUpdThreads = 64;
 constexpr int kUpdRows = kTile * kTile / 4 / kUpdThreads;
 
-__global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it) {
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it_arg) {
   const ConvDesc& c = a.c;
   const int j = blockIdx.z;
+  const int it = a.it_dev ? *a.it_dev : it_arg;
   if (a.scal[4 * j] == 0.f) return;  // this system has stopped
   const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
   if (blk == 0 && threadIdx.x == 0) atomicAdd(&a.counters[DC_CG_UPD_UNITS], 1ull);
@@ -1438,6 +1445,88 @@ __global__ void check_kernel(const float* scal, int R, int* active) {
   }
 }
 
+// ---- device-driven solver loop (CUDA graph with conditional nodes)
+//
+// The refinement passes and the CG iterations of a pass run as two nested WHILE
+// nodes of a graph, with an IF node around each pass; their conditions are set
+// by the kernels below from counters in device memory, so a likelihood-site
+// update needs no host round trip.  Every loop body starts by clearing its own
+// condition (cond_clear_kernel), so a body that did not set it again ends the
+// loop; the counters bound both loops (max_outer passes, max_iter iterations).
+// Iterative refinement of the likelihood-site solves: a true residual in
+// float-float, then FP32 preconditioned CG on the correction until its recurrence
+// residual has dropped below max(eta ||r||, (rtol / 2) ||b||), repeated until
+// ||r|| <= rtol ||b|| for every system.  With eta = 3.2e-5 the second term decides
+// once the warm start is within about 1e-4 relative of the solution (every sweep
+// after the first few), so a sweep normally needs one pass; a cold start still
+// moves in steps of eta, which FP32 CG reaches before its rounding floor.
+constexpr double kEta2 = 1e-9;
+
+struct LoopState {
+  int it;         // CG iteration within the current pass
+  int outer;      // passes started
+  int total;      // CG iterations of this update
+  int converged;  // 1 once a true residual met every system's target
+};
+
+__global__ void cond_clear_kernel(cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+}
+
+__global__ void loop_init_kernel(LoopState* ls) {
+  if (threadIdx.x == 0) {
+    ls->it = 0;
+    ls->outer = 0;
+    ls->total = 0;
+    ls->converged = 0;
+  }
+}
+
+// After a true residual and its thresholds: start another pass, or stop
+// (converged, or out of passes or iterations), as the host loop does.
+__global__ void pass_kernel(LoopState* ls, const int* active, int max_outer, int max_iter,
+                            cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_pass,
+                            cudaGraphConditionalHandle h_inner) {
+  if (threadIdx.x != 0) return;
+  unsigned go = 0;
+  if (*active == 0) {
+    ls->converged = 1;
+  } else if (ls->outer < max_outer && ls->total < max_iter) {
+    go = 1;
+    ls->it = 0;
+    ls->outer += 1;
+  }
+  cudaGraphSetConditional(h_pass, go);
+  cudaGraphSetConditional(h_outer, go);
+  cudaGraphSetConditional(h_inner, go);
+}
+
+// After a CG iteration: count it, and go on while a system is active and the
+// iteration budget lasts.
+__global__ void iter_kernel(LoopState* ls, const float* scal, int R, int max_iter,
+                            cudaGraphConditionalHandle h_inner) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int j = threadIdx.x; j < R; j += blockDim.x) mine += scal[4 * j] != 0.f;
+  if (mine) atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ls->it += 1;
+    ls->total += 1;
+    cudaGraphSetConditional(h_inner, (cnt > 0 && ls->total < max_iter) ? 1u : 0u);
+  }
+}
+
+__global__ void loop_finish_kernel(const LoopState* ls, unsigned* status,
+                                   unsigned long long* counters) {
+  if (threadIdx.x == 0) {
+    if (!ls->converged) atomicOr(status, ST_CG_NOCONV);
+    counters[DC_CG_ITERS] = (unsigned long long)ls->total;
+  }
+}
+
 // Rao-Blackwellised terms of the probes, by an explicit matvec of each computed
 // sample: with Q z = H^T H z / xi + d z and (H^T H)_ii = g0 = sum k^2, the
 // off-diagonal part of row i is
@@ -1633,6 +1722,14 @@ struct LikelihoodState {
   unsigned* d_arrive = nullptr; // [R + pairs] block-arrival counters (start and stay zero)
   int* d_act0 = nullptr;        // [R] systems that iterate in the current pass
   float* Ec = nullptr;          // R planes: FP32 correction of the current pass
+  // the update as a graph with conditional nodes, one per prior-site buffer
+  LoopState* d_loop = nullptr;
+  struct {
+    const float* tp = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } graph[2];
+  bool graph_failed = false;    // capture or instantiation refused: host-driven loop only
+  bool graph_last = false;      // the last update ran from a graph
   double* d_relres = nullptr;  // [R] sqrt(r.r / b.b) after the last true residual
   double* d_prev_rr = nullptr; // [R] r.r of the previous refinement pass
   double* d_rr0 = nullptr;     // [R] r.r at the start of the current pass
@@ -1668,6 +1765,7 @@ CgArgs cg_args(LikelihoodState* L) {
   a.rzs = L->d_rzs;
   a.arrive = L->d_arrive;
   a.act0 = L->d_act0;
+  a.it_dev = nullptr;
   a.Z = L->Z;
   a.Ec = L->Ec;
   const long long rn = (long long)L->R * L->nbmax;
@@ -2027,6 +2125,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
             cudaMalloc(&L->d_rzs, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_arrive, sizeof(unsigned) * (L->R + (L->R + 1) / 2)) == cudaSuccess &&
             cudaMalloc(&L->d_act0, sizeof(int) * L->R) == cudaSuccess &&
+            cudaMalloc(&L->d_loop, sizeof(LoopState)) == cudaSuccess &&
             cudaMalloc(&L->Ec, sizeof(float) * RN) == cudaSuccess &&
             cudaHostAlloc(&L->h_relres, sizeof(double) * L->R, cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc(&L->h_active, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess &&
@@ -2161,6 +2260,9 @@ void likelihood_destroy(LikelihoodState* L) {
   cudaFree(L->d_rzs);
   cudaFree(L->d_arrive);
   cudaFree(L->d_act0);
+  cudaFree(L->d_loop);
+  for (auto& g : L->graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(L->Ec);
   if (L->h_relres) cudaFreeHost(L->h_relres);
   if (L->h_active) cudaFreeHost(L->h_active);
@@ -2193,10 +2295,137 @@ ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const 
   return finish_probes(L, s);
 }
 
+namespace {
+
+// The likelihood-site update of likelihood_update below as one graph: the prior
+// sites tp/np in, site 0 out; the refinement passes and the CG iterations are
+// WHILE nodes, each pass an IF node (see LoopState).  Built by stream capture
+// into the graph and its conditional bodies, one at a time; false if CUDA
+// refuses any step (the caller then keeps the host-driven loop).
+bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* tp, const float* np,
+                        unsigned* status, unsigned long long* counters, cudaStream_t s,
+                        cudaGraphExec_t* out) {
+  *out = nullptr;
+  const ConvDesc& c = L->c;
+  const long long N = c.N;
+  CgArgs a = cg_args(L);
+  a.counters = counters;
+  a.it_dev = &L->d_loop->it;
+  const dim3 grid(c.tiles_x, c.tiles_y, L->R);
+  const int groups = (L->S + kRbGroup - 1) / kRbGroup;
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle h_outer = 0, h_pass = 0, h_inner = 0;
+  bool ok = cudaGraphConditionalHandleCreate(&h_outer, G, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&h_pass, G, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&h_inner, G, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  // a conditional node after the current capture dependencies of s; *body gets its graph
+  auto add_cond = [&](cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                      cudaGraph_t* body) -> bool {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+      return false;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p) != cudaSuccess) return false;
+    *body = p.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies) == cudaSuccess;
+  };
+  auto capture = [&](cudaGraph_t g, auto&& launches) -> bool {
+    if (cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      return false;
+    const bool fine = launches();
+    cudaGraph_t tmp = nullptr;
+    const bool ended = cudaStreamEndCapture(s, &tmp) == cudaSuccess;
+    return fine && ended && cudaGetLastError() == cudaSuccess;
+  };
+  cudaGraph_t b_outer = nullptr, b_pass = nullptr, b_inner = nullptr;
+  ok = ok && capture(G, [&]() {
+    prep_kernel<<<L->prep_blocks, kThreads, 0, s>>>(tp, np, N, c.g0_xi, L->D, L->Ncav, L->Minv,
+                                                    L->dpart);
+    mean_kernel<<<1, 1024, 0, s>>>(L->dpart, L->prep_blocks, 1.0 / (double)N, L->dbar);
+    loop_init_kernel<<<1, 32, 0, s>>>(L->d_loop);
+    if (!add_cond(h_outer, cudaGraphCondTypeWhile, &b_outer)) return false;
+    loop_finish_kernel<<<1, 32, 0, s>>>(L->d_loop, status, counters);
+    rb_offdiag_kernel<<<dim3(c.tiles_x, c.tiles_y, groups), kThreads, L->smem, s>>>(a, L->Qp);
+    site0_kernel<<<grid1d(N), 256, 0, s>>>(a, L->Qp, groups, tau, nu, L->min_tau, L->damping,
+                                           status, counters);
+    return true;
+  });
+  ok = ok && capture(b_outer, [&]() {
+    cond_clear_kernel<<<1, 32, 0, s>>>(h_outer);
+    residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
+    thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, a.part_rz, a.fft, L->R, L->nb,
+                                         L->rtol2_true, L->rtol2_probe, kEta2, L->thr, L->d_relres,
+                                         L->d_prev_rr, L->d_rr0, 0, &L->d_loop->outer, L->d_active,
+                                         L->d_scal, L->d_act0, L->d_rzs);
+    pass_kernel<<<1, 32, 0, s>>>(L->d_loop, L->d_active, L->max_outer, L->max_iter, h_outer, h_pass,
+                                 h_inner);
+    return add_cond(h_pass, cudaGraphCondTypeIf, &b_pass);
+  });
+  ok = ok && capture(b_pass, [&]() {
+    if (L->fft) precond_apply(L, a.part_rz, true, 1, counters, s);
+    if (!add_cond(h_inner, cudaGraphCondTypeWhile, &b_inner)) return false;
+    commit_kernel<<<dim3(std::min(grid1d(N), 1024), L->R), 256, 0, s>>>(L->X, L->Ec, L->d_act0, N);
+    return true;
+  });
+  ok = ok && capture(b_inner, [&]() {
+    cond_clear_kernel<<<1, 32, 0, s>>>(h_inner);
+    direction_kernel<<<grid, kThreads, L->smem, s>>>(a, 0);
+    update_kernel<<<grid, kUpdThreads, 0, s>>>(a, 0);
+    if (L->fft) precond_apply(L, a.part_rz, true, 0, counters, s);
+    iter_kernel<<<1, 64, 0, s>>>(L->d_loop, L->d_scal, L->R, L->max_iter, h_inner);
+    return true;
+  });
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, G, 0) == cudaSuccess;
+  cudaGraphDestroy(G);
+  cudaGetLastError();
+  *out = ok ? exec : nullptr;
+  return ok;
+}
+
+}  // namespace
+
 ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const float* tp,
                                const float* np, unsigned* status, unsigned long long* counters,
                                Tracer* tr, cudaStream_t s) {
   if (L->cs) return cs_update(L->cs, tau, nu, tp, np, status, counters, tr, s);
+  // Graph replay: the whole update with device-driven loops, one launch.  Not with
+  // tracing (which brackets every kernel launch) nor on the legacy default
+  // stream (which cannot be captured).
+  if (!tr->on && s != nullptr && !L->graph_failed) {
+    int slot = L->graph[0].tp == tp ? 0 : (L->graph[1].tp == tp ? 1 : -1);
+    if (slot < 0) {
+      slot = L->graph[0].exec ? 1 : 0;
+      if (L->graph[slot].exec) cudaGraphExecDestroy(L->graph[slot].exec);
+      L->graph[slot].exec = nullptr;
+      L->graph[slot].tp = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (build_update_graph(L, tau, nu, tp, np, status, counters, s, &exec)) {
+        L->graph[slot].exec = exec;
+        L->graph[slot].tp = tp;
+      } else {
+        L->graph_failed = true;
+      }
+    }
+    if (!L->graph_failed) {
+      if (cudaGraphLaunch(L->graph[slot].exec, s) != cudaSuccess) return EP_TV_ERR_CUDA;
+      L->graph_last = true;
+      return EP_TV_OK;
+    }
+  }
+  L->graph_last = false;
   const ConvDesc& c = L->c;
   const long long N = c.N;
   prep_kernel<<<L->prep_blocks, kThreads, 0, s>>>(tp, np, N, c.g0_xi, L->D, L->Ncav, L->Minv,
@@ -2205,14 +2434,9 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
   CgArgs a = cg_args(L);
   a.counters = counters;
   dim3 grid(c.tiles_x, c.tiles_y, L->R);
-  // Iterative refinement: true residual (float-float), then FP32 preconditioned CG
-  // on the correction until its recurrence residual has dropped below
-  // max(eta ||r||, (rtol / 2) ||b||), repeated until ||r|| <= rtol ||b|| for every
-  // system.  With eta = 3.2e-5 the second term decides once the warm start is
-  // within about 1e-4 relative of the solution (every sweep after the first few),
-  // so a sweep normally needs one pass; a cold start still moves in steps of
-  // eta, which FP32 CG reaches before its rounding floor.
-  const double eta2 = 1e-9;
+  // Iterative refinement (see kEta2): true residual (float-float), then FP32
+  // preconditioned CG on the correction, repeated until ||r|| <= rtol ||b||.
+  const double eta2 = kEta2;
   int total = 0, iters = 0;
   bool converged = false;
   for (int outer = 0;; ++outer) {
@@ -2221,8 +2445,8 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     tr->end(s, (double)L->R * N);
     thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, a.part_rz, a.fft, L->R, L->nb,
                                          L->rtol2_true, L->rtol2_probe, eta2, L->thr, L->d_relres,
-                                         L->d_prev_rr, L->d_rr0, outer == 0, L->d_active, L->d_scal,
-                                         L->d_act0, L->d_rzs);
+                                         L->d_prev_rr, L->d_rr0, outer == 0, nullptr, L->d_active,
+                                         L->d_scal, L->d_act0, L->d_rzs);
     if (cudaMemcpyAsync(L->h_active, L->d_active, sizeof(int), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(L->h_relres, L->d_relres, sizeof(double) * L->R, cudaMemcpyDeviceToHost,
@@ -2332,13 +2556,36 @@ double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
 
 int likelihood_systems(const LikelihoodState* L) { return L->R; }
 
-int likelihood_last_iters(const LikelihoodState* L) { return L->last_iters; }
+// After a graph replay the counts and residuals live in device memory only
+// (the callers have synchronised the context's stream).
+bool likelihood_graph_last(const LikelihoodState* L) { return !L->cs && L->graph_last; }
+
+int likelihood_last_iters(const LikelihoodState* L) {
+  if (L->cs || !L->graph_last) return L->last_iters;
+  LoopState ls;
+  if (cudaMemcpy(&ls, L->d_loop, sizeof(ls), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return ls.total;
+}
 
 void likelihood_report(const LikelihoodState* L, int* outer, double* relres_mean,
                        double* relres_probe) {
-  if (outer) *outer = L->rep_outer;
-  if (relres_mean) *relres_mean = L->rep_mean;
-  if (relres_probe) *relres_probe = L->rep_probe;
+  int o = L->rep_outer;
+  double rm = L->rep_mean, rp = L->rep_probe;
+  if (!L->cs && L->graph_last) {
+    LoopState ls;
+    std::vector<double> rel(L->R);
+    if (cudaMemcpy(&ls, L->d_loop, sizeof(ls), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemcpy(rel.data(), L->d_relres, sizeof(double) * L->R, cudaMemcpyDeviceToHost) ==
+            cudaSuccess) {
+      o = ls.outer;
+      rm = rel[0];
+      rp = 0.0;
+      for (int j = 1; j < L->R; ++j) rp = std::max(rp, rel[j]);
+    }
+  }
+  if (outer) *outer = o;
+  if (relres_mean) *relres_mean = rm;
+  if (relres_probe) *relres_probe = rp;
 }
 
 size_t likelihood_state_bytes(const LikelihoodState* L) {

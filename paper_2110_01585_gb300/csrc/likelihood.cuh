@@ -32,6 +32,8 @@ ep_tv_status likelihood_set_probes(LikelihoodState* L, const float* eps1, const 
                                    int n_samples, cudaStream_t s);
 // Diagonal noise covariance (dense operator; EP_TV_ERR_UNSUPPORTED otherwise).
 ep_tv_status likelihood_set_noise(LikelihoodState* L, const float* xi_m, cudaStream_t s);
+// Whether the last update ran as a graph replay (device-driven solver loops).
+bool likelihood_graph_last(const LikelihoodState* L);
 // One q_{x,0} update: cavity from sites 1..4, tilted moments of P_0
 // (Eq. tilted_P_1), site update (Eq. update_q0_x) with cap and damping.
 // tau0, nu0: likelihood site (updated in place); tp, np: prior sites, [4][N].

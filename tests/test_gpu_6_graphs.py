@@ -67,3 +67,30 @@ def test_batch_graph_equals_one_by_one():
         assert e1.graph_sweeps() == 8 and e2.graph_sweeps() == 0
     for e in batched + single:
         e.close()
+
+
+@pytest.mark.parametrize("h,w,kernel,em", [(64, 64, 9, 3), (48, 80, 5, 0)])
+def test_deconv_update_graph_equals_host_driven_loop(h, w, kernel, em):
+    """The deconvolution likelihood site as one graph per update (refinement
+    passes and CG iterations as conditional WHILE nodes on device counters)
+    against the host-driven loop that runs when tracing is on: the same kernels
+    in the same order on the same data, so the whole state (sites, solutions,
+    beta, a_u) agrees bit for bit, over both prior-site buffers and with EM."""
+    from paper_2110_01585_gb300 import OP_CONV_PERIODIC
+    torch = cuda()
+    stream = torch.cuda.Stream()
+    p = syn.deconv_problem(h, w, kernel=syn.uniform_kernel(kernel), bsnr_db=35.0, beta0=2.0, seed=h + w,
+                           grf_length=8.0)
+    y = torch.as_tensor(p.y.astype(np.float32), device="cuda")
+    kw = dict(op=OP_CONV_PERIODIC, kernel=p.kernel, rbmc_samples=6, stream=stream)
+    with EPTV(y, p.xi, p.beta, **kw) as g, EPTV(y, p.xi, p.beta, **kw) as host:
+        host.trace(True)  # tracing brackets every launch: the host-driven loop
+        for n in (3, 4):
+            g.sweep(n, em_every=em)
+            host.sweep(n, em_every=em)
+        assert g.status() == 0 and host.status() == 0
+        assert g.state_export() == host.state_export()
+        assert g.graph_sweeps() == 7 and host.graph_sweeps() == 0
+        assert g.stats()["cg_iters"] > 0
+        rep = g.solver_report()
+        assert rep["relres_mean"] <= 1e-9 and rep["relres_probe_max"] <= 1e-6
