@@ -221,14 +221,12 @@ def run_batch(args, rank, world):
         step()
     torch.cuda.synchronize()
     barrier(world)
-    for c in ctxs:
-        c.trace(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    cs = ClockSampler(dev.index)
-    with cs:
+
+    def timed(steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
         torch.cuda.synchronize()
-        for i in range(args.steps):
+        for i in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 ev[i][0].record(stream)
@@ -236,9 +234,19 @@ def run_batch(args, rank, world):
             with torch.cuda.stream(stream):
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    # timed untraced (deconvolution sites as graph replays); per-kernel times from
+    # a traced repeat of the same number of steps
+    cs = ClockSampler(dev.index)
+    with cs:
+        ms_local = timed(args.steps)
     barrier(world)
+    for c in ctxs:
+        c.trace(True)
+    timed(args.steps)
     # pixels per rank differ between replicas: the job rate sums the ranks' work
-    ms_total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    ms_total = max_over_ranks(ms_local, world, dev)
     n_px_job = n_px
     if world > 1:
         t = torch.tensor([float(n_px)], dtype=torch.float64, device=dev)
