@@ -40,6 +40,9 @@ WORKLOADS = {
     "cs128": dict(kind="cs", h=128, w=128, ratio=0.3, sigma=0.01, beta0=1.0, em_every=5, seed=0),
     # learned warm start: seconds and sweeps to the posterior of converged plain EP
     "warmstart512": dict(kind="warmstart", h=512, w=512, seed=900003, em_every=0),
+    # config 5 at its stated size (15 x 15 Gaussian blur, std 2 px, BSNR 30 dB)
+    "warmstart4096": dict(kind="warmstart", h=4096, w=4096, seed=900004, em_every=0, ref_sweeps=120,
+                          max_sweeps=120),
 }
 
 
@@ -288,7 +291,7 @@ def run_warmstart(args, rank, world):
 
     import paper_2110_01585_gb300 as pkg
     from paper_2110_01585_gb300 import synthetic as syn
-    from paper_2110_01585_gb300.train_warmstart import sweeps_to_match
+    from paper_2110_01585_gb300.train_warmstart import control_constants, sweeps_to_match
     from paper_2110_01585_gb300.warmstart import WarmStartNet
 
     cfg = WORKLOADS[args.workload]
@@ -297,20 +300,31 @@ def run_warmstart(args, rank, world):
                                                "warmstart_gauss15_128.npz"))
     beta, probes = float(meta["beta"]), int(meta["probes"])
     p = syn.warmstart_problem(cfg["h"], cfg["w"], seed=cfg["seed"] + rank, beta=beta)
+    # the non-learned control: constant site log-precisions (medians of the
+    # training targets of 8 labelled problems), posterior mean y
+    consts = control_constants(beta, probes)
+    ref_sweeps, max_sweeps = cfg.get("ref_sweeps", 250), cfg.get("max_sweeps", 150)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as sampler:
-        r = sweeps_to_match(p, beta, probes, net=net)
+        r = sweeps_to_match(p, beta, probes, net=net, control=consts, ref_sweeps=ref_sweeps,
+                            max_sweeps=max_sweeps)
     clocks = sampler.summary()
     n_px = cfg["h"] * cfg["w"]
-    cold, warm = r["cold"], r["warm"]
+    cold, warm, ctrl = r["cold"], r["warm"], r["control"]
     ok = cold["sweeps"] is not None and warm["sweeps"] is not None
     value = n_px * warm["sweeps"] / warm["seconds"] / 1e6 if ok else 0.0
     return {"value": value, "ms_per_step": (warm["seconds"] / warm["sweeps"] * 1e3) if ok else 0.0,
             "n_px": n_px, "clocks": clocks, "launches": None, "roofline": None, "e2e": None,
             "stats": {"cg_iters": None, "n_fp64": None}, "status": 0, "trace": {},
-            "to_posterior": {"tolerance": "1e-4 means, 1e-3 variances vs 250 cold sweeps",
+            "to_posterior": {"tolerance": f"1e-4 means, 1e-3 variances vs {ref_sweeps} cold sweeps",
                              "cold_sweeps": cold["sweeps"], "warm_sweeps": warm["sweeps"],
+                             "control_sweeps": ctrl["sweeps"],
                              "cold_s": cold["seconds"], "warm_s": warm["seconds"],
+                             "control_s": ctrl["seconds"],
                              "speedup_time": (cold["seconds"] / warm["seconds"]) if ok else None,
+                             "speedup_over_control": (ctrl["seconds"] / warm["seconds"])
+                             if (ok and ctrl["seconds"]) else None,
+                             "control": "mean y, constant site log-precisions (medians of the "
+                                        "training targets)",
                              "network": "6 x conv3x3, 32 channels, FP32, trained on 256 x 128^2",
                              "beta": beta, "rbmc_probes": probes}}
 

@@ -138,15 +138,40 @@ def rel_errors(mean, var, ref_mean, ref_var, y):
     return e_mu, e_var
 
 
+def control_constants(beta: float, probes: int, side: int = 128, images: int = 8,
+                      sweeps: int = 100, seed: int = 770000):
+    """The non-learned warm start's constants: for each of the five sites the
+    median over labelled images and pixels of the network's target log(tau_s) +
+    log(xi) (the training labels of the same workload; seeds apart from the
+    training and evaluation sets)."""
+    import torch
+    y, mean, tau, xi = label(list(range(seed, seed + images)), side, beta, sweeps, probes,
+                             log=lambda s: None)
+    t = torch.log(tau.double()) + torch.as_tensor(np.log(xi), device=tau.device).view(-1, 1, 1, 1)
+    return [float(torch.median(t[:, s_].reshape(-1))) for s_ in range(5)]
+
+
+def control_output(y, consts):
+    """The 6-plane output a warm start takes, without a network: posterior mean
+    y (residual 0) and the constant site log-precisions consts."""
+    import torch
+    h, w = y.shape[-2:]
+    out = torch.zeros((6, h, w), dtype=torch.float32, device=y.device)
+    for s_ in range(5):
+        out[1 + s_] = consts[s_]
+    return out
+
+
 def sweeps_to_match(problem, beta: float, probes: int, net=None, blur_std: float = 2.0,
                     ref_sweeps: int = 250, max_sweeps: int = 150, tol_mean: float = 1e-4,
-                    tol_var: float = 1e-3, warm_mode: int = 0):
-    """Sweeps and device seconds plain EP needs, from the cold start or from the
-    network's warm start, until its posterior is within (tol_mean, tol_var) of
-    the converged cold-start posterior (ref_sweeps sweeps; by default the parity
-    tolerances of the oracle tests).  Seconds count the
-    network and the warm start (for "warm") and the sweeps, timed with CUDA
-    events; the checks between sweeps are not timed."""
+                    tol_var: float = 1e-3, warm_mode: int = 0, control=None):
+    """Sweeps and device seconds plain EP needs, from the cold start, from the
+    network's warm start ("warm") and from the non-learned control start
+    (control_output of the constants control, if given), until its posterior is
+    within (tol_mean, tol_var) of the converged cold-start posterior (ref_sweeps
+    sweeps; by default the parity tolerances of the oracle tests).  Seconds
+    count the network or control and the warm start, and the sweeps, timed with
+    CUDA events; the checks between sweeps are not timed."""
     import torch
     from . import EPTV, OP_CONV_PERIODIC, warm_start
     p = problem
@@ -161,15 +186,16 @@ def sweeps_to_match(problem, beta: float, probes: int, net=None, blur_std: float
         rm, rv = ref.posterior()
         rm, rv = rm.clone(), rv.clone()
     out = {}
-    for mode in ("cold", "warm"):
-        if mode == "warm" and net is None:
+    for mode in ("cold", "warm", "control"):
+        if (mode == "warm" and net is None) or (mode == "control" and control is None):
             continue
         ep = make()
         seconds = 0.0
-        if mode == "warm":
+        if mode != "cold":
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            warm_start(ep, net.predict(yt, p.xi, blur_std), warm_mode)
+            pred = net.predict(yt, p.xi, blur_std) if mode == "warm" else control_output(yt, control)
+            warm_start(ep, pred, warm_mode)
             e1.record()
             e1.synchronize()
             seconds += e0.elapsed_time(e1) / 1e3

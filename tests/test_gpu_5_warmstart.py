@@ -153,22 +153,29 @@ def test_training_lowers_the_loss():
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
 
 
-def test_trained_network_gains_over_cold_start():
+def test_trained_network_against_cold_start_and_control():
     """The network shipped in the package (trained on the GPU by
     train_warmstart on 256 labelled 128^2 problems of the warm-start workload)
-    against plain cold-start EP on a held-out problem: sweeps until the
-    posterior is within the parity tolerances (1e-4 on means, 1e-3 on variances)
-    of the converged cold-start posterior.  Measured on GB300 when the network
-    was trained: 48 sweeps cold, 40 warm."""
+    against plain cold-start EP and against a non-learned control start (mean
+    y, each site at the median of the training targets) on a held-out problem:
+    sweeps and device seconds until the posterior is within the parity
+    tolerances (1e-4 on means, 1e-3 on variances) of the converged cold-start
+    posterior.  Measured on GB300 on three held-out seeds: cold 48/59/60 sweeps,
+    network 40/50/50, control 43/53/54; in time both warm starts are 20-45x
+    faster than the cold start (whose first likelihood-site solves, with a flat
+    cavity, take thousands of CG iterations) and within a few percent of each
+    other.  So most of the gain is that of any sensible initial state; the
+    network adds about 7% fewer sweeps at its training size (none at 512^2)."""
     import os
     import paper_2110_01585_gb300 as pkg
-    from paper_2110_01585_gb300.train_warmstart import sweeps_to_match
+    from paper_2110_01585_gb300.train_warmstart import control_constants, sweeps_to_match
     cuda()
     path = os.path.join(os.path.dirname(pkg.__file__), "data", "warmstart_gauss15_128.npz")
     net, meta = WarmStartNet.load(path)
     beta, probes = float(meta["beta"]), int(meta["probes"])
     p = syn.warmstart_problem(128, 128, seed=900002, beta=beta)
-    r = sweeps_to_match(p, beta, probes, net=net)
-    cold, warm = r["cold"]["sweeps"], r["warm"]["sweeps"]
-    assert cold is not None and warm is not None, r
-    assert warm < cold, r
+    r = sweeps_to_match(p, beta, probes, net=net, control=control_constants(beta, probes))
+    cold, warm, ctrl = r["cold"], r["warm"], r["control"]
+    assert None not in (cold["sweeps"], warm["sweeps"], ctrl["sweeps"]), r
+    assert warm["sweeps"] < ctrl["sweeps"] < cold["sweeps"], r
+    assert warm["seconds"] < 0.1 * cold["seconds"] and ctrl["seconds"] < 0.1 * cold["seconds"], r
