@@ -38,6 +38,9 @@ WORKLOADS = {
                         seed=0, n_rect=40),
     "batched256": dict(kind="batch", n=256, h=None, w=None, em_every=5, beta0=1.0, S=32, seed=0),
     "cs128": dict(kind="cs", h=128, w=128, ratio=0.3, sigma=0.01, beta0=1.0, em_every=5, seed=0),
+    # the same size with M uniformly drawn 2-D Hadamard patterns in place of the Gaussian rows
+    "cs128h": dict(kind="cs", op="hadamard", h=128, w=128, ratio=0.3, sigma=0.01, beta0=1.0,
+                   em_every=5, seed=0),
     # learned warm start: seconds and sweeps to the posterior of converged plain EP
     "warmstart512": dict(kind="warmstart", h=512, w=512, seed=900003, em_every=0),
     # config 5 at its stated size (15 x 15 Gaussian blur, std 2 px, BSNR 30 dB)
@@ -90,6 +93,9 @@ def _problem(cfg, rank=0):
         k = syn.uniform_kernel(cfg["kernel"][1])
         return syn.deconv_problem(cfg["h"], cfg["w"], kernel=k, bsnr_db=cfg["bsnr_db"],
                                   beta0=cfg["beta0"], seed=seed)
+    if cfg["kind"] == "cs" and cfg.get("op") == "hadamard":
+        return syn.hadamard_cs_problem(cfg["h"], cfg["w"], ratio=cfg["ratio"], sigma=cfg["sigma"],
+                                       beta0=cfg["beta0"], seed=seed)
     if cfg["kind"] == "cs":
         return syn.cs_problem(cfg["h"], cfg["w"], ratio=cfg["ratio"], sigma=cfg["sigma"],
                               beta0=cfg["beta0"], seed=seed)
@@ -333,7 +339,8 @@ def run_ours(args, rank, world):
     import numpy as np
     import torch
 
-    from paper_2110_01585_gb300 import EPTV, OP_CONV_PERIODIC, OP_DENSE, OP_IDENTITY, solve_host
+    from paper_2110_01585_gb300 import (EPTV, OP_CONV_PERIODIC, OP_DENSE, OP_HADAMARD, OP_IDENTITY,
+                                        solve_host)
 
     cfg = WORKLOADS[args.workload]
     if cfg["kind"] == "batch":
@@ -350,7 +357,9 @@ def run_ours(args, rank, world):
     if cfg["kind"] == "deconv":
         kw = dict(op=OP_CONV_PERIODIC, kernel=prob.kernel, rbmc_samples=cfg["S"])
     with torch.cuda.stream(stream):
-        if cfg["kind"] == "cs":
+        if cfg["kind"] == "cs" and cfg.get("op") == "hadamard":
+            kw = dict(op=OP_HADAMARD, patterns=prob.patterns, height=cfg["h"], width=cfg["w"])
+        elif cfg["kind"] == "cs":
             At = torch.as_tensor(prob.A.astype(np.float32), device=dev)
             kw = dict(op=OP_DENSE, dense=At, height=cfg["h"], width=cfg["w"])
         yt = torch.as_tensor(prob.y.astype(np.float32), device=dev)
@@ -436,7 +445,7 @@ def run_ours(args, rank, world):
         if cfg["kind"] == "deconv":
             extra = dict(op=OP_CONV_PERIODIC, kernel=prob.kernel, rbmc_samples=cfg["S"])
         if cfg["kind"] == "cs":
-            extra = dict(op=OP_DENSE, dense=At, height=cfg["h"], width=cfg["w"])
+            extra = dict(kw)  # the host call copies y; the operator is the same
         solve_host(y32, prob.xi, prob.beta, n_e2e, em_every=em_every, **extra)
         t1 = time.perf_counter()
         e2e = {"value": round(n_px * n_e2e / (t1 - t0) / 1e6, 3), "unit": "Mpixel-EP-sweeps/s",
@@ -472,6 +481,14 @@ def run_oracle_sample(cfg, budget_s=20.0):
         o = EPOracle("deconv", p.y, p.xi, p.beta, side, side, kernel=p.kernel, site0="rbmc_cg",
                      probes=pr)
         sample = f"{side}x{side} instance of the warm-start workload, CG mode"
+    elif cfg["kind"] == "cs" and cfg.get("op") == "hadamard":
+        from oracle import operators
+        side = 64
+        p = syn.hadamard_cs_problem(side, side, ratio=cfg["ratio"], sigma=cfg["sigma"],
+                                    beta0=cfg["beta0"], seed=cfg["seed"])
+        A = operators.hadamard_matrix(side, side, p.patterns)
+        o = EPOracle("cs", p.y, p.xi, p.beta, side, side, A=A, site0="woodbury")
+        sample = f"{side}x{side} instance (M = {A.shape[0]} Hadamard patterns) of the same generator"
     elif cfg["kind"] == "cs":
         side = 64
         p = syn.cs_problem(side, side, ratio=cfg["ratio"], sigma=cfg["sigma"], beta0=cfg["beta0"],
@@ -529,7 +546,9 @@ def main():
               "l2": "flushed before every timed step (256 MB write, untimed)"}
     if cfg["kind"] == "cs":
         config.update(m=int(0.3 * cfg["h"] * cfg["w"]), sigma=cfg["sigma"], beta0=cfg["beta0"],
-                      em_every=cfg["em_every"], precision="Woodbury in FP64")
+                      em_every=cfg["em_every"], precision="Woodbury in FP64",
+                      operator=("subsampled 2-D Hadamard (uniform patterns)"
+                                if cfg.get("op") == "hadamard" else "dense Gaussian N(0, 1/M)"))
     elif cfg["kind"] == "batch":
         config.update(problems=cfg["n"], sides="log-uniform 64..1024, even",
                       sigma="U[0.02, 0.2]", blur_widths=[1, 5, 9, 15], em_every=cfg["em_every"],

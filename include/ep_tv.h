@@ -58,24 +58,36 @@ typedef enum {
   EP_TV_ERR_UNSUPPORTED = 8   /* valid request this build does not implement */
 } ep_tv_status;
 
-/* Degradation operators (Sec. II-A): (i) identity, (ii) convolution, (iii) dense. */
+/* Degradation operators (Sec. II-A): (i) identity, (ii) convolution, (iii) compressive
+   sensing with a dense matrix or with subsampled 2-D Hadamard patterns. */
 typedef enum {
   EP_TV_OP_IDENTITY = 0,        /* denoising, M = N */
   EP_TV_OP_CONV_PERIODIC = 1,   /* periodic convolution with a centred odd kernel, M = N */
-  EP_TV_OP_DENSE = 2            /* compressive sensing, dense M x N matrix; the likelihood
+  EP_TV_OP_DENSE = 2,           /* compressive sensing, dense M x N matrix; the likelihood
                                    site uses the Woodbury identity in FP64 */
+  EP_TV_OP_HADAMARD = 3         /* compressive sensing with M rows of the 2-D Walsh-Hadamard
+                                   matrix (Sec. II-A (iii), single-pixel imaging); Woodbury
+                                   in FP64 with fast transforms in place of the dense products */
 } ep_tv_op;
 
 typedef struct {
   int32_t op;            /* ep_tv_op */
   int32_t height;        /* image rows H >= 1 */
   int32_t width;         /* image columns W >= 1 */
-  int32_t m;             /* length of y: N for IDENTITY and CONV_PERIODIC, M for DENSE */
+  int32_t m;             /* length of y: N for IDENTITY and CONV_PERIODIC, M for DENSE and
+                            HADAMARD */
   const float* kernel;   /* CONV_PERIODIC: HOST pointer, kh x kw row-major, copied at init.
                             (H x)[r,c] = sum_{a,b} k[a,b] x[(r-a+kh/2) mod H, (c-b+kw/2) mod W] */
   int32_t kh, kw;        /* odd kernel sizes, kh <= H, kw <= W */
   const float* dense;    /* DENSE: DEVICE pointer, M x N row-major.  Borrowed: it must stay
                             valid and unchanged for the life of the context. */
+  const int32_t* patterns; /* HADAMARD: HOST pointer, M distinct pattern indices, copied at
+                            init.  H and W must be powers of two.  Pattern p = kr * W + kc is
+                            the outer product of the Walsh functions of sequency kr (length H)
+                            and kc (length W), Paley order: entry (r, c) is
+                            (-1)^(popcount(r & rev(kr)) + popcount(c & rev(kc))), rev reversing
+                            the log2 H (log2 W) index bits.  Row m of A is pattern p_m over
+                            sqrt(M), so that A A^T = (N / M) I. */
 } ep_tv_operator;
 
 /* Edge factor phi(x_i - x_j; theta) of the prior (Sec. II-B). */

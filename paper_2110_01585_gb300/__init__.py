@@ -15,9 +15,11 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import OP_CONV_PERIODIC, OP_DENSE, OP_IDENTITY, PRIOR_BG, PRIOR_L1, PRIOR_MOG2, EPTVError
+from ._lib import (OP_CONV_PERIODIC, OP_DENSE, OP_HADAMARD, OP_IDENTITY, PRIOR_BG, PRIOR_L1, PRIOR_MOG2,
+                   EPTVError)
 
 __all__ = ["EPTV", "Batch", "solve_host", "EPTVError", "OP_IDENTITY", "OP_CONV_PERIODIC", "OP_DENSE",
+           "OP_HADAMARD",
            "PRIOR_L1", "PRIOR_MOG2", "PRIOR_BG",
            "default_params"]
 
@@ -40,25 +42,33 @@ def default_params(**kw) -> _lib.Params:
     return p
 
 
-def _operator(op: int, height: int, width: int, m: int, kernel=None, dense=None):
+def _operator(op: int, height: int, width: int, m: int, kernel=None, dense=None, patterns=None):
     o = _lib.Operator()
     o.op, o.height, o.width, o.m = op, height, width, m
-    keep = None
+    keep = []
     if kernel is not None:
-        keep = np.ascontiguousarray(kernel, dtype=np.float32)
-        o.kernel = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-        o.kh, o.kw = keep.shape
+        k = np.ascontiguousarray(kernel, dtype=np.float32)
+        o.kernel = k.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        o.kh, o.kw = k.shape
+        keep.append(k)
     if dense is not None:
         o.dense = ctypes.c_void_p(dense.data_ptr())
+    if patterns is not None:
+        pt = np.ascontiguousarray(patterns, dtype=np.int32)
+        o.patterns = pt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        keep.append(pt)
     return o, keep
 
 
 class EPTV:
     """One restoration problem on the GPU (wraps an ``ep_tv_ctx``).
 
-    y: CUDA float32 tensor, (H, W) for identity/convolution, (M,) for dense.
+    y: CUDA float32 tensor, (H, W) for identity/convolution, (M,) for dense and
+        Hadamard sensing.
     kernel: host array (kh, kw) for the periodic convolution.
     dense: CUDA float32 tensor (M, N) for compressive sensing; kept alive here.
+    patterns: host integer array of M Paley-ordered pattern indices p = kr * W + kc
+        for the subsampled Hadamard operator (op=OP_HADAMARD).
     xi_plane: CUDA float32 tensor of M noise variances (a diagonal noise
         covariance, ep_tv_init_noise); xi is then ignored.
     stream: torch.cuda.Stream (default: the current stream).
@@ -66,7 +76,8 @@ class EPTV:
     """
 
     def __init__(self, y, xi: float, beta: float, op: int = OP_IDENTITY, height: int = None,
-                 width: int = None, kernel=None, dense=None, stream=None, xi_plane=None, **params):
+                 width: int = None, kernel=None, dense=None, stream=None, xi_plane=None,
+                 patterns=None, **params):
         torch = _torch()
         self._lib = _lib.load()
         if not (isinstance(y, torch.Tensor) and y.is_cuda and y.dtype == torch.float32):
@@ -81,7 +92,8 @@ class EPTV:
         self.device = y.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(y.device)
         self._dense = dense.contiguous() if dense is not None else None
-        o, self._kernel_keep = _operator(op, self.height, self.width, y.numel(), kernel, self._dense)
+        o, self._kernel_keep = _operator(op, self.height, self.width, y.numel(), kernel, self._dense,
+                                         patterns)
         self.params = default_params(xi=float(xi), beta=float(beta), **params)
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -269,7 +281,8 @@ class Batch:
 
 
 def solve_host(y: np.ndarray, xi: float, beta: float, n_sweeps: int, em_every: int = 0,
-               op: int = OP_IDENTITY, kernel=None, dense=None, height=None, width=None, **params):
+               op: int = OP_IDENTITY, kernel=None, dense=None, height=None, width=None,
+               patterns=None, **params):
     """One complete restoration from host memory (``ep_tv_solve_host``).
 
     Returns (mean, var, beta) as numpy arrays / float.
@@ -278,7 +291,7 @@ def solve_host(y: np.ndarray, xi: float, beta: float, n_sweeps: int, em_every: i
     y = np.ascontiguousarray(y, dtype=np.float32)
     if height is None or width is None:
         height, width = y.shape
-    o, keep = _operator(op, int(height), int(width), y.size, kernel, dense)
+    o, keep = _operator(op, int(height), int(width), y.size, kernel, dense, patterns)
     p = default_params(xi=float(xi), beta=float(beta), **params)
     mean = np.empty((height, width), np.float32)
     var = np.empty((height, width), np.float32)

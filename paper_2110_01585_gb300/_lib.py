@@ -18,7 +18,7 @@ STATUS_NAMES = {
     7: "EP_TV_ERR_STATE", 8: "EP_TV_ERR_UNSUPPORTED",
 }
 
-OP_IDENTITY, OP_CONV_PERIODIC, OP_DENSE = 0, 1, 2
+OP_IDENTITY, OP_CONV_PERIODIC, OP_DENSE, OP_HADAMARD = 0, 1, 2, 3
 PRIOR_L1, PRIOR_MOG2, PRIOR_BG = 0, 1, 2
 KERNELS = {0: "prior_sweep", 1: "cg_direction", 2: "cg_update", 3: "cg_residual", 4: "site0",
            5: "cg_precond", 6: "cs_woodbury", 7: "cg_commit"}
@@ -30,7 +30,8 @@ c_void_p, c_int32, c_double, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.
 class Operator(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("m", ctypes.c_int32), ("kernel", ctypes.POINTER(ctypes.c_float)),
-                ("kh", ctypes.c_int32), ("kw", ctypes.c_int32), ("dense", ctypes.c_void_p)]
+                ("kh", ctypes.c_int32), ("kw", ctypes.c_int32), ("dense", ctypes.c_void_p),
+                ("patterns", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Block(ctypes.Structure):

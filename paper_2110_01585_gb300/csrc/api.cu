@@ -127,6 +127,17 @@ ep_tv_status check_params(const ep_tv_operator* op, const ep_tv_params* p) {
     case EP_TV_OP_DENSE:
       if (op->m < 1 || !op->dense) return EP_TV_ERR_ARG;
       break;
+    case EP_TV_OP_HADAMARD: {
+      if (op->m < 1 || op->m > n || !op->patterns) return EP_TV_ERR_ARG;
+      if ((op->height & (op->height - 1)) || (op->width & (op->width - 1))) return EP_TV_ERR_ARG;
+      std::vector<char> seen((size_t)n, 0);  // M distinct indices in [0, N)
+      for (int i = 0; i < op->m; ++i) {
+        const int32_t q = op->patterns[i];
+        if (q < 0 || q >= n || seen[q]) return EP_TV_ERR_ARG;
+        seen[q] = 1;
+      }
+      break;
+    }
     default:
       return EP_TV_ERR_ARG;
   }
@@ -318,6 +329,7 @@ ep_tv_status ep_tv_init(const ep_tv_operator* op, const float* y, const ep_tv_pa
   ep_tv_ctx* c = new (std::nothrow) ep_tv_ctx();
   if (!c) return EP_TV_ERR_NOMEM;
   c->op = *op;
+  c->op.patterns = nullptr;  // copied into the likelihood state below; not kept
   c->p = *p;
   c->height = op->height;
   c->width = op->width;
@@ -740,7 +752,7 @@ ep_tv_status ep_tv_reset(ep_tv_ctx* c) {
 }
 
 ep_tv_status ep_tv_warm_start(ep_tv_ctx* c, const float* out, int32_t mode) {
-  if (!c || !out || c->op.op == EP_TV_OP_DENSE) return EP_TV_ERR_ARG;
+  if (!c || !out || c->op.op == EP_TV_OP_DENSE || c->op.op == EP_TV_OP_HADAMARD) return EP_TV_ERR_ARG;
   if (mode != EP_TV_WARM_ALL_SITES && mode != EP_TV_WARM_SITE0 && mode != EP_TV_WARM_PRIOR)
     return EP_TV_ERR_ARG;
   if (c->failed) return EP_TV_ERR_STATE;

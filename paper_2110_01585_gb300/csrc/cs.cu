@@ -12,6 +12,17 @@
 // to within 1e-4 of 1; an FP32 or BF16 factorisation loses every digit of
 // 1 - c_i w_i there.  GB300's FP64 rate is low, so this path is ALU-bound.
 //
+// Subsampled 2-D Hadamard operator (Sec. II-A (iii)): A = S W / sqrt(M), W the
+// N x N Walsh-Hadamard matrix in Sylvester order (entry (a, b) = (-1)^popcount(a & b),
+// the Kronecker product of the row and column matrices), S the M selected rows
+// s_1..s_M.  Walsh functions multiply by XOR of their indices, so
+//   K[m, m'] = xi delta + (1/M) sum_i W[s_m, i] W[s_m', i] c_i = xi delta + (W c)[s_m ^ s_m'] / M:
+// one fast transform of c and a gather form K, with no GEMM.  And
+//   W_A = L^{-1} A = (L^{-1} S) W / sqrt(M):
+// the triangular inverse L^{-1} scattered to the selected columns, then one fast
+// transform per row, in place of the M x N triangular solve.  The mean uses
+// A m = (W m)[s] / sqrt(M) and W_A^T.  Same FP64 precision as the dense path.
+//
 // Kernels: an FP64 tiled GEMM (C -= A B^T or C -= A B, 64 x 64 tiles, 4 x 4 per
 // thread), used for K, the trailing updates of a blocked right-looking Cholesky
 // and the block updates of the triangular solve; a 64 x 64 Cholesky of one
@@ -283,6 +294,97 @@ __global__ void cs_site0_kernel(const double* w, const double* g, const double* 
   if (capped) atomicAdd(&counters[DC_CAPPED], (unsigned long long)capped);
 }
 
+// ---- Hadamard operator
+//
+// Fast Walsh-Hadamard transform (Sylvester order, unnormalised) of rows of n
+// doubles, n a power of two: one row per block in shared memory (n <= 16384), the
+// butterflies (a, b) -> (a + b, a - b) at strides 1, 2, 4, ...
+constexpr int kFwhtThreads = 1024;
+constexpr int kFwhtMaxSmem = 16384;
+
+__global__ void __launch_bounds__(kFwhtThreads) fwht_rows_smem_kernel(double* rows, int n) {
+  extern __shared__ double v[];
+  double* row = rows + (long long)blockIdx.x * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = row[i];
+  __syncthreads();
+  for (int h = 1; h < n; h <<= 1) {
+    for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+      const int i = (t / h) * 2 * h + (t % h), j = i + h;
+      const double a = v[i], b = v[j];
+      v[i] = a + b;
+      v[j] = a - b;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] = v[i];
+}
+
+// One butterfly stage (stride h) over rows rows of n doubles in global memory.
+__global__ void fwht_stage_kernel(double* rows, int n, int h, long long pairs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pairs;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / (n / 2);
+    const int t = (int)(e - r * (n / 2));
+    const int i = (t / h) * 2 * h + (t % h);
+    double* row = rows + r * n;
+    const double a = row[i], b = row[i + h];
+    row[i] = a + b;
+    row[i + h] = a - b;
+  }
+}
+
+// K = diag(xi) + (W c)[s_m ^ s_m'] / M, from wc = W c.
+__global__ void hadamard_k_kernel(double* K, int M, const int* sel, const double* wc, double xi,
+                                  const double* xi_v) {
+  const long long total = (long long)M * M;
+  const double inv_m = 1.0 / (double)M;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / M), j = (int)(e - (long long)i * M);
+    double v = wc[sel[i] ^ sel[j]] * inv_m;
+    if (i == j) v += xi_v ? xi_v[i] : xi;
+    K[e] = v;
+  }
+}
+
+// X = I (M x M)
+__global__ void identity_kernel(double* X, int M) {
+  const long long total = (long long)M * M;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / M), j = (int)(e - (long long)i * M);
+    X[e] = i == j ? 1.0 : 0.0;
+  }
+}
+
+// G = 0, then G[m, s_j] = Z[m, j] / sqrt(M) for the lower triangle of Z (L^{-1} is lower).
+__global__ void hadamard_scatter_kernel(const double* Z, int M, const int* sel, double* G, int N) {
+  const long long total = (long long)M * M;
+  const double scale = 1.0 / sqrt((double)M);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / M), j = (int)(e - (long long)i * M);
+    if (j <= i) G[(long long)i * N + sel[j]] = Z[e] * scale;
+  }
+}
+
+// t = y - (W m)[s] / sqrt(M), from wm = W m.
+__global__ void hadamard_resid_kernel(const float* y, const double* wm, const int* sel, int M,
+                                      double* t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) t[i] = (double)y[i] - wm[sel[i]] / sqrt((double)M);
+}
+
+// v[s_m] = y_m (v zeroed before): the input of the back-projection A^T y.
+__global__ void hadamard_place_kernel(const float* y, const int* sel, int M, double* v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) v[sel[i]] = (double)y[i];
+}
+__global__ void to_f32_scaled_kernel(const double* in, float* out, int n, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)(in[i] * scale);
+}
+
 // mu0 = A^T y (one thread per column, FP64 accumulation)
 __global__ void aty_kernel(const float* A, const float* y, int M, int N, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,6 +397,19 @@ __global__ void aty_kernel(const float* A, const float* y, int M, int N, float* 
 inline int g1d(long long n) {
   long long b = (n + 255) / 256;
   return (int)std::min<long long>(std::max<long long>(b, 1), 1 << 20);
+}
+
+// Unnormalised fast Walsh-Hadamard transform of nrows contiguous rows of n doubles:
+// the strides below kFwhtMaxSmem in shared memory (one block per chunk of that
+// length; the chunks tile every row), the larger strides one global pass each.
+void fwht_rows(double* rows, long long nrows, int n, cudaStream_t s) {
+  if (n < 2 || nrows < 1) return;
+  const int chunk = std::min(n, kFwhtMaxSmem);
+  const int threads = std::min(kFwhtThreads, std::max(32, chunk / 2));
+  fwht_rows_smem_kernel<<<(unsigned)(nrows * (n / chunk)), threads, sizeof(double) * chunk, s>>>(
+      rows, chunk);
+  const long long pairs = nrows * (n / 2);
+  for (int h = chunk; h < n; h <<= 1) fwht_stage_kernel<<<g1d(pairs), 256, 0, s>>>(rows, n, h, pairs);
 }
 
 void gemm(bool nt, int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C,
@@ -313,6 +428,7 @@ void gemm(bool nt, int m, int n, int k, const double* A, int lda, const double* 
 
 struct CsState {
   int M = 0, N = 0;
+  bool hadamard = false;      // subsampled Hadamard rows in place of the dense matrix
   double xi = 0.0;
   float damping = 0.5f, min_tau = 1e-8f;
   const float* A = nullptr;   // borrowed, M x N FP32
@@ -327,6 +443,8 @@ struct CsState {
   double* g = nullptr;
   double* t = nullptr;        // M
   double* xi_v = nullptr;     // M noise variances (diagonal noise covariance), or NULL
+  int* sel = nullptr;         // Hadamard: M Sylvester row indices
+  double* Z = nullptr;        // Hadamard: M x M, L^{-1}
 };
 
 namespace {
@@ -342,7 +460,87 @@ void cs_free(CsState* S) {
   cudaFree(S->g);
   cudaFree(S->t);
   cudaFree(S->xi_v);
+  cudaFree(S->sel);
+  cudaFree(S->Z);
   delete S;
+}
+
+unsigned bit_reverse(unsigned k, int bits) {
+  unsigned out = 0;
+  for (int i = 0; i < bits; ++i)
+    if (k >> i & 1u) out |= 1u << (bits - 1 - i);
+  return out;
+}
+
+int log2_exact(int v) {
+  int b = 0;
+  while ((1 << b) < v) ++b;
+  return (1 << b) == v ? b : -1;
+}
+
+// Hadamard operator: Sylvester row of every Paley-ordered pattern, the buffers,
+// and mu0 = A^T y = W (S^T y) / sqrt(M).
+ep_tv_status hadamard_create(const LikelihoodConfig& cfg, CsState* S, cudaStream_t s, float* mu0) {
+  const int hb = log2_exact(cfg.height), wb = log2_exact(cfg.width);
+  const int M = S->M, N = S->N;
+  if (hb < 0 || wb < 0 || !cfg.op->patterns || M > N) return EP_TV_ERR_ARG;
+  std::vector<int> sel(M);  // the patterns are distinct and in [0, N) (checked at init)
+  for (int i = 0; i < M; ++i) {
+    const int p = cfg.op->patterns[i];
+    const unsigned kr = (unsigned)(p / cfg.width), kc = (unsigned)(p % cfg.width);
+    sel[i] = (int)((bit_reverse(kr, hb) << wb) | bit_reverse(kc, wb));
+  }
+  const long long MN = (long long)M * N;
+  bool ok = cudaMalloc(&S->G, sizeof(double) * MN) == cudaSuccess &&
+            cudaMalloc(&S->K, sizeof(double) * (long long)M * M) == cudaSuccess &&
+            cudaMalloc(&S->Z, sizeof(double) * (long long)M * M) == cudaSuccess &&
+            cudaMalloc(&S->sel, sizeof(int) * M) == cudaSuccess &&
+            cudaMalloc(&S->c, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&S->sqc, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&S->m, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&S->w, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&S->g, sizeof(double) * N) == cudaSuccess &&
+            cudaMalloc(&S->t, sizeof(double) * M) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return EP_TV_ERR_NOMEM;
+  }
+  if (cudaFuncSetAttribute(fwht_rows_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(double) * kFwhtMaxSmem) != cudaSuccess ||
+      cudaMemcpyAsync(S->sel, sel.data(), sizeof(int) * M, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(S->g, 0, sizeof(double) * N, s) != cudaSuccess)
+    return EP_TV_ERR_CUDA;
+  // the host vector must outlive the copy
+  if (cudaStreamSynchronize(s) != cudaSuccess) return EP_TV_ERR_CUDA;
+  hadamard_place_kernel<<<(M + 255) / 256, 256, 0, s>>>(S->y, S->sel, M, S->g);
+  fwht_rows(S->g, 1, N, s);
+  to_f32_scaled_kernel<<<(N + 255) / 256, 256, 0, s>>>(S->g, mu0, N, 1.0 / std::sqrt((double)M));
+  return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
+}
+
+// X = L^{-1} X in place for the M x ncols block X (ld ldx), L the lower factor in K:
+// blocked forward substitution, the block updates as GEMMs.
+void forward_solve(const double* L, int M, double* X, int ldx, int ncols, cudaStream_t s) {
+  for (int k0 = 0; k0 < M; k0 += kNb) {
+    const int b = std::min(kNb, M - k0);
+    if (k0 > 0)  // X[k0:k0+b, :] -= L[k0:k0+b, 0:k0] X[0:k0, :]
+      gemm(false, b, ncols, k0, L + (long long)k0 * M, M, X, ldx, X + (long long)k0 * ldx, ldx, 1.0,
+           -1.0, false, s);
+    trsm_block_cols_kernel<<<(ncols + 127) / 128, 128, 0, s>>>(L, M, k0, b, X, ldx, ncols);
+  }
+}
+
+// Z = L^{-1}: forward substitution on the identity; L^{-1} is lower triangular, so
+// block row k0 only involves columns 0 .. k0 + b.
+void lower_inverse(const double* L, int M, double* Z, cudaStream_t s) {
+  identity_kernel<<<g1d((long long)M * M), 256, 0, s>>>(Z, M);
+  for (int k0 = 0; k0 < M; k0 += kNb) {
+    const int b = std::min(kNb, M - k0);
+    if (k0 > 0)
+      gemm(false, b, k0, k0, L + (long long)k0 * M, M, Z, M, Z + (long long)k0 * M, M, 1.0, -1.0,
+           false, s);
+    trsm_block_cols_kernel<<<(k0 + b + 127) / 128, 128, 0, s>>>(L, M, k0, b, Z, M, k0 + b);
+  }
 }
 
 }  // namespace
@@ -358,6 +556,16 @@ ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** ou
   S->min_tau = (float)(1.0 / cfg.p->var_cap);
   S->A = cfg.op->dense;
   S->y = cfg.y;
+  if (cfg.op->op == EP_TV_OP_HADAMARD) {
+    S->hadamard = true;
+    const ep_tv_status st = hadamard_create(cfg, S, s, mu0);
+    if (st != EP_TV_OK) {
+      cs_free(S);
+      return st;
+    }
+    *out = S;
+    return EP_TV_OK;
+  }
   const long long MN = (long long)S->M * S->N;
   bool ok = cudaMalloc(&S->A64, sizeof(double) * MN) == cudaSuccess &&
             cudaMalloc(&S->G, sizeof(double) * MN) == cudaSuccess &&
@@ -404,10 +612,18 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
   const long long MN = (long long)M * N;
   tr->begin(EP_TV_K_CS, s);
   cs_cavity_kernel<<<g1d(N), 256, 0, s>>>(tp, np, N, S->c, S->sqc, S->m);
-  // K = xi I + (A C^{1/2})(A C^{1/2})^T, lower triangle
-  scale_cols_kernel<<<g1d(MN), 256, 0, s>>>(S->A, S->sqc, S->G, M, N);
-  init_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->xi, S->xi_v);
-  gemm(true, M, M, N, S->G, N, S->G, N, S->K, M, 1.0, 1.0, true, s);
+  if (S->hadamard) {
+    // K = diag(xi) + (W c)[s_m ^ s_m'] / M
+    if (cudaMemcpyAsync(S->g, S->c, sizeof(double) * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return EP_TV_ERR_CUDA;
+    fwht_rows(S->g, 1, N, s);
+    hadamard_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->sel, S->g, S->xi, S->xi_v);
+  } else {
+    // K = xi I + (A C^{1/2})(A C^{1/2})^T, lower triangle
+    scale_cols_kernel<<<g1d(MN), 256, 0, s>>>(S->A, S->sqc, S->G, M, N);
+    init_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->xi, S->xi_v);
+    gemm(true, M, M, N, S->G, N, S->G, N, S->K, M, 1.0, 1.0, true, s);
+  }
   // blocked right-looking Cholesky K = L L^T (lower)
   for (int k0 = 0; k0 < M; k0 += kNb) {
     const int b = std::min(kNb, M - k0);
@@ -421,25 +637,30 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
            true, s);
     }
   }
-  // W = L^{-1} A (blocked forward substitution on all N columns), into G
-  if (cudaMemcpyAsync(S->G, S->A64, sizeof(double) * MN, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return EP_TV_ERR_CUDA;
-  for (int k0 = 0; k0 < M; k0 += kNb) {
-    const int b = std::min(kNb, M - k0);
-    if (k0 > 0)  // X[k0:k0+b, :] -= L[k0:k0+b, 0:k0] X[0:k0, :]
-      gemm(false, b, N, k0, S->K + (long long)k0 * M, M, S->G, N, S->G + (long long)k0 * N, N, 1.0,
-           -1.0, false, s);
-    trsm_block_cols_kernel<<<(N + 127) / 128, 128, 0, s>>>(S->K, M, k0, b, S->G, N, N);
+  if (S->hadamard) {
+    // W = (L^{-1} S) W_N / sqrt(M): the lower inverse scattered to the selected
+    // columns, then a fast transform of every row
+    lower_inverse(S->K, M, S->Z, s);
+    if (cudaMemsetAsync(S->G, 0, sizeof(double) * MN, s) != cudaSuccess) return EP_TV_ERR_CUDA;
+    hadamard_scatter_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->Z, M, S->sel, S->G, N);
+    fwht_rows(S->G, M, N, s);
+  } else {
+    // W = L^{-1} A (blocked forward substitution on all N columns), into G
+    if (cudaMemcpyAsync(S->G, S->A64, sizeof(double) * MN, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return EP_TV_ERR_CUDA;
+    forward_solve(S->K, M, S->G, N, N, s);
   }
   colsq_kernel<<<(N + 255) / 256, 256, 0, s>>>(S->G, M, N, S->w);
   // mean: t = y - A m, v = L^{-1} t, g = W^T v, E = m + c g
-  resid_vec_kernel<<<(M + 7) / 8, 256, 0, s>>>(S->A, S->y, S->m, M, N, S->t);
-  for (int k0 = 0; k0 < M; k0 += kNb) {
-    const int b = std::min(kNb, M - k0);
-    if (k0 > 0) gemm(false, b, 1, k0, S->K + (long long)k0 * M, M, S->t, 1, S->t + k0, 1, 1.0, -1.0,
-                     false, s);
-    trsm_block_cols_kernel<<<1, 128, 0, s>>>(S->K, M, k0, b, S->t, 1, 1);
+  if (S->hadamard) {
+    if (cudaMemcpyAsync(S->g, S->m, sizeof(double) * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return EP_TV_ERR_CUDA;
+    fwht_rows(S->g, 1, N, s);
+    hadamard_resid_kernel<<<(M + 255) / 256, 256, 0, s>>>(S->y, S->g, S->sel, M, S->t);
+  } else {
+    resid_vec_kernel<<<(M + 7) / 8, 256, 0, s>>>(S->A, S->y, S->m, M, N, S->t);
   }
+  forward_solve(S->K, M, S->t, 1, 1, s);
   wtv_kernel<<<(N + 255) / 256, 256, 0, s>>>(S->G, S->t, M, N, S->g);
   cs_site0_kernel<<<g1d(N), 256, 0, s>>>(S->w, S->g, S->c, S->m, N, tau0, nu0, S->min_tau, S->damping,
                                          status, counters);
@@ -449,6 +670,11 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
 
 double cs_flops(const CsState* S) {
   const double M = S->M, N = S->N;
+  if (S->hadamard) {
+    // K from one transform, Cholesky, the lower inverse, M row transforms, column sums, mean
+    const double lg = std::log2(N);
+    return N * lg + M * M * M / 3.0 + M * M * M / 3.0 + M * N * lg + 2.0 * M * N + 4.0 * M * N;
+  }
   // K (lower half of G G^T), Cholesky, W = L^{-1} A, column sums and the mean
   return M * M * N + M * M * M / 3.0 + M * M * N + 2.0 * M * N + 4.0 * M * N;
 }

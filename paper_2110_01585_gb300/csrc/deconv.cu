@@ -1959,7 +1959,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
                                float* mu0) {
   *out = nullptr;
   const ep_tv_operator* op = cfg.op;
-  if (op->op == EP_TV_OP_DENSE) {
+  if (op->op == EP_TV_OP_DENSE || op->op == EP_TV_OP_HADAMARD) {
     LikelihoodState* L = new (std::nothrow) LikelihoodState();
     if (!L) return EP_TV_ERR_NOMEM;
     ep_tv_status st = cs_create(cfg, s, &L->cs, mu0);

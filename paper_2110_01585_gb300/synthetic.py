@@ -47,6 +47,7 @@ class Problem:
     kernel: Optional[np.ndarray] = None   # (kh, kw) blur kernel, deconv only
     A: Optional[np.ndarray] = None        # (M, N) sensing matrix, cs only
     seed: int = 0
+    patterns: Optional[np.ndarray] = None  # Hadamard CS: the M selected pattern indices
 
     @property
     def shape(self):
@@ -222,6 +223,39 @@ def cs_problem(h: int = 128, w: int = 128, ratio: float = 0.3, sigma: float = 0.
     A = rng.standard_normal((m, n)) / math.sqrt(m)
     y = A @ x.reshape(-1) + sigma * rng.standard_normal(m)
     return Problem("cs", x, y, sigma * sigma, beta0, A=A, seed=seed)
+
+
+def _fwht(v: np.ndarray) -> np.ndarray:
+    """Unnormalised Walsh-Hadamard transform of a vector of power-of-two length
+    (Sylvester order): out[a] = sum_b (-1)^popcount(a & b) v[b]."""
+    out = np.array(v, dtype=np.float64)
+    n, h = out.size, 1
+    while h < n:
+        out = out.reshape(-1, 2, h)
+        out = np.stack([out[:, 0] + out[:, 1], out[:, 0] - out[:, 1]], axis=1).reshape(-1)
+        h *= 2
+    return out
+
+
+def _bitrev(k: int, bits: int) -> int:
+    return int(format(k, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+def hadamard_cs_problem(h: int = 128, w: int = 128, ratio: float = 0.3, sigma: float = 0.01,
+                        beta0: float = 1.0, seed: int = 0) -> Problem:
+    """Compressive sensing with M uniformly chosen patterns of the 2-D Hadamard
+    matrix (Paley-ordered indices p = kr * w + kc), scaled by 1/sqrt(M): the
+    observation y = H x + n computed with a fast transform (Sylvester row =
+    bit-reversed Paley index along each axis)."""
+    rng = np.random.default_rng(seed)
+    x = piecewise_image(h, w, rng, n_rect=8, n_disc=4, grf_length=h / 16.0)
+    n = h * w
+    m = int(math.floor(ratio * n))
+    patterns = np.sort(rng.choice(n, size=m, replace=False))
+    hb, wb = h.bit_length() - 1, w.bit_length() - 1
+    sylv = np.array([(_bitrev(int(p) // w, hb) << wb) | _bitrev(int(p) % w, wb) for p in patterns])
+    y = _fwht(x.reshape(-1))[sylv] / math.sqrt(m) + sigma * rng.standard_normal(m)
+    return Problem("cs", x, y, sigma * sigma, beta0, seed=seed, patterns=patterns)
 
 
 def batched_problems(n: int = 256, seed: int = 0, min_side: int = 64, max_side: int = 1024):

@@ -86,6 +86,35 @@ def test_invalid_arguments_are_rejected_on_the_host(lib, mutate):
     assert not ctx.value
 
 
+def _hadamard_op(h, w, patterns):
+    o = _op(h, w, op=_lib.OP_HADAMARD, m=len(patterns))
+    keep = (ctypes.c_int32 * max(len(patterns), 1))(*patterns)
+    o.patterns = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int32))
+    return o, keep
+
+
+@pytest.mark.parametrize("h,w,patterns", [
+    (8, 12, [0, 1, 2]),          # sides must be powers of two
+    (6, 8, [0, 1, 2]),
+    (8, 8, [0, 1, 1]),           # patterns must be distinct
+    (8, 8, [0, 64]),             # and inside [0, N)
+    (8, 8, [-1, 3]),
+    (2, 2, [0, 1, 2, 3, 0]),     # M > N
+])
+def test_invalid_hadamard_operator_is_rejected_on_the_host(lib, h, w, patterns):
+    o, keep = _hadamard_op(h, w, patterns)
+    p = _lib.Params()
+    lib.ep_tv_default_params(ctypes.byref(p))
+    p.xi, p.beta = 0.01, 1.0
+    ctx = ctypes.c_void_p()
+    assert lib.ep_tv_init(ctypes.byref(o), ctypes.c_void_p(16), ctypes.byref(p), None,
+                          ctypes.byref(ctx)) == 1
+    assert not ctx.value
+    o.patterns = None  # no pattern list
+    assert lib.ep_tv_init(ctypes.byref(o), ctypes.c_void_p(16), ctypes.byref(p), None,
+                          ctypes.byref(ctx)) == 1
+
+
 def test_null_context_calls_return_arg_error(lib):
     assert lib.ep_tv_sweep(None, 1, None, 0) == 1
     assert lib.ep_tv_em_beta(None, None, None) == 1

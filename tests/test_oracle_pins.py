@@ -420,6 +420,39 @@ def test_em_options_agree_at_lambda_zero():
     assert abs(o.em_statistic(1) / ref_q - 1) <= 1e-10
 
 
+# ---------------------------------------------------------------- Hadamard operator
+def test_paley_ordered_walsh_functions_from_rademacher_products():
+    """Sec. II-A (iii): row k of the Paley-ordered Walsh matrix is the product of
+    the Rademacher functions r_i(t) = sign(sin(2^i pi t)) over the set bits i of k
+    (bit 0 -> r_1), sampled at t = (x + 1/2) / n; the oracle builds it as the
+    Sylvester row with the bits of k reversed."""
+    for n in (2, 8, 32):
+        bits = n.bit_length() - 1
+        t = (np.arange(n) + 0.5) / n
+        for k in range(n):
+            ref = np.ones(n)
+            for i in range(bits):
+                if k >> i & 1:
+                    ref *= np.sign(np.sin(2.0 ** (i + 1) * np.pi * t))
+            row = operators.hadamard_matrix(1, n, [k])[0] * 1.0  # M = 1: unscaled
+            np.testing.assert_array_equal(row, ref)
+
+
+def test_hadamard_rows_orthogonal_and_kronecker():
+    """All N patterns give sqrt(N) times an orthogonal matrix (H H^T = N/M I with
+    M = N), and a 2-D pattern is the outer product of its 1-D row and column
+    Walsh functions."""
+    h, w = 4, 8
+    n = h * w
+    H = operators.hadamard_matrix(h, w, range(n)) * math.sqrt(n)
+    np.testing.assert_array_equal(H @ H.T, n * np.eye(n))
+    rows = operators.hadamard_matrix(1, h, range(h)) * math.sqrt(h)
+    cols = operators.hadamard_matrix(1, w, range(w)) * math.sqrt(w)
+    for kr in range(h):
+        for kc in range(w):
+            np.testing.assert_array_equal(H[kr * w + kc], np.outer(rows[kr], cols[kc]).ravel())
+
+
 # ---------------------------------------------------------------- non-i.i.d. noise
 def _noise_plane(n, seed):
     """Noise variances spread over a factor of 20 (seeded)."""
