@@ -288,11 +288,15 @@ typedef enum {
   EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
   EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one
                                 transformed system (pairs of stopped systems are skipped) */
-  EP_TV_K_CS = 6,            /* dense-operator likelihood site (Woodbury, FP64), unit = pixel;
-                                its per-unit figure is FP64 flops, not bytes */
+  EP_TV_K_CS = 6,            /* compressive-sensing likelihood site (Woodbury, FP64-accurate)
+                                except its tensor-core products, unit = pixel; its per-unit
+                                figure is FP64 CUDA-core flops, not bytes */
   EP_TV_K_CG_COMMIT = 7,     /* adds a refinement pass's FP32 correction to the FP64 solution,
                                 unit = pixel of one system that iterated in the pass */
-  EP_TV_K_COUNT = 8
+  EP_TV_K_CS_MMA = 8,        /* the compressive-sensing site's products as exact BF16 slice
+                                products on the tensor cores (packing included), unit = BF16
+                                tensor flop (per-unit figure 1) */
+  EP_TV_K_COUNT = 9
 } ep_tv_kernel;
 
 /* Tracing: with on != 0, every launch of the kernel classes above is bracketed
@@ -439,6 +443,20 @@ typedef enum {
    start and keeps (1/xi, y/xi) (EP_TV_WARM_SITE0 then changes nothing).  Call it
    after ep_tv_init (or ep_tv_reset) and before sweeping. */
 ep_tv_status ep_tv_warm_start(ep_tv_ctx* ctx, const float* out, int32_t mode);
+
+/* The FP64-accurate product of the compressive-sensing site on the BF16 tensor
+   cores (Sec. III-C, the products of the Woodbury form), exposed to check it on
+   its own: C = A B^T for row-major A (m x k), B (n x k) and C (m x n), all DEVICE
+   pointers, on cuda_stream (NULL: the legacy stream).  Every FP64 entry is split
+   into eight 7-bit BF16 digit slices under a power-of-two scale per row; the 36
+   slice products with the largest weights run as BF16 MMAs (tcgen05) whose
+   partial sums are exact.  |C - A B^T| <~ 2^-52 sum_k |A_ik||B_jk| plus one
+   rounding of the result.  Allocates and frees its packing buffers (about
+   16 (m + n) k bytes) and synchronises the stream.  EP_TV_ERR_ARG for NULL
+   pointers or sizes below 1, EP_TV_ERR_NOMEM, EP_TV_ERR_TIMEOUT if a bounded
+   device-side wait gave up. */
+ep_tv_status ep_tv_tc_gemm_f64(const double* A, const double* B, double* C, int32_t m, int32_t n,
+                               int32_t k, void* cuda_stream);
 
 /* Frees the context (synchronises its stream first).  NULL is accepted. */
 void ep_tv_destroy(ep_tv_ctx* ctx);

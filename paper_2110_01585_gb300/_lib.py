@@ -21,7 +21,7 @@ STATUS_NAMES = {
 OP_IDENTITY, OP_CONV_PERIODIC, OP_DENSE, OP_HADAMARD = 0, 1, 2, 3
 PRIOR_L1, PRIOR_MOG2, PRIOR_BG = 0, 1, 2
 KERNELS = {0: "prior_sweep", 1: "cg_direction", 2: "cg_update", 3: "cg_residual", 4: "site0",
-           5: "cg_precond", 6: "cs_woodbury", 7: "cg_commit"}
+           5: "cg_precond", 6: "cs_woodbury", 7: "cg_commit", 8: "cs_mma"}
 
 # Every function declared in include/ep_tv.h, with its ctypes signature.
 c_void_p, c_int32, c_double, c_size_t = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
@@ -101,6 +101,7 @@ SIGNATURES = {
                                        c_void_p, c_void_p, ctypes.c_float, c_void_p, c_void_p,
                                        c_void_p]),
     "ep_tv_warm_start": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "ep_tv_tc_gemm_f64": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
     "ep_tv_destroy": (None, [c_void_p]),
     "ep_tv_status_str": (ctypes.c_char_p, [c_int32]),
 }

@@ -7,10 +7,11 @@
 //   Var_i = c_i - c_i^2 w_i,        E = m + C A^T K^{-1} (y - A m) = m + c * W^T L^{-1}(y - A m).
 // The site update of Eq. update_q0_x then needs 1/Var_i - 1/c_i = w_i / (1 - c_i w_i).
 //
-// Precision: all of it runs in FP64.  c spans 1e-2 .. 1e8 (prior sites at their
-// variance cap), which drives cond(K) to 1e7 .. 1e8 within a few sweeps and c_i w_i
-// to within 1e-4 of 1; an FP32 or BF16 factorisation loses every digit of
-// 1 - c_i w_i there.  GB300's FP64 rate is low, so this path is ALU-bound.
+// Precision: all of it is FP64-accurate.  c spans 1e-2 .. 1e8 (prior sites at
+// their variance cap), which drives cond(K) to 1e7 .. 1e8 within a few sweeps and
+// c_i w_i to within 1e-4 of 1; an FP32 or plain BF16 factorisation loses every
+// digit of 1 - c_i w_i there.  GB300's FP64 rate is low (1.25 TFLOP/s), so the
+// large products run as exact BF16 slice products on the tensor cores instead.
 //
 // Subsampled 2-D Hadamard operator (Sec. II-A (iii)): A = S W / sqrt(M), W the
 // N x N Walsh-Hadamard matrix in Sylvester order (entry (a, b) = (-1)^popcount(a & b),
@@ -23,11 +24,16 @@
 // transform per row, in place of the M x N triangular solve.  The mean uses
 // A m = (W m)[s] / sqrt(M) and W_A^T.  Same FP64 precision as the dense path.
 //
-// Kernels: an FP64 tiled GEMM (C -= A B^T or C -= A B, 64 x 64 tiles, 4 x 4 per
-// thread), used for K, the trailing updates of a blocked right-looking Cholesky
-// and the block updates of the triangular solve; a 64 x 64 Cholesky of one
-// diagonal block in shared memory; panel and block triangular solves; column
-// sums; matrix-vector products.
+// Structure of one update.  The products with A (K = A C A^T and W = L^{-1} A =
+// Z A, Z = L^{-1}) run on the BF16 tensor cores in the FP64-accurate split form of
+// ozaki.cu.  K = L L^T and Z = L^{-1} come together from a recursion on halves
+// (L21 = K21 Z11^T, K22 -= L21 L21^T, Z21 = -Z22 L21 Z11) in FP64 on the CUDA
+// cores.  The mean uses v = Z t and g = W^T v.
+//
+// Kernels here: an FP64 tiled GEMM (64 x 64 tiles, 4 x 4 per thread) for the
+// small products; the Cholesky factor and inverse of one block of at most 64 rows
+// in shared memory; column sums; matrix-vector products; the fast Walsh-Hadamard
+// transform and the gathers of the Hadamard operator.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -40,6 +46,7 @@
 
 #include "internal.cuh"
 #include "likelihood.cuh"
+#include "ozaki.cuh"
 
 namespace eptv {
 
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int m, int n, int k, cons
       const int gj = bj + tx * 4 + v;
       if (gj >= n) continue;
       double* cp = C + (long long)gi * ldc + gj;
-      *cp = alpha * *cp + beta_ * acc[u][v];
+      *cp = alpha == 0.0 ? beta_ * acc[u][v] : alpha * *cp + beta_ * acc[u][v];
     }
   }
 }
@@ -176,48 +183,6 @@ __global__ void potrf_block_kernel(double* K, int ldk, int k0, int b, unsigned* 
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e / b, j = e - i * b;
     K[(long long)(k0 + i) * ldk + k0 + j] = j <= i ? S[i][j] : 0.0;
-  }
-}
-
-// Panel: rows r >= k0 + b of column block k0..k0+b solve X L_kk^T = K_panel, i.e.
-// L[r, k0 + j] = (K[r, k0 + j] - sum_{l<j} L[r, k0 + l] L[k0 + j, k0 + l]) / L[k0 + j, k0 + j].
-// One thread per row.
-__global__ void trsm_panel_kernel(double* K, int ldk, int k0, int b, int M) {
-  __shared__ double Lkk[kNb][kNb + 1];
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e - i * b;
-    Lkk[i][j] = K[(long long)(k0 + i) * ldk + k0 + j];
-  }
-  __syncthreads();
-  const int r = k0 + b + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= M) return;
-  double x[kNb];
-  double* row = K + (long long)r * ldk + k0;
-  for (int j = 0; j < b; ++j) {
-    double v = row[j];
-    for (int l = 0; l < j; ++l) v -= x[l] * Lkk[j][l];
-    x[j] = v / Lkk[j][j];
-  }
-  for (int j = 0; j < b; ++j) row[j] = x[j];
-}
-
-// Block forward solve: X[rows k0..k0+b, :] = L_kk^{-1} X[rows, :], one thread per column.
-__global__ void trsm_block_cols_kernel(const double* L, int ldl, int k0, int b, double* X, int ldx,
-                                       int ncols) {
-  __shared__ double Lkk[kNb][kNb + 1];
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e - i * b;
-    Lkk[i][j] = L[(long long)(k0 + i) * ldl + k0 + j];
-  }
-  __syncthreads();
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncols) return;
-  double x[kNb];
-  for (int i = 0; i < b; ++i) {
-    double v = X[(long long)(k0 + i) * ldx + col];
-    for (int l = 0; l < i; ++l) v -= Lkk[i][l] * x[l];
-    x[i] = v / Lkk[i][i];
-    X[(long long)(k0 + i) * ldx + col] = x[i];
   }
 }
 
@@ -347,16 +312,6 @@ __global__ void hadamard_k_kernel(double* K, int M, const int* sel, const double
   }
 }
 
-// X = I (M x M)
-__global__ void identity_kernel(double* X, int M) {
-  const long long total = (long long)M * M;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / M), j = (int)(e - (long long)i * M);
-    X[e] = i == j ? 1.0 : 0.0;
-  }
-}
-
 // G = 0, then G[m, s_j] = Z[m, j] / sqrt(M) for the lower triangle of Z (L^{-1} is lower).
 __global__ void hadamard_scatter_kernel(const double* Z, int M, const int* sel, double* G, int N) {
   const long long total = (long long)M * M;
@@ -392,6 +347,41 @@ __global__ void aty_kernel(const float* A, const float* y, int M, int N, float* 
   double s = 0.0;
   for (int m = 0; m < M; ++m) s = fma((double)A[(long long)m * N + i], (double)y[m], s);
   out[i] = (float)s;
+}
+
+// Z = L^{-1} for the n x n (n <= 64) lower block L (leading dimension ld), zeros
+// above the diagonal; forward substitution on the unit vectors, one thread per
+// column (each thread reads back only the entries of Z it wrote itself).
+__global__ void trinv_block_kernel(const double* L, long long ld, double* Z, long long ldz, int n) {
+  __shared__ double Ls[kNb][kNb + 1];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    Ls[i][j] = j <= i ? L[(long long)i * ld + j] : 0.0;
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= n) return;
+  for (int i = 0; i < n; ++i) {
+    double z = 0.0;
+    if (i >= j) {
+      double v = i == j ? 1.0 : 0.0;
+      for (int l = j; l < i; ++l) v -= Ls[i][l] * Z[(long long)l * ldz + j];
+      z = v / Ls[i][i];
+    }
+    Z[(long long)i * ldz + j] = z;
+  }
+}
+
+// v = Z t for lower-triangular Z (M x M), one warp per row.
+__global__ void trmv_lower_kernel(const double* Z, int M, const double* t, double* v) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  double acc = 0.0;
+  for (int k = lane; k <= row; k += 32) acc = fma(Z[(long long)row * M + k], t[k], acc);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) v[row] = acc;
 }
 
 inline int g1d(long long n) {
@@ -433,36 +423,118 @@ struct CsState {
   float damping = 0.5f, min_tau = 1e-8f;
   const float* A = nullptr;   // borrowed, M x N FP32
   const float* y = nullptr;   // context copy
-  double* A64 = nullptr;      // M x N
-  double* G = nullptr;        // M x N, then W
-  double* K = nullptr;        // M x M, then L
+  double* G = nullptr;        // M x N: W = L^{-1} A
+  double* K = nullptr;        // M x M: K, overwritten by the factorisation
+  double* Z = nullptr;        // M x M: L^{-1} (lower)
+  double* pool = nullptr;     // M x M: L21 and L21 Z11 blocks of the recursion
   double* c = nullptr;
   double* sqc = nullptr;
   double* m = nullptr;
   double* w = nullptr;
   double* g = nullptr;
   double* t = nullptr;        // M
+  double* v = nullptr;        // M
   double* xi_v = nullptr;     // M noise variances (diagonal noise covariance), or NULL
   int* sel = nullptr;         // Hadamard: M Sylvester row indices
-  double* Z = nullptr;        // Hadamard: M x M, L^{-1}
+  // split-BF16 tensor-core products: packed operands and their row exponents
+  uint8_t* pack_a = nullptr;  // dense: left operands (G, then Z)
+  uint8_t* pack_at = nullptr; // dense: A^T, packed once
+  int* exp_a = nullptr;
+  int* exp_at = nullptr;
+  unsigned* status = nullptr; // the context's status word (set per update)
+  Tracer* tr = nullptr;       // the context's tracer (set per update)
+  double simt_flops = 0.0;    // FP64 CUDA-core flops of one update (counted on the host)
+  double mma_flops = 0.0;     // BF16 tensor flops of one update
 };
 
 namespace {
 
 void cs_free(CsState* S) {
-  cudaFree(S->A64);
   cudaFree(S->G);
   cudaFree(S->K);
+  cudaFree(S->Z);
+  cudaFree(S->pool);
   cudaFree(S->c);
   cudaFree(S->sqc);
   cudaFree(S->m);
   cudaFree(S->w);
   cudaFree(S->g);
   cudaFree(S->t);
+  cudaFree(S->v);
   cudaFree(S->xi_v);
   cudaFree(S->sel);
-  cudaFree(S->Z);
+  cudaFree(S->pack_a);
+  cudaFree(S->pack_at);
+  cudaFree(S->exp_a);
+  cudaFree(S->exp_at);
   delete S;
+}
+
+// The tracer brackets the update as CS segments with the tensor-core products
+// cut out as CS_MMA segments.
+struct Segment {
+  CsState* S;
+  cudaStream_t s;
+  double flops;
+  Segment(CsState* S_, cudaStream_t s_, double flops_) : S(S_), s(s_), flops(flops_) {
+    S->tr->end(s, 0.0);
+    S->tr->begin(EP_TV_K_CS_MMA, s);
+  }
+  ~Segment() {
+    S->tr->end(s, flops);
+    S->tr->begin(EP_TV_K_CS, s);
+  }
+};
+
+// C = alpha C + beta X Y^T in the FP64 SIMT GEMM, X (m x k) row-major at ldx,
+// Y(j, kk) = Y[j * ldy + kk] or, when y_trans, Y[kk * ldy + j].  The products of
+// the factorisation stay in FP64: the Schur complement K22 - L21 L21^T cancels
+// to the size of xi while its terms carry the capped cavity variances, which
+// needs an error relative to sum_k |L_ik L_jk| (an FP64 GEMM's), not to the
+// rows' largest entries (the split form's).
+void product(CsState* S, const double* X, long long ldx, const double* Y, long long ldy, bool y_trans, int m,
+             int n, int k, double* C, long long ldc, double alpha, double beta, bool lower_only, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return;
+  gemm(!y_trans, m, n, k, X, (int)ldx, Y, (int)ldy, C, (int)ldc, alpha, beta, lower_only, s);
+  S->simt_flops += 2.0 * m * n * k;
+}
+
+int split_point(int n) {
+  const int half = (n + 1) / 2;
+  return (half + kNb - 1) / kNb * kNb;
+}
+
+// Cholesky factorisation and triangular inverse together, by halves: for
+// K = [K11 .; K21 K22] (lower triangle read),
+//   L11 Z11 from K11;  L21 = K21 Z11^T;  K22 <- K22 - L21 L21^T;  L22 Z22 from K22;
+//   Z21 = -Z22 (L21 Z11),
+// with Z = L^{-1} written into Z (ldz; the block above the diagonal must be zero
+// already).  Blocks of at most 64 rows: shared-memory Cholesky and inverse.
+// The recursion exposes large FP64 products (the top level's are n/2 square)
+// where a column-by-column factorisation has only 64-row panels.
+// pool: scratch for the L21 and L21 Z11 blocks of every level.
+void chol_inv(CsState* S, double* K, long long ld, double* Z, long long ldz, int n, double* pool,
+              cudaStream_t s) {
+  if (n <= kNb) {
+    potrf_block_kernel<<<1, 256, 0, s>>>(K, (int)ld, 0, n, S->status);
+    trinv_block_kernel<<<1, kNb, 0, s>>>(K, ld, Z, ldz, n);
+    S->simt_flops += 2.0 * n * n * n / 3.0;
+    return;
+  }
+  const int n1 = split_point(n), n2 = n - n1;
+  double* K21 = K + (long long)n1 * ld;
+  double* K22 = K21 + n1;
+  double* Z21 = Z + (long long)n1 * ldz;
+  double* Z22 = Z21 + n1;
+  chol_inv(S, K, ld, Z, ldz, n1, pool, s);
+  double* L21 = pool;                       // n2 x n1
+  double* T = pool + (long long)n2 * n1;    // n2 x n1
+  double* rest = T + (long long)n2 * n1;
+  product(S, K21, ld, Z, ldz, false, n2, n1, n1, L21, n1, 0.0, 1.0, false, s);
+  product(S, L21, n1, L21, n1, false, n2, n2, n1, K22, ld, 1.0, -1.0, true, s);
+  chol_inv(S, K22, ld, Z22, ldz, n2, rest, s);
+  product(S, L21, n1, Z, ldz, true, n2, n1, n1, T, n1, 0.0, 1.0, false, s);
+  product(S, Z22, ldz, T, n1, true, n2, n1, n2, Z21, ldz, 0.0, -1.0, false, s);
 }
 
 unsigned bit_reverse(unsigned k, int bits) {
@@ -478,8 +550,28 @@ int log2_exact(int v) {
   return (1 << b) == v ? b : -1;
 }
 
-// Hadamard operator: Sylvester row of every Paley-ordered pattern, the buffers,
-// and mu0 = A^T y = W (S^T y) / sqrt(M).
+// Buffers of both operators.
+bool alloc_common(CsState* S) {
+  const int M = S->M, N = S->N;
+  const long long MN = (long long)M * N, MM = (long long)M * M;
+  const size_t pa = ozaki_pack_bytes(M, std::max(M, N));  // G (M x N), then Z (M x M)
+  return cudaMalloc(&S->G, sizeof(double) * MN) == cudaSuccess &&
+         cudaMalloc(&S->K, sizeof(double) * MM) == cudaSuccess &&
+         cudaMalloc(&S->Z, sizeof(double) * MM) == cudaSuccess &&
+         cudaMalloc(&S->pool, sizeof(double) * MM) == cudaSuccess &&
+         cudaMalloc(&S->c, sizeof(double) * N) == cudaSuccess &&
+         cudaMalloc(&S->sqc, sizeof(double) * N) == cudaSuccess &&
+         cudaMalloc(&S->m, sizeof(double) * N) == cudaSuccess &&
+         cudaMalloc(&S->w, sizeof(double) * N) == cudaSuccess &&
+         cudaMalloc(&S->g, sizeof(double) * N) == cudaSuccess &&
+         cudaMalloc(&S->t, sizeof(double) * M) == cudaSuccess &&
+         cudaMalloc(&S->v, sizeof(double) * M) == cudaSuccess &&
+         (S->hadamard || (cudaMalloc(&S->pack_a, pa) == cudaSuccess &&
+                          cudaMalloc(&S->exp_a, sizeof(int) * M) == cudaSuccess));
+}
+
+// Hadamard operator: Sylvester row of every Paley-ordered pattern, and
+// mu0 = A^T y = W (S^T y) / sqrt(M).
 ep_tv_status hadamard_create(const LikelihoodConfig& cfg, CsState* S, cudaStream_t s, float* mu0) {
   const int hb = log2_exact(cfg.height), wb = log2_exact(cfg.width);
   const int M = S->M, N = S->N;
@@ -490,18 +582,7 @@ ep_tv_status hadamard_create(const LikelihoodConfig& cfg, CsState* S, cudaStream
     const unsigned kr = (unsigned)(p / cfg.width), kc = (unsigned)(p % cfg.width);
     sel[i] = (int)((bit_reverse(kr, hb) << wb) | bit_reverse(kc, wb));
   }
-  const long long MN = (long long)M * N;
-  bool ok = cudaMalloc(&S->G, sizeof(double) * MN) == cudaSuccess &&
-            cudaMalloc(&S->K, sizeof(double) * (long long)M * M) == cudaSuccess &&
-            cudaMalloc(&S->Z, sizeof(double) * (long long)M * M) == cudaSuccess &&
-            cudaMalloc(&S->sel, sizeof(int) * M) == cudaSuccess &&
-            cudaMalloc(&S->c, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&S->sqc, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&S->m, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&S->w, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&S->g, sizeof(double) * N) == cudaSuccess &&
-            cudaMalloc(&S->t, sizeof(double) * M) == cudaSuccess;
-  if (!ok) {
+  if (!alloc_common(S) || cudaMalloc(&S->sel, sizeof(int) * M) != cudaSuccess) {
     cudaGetLastError();
     return EP_TV_ERR_NOMEM;
   }
@@ -518,35 +599,11 @@ ep_tv_status hadamard_create(const LikelihoodConfig& cfg, CsState* S, cudaStream
   return cudaGetLastError() == cudaSuccess ? EP_TV_OK : EP_TV_ERR_CUDA;
 }
 
-// X = L^{-1} X in place for the M x ncols block X (ld ldx), L the lower factor in K:
-// blocked forward substitution, the block updates as GEMMs.
-void forward_solve(const double* L, int M, double* X, int ldx, int ncols, cudaStream_t s) {
-  for (int k0 = 0; k0 < M; k0 += kNb) {
-    const int b = std::min(kNb, M - k0);
-    if (k0 > 0)  // X[k0:k0+b, :] -= L[k0:k0+b, 0:k0] X[0:k0, :]
-      gemm(false, b, ncols, k0, L + (long long)k0 * M, M, X, ldx, X + (long long)k0 * ldx, ldx, 1.0,
-           -1.0, false, s);
-    trsm_block_cols_kernel<<<(ncols + 127) / 128, 128, 0, s>>>(L, M, k0, b, X, ldx, ncols);
-  }
-}
-
-// Z = L^{-1}: forward substitution on the identity; L^{-1} is lower triangular, so
-// block row k0 only involves columns 0 .. k0 + b.
-void lower_inverse(const double* L, int M, double* Z, cudaStream_t s) {
-  identity_kernel<<<g1d((long long)M * M), 256, 0, s>>>(Z, M);
-  for (int k0 = 0; k0 < M; k0 += kNb) {
-    const int b = std::min(kNb, M - k0);
-    if (k0 > 0)
-      gemm(false, b, k0, k0, L + (long long)k0 * M, M, Z, M, Z + (long long)k0 * M, M, 1.0, -1.0,
-           false, s);
-    trsm_block_cols_kernel<<<(k0 + b + 127) / 128, 128, 0, s>>>(L, M, k0, b, Z, M, k0 + b);
-  }
-}
-
 }  // namespace
 
 ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** out, float* mu0) {
   *out = nullptr;
+  if (ozaki_init() != EP_TV_OK) return EP_TV_ERR_CUDA;
   CsState* S = new (std::nothrow) CsState();
   if (!S) return EP_TV_ERR_NOMEM;
   S->M = cfg.m;
@@ -566,22 +623,14 @@ ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** ou
     *out = S;
     return EP_TV_OK;
   }
-  const long long MN = (long long)S->M * S->N;
-  bool ok = cudaMalloc(&S->A64, sizeof(double) * MN) == cudaSuccess &&
-            cudaMalloc(&S->G, sizeof(double) * MN) == cudaSuccess &&
-            cudaMalloc(&S->K, sizeof(double) * (long long)S->M * S->M) == cudaSuccess &&
-            cudaMalloc(&S->c, sizeof(double) * S->N) == cudaSuccess &&
-            cudaMalloc(&S->sqc, sizeof(double) * S->N) == cudaSuccess &&
-            cudaMalloc(&S->m, sizeof(double) * S->N) == cudaSuccess &&
-            cudaMalloc(&S->w, sizeof(double) * S->N) == cudaSuccess &&
-            cudaMalloc(&S->g, sizeof(double) * S->N) == cudaSuccess &&
-            cudaMalloc(&S->t, sizeof(double) * S->M) == cudaSuccess;
-  if (!ok) {
+  if (!alloc_common(S) || cudaMalloc(&S->pack_at, ozaki_pack_bytes(S->N, S->M)) != cudaSuccess ||
+      cudaMalloc(&S->exp_at, sizeof(int) * S->N) != cudaSuccess) {
     cudaGetLastError();
     cs_free(S);
     return EP_TV_ERR_NOMEM;
   }
-  to_f64_kernel<<<g1d(MN), 256, 0, s>>>(S->A, S->A64, MN);
+  // A^T (N rows of M) packed once for W = Z A
+  ozaki_pack(S->A, S->N, true, S->N, S->M, nullptr, S->exp_at, S->pack_at, s);
   // Algorithm 1 initialises the mean of site 0 at y; y has M < N entries here, and
   // the back-projection A^T y takes its place
   aty_kernel<<<(S->N + 255) / 256, 256, 0, s>>>(S->A, S->y, S->M, S->N, mu0);
@@ -609,7 +658,11 @@ ep_tv_status cs_set_noise(CsState* S, const float* xi_m, cudaStream_t s) {
 ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, const float* np,
                        unsigned* status, unsigned long long* counters, Tracer* tr, cudaStream_t s) {
   const int M = S->M, N = S->N;
-  const long long MN = (long long)M * N;
+  const long long MN = (long long)M * N, MM = (long long)M * M;
+  S->status = status;
+  S->tr = tr;
+  S->simt_flops = 0.0;
+  S->mma_flops = 0.0;
   tr->begin(EP_TV_K_CS, s);
   cs_cavity_kernel<<<g1d(N), 256, 0, s>>>(tp, np, N, S->c, S->sqc, S->m);
   if (S->hadamard) {
@@ -617,38 +670,34 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
     if (cudaMemcpyAsync(S->g, S->c, sizeof(double) * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return EP_TV_ERR_CUDA;
     fwht_rows(S->g, 1, N, s);
-    hadamard_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->sel, S->g, S->xi, S->xi_v);
+    hadamard_k_kernel<<<g1d(MM), 256, 0, s>>>(S->K, M, S->sel, S->g, S->xi, S->xi_v);
   } else {
-    // K = xi I + (A C^{1/2})(A C^{1/2})^T, lower triangle
-    scale_cols_kernel<<<g1d(MN), 256, 0, s>>>(S->A, S->sqc, S->G, M, N);
-    init_k_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->K, M, S->xi, S->xi_v);
-    gemm(true, M, M, N, S->G, N, S->G, N, S->K, M, 1.0, 1.0, true, s);
+    // K = diag(xi) + (A C^{1/2})(A C^{1/2})^T, lower triangle, on the tensor cores
+    init_k_kernel<<<g1d(MM), 256, 0, s>>>(S->K, M, S->xi, S->xi_v);
+    const double f = ozaki_tensor_flops(M, M, N) / 2.0;
+    S->mma_flops += f;
+    Segment seg(S, s, f);
+    ozaki_pack(S->A, N, false, M, N, S->sqc, S->exp_a, S->pack_a, s);
+    OzakiOperand g{S->pack_a, S->exp_a};
+    ozaki_gemm(g, g, N, S->K, M, M, M, 1.0, 1.0, true, false, status, s);
   }
-  // blocked right-looking Cholesky K = L L^T (lower)
-  for (int k0 = 0; k0 < M; k0 += kNb) {
-    const int b = std::min(kNb, M - k0);
-    potrf_block_kernel<<<1, 256, 0, s>>>(S->K, M, k0, b, status);
-    const int rest = M - k0 - b;
-    if (rest > 0) {
-      trsm_panel_kernel<<<(rest + 127) / 128, 128, 0, s>>>(S->K, M, k0, b, M);
-      // trailing K[k0+b:, k0+b:] -= L_panel L_panel^T (lower tiles)
-      const double* P = S->K + (long long)(k0 + b) * M + k0;
-      gemm(true, rest, rest, b, P, M, P, M, S->K + (long long)(k0 + b) * M + (k0 + b), M, 1.0, -1.0,
-           true, s);
-    }
-  }
+  // K = L L^T and Z = L^{-1}
+  if (cudaMemsetAsync(S->Z, 0, sizeof(double) * MM, s) != cudaSuccess) return EP_TV_ERR_CUDA;
+  chol_inv(S, S->K, M, S->Z, M, M, S->pool, s);
   if (S->hadamard) {
     // W = (L^{-1} S) W_N / sqrt(M): the lower inverse scattered to the selected
     // columns, then a fast transform of every row
-    lower_inverse(S->K, M, S->Z, s);
     if (cudaMemsetAsync(S->G, 0, sizeof(double) * MN, s) != cudaSuccess) return EP_TV_ERR_CUDA;
-    hadamard_scatter_kernel<<<g1d((long long)M * M), 256, 0, s>>>(S->Z, M, S->sel, S->G, N);
+    hadamard_scatter_kernel<<<g1d(MM), 256, 0, s>>>(S->Z, M, S->sel, S->G, N);
     fwht_rows(S->G, M, N, s);
   } else {
-    // W = L^{-1} A (blocked forward substitution on all N columns), into G
-    if (cudaMemcpyAsync(S->G, S->A64, sizeof(double) * MN, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return EP_TV_ERR_CUDA;
-    forward_solve(S->K, M, S->G, N, N, s);
+    // W = Z A on the tensor cores (Z lower triangular)
+    const double f = ozaki_tensor_flops(M, N, M) / 2.0;
+    S->mma_flops += f;
+    Segment seg(S, s, f);
+    ozaki_pack(S->Z, M, false, M, M, nullptr, S->exp_a, S->pack_a, s);
+    ozaki_gemm(OzakiOperand{S->pack_a, S->exp_a}, OzakiOperand{S->pack_at, S->exp_at}, M, S->G, N, M, N, 0.0,
+               1.0, false, true, status, s);
   }
   colsq_kernel<<<(N + 255) / 256, 256, 0, s>>>(S->G, M, N, S->w);
   // mean: t = y - A m, v = L^{-1} t, g = W^T v, E = m + c g
@@ -660,8 +709,8 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
   } else {
     resid_vec_kernel<<<(M + 7) / 8, 256, 0, s>>>(S->A, S->y, S->m, M, N, S->t);
   }
-  forward_solve(S->K, M, S->t, 1, 1, s);
-  wtv_kernel<<<(N + 255) / 256, 256, 0, s>>>(S->G, S->t, M, N, S->g);
+  trmv_lower_kernel<<<(M + 7) / 8, 256, 0, s>>>(S->Z, M, S->t, S->v);
+  wtv_kernel<<<(N + 255) / 256, 256, 0, s>>>(S->G, S->v, M, N, S->g);
   cs_site0_kernel<<<g1d(N), 256, 0, s>>>(S->w, S->g, S->c, S->m, N, tau0, nu0, S->min_tau, S->damping,
                                          status, counters);
   tr->end(s, (double)N);
@@ -669,14 +718,12 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
 }
 
 double cs_flops(const CsState* S) {
+  // FP64 flops on the CUDA cores: the small products and blocks of the
+  // factorisation (counted during the last update), column sums and the mean
   const double M = S->M, N = S->N;
-  if (S->hadamard) {
-    // K from one transform, Cholesky, the lower inverse, M row transforms, column sums, mean
-    const double lg = std::log2(N);
-    return N * lg + M * M * M / 3.0 + M * M * M / 3.0 + M * N * lg + 2.0 * M * N + 4.0 * M * N;
-  }
-  // K (lower half of G G^T), Cholesky, W = L^{-1} A, column sums and the mean
-  return M * M * N + M * M * M / 3.0 + M * M * N + 2.0 * M * N + 4.0 * M * N;
+  return S->simt_flops + 2.0 * M * N + 4.0 * M * N + M * M;
 }
+
+double cs_mma_flops(const CsState* S) { return S->mma_flops; }
 
 }  // namespace eptv

@@ -2538,7 +2538,7 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
 // What each kernel class must move at least once per unit (the method's data,
 // not the implementation's intermediates), for the roofline.
 double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
-  if (L->cs) return kernel == EP_TV_K_CS ? cs_flops(L->cs) : 0.0;
+  if (L->cs) return kernel == EP_TV_K_CS ? cs_flops(L->cs) : kernel == EP_TV_K_CS_MMA ? 1.0 : 0.0;
   const double groups = (double)((L->S + kRbGroup - 1) / kRbGroup);
   switch (kernel) {
     case EP_TV_K_CG_DIRECTION: return 16.0;  // read z, p; write p, Q p (per active system pixel)

@@ -59,6 +59,7 @@ void cs_destroy(CsState* S);
 ep_tv_status cs_set_noise(CsState* S, const float* xi_m, cudaStream_t s);
 ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, const float* np,
                        unsigned* status, unsigned long long* counters, Tracer* tr, cudaStream_t s);
-double cs_flops(const CsState* S);  // FP64 flops of one update
+double cs_flops(const CsState* S);      // FP64 CUDA-core flops of the last update
+double cs_mma_flops(const CsState* S);  // BF16 tensor flops of the last update
 
 }  // namespace eptv

@@ -1,0 +1,42 @@
+// FP64-accurate matrix products on the BF16 tensor cores (ozaki.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ep_tv.h"
+
+namespace eptv {
+
+// A packed operand: BF16 digit slices in the tensor core's shared-memory order
+// plus one power-of-two exponent per row.
+struct OzakiOperand {
+  const uint8_t* packed;
+  const int* exps;
+};
+
+// Bytes of the packed form of a rows x k operand.
+size_t ozaki_pack_bytes(int rows, int k);
+// Raises the kernel's dynamic shared-memory limit (once per process and device).
+ep_tv_status ozaki_init();
+// Packs rows x k operand X(r, k) = X[r * ld + k] (trans: X[k * ld + r]), times
+// kscale[k] when kscale is not NULL, into out (ozaki_pack_bytes(rows, k) bytes)
+// and its row exponents into e (rows ints).
+void ozaki_pack(const double* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
+                uint8_t* out, cudaStream_t s);
+void ozaki_pack(const float* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
+                uint8_t* out, cudaStream_t s);
+// C = alpha C + beta A B^T for packed A (m x k) and B (n x k); C row-major, ldc.
+// lower_only: only entries with col <= row are written.  a_lower: A is lower
+// triangular (row i has no entries beyond k = i), so row tiles stop early.
+// A timed-out wait raises ST_TIMEOUT in status.
+void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, long long ldc, int m, int n,
+                double alpha, double beta, bool lower_only, bool a_lower, unsigned* status, cudaStream_t s);
+// C = A B^T for row-major A (m x k), B (n x k), C (m x n), all device memory,
+// with its own packing buffers (the exported ep_tv_tc_gemm_f64).
+ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k,
+                                   cudaStream_t s);
+// BF16 tensor flops of one product: the 36 slice products of m x n x k (padding not counted).
+double ozaki_tensor_flops(int m, int n, int k);
+
+}  // namespace eptv

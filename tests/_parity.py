@@ -20,6 +20,7 @@ def parity_errors(mu, var, mu_ref, var_ref, y):
 
 def assert_parity(mu, var, mu_ref, var_ref, y, rtol_mean=RTOL_MEAN, rtol_var=RTOL_VAR):
     e_mu, e_var = parity_errors(mu, var, mu_ref, var_ref, y)
+    print(f"parity: mean {e_mu:.3e} (tol {rtol_mean:.0e}), variance {e_var:.3e} (tol {rtol_var:.0e})")
     assert e_mu <= rtol_mean and e_var <= rtol_var, (e_mu, e_var)
     return e_mu, e_var
 
