@@ -438,6 +438,7 @@ struct CsState {
   int* sel = nullptr;         // Hadamard: M Sylvester row indices
   // split-BF16 tensor-core products: packed operands and their row exponents
   uint8_t* pack_a = nullptr;  // dense: left operands (G, then Z)
+  uint8_t* pack_b = nullptr;  // dense: G as the right operand of G G^T
   uint8_t* pack_at = nullptr; // dense: A^T, packed once
   int* exp_a = nullptr;
   int* exp_at = nullptr;
@@ -464,6 +465,7 @@ void cs_free(CsState* S) {
   cudaFree(S->xi_v);
   cudaFree(S->sel);
   cudaFree(S->pack_a);
+  cudaFree(S->pack_b);
   cudaFree(S->pack_at);
   cudaFree(S->exp_a);
   cudaFree(S->exp_at);
@@ -624,13 +626,14 @@ ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** ou
     return EP_TV_OK;
   }
   if (!alloc_common(S) || cudaMalloc(&S->pack_at, ozaki_pack_bytes(S->N, S->M)) != cudaSuccess ||
+      cudaMalloc(&S->pack_b, ozaki_pack_bytes(S->M, S->N)) != cudaSuccess ||
       cudaMalloc(&S->exp_at, sizeof(int) * S->N) != cudaSuccess) {
     cudaGetLastError();
     cs_free(S);
     return EP_TV_ERR_NOMEM;
   }
   // A^T (N rows of M) packed once for W = Z A
-  ozaki_pack(S->A, S->N, true, S->N, S->M, nullptr, S->exp_at, S->pack_at, s);
+  ozaki_pack(S->A, S->N, true, S->N, S->M, nullptr, S->exp_at, S->pack_at, OzakiSide::kRight, true, s);
   // Algorithm 1 initialises the mean of site 0 at y; y has M < N entries here, and
   // the back-projection A^T y takes its place
   aty_kernel<<<(S->N + 255) / 256, 256, 0, s>>>(S->A, S->y, S->M, S->N, mu0);
@@ -677,9 +680,10 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
     const double f = ozaki_tensor_flops(M, M, N) / 2.0;
     S->mma_flops += f;
     Segment seg(S, s, f);
-    ozaki_pack(S->A, N, false, M, N, S->sqc, S->exp_a, S->pack_a, s);
-    OzakiOperand g{S->pack_a, S->exp_a};
-    ozaki_gemm(g, g, N, S->K, M, M, M, 1.0, 1.0, true, false, status, s);
+    ozaki_pack(S->A, N, false, M, N, S->sqc, S->exp_a, S->pack_a, OzakiSide::kLeft, true, s);
+    ozaki_pack(S->A, N, false, M, N, S->sqc, S->exp_a, S->pack_b, OzakiSide::kRight, false, s);
+    ozaki_gemm(OzakiOperand{S->pack_a, S->exp_a}, OzakiOperand{S->pack_b, S->exp_a}, N, S->K, M, M, M, 1.0,
+               1.0, true, false, status, s);
   }
   // K = L L^T and Z = L^{-1}
   if (cudaMemsetAsync(S->Z, 0, sizeof(double) * MM, s) != cudaSuccess) return EP_TV_ERR_CUDA;
@@ -695,7 +699,7 @@ ep_tv_status cs_update(CsState* S, float* tau0, float* nu0, const float* tp, con
     const double f = ozaki_tensor_flops(M, N, M) / 2.0;
     S->mma_flops += f;
     Segment seg(S, s, f);
-    ozaki_pack(S->Z, M, false, M, M, nullptr, S->exp_a, S->pack_a, s);
+    ozaki_pack(S->Z, M, false, M, M, nullptr, S->exp_a, S->pack_a, OzakiSide::kLeft, true, s);
     ozaki_gemm(OzakiOperand{S->pack_a, S->exp_a}, OzakiOperand{S->pack_at, S->exp_at}, M, S->G, N, M, N, 0.0,
                1.0, false, true, status, s);
   }

@@ -24,15 +24,18 @@
 // error of 2^-50, which this split removes.)  The result is FP64-accurate:
 // |error| <~ 2^-52 sum_k |A_ik||B_jk| plus one final rounding.
 //
-// Kernel: one CTA of 4 warps per 128 x 64 output tile; K in stages of 16 (one
-// MMA K step), four shared-memory stages filled by bulk asynchronous copies
-// (cp.async.bulk, the TMA engine) from operands packed in the tensor core's
-// shared-memory core-matrix order, so every stage is a few contiguous copies.
-// Thread 0 issues the copies and the 36 MMAs of a stage (M = 128, N = 64,
-// K = 16, BF16 inputs, FP32 accumulators in tensor memory); the four warps read
-// the accumulators back (tcgen05.ld) at every chunk end.  Every wait on an
-// mbarrier gives up after two seconds: the kernel then raises ST_TIMEOUT, waits
-// (bounded) for its copies and MMAs in flight, frees its tensor memory and exits.
+// Kernel: one CTA per 128 x 64 output tile; K in stages of 16 (one MMA K step),
+// four shared-memory stages filled by bulk asynchronous copies (cp.async.bulk,
+// the TMA engine) from operands packed in the tensor core's shared-memory
+// core-matrix order, so that a stage is two contiguous copies (A: 128 rows, B:
+// 64 rows, 8 slices each).  Warp-specialised: one thread issues the copies and
+// waits only for stages to free up, one thread issues the 36 MMAs of a stage
+// (M = 128, N = 64, K = 16, BF16 inputs, FP32 accumulators in tensor memory) and
+// waits only for stages to land, and four warps read the accumulators back
+// (tcgen05.ld) at every chunk end, handing them back to the MMA thread through
+// a second pair of barriers.  Every wait on an mbarrier gives up after two
+// seconds: the kernel then raises ST_TIMEOUT, waits (bounded) for its copies and
+// MMAs in flight, frees its tensor memory and exits.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -193,12 +196,14 @@ __global__ void row_exponent_kernel(const T* X, long long ld, int trans, const d
 }
 
 // Digits of 8 consecutive k of one row, written as 8 slices of 16 bytes into the
-// packed layout: block (row tile, K stage) of kBlockBytes; in it slice s, K half
-// kc (8 values of k), row group g, row w at ((s * 2 + kc) * 16 + g) * 128 + w * 16.
-// Rows >= R and k >= K (the padding) are written as zeros.
+// packed layout: blocks of (tile rows TR) x (one K stage of 16) holding, for slice s
+// and K half kc (8 values of k), TR / 8 core matrices of 8 rows x 16 bytes:
+// byte ((s * 2 + kc) * TR / 8 + g) * 128 + w * 16 of the block for row 8 g + w.
+// Every block is one contiguous bulk copy.  Rows >= R and k >= K (the padding)
+// are written as zeros.
 template <typename T>
 __global__ void pack_kernel(const T* X, long long ld, int trans, const double* ks, int R, int K, const int* e,
-                            uint8_t* out, int r_pad, int n_oct) {
+                            uint8_t* out, int tile_rows, int r_pad, int n_oct) {
   const long long total = (long long)r_pad * n_oct;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= total) return;
@@ -222,9 +227,11 @@ __global__ void pack_kernel(const T* X, long long ld, int trans, const double* k
     v[i] = ldexp(x, -ex);
   }
   const int nkt = n_oct / 2;
-  const int rt = r / kTM, rr = r % kTM, g = rr / 8, w = rr % 8;
+  const int groups = tile_rows / 8;
+  const int rt = r / tile_rows, rr = r % tile_rows, g = rr / 8, w = rr % 8;
   const int kt = o / 2, kc = o % 2;
-  uint8_t* base = out + ((long long)rt * nkt + kt) * kBlockBytes + (long long)kc * kSliceKc + g * kCore + w * 16;
+  const long long block_bytes = (long long)kSlices * 2 * groups * kCore;
+  uint8_t* base = out + ((long long)rt * nkt + kt) * block_bytes + ((long long)kc * groups + g) * kCore + w * 16;
 #pragma unroll
   for (int s = 0; s < kSlices; ++s) {
     const float w_s = exp2f(-(float)(kDigitBits * (s + 1)));
@@ -239,7 +246,7 @@ __global__ void pack_kernel(const T* X, long long ld, int trans, const double* k
       const unsigned short b1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1 * w_s));
       packed[i / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
     }
-    *reinterpret_cast<uint4*>(base + (long long)s * 2 * kSliceKc) =
+    *reinterpret_cast<uint4*>(base + (long long)s * 2 * groups * kCore) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
   }
 }
@@ -247,8 +254,8 @@ __global__ void pack_kernel(const T* X, long long ld, int trans, const double* k
 // ---- the product
 
 struct GemmArgs {
-  const uint8_t* pa;   // packed A (rows of the output)
-  const uint8_t* pb;   // packed B (columns of the output)
+  const uint8_t* pa;   // packed A (rows of the output), 128-row tiles
+  const uint8_t* pb;   // packed B (columns of the output), 64-row tiles
   const int* ea;
   const int* eb;
   int nkt;             // K stages of both packings
@@ -261,26 +268,44 @@ struct GemmArgs {
   unsigned* status;
 };
 
-__global__ void __launch_bounds__(128, 1) ozaki_gemm_kernel(GemmArgs a) {
+// Roles: warps 0-7 read the accumulators (warp w reads tensor-memory lanes
+// 32 (w % 4) .. + 31, i.e. output rows, and output columns 32 (w / 4) .. + 31);
+// warp 8 lane 0 issues the MMAs; warp 9 lane 0 issues the bulk copies.  Barriers:
+// full[b] (a stage's copies landed), empty[b] (the MMAs reading stage b
+// finished), acc_full (a chunk's MMAs finished), acc_empty (the reading warps are
+// done with the chunk's accumulators).
+constexpr int kEpiWarps = 8;
+constexpr int kEpiCols = kTN / 2;  // output columns per reading warp
+constexpr int kThreads = (kEpiWarps + 2) * 32;
+
+__global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + 8192);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* produced_out = reinterpret_cast<int*>(tmem_slot + 2);
+  int* committed_out = reinterpret_cast<int*>(tmem_slot + 3);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.y * kTM, col0 = blockIdx.x * kTN;
   if (a.lower_only && col0 > row0 + kTM - 1) return;
   int nst = a.nkt;
   if (a.a_lower) nst = min(nst, (row0 + kTM + kKS - 1) / kKS);
+  const int n_chunks = (nst + kChunkStages - 1) / kChunkStages;
 
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
+  const uint32_t acc_full = smem_u32(bars + 2 * kStages), acc_empty = acc_full + 8;
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(full0 + 8 * i, 1);
       mbar_init(empty0 + 8 * i, 1);
     }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
     *abort_flag = 0;
+    *produced_out = 0;
+    *committed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -294,93 +319,95 @@ __global__ void __launch_bounds__(128, 1) ozaki_gemm_kernel(GemmArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  const uint8_t* pa = a.pa + (long long)blockIdx.y * a.nkt * kBlockBytes;
-  const uint8_t* pb = a.pb + (long long)(col0 / kTM) * a.nkt * kBlockBytes + ((col0 % kTM) / kTN) * (kTN / 8 * kCore);
   const uint32_t sbase = smem_u32(smem);
 
-  auto issue_load = [&](int st) {
-    const int b = st % kStages;
-    const uint32_t bar = full0 + 8 * b;
-    const uint32_t dst = sbase + b * kStageBytes;
-    expect_tx(bar, kStageBytes);
-    bulk_load(dst, pa + (long long)st * kBlockBytes, kAStage, bar);
-    const uint8_t* src = pb + (long long)st * kBlockBytes;
-#pragma unroll 1
-    for (int q = 0; q < kSlices * 2; ++q)
-      bulk_load(dst + kAStage + q * (kTN / 8 * kCore), src + q * kSliceKc, kTN / 8 * kCore, bar);
-  };
-
-  long long acc[kTN];
-#pragma unroll
-  for (int j = 0; j < kTN; ++j) acc[j] = 0;
-
-  int loaded = 0, waited_full = 0, committed = 0;  // thread 0's bookkeeping
-  bool tail_started = false;
-  if (tid == 0) {
-    for (; loaded < min(kStages - 1, nst); ++loaded) issue_load(loaded);
-  }
-
-  for (int c0 = 0; c0 < nst; c0 += kChunkStages) {
-    const int c1 = min(nst, c0 + kChunkStages);
-    if (tid == 0) {
-      bool started[kExact] = {false, false, false, false, false};
-      for (int st = c0; st < c1; ++st) {
+  if (warp == kEpiWarps + 1) {
+    // producer: one A block (128 x 16, 32 KB) and one B block (64 x 16, 16 KB) per stage
+    if (lane == 0) {
+      const uint8_t* pa = a.pa + (long long)blockIdx.y * a.nkt * kAStage;
+      const uint8_t* pb = a.pb + (long long)blockIdx.x * a.nkt * kBStage;
+      int st = 0;
+      for (; st < nst && !*abort_flag; ++st) {
         const int b = st % kStages;
-        if (!mbar_wait(full0 + 8 * b, (st / kStages) & 1)) {
+        if (st >= kStages && !mbar_wait(empty0 + 8 * b, ((st / kStages) - 1) & 1)) {
           *abort_flag = 1;
           break;
         }
-        ++waited_full;
-        tc_fence_after();
-        const uint32_t ab = sbase + b * kStageBytes, bb = ab + kAStage;
-#pragma unroll 1
-        for (int s = 0; s < kSlices; ++s) {
-          const uint64_t ad = smem_desc(ab + s * 2 * kSliceKc, kSliceKc, kCore);
-#pragma unroll 1
-          for (int t = 0; s + t < kSlices; ++t) {
-            const int q = min(s + t, kExact);
-            const uint64_t bd = smem_desc(bb + t * 2 * (kTN / 8 * kCore), kTN / 8 * kCore, kCore);
-            uint32_t accumulate;
-            if (q < kExact) {
-              accumulate = started[q] ? 1u : 0u;
-              started[q] = true;
-            } else {
-              accumulate = tail_started ? 1u : 0u;
-              tail_started = true;
-            }
-            mma_bf16(tmem + q * kTN, ad, bd, accumulate);
-          }
+        const uint32_t bar = full0 + 8 * b, dst = sbase + b * kStageBytes;
+        expect_tx(bar, kStageBytes);
+        bulk_load(dst, pa + (long long)st * kAStage, kAStage, bar);
+        bulk_load(dst + kAStage, pb + (long long)st * kBStage, kBStage, bar);
+      }
+      *produced_out = st;
+    }
+  } else if (warp == kEpiWarps) {
+    // MMA issuer
+    if (lane == 0) {
+      int st = 0;
+      bool tail_started = false;  // the tail accumulator runs over the whole of k
+      for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
+        if (c > 0 && !mbar_wait(acc_empty, (c - 1) & 1)) {
+          *abort_flag = 1;
+          break;
         }
-        mma_commit(empty0 + 8 * b);
-        committed = st + 1;
-        const int nxt = st + kStages - 1;
-        if (nxt < nst) {
-          if (st >= 1 && !mbar_wait(empty0 + 8 * ((st - 1) % kStages), ((st - 1) / kStages) & 1)) {
+        tc_fence_after();
+        uint32_t started = 0;  // bit q: accumulator q has been written in this chunk
+        const int c1 = min(nst, (c + 1) * kChunkStages);
+        for (; st < c1; ++st) {
+          const int b = st % kStages;
+          if (!mbar_wait(full0 + 8 * b, (st / kStages) & 1)) {
             *abort_flag = 1;
             break;
           }
-          issue_load(nxt);
-          loaded = nxt + 1;
+          tc_fence_after();
+          const uint32_t ab = sbase + b * kStageBytes, bb = ab + kAStage;
+          // the 36 slice pairs, unrolled: every offset and accumulator index is a
+          // compile-time constant and the flags stay in registers
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) {
+            const uint64_t ad = smem_desc(ab + s * 2 * kSliceKc, kSliceKc, kCore);
+#pragma unroll
+            for (int t = 0; t < kSlices - s; ++t) {
+              const int q = s + t < kExact ? s + t : kExact;
+              const uint64_t bd = smem_desc(bb + t * 2 * (kTN / 8 * kCore), kTN / 8 * kCore, kCore);
+              uint32_t accumulate;
+              if (q < kExact) {
+                accumulate = (started >> q) & 1u;
+                started |= 1u << q;
+              } else {
+                accumulate = tail_started ? 1u : 0u;
+                tail_started = true;
+              }
+              mma_bf16(tmem + q * kTN, ad, bd, accumulate);
+            }
+          }
+          mma_commit(empty0 + 8 * b);
+          *committed_out = st + 1;
         }
+        if (*abort_flag) break;
+        mma_commit(acc_full);  // arrives once every MMA of the chunk has finished
       }
     }
-    __syncthreads();
-    if (*abort_flag) break;
-    // the chunk's MMAs are complete once the commit of its last stage arrived
-    const int lst = c1 - 1;
-    // warp-uniform, so that the .sync.aligned loads below run on whole warps
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(empty0 + 8 * (lst % kStages), (lst / kStages) & 1));
-    if (!ok) atomicExch(abort_flag, 1);
-    tc_fence_after();
-    if (ok) {
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  } else {
+    // readers: fold every chunk's exact sums into 64-bit integers; write C at the end
+    const int quarter = warp % 4, c_half = warp / 4;
+    long long acc[kEpiCols];
+#pragma unroll
+    for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + c_half * kEpiCols;
+    for (int c = 0; c < n_chunks; ++c) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, c & 1));
+      if (!ok) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
 #pragma unroll
       for (int q = 0; q < kExact; ++q) {
         const float to_int = exp2f((float)(kDigitBits * (q + 2)));
         const int shift = kDigitBits * (kExact - 1 - q);
 #pragma unroll
-        for (int cb = 0; cb < kTN / 16; ++cb) {
+        for (int cb = 0; cb < kEpiCols / 16; ++cb) {
           uint32_t r[16];
           tmem_ld16(lane_addr + q * kTN + cb * 16, r);
 #pragma unroll
@@ -388,41 +415,42 @@ __global__ void __launch_bounds__(128, 1) ozaki_gemm_kernel(GemmArgs a) {
             acc[cb * 16 + i] += (long long)__float2int_rn(__uint_as_float(r[i]) * to_int) << shift;
         }
       }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_flag) break;
-  }
-
-  const bool aborted = *abort_flag != 0;
-  if (!aborted) {
-    // the tail accumulator, then C = alpha C + beta 2^{e_i + f_j} (acc 2^-42 + tail)
-    const int row = row0 + warp * 32 + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + kExact * kTN;
-    const int ei = row < a.m ? a.ea[row] : 0;
+      if (c == n_chunks - 1) {
+        // the tail accumulator, then C = alpha C + beta 2^{e_i + f_j} (acc 2^-42 + tail)
+        const int row = row0 + quarter * 32 + lane;
+        const int ei = row < a.m ? a.ea[row] : 0;
 #pragma unroll
-    for (int cb = 0; cb < kTN / 16; ++cb) {
-      uint32_t r[16];
-      tmem_ld16(lane_addr + cb * 16, r);
-      if (row < a.m) {
+        for (int cb = 0; cb < kEpiCols / 16; ++cb) {
+          uint32_t r[16];
+          tmem_ld16(lane_addr + kExact * kTN + cb * 16, r);
+          if (row < a.m) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int col = col0 + cb * 16 + i;
-          if (col >= a.n || (a.lower_only && col > row)) continue;
-          const int ex = ei + a.eb[col];
-          const double tail = (double)__uint_as_float(r[i]);  // every stage feeds the tail
-          const double v = ldexp((double)acc[cb * 16 + i], ex - kDigitBits * (kExact + 1)) + ldexp(tail, ex);
-          double* cp = a.C + (long long)row * a.ldc + col;
-          *cp = a.alpha == 0.0 ? a.beta * v : a.alpha * *cp + a.beta * v;
+            for (int i = 0; i < 16; ++i) {
+              const int col = col0 + c_half * kEpiCols + cb * 16 + i;
+              if (col >= a.n || (a.lower_only && col > row)) continue;
+              const int ex = ei + a.eb[col];
+              const double v = ldexp((double)acc[cb * 16 + i], ex - kDigitBits * (kExact + 1)) +
+                               ldexp((double)__uint_as_float(r[i]), ex);
+              double* cp = a.C + (long long)row * a.ldc + col;
+              *cp = a.alpha == 0.0 ? a.beta * v : a.alpha * *cp + a.beta * v;
+            }
+          }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acc_empty) : "memory");
     }
-  } else if (tid == 0) {
+  }
+
+  __syncthreads();
+  if (*abort_flag && tid == 0) {
     atomicOr(a.status, ST_TIMEOUT);
     // copies and MMAs in flight must land before the CTA's shared and tensor memory go
-    for (int st = waited_full; st < loaded; ++st) mbar_wait(full0 + 8 * (st % kStages), (st / kStages) & 1);
-    if (committed > 0)
-      mbar_wait(empty0 + 8 * ((committed - 1) % kStages), ((committed - 1) / kStages) & 1);
+    const int produced = *produced_out, committed = *committed_out;
+    for (int st = max(0, produced - kStages); st < produced; ++st)
+      mbar_wait(full0 + 8 * (st % kStages), (st / kStages) & 1);
+    if (committed > 0) mbar_wait(empty0 + 8 * ((committed - 1) % kStages), ((committed - 1) / kStages) & 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -439,7 +467,7 @@ inline unsigned blocks_for(long long n, int threads) {
 }  // namespace
 
 size_t ozaki_pack_bytes(int rows, int k) {
-  const long long r_pad = (long long)(rows + kTM - 1) / kTM * kTM;
+  const long long r_pad = (long long)(rows + kTM - 1) / kTM * kTM;  // covers both tile heights
   const long long k_pad = (long long)(k + kKS - 1) / kKS * kKS;
   return (size_t)(r_pad * k_pad * kSlices * 2);
 }
@@ -455,28 +483,31 @@ namespace {
 
 template <typename T>
 void pack_any(const T* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e, uint8_t* out,
-              cudaStream_t s) {
+              OzakiSide side, bool exponents, cudaStream_t s) {
   if (rows <= 0 || k <= 0) return;
-  if (trans)
-    row_exponent_kernel<T><<<blocks_for(rows, 256), 256, 0, s>>>(X, ld, 1, kscale, rows, k, e);
-  else
-    row_exponent_kernel<T><<<blocks_for(rows, 8), 256, 0, s>>>(X, ld, 0, kscale, rows, k, e);
-  const int r_pad = (rows + kTM - 1) / kTM * kTM;
+  if (exponents) {
+    if (trans)
+      row_exponent_kernel<T><<<blocks_for(rows, 256), 256, 0, s>>>(X, ld, 1, kscale, rows, k, e);
+    else
+      row_exponent_kernel<T><<<blocks_for(rows, 8), 256, 0, s>>>(X, ld, 0, kscale, rows, k, e);
+  }
+  const int tile_rows = side == OzakiSide::kLeft ? kTM : kTN;
+  const int r_pad = (rows + tile_rows - 1) / tile_rows * tile_rows;
   const int n_oct = (k + kKS - 1) / kKS * 2;
   pack_kernel<T><<<blocks_for((long long)r_pad * n_oct, 256), 256, 0, s>>>(X, ld, trans ? 1 : 0, kscale, rows, k,
-                                                                          e, out, r_pad, n_oct);
+                                                                          e, out, tile_rows, r_pad, n_oct);
 }
 
 }  // namespace
 
 void ozaki_pack(const double* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
-                uint8_t* out, cudaStream_t s) {
-  pack_any(X, ld, trans, rows, k, kscale, e, out, s);
+                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s) {
+  pack_any(X, ld, trans, rows, k, kscale, e, out, side, exponents, s);
 }
 
 void ozaki_pack(const float* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
-                uint8_t* out, cudaStream_t s) {
-  pack_any(X, ld, trans, rows, k, kscale, e, out, s);
+                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s) {
+  pack_any(X, ld, trans, rows, k, kscale, e, out, side, exponents, s);
 }
 
 void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, long long ldc, int m, int n,
@@ -498,7 +529,7 @@ void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, 
   g.a_lower = a_lower ? 1 : 0;
   g.status = status;
   dim3 grid((n + kTN - 1) / kTN, (m + kTM - 1) / kTM);
-  ozaki_gemm_kernel<<<grid, 128, kSmemBytes, s>>>(g);
+  ozaki_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(g);
 }
 
 ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k,
@@ -517,8 +548,8 @@ ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, 
   unsigned h_status = 0;
   if (st == EP_TV_OK) {
     cudaMemsetAsync(status, 0, sizeof(unsigned), s);
-    ozaki_pack(A, k, false, m, k, nullptr, ea, pa, s);
-    ozaki_pack(B, k, false, n, k, nullptr, eb, pb, s);
+    ozaki_pack(A, k, false, m, k, nullptr, ea, pa, OzakiSide::kLeft, true, s);
+    ozaki_pack(B, k, false, n, k, nullptr, eb, pb, OzakiSide::kRight, true, s);
     ozaki_gemm(OzakiOperand{pa, ea}, OzakiOperand{pb, eb}, k, C, n, m, n, 0.0, 1.0, false, false, status, s);
     if (cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -15,18 +15,24 @@ struct OzakiOperand {
   const int* exps;
 };
 
-// Bytes of the packed form of a rows x k operand.
+// Which operand a packing is for: left (rows of the output, 128-row tiles) or
+// right (columns of the output, 64-row tiles).
+enum class OzakiSide { kLeft, kRight };
+
+// Bytes of the packed form of a rows x k operand (either side).
 size_t ozaki_pack_bytes(int rows, int k);
 // Raises the kernel's dynamic shared-memory limit (once per process and device).
 ep_tv_status ozaki_init();
 // Packs rows x k operand X(r, k) = X[r * ld + k] (trans: X[k * ld + r]), times
-// kscale[k] when kscale is not NULL, into out (ozaki_pack_bytes(rows, k) bytes)
-// and its row exponents into e (rows ints).
+// kscale[k] when kscale is not NULL, into out (ozaki_pack_bytes(rows, k) bytes);
+// with exponents, first writes its row exponents into e (rows ints), else
+// uses those in e (packing one matrix for both sides).
 void ozaki_pack(const double* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
-                uint8_t* out, cudaStream_t s);
+                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s);
 void ozaki_pack(const float* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
-                uint8_t* out, cudaStream_t s);
-// C = alpha C + beta A B^T for packed A (m x k) and B (n x k); C row-major, ldc.
+                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s);
+// C = alpha C + beta A B^T for packed A (m x k, left side) and B (n x k, right
+// side); C row-major, ldc.
 // lower_only: only entries with col <= row are written.  a_lower: A is lower
 // triangular (row i has no entries beyond k = i), so row tiles stop early.
 // A timed-out wait raises ST_TIMEOUT in status.
