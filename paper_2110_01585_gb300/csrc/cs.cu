@@ -58,18 +58,26 @@ constexpr int kGk = 16;      // GEMM k step
 
 // C[i, j] = alpha * C[i, j] + beta_ * sum_k A[i, k] * B(k, j) for a tile of
 // (m x n); B(k, j) = B[j * ldb + k] (transposed, "NT") or B[k * ldb + j] ("NN").
-// lower_only: skip tiles strictly above the diagonal (C symmetric).
+// lower_only: skip tiles strictly above the diagonal (C symmetric).  a_lower: A
+// is lower triangular; b_lower: the matrix stored in B is lower triangular.  A
+// tile then skips the range of k where every product is zero (the sums of the
+// remaining terms are formed in the same order, so the result does not change).
 template <bool kNT>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(int m, int n, int k, const double* A, int lda,
                                                        const double* B, int ldb, double* C, int ldc,
-                                                       double alpha, double beta_, int lower_only) {
+                                                       double alpha, double beta_, int lower_only, int a_lower,
+                                                       int b_lower) {
   const int bi = blockIdx.y * kGt, bj = blockIdx.x * kGt;
   if (lower_only && bj > bi + kGt - 1) return;
   __shared__ double As[kGk][kGt + 1];
   __shared__ double Bs[kGk][kGt + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 each
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < k; k0 += kGk) {
+  int k_lo = 0, k_hi = k;
+  if (a_lower) k_hi = min(k_hi, bi + kGt);                     // A(i, kk) = 0 for kk > i
+  if (b_lower && kNT) k_hi = min(k_hi, bj + kGt);              // B(kk, j) = B_jkk = 0 for kk > j
+  if (b_lower && !kNT) k_lo = bj / kGk * kGk;                  // B(kk, j) = B_kkj = 0 for kk < j
+  for (int k0 = k_lo; k0 < k_hi; k0 += kGk) {
     // A tile: rows bi..bi+63, cols k0..k0+15
     for (int e = threadIdx.x; e < kGt * kGk; e += 256) {
       const int r = e / kGk, kk = e - r * kGk;
@@ -120,25 +128,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int m, int n, int k, cons
   }
 }
 
-// G = A diag(sqrt(c)) in FP64 (A is FP32, M x N row-major).
-__global__ void scale_cols_kernel(const float* A, const double* sqc, double* G, int M, int N) {
-  const long long total = (long long)M * N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % N);
-    G[e] = (double)A[e] * sqc[i];
-  }
-}
-
-// A as FP64 (kept for the triangular solve)
-__global__ void to_f64_kernel(const float* A, double* out, long long total) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x)
-    out[e] = (double)A[e];
-}
-
 // K = 0, then the diagonal gets the noise covariance: xi, or xi_v[i] for a
-// diagonal (non-i.i.d.) noise covariance (the GEMM adds G G^T with beta = 1).
+// diagonal (non-i.i.d.) noise covariance (the product adds G G^T with beta = 1).
 __global__ void init_k_kernel(double* K, int M, double xi, const double* xi_v) {
   const long long total = (long long)M * M;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -403,15 +394,16 @@ void fwht_rows(double* rows, long long nrows, int n, cudaStream_t s) {
 }
 
 void gemm(bool nt, int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C,
-          int ldc, double alpha, double beta_, bool lower_only, cudaStream_t s) {
+          int ldc, double alpha, double beta_, bool lower_only, cudaStream_t s, bool a_lower = false,
+          bool b_lower = false) {
   if (m <= 0 || n <= 0 || k <= 0) return;
   dim3 grid((n + kGt - 1) / kGt, (m + kGt - 1) / kGt);
   if (nt)
     gemm_f64_kernel<true><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta_,
-                                               lower_only ? 1 : 0);
+                                               lower_only ? 1 : 0, a_lower ? 1 : 0, b_lower ? 1 : 0);
   else
     gemm_f64_kernel<false><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta_,
-                                                lower_only ? 1 : 0);
+                                                lower_only ? 1 : 0, a_lower ? 1 : 0, b_lower ? 1 : 0);
 }
 
 }  // namespace
@@ -489,16 +481,18 @@ struct Segment {
 };
 
 // C = alpha C + beta X Y^T in the FP64 SIMT GEMM, X (m x k) row-major at ldx,
-// Y(j, kk) = Y[j * ldy + kk] or, when y_trans, Y[kk * ldy + j].  The products of
+// Y(j, kk) = Y[j * ldy + kk] or, when y_trans, Y[kk * ldy + j]; x_lower / y_lower:
+// the stored X / Y is lower triangular (the zero products are skipped).  The products of
 // the factorisation stay in FP64: the Schur complement K22 - L21 L21^T cancels
 // to the size of xi while its terms carry the capped cavity variances, which
 // needs an error relative to sum_k |L_ik L_jk| (an FP64 GEMM's), not to the
 // rows' largest entries (the split form's).
-void product(CsState* S, const double* X, long long ldx, const double* Y, long long ldy, bool y_trans, int m,
-             int n, int k, double* C, long long ldc, double alpha, double beta, bool lower_only, cudaStream_t s) {
+void product(CsState* S, const double* X, long long ldx, bool x_lower, const double* Y, long long ldy,
+             bool y_trans, bool y_lower, int m, int n, int k, double* C, long long ldc, double alpha, double beta,
+             bool lower_only, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return;
-  gemm(!y_trans, m, n, k, X, (int)ldx, Y, (int)ldy, C, (int)ldc, alpha, beta, lower_only, s);
-  S->simt_flops += 2.0 * m * n * k;
+  gemm(!y_trans, m, n, k, X, (int)ldx, Y, (int)ldy, C, (int)ldc, alpha, beta, lower_only, s, x_lower, y_lower);
+  S->simt_flops += (x_lower || y_lower ? 1.0 : 2.0) * m * n * k;  // a triangle halves the products
 }
 
 int split_point(int n) {
@@ -532,11 +526,11 @@ void chol_inv(CsState* S, double* K, long long ld, double* Z, long long ldz, int
   double* L21 = pool;                       // n2 x n1
   double* T = pool + (long long)n2 * n1;    // n2 x n1
   double* rest = T + (long long)n2 * n1;
-  product(S, K21, ld, Z, ldz, false, n2, n1, n1, L21, n1, 0.0, 1.0, false, s);
-  product(S, L21, n1, L21, n1, false, n2, n2, n1, K22, ld, 1.0, -1.0, true, s);
+  product(S, K21, ld, false, Z, ldz, false, true, n2, n1, n1, L21, n1, 0.0, 1.0, false, s);
+  product(S, L21, n1, false, L21, n1, false, false, n2, n2, n1, K22, ld, 1.0, -1.0, true, s);
   chol_inv(S, K22, ld, Z22, ldz, n2, rest, s);
-  product(S, L21, n1, Z, ldz, true, n2, n1, n1, T, n1, 0.0, 1.0, false, s);
-  product(S, Z22, ldz, T, n1, true, n2, n1, n2, Z21, ldz, 0.0, -1.0, false, s);
+  product(S, L21, n1, false, Z, ldz, true, true, n2, n1, n1, T, n1, 0.0, 1.0, false, s);
+  product(S, Z22, ldz, true, T, n1, true, false, n2, n1, n2, Z21, ldz, 0.0, -1.0, false, s);
 }
 
 unsigned bit_reverse(unsigned k, int bits) {
