@@ -1207,6 +1207,37 @@ __global__ void tw512_kernel(float2* tw) {
   }
 }
 
+// L2 eviction priorities for the preconditioner's planes: the complex plane of
+// each system pair and the residual read by both row passes are kept (evict
+// last) from their first touch to their last read, which releases them (evict
+// first); the streamed CG planes of the other kernels then go first.  The kept
+// footprint, one complex plane per pair plus the residuals, is about 70 MB at
+// 512^2 with 33 systems, inside the 129 MB L2.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_release() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol)
+               : "memory");
+}
+
 // Which passes take the 512-point kernels (the others take the Stockham ones).
 inline bool fft512_rows(const FftDesc& f) { return f.WP == kF; }
 inline bool fft512_cols(const FftDesc& f) { return f.HP == kF && f.WP >= kF512Warps; }
@@ -1277,6 +1308,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
   const float* r1p = Rr + (long long)j1 * N;
   float2* out = f.tmp + (long long)pair * f.H * kF;
   const int rend = min(f.H, (blockIdx.x + 1) * rpb);
+  const uint64_t keep = l2_policy_keep();
   for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
     const long long p0 = (long long)row * f.W;
     float2 v[16];
@@ -1284,11 +1316,11 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
     for (int m = 0; m < 16; ++m) {
       const int c = 32 * m + l;
       v[m] = make_float2(0.f, 0.f);
-      if (c < f.W) v[m] = make_float2(r0p[p0 + c], two ? r1p[p0 + c] : 0.f);
+      if (c < f.W) v[m] = make_float2(ld_hint(r0p + p0 + c, keep), two ? ld_hint(r1p + p0 + c, keep) : 0.f);
     }
     fft512_warp(v, scratch[w], tw);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) out[(long long)row * kF + 32 * m + l] = v[m];
+    for (int m = 0; m < 16; ++m) st_hint(out + (long long)row * kF + 32 * m + l, v[m], keep);
   }
 }
 
@@ -1307,12 +1339,13 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
   const int c0 = blockIdx.x * kF512Warps;
   float2* t = f.tmp + (long long)blockIdx.y * f.H * f.WP;
   const int cc = threadIdx.x & 7, ro = threadIdx.x >> 3;  // 32 rows x 8 columns per block step
+  const uint64_t keep = l2_policy_keep();
   {
     float2 x[16];  // all of the thread's tile loads in flight at once
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int i = 32 * u + ro;
-      x[u] = i < f.H ? t[(long long)i * f.WP + c0 + cc] : make_float2(0.f, 0.f);
+      x[u] = i < f.H ? ld_hint(t + (long long)i * f.WP + c0 + cc, keep) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 16; ++u) cols[cc][32 * u + ro] = x[u];
@@ -1342,7 +1375,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int i = 32 * u + ro;
-    if (i < f.H) t[(long long)i * f.WP + c0 + cc] = cols[cc][i];
+    if (i < f.H) st_hint(t + (long long)i * f.WP + c0 + cc, cols[cc][i], keep);
   }
 }
 
@@ -1365,18 +1398,19 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDes
   const int rows_per = (f.H + f.nbz - 1) / f.nbz;
   const int rend = min(f.H, (blockIdx.x + 1) * rows_per);
   const float2* tin = f.tmp + (long long)pair * f.H * kF;
+  const uint64_t release = l2_policy_release();
   double acc0 = 0.0, acc1 = 0.0;
   for (int row = blockIdx.x * rows_per + w; row < rend; row += kF512Warps) {
     const long long p0 = (long long)row * f.W;
     float2 v[16], rr[16];  // rr: the residuals of both systems, loaded before the transform
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      v[m] = cconj(tin[(long long)row * kF + 32 * m + l]);
+      v[m] = cconj(ld_hint(tin + (long long)row * kF + 32 * m + l, release));
       const int c = 32 * m + l;
       rr[m] = make_float2(0.f, 0.f);
       if (c < f.W) {
-        rr[m].x = Rr[(long long)j0 * N + p0 + c];
-        if (two) rr[m].y = Rr[(long long)j1 * N + p0 + c];
+        rr[m].x = ld_hint(Rr + (long long)j0 * N + p0 + c, release);
+        if (two) rr[m].y = ld_hint(Rr + (long long)j1 * N + p0 + c, release);
       }
     }
     fft512_warp(v, scratch[w], tw);
