@@ -1095,7 +1095,23 @@ ep_tv_status ep_tv_batch_sweep(ep_tv_batch* b, int32_t n_sweeps, int32_t em_ever
       c->cur ^= 1;
       ++c->sweeps;
     }
-    if (!b->lik.empty()) {
+    if (!b->lik.empty() && !tracing) {
+      // every likelihood update is one graph replay (its solver loops run on the
+      // device): enqueue them all from this thread, each on its own stream after
+      // the prior pass, and join them below
+      CK(cudaEventRecord(b->prior_done, b->stream));
+      for (size_t k = 0; k < b->lik.size(); ++k) {
+        ep_tv_ctx* c = b->ctx[b->lik[k]];
+        CK(cudaStreamWaitEvent(b->wstream[k], b->prior_done, 0));
+        const ep_tv_status st = likelihood_update(c->lik, c->tau0, c->nu0, c->ptau[c->cur], c->pnu[c->cur],
+                                                  c->status, c->counters, &c->tracer, b->wstream[k]);
+        if (st != EP_TV_OK) return st;
+        if (likelihood_graph_last(c->lik)) ++c->graph_sweeps;
+        CK(cudaEventRecord(b->wdone[k], b->wstream[k]));
+      }
+      for (size_t k = 0; k < b->lik.size(); ++k) CK(cudaStreamWaitEvent(b->stream, b->wdone[k], 0));
+    } else if (!b->lik.empty()) {
+      // traced: the host-driven solver loops poll convergence, one host thread each
       CK(cudaEventRecord(b->prior_done, b->stream));
       {
         std::lock_guard<std::mutex> lock(b->mu);

@@ -1,7 +1,6 @@
 // FP64-accurate matrix products on the BF16 tensor cores (tcgen05), for the
 // compressive-sensing likelihood site (the operator products of Sec. III-C's
-// Woodbury form: K = A C A^T, W = L^{-1} A, and the blocks of the Cholesky
-// factorisation and triangular inverse of K).
+// Woodbury form: K = A C A^T and W = L^{-1} A = Z A).
 //
 // Splitting (Ozaki's error-free splitting of a product into exact slice
 // products).  Every operand row r is scaled by 2^-e_r, e_r the binary exponent
@@ -21,8 +20,10 @@
 // carry 2^-35 or less of the result and go to a sixth FP32 accumulator over the
 // whole of k.  (The tensor core's FP32 accumulation is not round-to-nearest at
 // every add: measured on a single product, a tail starting at s + t = 6 left an
-// error of 2^-50, which this split removes.)  The result is FP64-accurate:
-// |error| <~ 2^-52 sum_k |A_ik||B_jk| plus one final rounding.
+// error of 2^-50, which this split removes.)  The error is relative to the rows'
+// largest entries, as for every split of this kind:
+//   |error| <~ 2^-55 (max|A_i| sum|B_j| + max|B_j| sum|A_i|) + 2^-52 k max|A_i| max|B_j|
+// plus one final rounding; for operands of one scale that is an FP64 product's.
 //
 // Kernel: one CTA per 128 x 64 output tile; K in stages of 16 (one MMA K step),
 // four shared-memory stages filled by bulk asynchronous copies (cp.async.bulk,
@@ -31,7 +32,7 @@
 // 64 rows, 8 slices each).  Warp-specialised: one thread issues the copies and
 // waits only for stages to free up, one thread issues the 36 MMAs of a stage
 // (M = 128, N = 64, K = 16, BF16 inputs, FP32 accumulators in tensor memory) and
-// waits only for stages to land, and four warps read the accumulators back
+// waits only for stages to land, and eight warps read the accumulators back
 // (tcgen05.ld) at every chunk end, handing them back to the MMA thread through
 // a second pair of barriers.  Every wait on an mbarrier gives up after two
 // seconds: the kernel then raises ST_TIMEOUT, waits (bounded) for its copies and

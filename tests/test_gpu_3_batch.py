@@ -44,6 +44,10 @@ def test_batch_equals_one_by_one():
     with Batch(batched) as b:
         b.sweep(6, em_every=3)
     torch.cuda.synchronize()
+    # the deconvolution sites of the batch ran as graph replays, enqueued without host threads
+    for (k, _, _), e in zip(probs, batched):
+        if k != "denoise":
+            assert e.graph_sweeps() == 6
     for e1, e2 in zip(single, batched):
         assert e1.status() == 0 and e2.status() == 0
         m1, v1 = e1.posterior()
