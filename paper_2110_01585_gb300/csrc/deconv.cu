@@ -1197,6 +1197,9 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f,
 constexpr int kF = 512;
 constexpr int kXs = 578;        // scratch / staged-column pitch in float2
 constexpr int kF512Warps = 8;   // warps per block of the 512-point kernels
+// Rows per warp of the 512-point row passes: a warp loads its next row into
+// registers while it transforms the current one.
+constexpr int kRowsPerWarp512 = 4;
 
 __global__ void tw512_kernel(float2* tw) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1309,15 +1312,23 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
   float2* out = f.tmp + (long long)pair * f.H * kF;
   const int rend = min(f.H, (blockIdx.x + 1) * rpb);
   const uint64_t keep = l2_policy_keep();
-  for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
-    const long long p0 = (long long)row * f.W;
-    float2 v[16];
+  float2 nx[16];  // the warp's next row, in flight during the current transform
+  auto load_row = [&](int rw) {
+    const long long p0 = (long long)rw * f.W;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int c = 32 * m + l;
-      v[m] = make_float2(0.f, 0.f);
-      if (c < f.W) v[m] = make_float2(ld_hint(r0p + p0 + c, keep), two ? ld_hint(r1p + p0 + c, keep) : 0.f);
+      nx[m] = make_float2(0.f, 0.f);
+      if (c < f.W) nx[m] = make_float2(ld_hint(r0p + p0 + c, keep), two ? ld_hint(r1p + p0 + c, keep) : 0.f);
     }
+  };
+  int row = blockIdx.x * rpb + w;
+  if (row < rend) load_row(row);
+  for (; row < rend; row += kF512Warps) {
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = nx[m];
+    if (row + kF512Warps < rend) load_row(row + kF512Warps);
     fft512_warp(v, scratch[w], tw);
 #pragma unroll
     for (int m = 0; m < 16; ++m) st_hint(out + (long long)row * kF + 32 * m + l, v[m], keep);
@@ -1381,7 +1392,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(Fft
 
 // fft_rows_inv_kernel for WP = 512: one warp per row of the block's range
 // [blockIdx.x rows_per, +rows_per), rows_per = ceil(H / nbz).
-__global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDesc f,
+__global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_rows_inv_kernel(FftDesc f,
                                                                          const float* __restrict__ Rr,
                                                                          float* Z, double* part_rz) {
   if (pair_idle(f, blockIdx.y)) return;
@@ -1400,19 +1411,33 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_inv_kernel(FftDes
   const float2* tin = f.tmp + (long long)pair * f.H * kF;
   const uint64_t release = l2_policy_release();
   double acc0 = 0.0, acc1 = 0.0;
-  for (int row = blockIdx.x * rows_per + w; row < rend; row += kF512Warps) {
-    const long long p0 = (long long)row * f.W;
-    float2 v[16], rr[16];  // rr: the residuals of both systems, loaded before the transform
+  // the warp's next row (transform input and both residuals), in flight during
+  // the current transform
+  float2 nv[16], nr[16];
+  auto load_row = [&](int rw) {
+    const long long p0 = (long long)rw * f.W;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      v[m] = cconj(ld_hint(tin + (long long)row * kF + 32 * m + l, release));
+      nv[m] = cconj(ld_hint(tin + (long long)rw * kF + 32 * m + l, release));
       const int c = 32 * m + l;
-      rr[m] = make_float2(0.f, 0.f);
+      nr[m] = make_float2(0.f, 0.f);
       if (c < f.W) {
-        rr[m].x = ld_hint(Rr + (long long)j0 * N + p0 + c, release);
-        if (two) rr[m].y = ld_hint(Rr + (long long)j1 * N + p0 + c, release);
+        nr[m].x = ld_hint(Rr + (long long)j0 * N + p0 + c, release);
+        if (two) nr[m].y = ld_hint(Rr + (long long)j1 * N + p0 + c, release);
       }
     }
+  };
+  int row = blockIdx.x * rows_per + w;
+  if (row < rend) load_row(row);
+  for (; row < rend; row += kF512Warps) {
+    const long long p0 = (long long)row * f.W;
+    float2 v[16], rr[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      v[m] = nv[m];
+      rr[m] = nr[m];
+    }
+    if (row + kF512Warps < rend) load_row(row + kF512Warps);
     fft512_warp(v, scratch[w], tw);
     float rz0 = 0.f, rz1 = 0.f;
 #pragma unroll
@@ -1835,7 +1860,7 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
   f.arrive = L->d_arrive + L->R;
   f.first = first;
   f.counters = counters;
-  constexpr int kRows512 = kF512Warps;  // one row per warp: more blocks in flight hide load latency
+  constexpr int kRows512 = kF512Warps * kRowsPerWarp512;
   if (fft512_rows(f))
     fft512_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs), 32 * kF512Warps, 0, s>>>(
         f, L->Rr, kRows512);
@@ -2104,8 +2129,10 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     const int cap = kFftMaxItems * kFftThreads;
     f.rpb = std::max(1, std::min({HP, 4096 / WP, cap * rmin(WP) / WP}));
     f.cw = std::max(1, std::min({WP, 16, cap * rmin(HP) / HP}));
-    // r.z partials: one per block of the inverse row pass (8 rows each for 512-point rows)
-    f.nbz = WP == kF ? (c.H + 7) / 8 : std::min(c.H, 64);
+    // r.z partials: one per block of the inverse row pass (kF512Warps * kRowsPerWarp512
+    // rows each for 512-point rows)
+    constexpr int kRowsInv512 = kF512Warps * kRowsPerWarp512;
+    f.nbz = WP == kF ? (c.H + kRowsInv512 - 1) / kRowsInv512 : std::min(c.H, 64);
     L->nbz = f.nbz;
     L->smem_rows = sizeof(float2) * ((size_t)WP + (size_t)f.rpb * WP);
     L->smem_cols = sizeof(float2) * ((size_t)HP + (size_t)HP * f.cw);
