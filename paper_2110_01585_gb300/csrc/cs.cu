@@ -27,8 +27,10 @@
 // Structure of one update.  The products with A (K = A C A^T and W = L^{-1} A =
 // Z A, Z = L^{-1}) run on the BF16 tensor cores in the FP64-accurate split form of
 // ozaki.cu.  K = L L^T and Z = L^{-1} come together from a recursion on halves
-// (L21 = K21 Z11^T, K22 -= L21 L21^T, Z21 = -Z22 L21 Z11) in FP64 on the CUDA
-// cores.  The mean uses v = Z t and g = W^T v.
+// (L21 = K21 Z11^T, K22 -= L21 L21^T, Z21 = -Z22 L21 Z11) whose large products
+// run in the same split form with 10 digit slices and seven exact diagonals (as
+// accurate as FP64 on these operands); blocks of 64 rows and products below 256
+// stay on the FP64 CUDA cores.  The mean uses v = Z t and g = W^T v.
 //
 // Kernels here: an FP64 tiled GEMM (64 x 64 tiles, 4 x 4 per thread) for the
 // small products; the Cholesky factor and inverse of one block of at most 64 rows
@@ -429,10 +431,11 @@ struct CsState {
   double* xi_v = nullptr;     // M noise variances (diagonal noise covariance), or NULL
   int* sel = nullptr;         // Hadamard: M Sylvester row indices
   // split-BF16 tensor-core products: packed operands and their row exponents
-  uint8_t* pack_a = nullptr;  // dense: left operands (G, then Z)
-  uint8_t* pack_b = nullptr;  // dense: G as the right operand of G G^T
+  uint8_t* pack_a = nullptr;  // left operands: G, Z, the factorisation's blocks
+  uint8_t* pack_b = nullptr;  // right operands: G of G G^T, the factorisation's blocks
   uint8_t* pack_at = nullptr; // dense: A^T, packed once
   int* exp_a = nullptr;
+  int* exp_b = nullptr;
   int* exp_at = nullptr;
   unsigned* status = nullptr; // the context's status word (set per update)
   Tracer* tr = nullptr;       // the context's tracer (set per update)
@@ -460,6 +463,7 @@ void cs_free(CsState* S) {
   cudaFree(S->pack_b);
   cudaFree(S->pack_at);
   cudaFree(S->exp_a);
+  cudaFree(S->exp_b);
   cudaFree(S->exp_at);
   delete S;
 }
@@ -480,19 +484,45 @@ struct Segment {
   }
 };
 
-// C = alpha C + beta X Y^T in the FP64 SIMT GEMM, X (m x k) row-major at ldx,
-// Y(j, kk) = Y[j * ldy + kk] or, when y_trans, Y[kk * ldy + j]; x_lower / y_lower:
-// the stored X / Y is lower triangular (the zero products are skipped).  The products of
-// the factorisation stay in FP64: the Schur complement K22 - L21 L21^T cancels
-// to the size of xi while its terms carry the capped cavity variances, which
-// needs an error relative to sum_k |L_ik L_jk| (an FP64 GEMM's), not to the
-// rows' largest entries (the split form's).
+// Products of the factorisation at least this large in every dimension run on the
+// tensor cores; smaller ones in the FP64 SIMT GEMM.
+constexpr int kMmaMin = 256;
+// Digit slices of the factorisation's products.  The Schur complement
+// K22 - L21 L21^T cancels to the size of xi while its terms carry the capped
+// cavity variances, and the split form's error is relative to the rows' largest
+// entries.  With the operator products' form (8 slices, FP32 tail from s + t = 7)
+// the Hadamard 128^2 case missed parity by 100x; the error was the tail's FP32
+// accumulation (10 slices alone changed nothing; a tail from s + t = 8 cut it 70x).
+// 10 slices with seven exact diagonals (tail from s + t = 9) reproduce the FP64
+// factorisation's parity errors to four digits on every case.
+constexpr int kFactorSlices = 10;
+constexpr int kFactorMaxK = 8192;  // the 10-slice product's integer accumulators hold k <= 8192
+
+// C = alpha C + beta X Y^T, X (m x k) row-major at ldx, Y(j, kk) = Y[j * ldy + kk]
+// or, when y_trans, Y[kk * ldy + j]; x_lower / y_lower: the stored X / Y is lower
+// triangular (the SIMT GEMM skips the zero products; the split product stops a
+// row tile of a triangular X at its diagonal).  same: Y is X.
 void product(CsState* S, const double* X, long long ldx, bool x_lower, const double* Y, long long ldy,
-             bool y_trans, bool y_lower, int m, int n, int k, double* C, long long ldc, double alpha, double beta,
-             bool lower_only, cudaStream_t s) {
+             bool y_trans, bool y_lower, bool same, int m, int n, int k, double* C, long long ldc, double alpha,
+             double beta, bool lower_only, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return;
-  gemm(!y_trans, m, n, k, X, (int)ldx, Y, (int)ldy, C, (int)ldc, alpha, beta, lower_only, s, x_lower, y_lower);
-  S->simt_flops += (x_lower || y_lower ? 1.0 : 2.0) * m * n * k;  // a triangle halves the products
+  if (std::min(m, n) < kMmaMin || k < kMmaMin || k > kFactorMaxK) {
+    gemm(!y_trans, m, n, k, X, (int)ldx, Y, (int)ldy, C, (int)ldc, alpha, beta, lower_only, s, x_lower,
+         y_lower);
+    S->simt_flops += (x_lower || y_lower ? 1.0 : 2.0) * m * n * k;  // a triangle halves the products
+    return;
+  }
+  const int sl = kFactorSlices;
+  const double f = ozaki_tensor_flops(m, n, k, sl) * (x_lower || lower_only ? 0.5 : 1.0);
+  S->mma_flops += f;
+  Segment seg(S, s, f);
+  ozaki_pack(X, ldx, false, m, k, nullptr, S->exp_a, S->pack_a, OzakiSide::kLeft, true, s, sl);
+  if (same)
+    ozaki_pack(X, ldx, false, m, k, nullptr, S->exp_a, S->pack_b, OzakiSide::kRight, false, s, sl);
+  else
+    ozaki_pack(Y, ldy, y_trans, n, k, nullptr, S->exp_b, S->pack_b, OzakiSide::kRight, true, s, sl);
+  ozaki_gemm(OzakiOperand{S->pack_a, S->exp_a, sl}, OzakiOperand{S->pack_b, same ? S->exp_a : S->exp_b, sl}, k,
+             C, ldc, m, n, alpha, beta, lower_only, x_lower, S->status, s);
 }
 
 int split_point(int n) {
@@ -526,11 +556,11 @@ void chol_inv(CsState* S, double* K, long long ld, double* Z, long long ldz, int
   double* L21 = pool;                       // n2 x n1
   double* T = pool + (long long)n2 * n1;    // n2 x n1
   double* rest = T + (long long)n2 * n1;
-  product(S, K21, ld, false, Z, ldz, false, true, n2, n1, n1, L21, n1, 0.0, 1.0, false, s);
-  product(S, L21, n1, false, L21, n1, false, false, n2, n2, n1, K22, ld, 1.0, -1.0, true, s);
+  product(S, K21, ld, false, Z, ldz, false, true, false, n2, n1, n1, L21, n1, 0.0, 1.0, false, s);
+  product(S, L21, n1, false, L21, n1, false, false, true, n2, n2, n1, K22, ld, 1.0, -1.0, true, s);
   chol_inv(S, K22, ld, Z22, ldz, n2, rest, s);
-  product(S, L21, n1, false, Z, ldz, true, true, n2, n1, n1, T, n1, 0.0, 1.0, false, s);
-  product(S, Z22, ldz, true, T, n1, true, false, n2, n1, n2, Z21, ldz, 0.0, -1.0, false, s);
+  product(S, L21, n1, false, Z, ldz, true, true, false, n2, n1, n1, T, n1, 0.0, 1.0, false, s);
+  product(S, Z22, ldz, true, T, n1, true, false, false, n2, n1, n2, Z21, ldz, 0.0, -1.0, false, s);
 }
 
 unsigned bit_reverse(unsigned k, int bits) {
@@ -550,7 +580,10 @@ int log2_exact(int v) {
 bool alloc_common(CsState* S) {
   const int M = S->M, N = S->N;
   const long long MN = (long long)M * N, MM = (long long)M * M;
-  const size_t pa = ozaki_pack_bytes(M, std::max(M, N));  // G (M x N), then Z (M x M)
+  // left operands: G (M x N, dense operator), Z (M x M) and the factorisation's blocks;
+  // right operands: G (dense) and the factorisation's blocks
+  const size_t fac = ozaki_pack_bytes(M, M, kFactorSlices);
+  const size_t pa = std::max(S->hadamard ? 0 : ozaki_pack_bytes(M, N), fac);
   return cudaMalloc(&S->G, sizeof(double) * MN) == cudaSuccess &&
          cudaMalloc(&S->K, sizeof(double) * MM) == cudaSuccess &&
          cudaMalloc(&S->Z, sizeof(double) * MM) == cudaSuccess &&
@@ -562,8 +595,9 @@ bool alloc_common(CsState* S) {
          cudaMalloc(&S->g, sizeof(double) * N) == cudaSuccess &&
          cudaMalloc(&S->t, sizeof(double) * M) == cudaSuccess &&
          cudaMalloc(&S->v, sizeof(double) * M) == cudaSuccess &&
-         (S->hadamard || (cudaMalloc(&S->pack_a, pa) == cudaSuccess &&
-                          cudaMalloc(&S->exp_a, sizeof(int) * M) == cudaSuccess));
+         cudaMalloc(&S->pack_a, pa) == cudaSuccess && cudaMalloc(&S->pack_b, pa) == cudaSuccess &&
+         cudaMalloc(&S->exp_a, sizeof(int) * M) == cudaSuccess &&
+         cudaMalloc(&S->exp_b, sizeof(int) * M) == cudaSuccess;
 }
 
 // Hadamard operator: Sylvester row of every Paley-ordered pattern, and
@@ -620,7 +654,6 @@ ep_tv_status cs_create(const LikelihoodConfig& cfg, cudaStream_t s, CsState** ou
     return EP_TV_OK;
   }
   if (!alloc_common(S) || cudaMalloc(&S->pack_at, ozaki_pack_bytes(S->N, S->M)) != cudaSuccess ||
-      cudaMalloc(&S->pack_b, ozaki_pack_bytes(S->M, S->N)) != cudaSuccess ||
       cudaMalloc(&S->exp_at, sizeof(int) * S->N) != cudaSuccess) {
     cudaGetLastError();
     cs_free(S);

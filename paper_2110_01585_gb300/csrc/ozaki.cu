@@ -1,6 +1,7 @@
 // FP64-accurate matrix products on the BF16 tensor cores (tcgen05), for the
-// compressive-sensing likelihood site (the operator products of Sec. III-C's
-// Woodbury form: K = A C A^T and W = L^{-1} A = Z A).
+// compressive-sensing likelihood site (Sec. III-C's Woodbury form: the operator
+// products K = A C A^T and W = L^{-1} A = Z A, and the large products of the
+// Cholesky factorisation and inverse of K).
 //
 // Splitting (Ozaki's error-free splitting of a product into exact slice
 // products).  Every operand row r is scaled by 2^-e_r, e_r the binary exponent
@@ -32,9 +33,10 @@
 // 64 rows, 8 slices each).  Warp-specialised: one thread issues the copies and
 // waits only for stages to free up, one thread issues the 36 MMAs of a stage
 // (M = 128, N = 64, K = 16, BF16 inputs, FP32 accumulators in tensor memory) and
-// waits only for stages to land, and eight warps read the accumulators back
+// waits only for stages to land, and sixteen warps read the accumulators back
 // (tcgen05.ld) at every chunk end, handing them back to the MMA thread through
-// a second pair of barriers.  Every wait on an mbarrier gives up after two
+// a second pair of barriers.  A second form, 10 slices with seven exact
+// diagonals (Split<10>), serves the Cholesky factorisation's products.  Every wait on an mbarrier gives up after two
 // seconds: the kernel then raises ST_TIMEOUT, waits (bounded) for its copies and
 // MMAs in flight, frees its tensor memory and exits.
 #include <cuda_bf16.h>
@@ -50,27 +52,41 @@ namespace eptv {
 
 namespace {
 
-constexpr int kSlices = 8;
 constexpr int kDigitBits = 7;
 constexpr int kTM = 128;             // output tile rows; packing row tile
 constexpr int kTN = 64;              // output tile columns
 constexpr int kKS = 16;              // K per stage (one MMA K step)
-constexpr int kStages = 4;
-constexpr int kChunkStages = 16;     // exact accumulation over 256 values of k
-constexpr int kExact = 5;            // accumulators of the diagonals s + t = 2..6
 constexpr int kCore = 128;           // one core matrix: 8 rows x 16 bytes
 constexpr int kSliceKc = kTM / 8 * kCore;               // 16 row groups: 2048 bytes
-constexpr int kBlockBytes = kSlices * 2 * kSliceKc;     // packed 128 x 16 block: 32 KB
-constexpr int kAStage = kBlockBytes;
-constexpr int kBStage = kSlices * 2 * (kTN / 8 * kCore);  // 64-row half: 16 KB
-constexpr int kStageBytes = kAStage + kBStage;          // 48 KB
-// Dynamic shared memory: the stages, 8 KB of slack past the last stage (so that
-// every descriptor address stays inside the allocation) and the barriers.
-constexpr int kSmemBytes = 1024 + kStages * kStageBytes + 8192 + 256;
-constexpr int kTmemCols = 512;       // 6 accumulators of 64 columns, rounded up
+constexpr int kSliceKcB = kTN / 8 * kCore;              // 8 row groups: 1024 bytes
+constexpr int kTmemCols = 512;  // the accumulators (at most 7 of 64 columns), rounded up
+
+// Shapes that depend on the number of digit slices S (8 for the operator
+// products, 10 where the product is to be more accurate than an FP64 GEMM):
+// a stage holds the S slices of a 128 x 16 A block and a 64 x 16 B block; as many
+// stages as fit in shared memory (four of 48 KB for S = 8, three of 60 KB for 10).
+template <int S>
+struct Split {
+  // exact accumulators (the diagonals s + t = 2 .. kExact + 1) and the chunk of k
+  // over which their sums stay exact integers (below 2^22.2 of their unit): for
+  // S = 8 five diagonals over 256 values, the FP32 tail from s + t = 7 (2^-35 of
+  // the result); for S = 10 seven over 128, the tail from s + t = 9 (2^-49).  The
+  // chunk sums go into two 64-bit integers per output, diagonals 2-4 and the rest,
+  // which stay below 2^51 for k <= 8192 (S = 10) or 65536 (S = 8)
+  static constexpr int kExact = S <= 8 ? 5 : 7;
+  static constexpr int kChunkStages = S <= 8 ? 16 : 8;
+  static_assert(kTN * (kExact + 1) <= kTmemCols, "tensor memory");
+  static constexpr int kAStage = S * 2 * kSliceKc;
+  static constexpr int kBStage = S * 2 * kSliceKcB;
+  static constexpr int kStageBytes = kAStage + kBStage;
+  static constexpr int kStages = S <= 8 ? 4 : 3;
+  // the stages, 8 KB of slack past the last stage (so that every descriptor
+  // address stays inside the allocation) and the barriers
+  static constexpr int kSmemBytes = 1024 + kStages * kStageBytes + 8192 + 256;
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
-static_assert(kTN * (kExact + 1) <= kTmemCols, "tensor memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -202,7 +218,7 @@ __global__ void row_exponent_kernel(const T* X, long long ld, int trans, const d
 // byte ((s * 2 + kc) * TR / 8 + g) * 128 + w * 16 of the block for row 8 g + w.
 // Every block is one contiguous bulk copy.  Rows >= R and k >= K (the padding)
 // are written as zeros.
-template <typename T>
+template <typename T, int S>
 __global__ void pack_kernel(const T* X, long long ld, int trans, const double* ks, int R, int K, const int* e,
                             uint8_t* out, int tile_rows, int r_pad, int n_oct) {
   const long long total = (long long)r_pad * n_oct;
@@ -231,10 +247,10 @@ __global__ void pack_kernel(const T* X, long long ld, int trans, const double* k
   const int groups = tile_rows / 8;
   const int rt = r / tile_rows, rr = r % tile_rows, g = rr / 8, w = rr % 8;
   const int kt = o / 2, kc = o % 2;
-  const long long block_bytes = (long long)kSlices * 2 * groups * kCore;
+  const long long block_bytes = (long long)S * 2 * groups * kCore;
   uint8_t* base = out + ((long long)rt * nkt + kt) * block_bytes + ((long long)kc * groups + g) * kCore + w * 16;
 #pragma unroll
-  for (int s = 0; s < kSlices; ++s) {
+  for (int s = 0; s < S; ++s) {
     const float w_s = exp2f(-(float)(kDigitBits * (s + 1)));
     uint32_t packed[4];
 #pragma unroll
@@ -269,17 +285,22 @@ struct GemmArgs {
   unsigned* status;
 };
 
-// Roles: warps 0-7 read the accumulators (warp w reads tensor-memory lanes
-// 32 (w % 4) .. + 31, i.e. output rows, and output columns 32 (w / 4) .. + 31);
-// warp 8 lane 0 issues the MMAs; warp 9 lane 0 issues the bulk copies.  Barriers:
-// full[b] (a stage's copies landed), empty[b] (the MMAs reading stage b
+// Roles: warps 0-15 read the accumulators (warp w reads tensor-memory lanes
+// 32 (w % 4) .. + 31, i.e. output rows, and output columns 16 (w / 4) .. + 15);
+// warp 16 lane 0 issues the MMAs; warp 17 lane 0 issues the bulk copies.
+// Barriers: full[b] (a stage's copies landed), empty[b] (the MMAs reading stage b
 // finished), acc_full (a chunk's MMAs finished), acc_empty (the reading warps are
 // done with the chunk's accumulators).
-constexpr int kEpiWarps = 8;
-constexpr int kEpiCols = kTN / 2;  // output columns per reading warp
+constexpr int kEpiWarps = 16;
+constexpr int kEpiCols = kTN / 4;  // output columns per reading warp
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
+  using Sh = Split<S>;
+  constexpr int kStages = Sh::kStages, kStageBytes = Sh::kStageBytes;
+  constexpr int kExact = Sh::kExact, kChunkStages = Sh::kChunkStages;
+  constexpr int kAStage = Sh::kAStage, kBStage = Sh::kBStage;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + 8192);
@@ -362,15 +383,15 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
           }
           tc_fence_after();
           const uint32_t ab = sbase + b * kStageBytes, bb = ab + kAStage;
-          // the 36 slice pairs, unrolled: every offset and accumulator index is a
-          // compile-time constant and the flags stay in registers
+          // the S (S + 1) / 2 slice pairs, unrolled: every offset and accumulator
+          // index is a compile-time constant and the flags stay in registers
 #pragma unroll
-          for (int s = 0; s < kSlices; ++s) {
+          for (int s = 0; s < S; ++s) {
             const uint64_t ad = smem_desc(ab + s * 2 * kSliceKc, kSliceKc, kCore);
 #pragma unroll
-            for (int t = 0; t < kSlices - s; ++t) {
+            for (int t = 0; t < S - s; ++t) {
               const int q = s + t < kExact ? s + t : kExact;
-              const uint64_t bd = smem_desc(bb + t * 2 * (kTN / 8 * kCore), kTN / 8 * kCore, kCore);
+              const uint64_t bd = smem_desc(bb + t * 2 * kSliceKcB, kSliceKcB, kCore);
               uint32_t accumulate;
               if (q < kExact) {
                 accumulate = (started >> q) & 1u;
@@ -390,12 +411,14 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
       }
     }
   } else {
-    // readers: fold every chunk's exact sums into 64-bit integers; write C at the end
-    const int quarter = warp % 4, c_half = warp / 4;
-    long long acc[kEpiCols];
+    // readers: fold every chunk's exact sums into two 64-bit integers per output,
+    // acc_hi for the diagonals s + t = 2..4 (unit 2^-28) and acc_lo for the others
+    // (unit 2^-7 (kExact + 1)); write C at the end
+    const int quarter = warp % 4, c_part = warp / 4;
+    long long acc_hi[kEpiCols], acc_lo[kEpiCols];
 #pragma unroll
-    for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
-    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + c_half * kEpiCols;
+    for (int j = 0; j < kEpiCols; ++j) acc_hi[j] = acc_lo[j] = 0;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + c_part * kEpiCols;
     for (int c = 0; c < n_chunks; ++c) {
       const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, c & 1));
       if (!ok) {
@@ -406,18 +429,24 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
 #pragma unroll
       for (int q = 0; q < kExact; ++q) {
         const float to_int = exp2f((float)(kDigitBits * (q + 2)));
-        const int shift = kDigitBits * (kExact - 1 - q);
+        const int shift = q < 3 ? kDigitBits * (2 - q) : kDigitBits * (kExact - 1 - q);
 #pragma unroll
         for (int cb = 0; cb < kEpiCols / 16; ++cb) {
           uint32_t r[16];
           tmem_ld16(lane_addr + q * kTN + cb * 16, r);
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            acc[cb * 16 + i] += (long long)__float2int_rn(__uint_as_float(r[i]) * to_int) << shift;
+          for (int i = 0; i < 16; ++i) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[i]) * to_int) << shift;
+            if (q < 3)
+              acc_hi[cb * 16 + i] += v;
+            else
+              acc_lo[cb * 16 + i] += v;
+          }
         }
       }
       if (c == n_chunks - 1) {
-        // the tail accumulator, then C = alpha C + beta 2^{e_i + f_j} (acc 2^-42 + tail)
+        // the tail accumulator, then
+        // C = alpha C + beta 2^{e_i + f_j} (acc_hi 2^-28 + acc_lo 2^-7 (kExact + 1) + tail)
         const int row = row0 + quarter * 32 + lane;
         const int ei = row < a.m ? a.ea[row] : 0;
 #pragma unroll
@@ -427,10 +456,11 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
           if (row < a.m) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const int col = col0 + c_half * kEpiCols + cb * 16 + i;
+              const int col = col0 + c_part * kEpiCols + cb * 16 + i;
               if (col >= a.n || (a.lower_only && col > row)) continue;
               const int ex = ei + a.eb[col];
-              const double v = ldexp((double)acc[cb * 16 + i], ex - kDigitBits * (kExact + 1)) +
+              const double v = ldexp((double)acc_hi[cb * 16 + i], ex - kDigitBits * 4) +
+                               ldexp((double)acc_lo[cb * 16 + i], ex - kDigitBits * (kExact + 1)) +
                                ldexp((double)__uint_as_float(r[i]), ex);
               double* cp = a.C + (long long)row * a.ldc + col;
               *cp = a.alpha == 0.0 ? a.beta * v : a.alpha * *cp + a.beta * v;
@@ -467,24 +497,25 @@ inline unsigned blocks_for(long long n, int threads) {
 
 }  // namespace
 
-size_t ozaki_pack_bytes(int rows, int k) {
+size_t ozaki_pack_bytes(int rows, int k, int slices) {
   const long long r_pad = (long long)(rows + kTM - 1) / kTM * kTM;  // covers both tile heights
   const long long k_pad = (long long)(k + kKS - 1) / kKS * kKS;
-  return (size_t)(r_pad * k_pad * kSlices * 2);
+  return (size_t)(r_pad * k_pad * slices * 2);
 }
 
 ep_tv_status ozaki_init() {
-  return cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
-                 cudaSuccess
-             ? EP_TV_OK
-             : EP_TV_ERR_CUDA;
+  const bool ok = cudaFuncSetAttribute(ozaki_gemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Split<8>::kSmemBytes) == cudaSuccess &&
+                  cudaFuncSetAttribute(ozaki_gemm_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Split<10>::kSmemBytes) == cudaSuccess;
+  return ok ? EP_TV_OK : EP_TV_ERR_CUDA;
 }
 
 namespace {
 
 template <typename T>
 void pack_any(const T* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e, uint8_t* out,
-              OzakiSide side, bool exponents, cudaStream_t s) {
+              OzakiSide side, bool exponents, int slices, cudaStream_t s) {
   if (rows <= 0 || k <= 0) return;
   if (exponents) {
     if (trans)
@@ -495,20 +526,23 @@ void pack_any(const T* X, long long ld, bool trans, int rows, int k, const doubl
   const int tile_rows = side == OzakiSide::kLeft ? kTM : kTN;
   const int r_pad = (rows + tile_rows - 1) / tile_rows * tile_rows;
   const int n_oct = (k + kKS - 1) / kKS * 2;
-  pack_kernel<T><<<blocks_for((long long)r_pad * n_oct, 256), 256, 0, s>>>(X, ld, trans ? 1 : 0, kscale, rows, k,
-                                                                          e, out, tile_rows, r_pad, n_oct);
+  const unsigned nb = blocks_for((long long)r_pad * n_oct, 256);
+  if (slices == 10)
+    pack_kernel<T, 10><<<nb, 256, 0, s>>>(X, ld, trans ? 1 : 0, kscale, rows, k, e, out, tile_rows, r_pad, n_oct);
+  else
+    pack_kernel<T, 8><<<nb, 256, 0, s>>>(X, ld, trans ? 1 : 0, kscale, rows, k, e, out, tile_rows, r_pad, n_oct);
 }
 
 }  // namespace
 
 void ozaki_pack(const double* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
-                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s) {
-  pack_any(X, ld, trans, rows, k, kscale, e, out, side, exponents, s);
+                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s, int slices) {
+  pack_any(X, ld, trans, rows, k, kscale, e, out, side, exponents, slices, s);
 }
 
 void ozaki_pack(const float* X, long long ld, bool trans, int rows, int k, const double* kscale, int* e,
-                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s) {
-  pack_any(X, ld, trans, rows, k, kscale, e, out, side, exponents, s);
+                uint8_t* out, OzakiSide side, bool exponents, cudaStream_t s, int slices) {
+  pack_any(X, ld, trans, rows, k, kscale, e, out, side, exponents, slices, s);
 }
 
 void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, long long ldc, int m, int n,
@@ -530,7 +564,10 @@ void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, 
   g.a_lower = a_lower ? 1 : 0;
   g.status = status;
   dim3 grid((n + kTN - 1) / kTN, (m + kTM - 1) / kTM);
-  ozaki_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(g);
+  if (A.slices == 10)
+    ozaki_gemm_kernel<10><<<grid, kThreads, Split<10>::kSmemBytes, s>>>(g);
+  else
+    ozaki_gemm_kernel<8><<<grid, kThreads, Split<8>::kSmemBytes, s>>>(g);
 }
 
 ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k,
@@ -566,9 +603,9 @@ ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, 
   return st;
 }
 
-double ozaki_tensor_flops(int m, int n, int k) {
-  // the 36 slice products of the split form, each a BF16 product of m x n x k
-  return 36.0 * 2.0 * (double)m * (double)n * (double)k;
+double ozaki_tensor_flops(int m, int n, int k, int slices) {
+  // the S (S + 1) / 2 slice products of the split form, each a BF16 product of m x n x k
+  return slices * (slices + 1) / 2.0 * 2.0 * (double)m * (double)n * (double)k;
 }
 
 }  // namespace eptv
