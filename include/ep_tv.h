@@ -448,15 +448,18 @@ ep_tv_status ep_tv_warm_start(ep_tv_ctx* ctx, const float* out, int32_t mode);
    cores (Sec. III-C, the products of the Woodbury form), exposed to check it on
    its own: C = A B^T for row-major A (m x k), B (n x k) and C (m x n), all DEVICE
    pointers, on cuda_stream (NULL: the legacy stream).  Every FP64 entry is split
-   into eight 7-bit BF16 digit slices under a power-of-two scale per row; the 36
-   slice products with the largest weights run as BF16 MMAs (tcgen05) whose
-   partial sums are exact.  |C - A B^T| <~ 2^-52 sum_k |A_ik||B_jk| plus one
-   rounding of the result.  Allocates and frees its packing buffers (about
-   16 (m + n) k bytes) and synchronises the stream.  EP_TV_ERR_ARG for NULL
-   pointers or sizes below 1, EP_TV_ERR_NOMEM, EP_TV_ERR_TIMEOUT if a bounded
-   device-side wait gave up. */
+   into `slices` 7-bit BF16 digit slices under a power-of-two scale per row; the
+   slices (slices + 1) / 2 slice products with the largest weights run as BF16
+   MMAs (tcgen05) whose partial sums are exact up to a short FP32 tail.
+   slices = 8 is the form of the site's operator products: |C - A B^T| <~
+   2^-55 (max|A_i| sum|B_j| + max|B_j| sum|A_i|) + 2^-52 k max|A_i| max|B_j| plus one
+   rounding of the result.  slices = 10 (k <= 8192) is the form of its Cholesky
+   factorisation's products, about 2^-14 of that error.  Allocates and frees its
+   packing buffers (about 2 slices (m + n) k bytes) and synchronises the stream.
+   EP_TV_ERR_ARG for NULL pointers, sizes below 1 or another slice count,
+   EP_TV_ERR_NOMEM, EP_TV_ERR_TIMEOUT if a bounded device-side wait gave up. */
 ep_tv_status ep_tv_tc_gemm_f64(const double* A, const double* B, double* C, int32_t m, int32_t n,
-                               int32_t k, void* cuda_stream);
+                               int32_t k, int32_t slices, void* cuda_stream);
 
 /* Frees the context (synchronises its stream first).  NULL is accepted. */
 void ep_tv_destroy(ep_tv_ctx* ctx);

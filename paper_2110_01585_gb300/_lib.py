@@ -101,7 +101,7 @@ SIGNATURES = {
                                        c_void_p, c_void_p, ctypes.c_float, c_void_p, c_void_p,
                                        c_void_p]),
     "ep_tv_warm_start": (c_int32, [c_void_p, c_void_p, c_int32]),
-    "ep_tv_tc_gemm_f64": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
+    "ep_tv_tc_gemm_f64": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
     "ep_tv_destroy": (None, [c_void_p]),
     "ep_tv_status_str": (ctypes.c_char_p, [c_int32]),
 }

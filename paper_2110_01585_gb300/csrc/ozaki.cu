@@ -570,15 +570,15 @@ void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, 
     ozaki_gemm_kernel<8><<<grid, kThreads, Split<8>::kSmemBytes, s>>>(g);
 }
 
-ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k,
+ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k, int slices,
                                    cudaStream_t s) {
   if (ozaki_init() != EP_TV_OK) return EP_TV_ERR_CUDA;
   uint8_t *pa = nullptr, *pb = nullptr;
   int *ea = nullptr, *eb = nullptr;
   unsigned* status = nullptr;
   ep_tv_status st = EP_TV_OK;
-  if (cudaMalloc(&pa, ozaki_pack_bytes(m, k)) != cudaSuccess ||
-      cudaMalloc(&pb, ozaki_pack_bytes(n, k)) != cudaSuccess || cudaMalloc(&ea, sizeof(int) * m) != cudaSuccess ||
+  if (cudaMalloc(&pa, ozaki_pack_bytes(m, k, slices)) != cudaSuccess ||
+      cudaMalloc(&pb, ozaki_pack_bytes(n, k, slices)) != cudaSuccess || cudaMalloc(&ea, sizeof(int) * m) != cudaSuccess ||
       cudaMalloc(&eb, sizeof(int) * n) != cudaSuccess || cudaMalloc(&status, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     st = EP_TV_ERR_NOMEM;
@@ -586,9 +586,10 @@ ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, 
   unsigned h_status = 0;
   if (st == EP_TV_OK) {
     cudaMemsetAsync(status, 0, sizeof(unsigned), s);
-    ozaki_pack(A, k, false, m, k, nullptr, ea, pa, OzakiSide::kLeft, true, s);
-    ozaki_pack(B, k, false, n, k, nullptr, eb, pb, OzakiSide::kRight, true, s);
-    ozaki_gemm(OzakiOperand{pa, ea}, OzakiOperand{pb, eb}, k, C, n, m, n, 0.0, 1.0, false, false, status, s);
+    ozaki_pack(A, k, false, m, k, nullptr, ea, pa, OzakiSide::kLeft, true, s, slices);
+    ozaki_pack(B, k, false, n, k, nullptr, eb, pb, OzakiSide::kRight, true, s, slices);
+    ozaki_gemm(OzakiOperand{pa, ea, slices}, OzakiOperand{pb, eb, slices}, k, C, n, m, n, 0.0, 1.0, false, false,
+               status, s);
     if (cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       st = EP_TV_ERR_CUDA;
@@ -611,7 +612,8 @@ double ozaki_tensor_flops(int m, int n, int k, int slices) {
 }  // namespace eptv
 
 extern "C" ep_tv_status ep_tv_tc_gemm_f64(const double* A, const double* B, double* C, int32_t m, int32_t n,
-                                          int32_t k, void* cuda_stream) {
+                                          int32_t k, int32_t slices, void* cuda_stream) {
   if (!A || !B || !C || m < 1 || n < 1 || k < 1) return EP_TV_ERR_ARG;
-  return eptv::ozaki_gemm_standalone(A, B, C, m, n, k, static_cast<cudaStream_t>(cuda_stream));
+  if (slices != 8 && !(slices == 10 && k <= 8192)) return EP_TV_ERR_ARG;
+  return eptv::ozaki_gemm_standalone(A, B, C, m, n, k, slices, static_cast<cudaStream_t>(cuda_stream));
 }

@@ -43,7 +43,7 @@ void ozaki_gemm(const OzakiOperand& A, const OzakiOperand& B, int k, double* C, 
                 double alpha, double beta, bool lower_only, bool a_lower, unsigned* status, cudaStream_t s);
 // C = A B^T for row-major A (m x k), B (n x k), C (m x n), all device memory,
 // with its own packing buffers (the exported ep_tv_tc_gemm_f64).
-ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k,
+ep_tv_status ozaki_gemm_standalone(const double* A, const double* B, double* C, int m, int n, int k, int slices,
                                    cudaStream_t s);
 // BF16 tensor flops of one product: the S (S + 1) / 2 slice products of m x n x k
 // (padding not counted).
