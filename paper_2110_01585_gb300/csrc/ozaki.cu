@@ -17,7 +17,8 @@
 // accumulator in tensor memory; over a chunk of 256 values of k each such sum is
 // an integer multiple of 2^{-7(s+t)} below 2^23 of it, so the tensor core adds it
 // exactly, and after every chunk the five accumulators are converted to integers
-// and added into one 64-bit integer per output.  The products with s + t = 7..9
+// and added into two 64-bit integers per output (diagonals 2-4 and 5-6).  The
+// products with s + t = 7..9
 // carry 2^-35 or less of the result and go to a sixth FP32 accumulator over the
 // whole of k.  (The tensor core's FP32 accumulation is not round-to-nearest at
 // every add: measured on a single product, a tail starting at s + t = 6 left an
@@ -36,9 +37,10 @@
 // waits only for stages to land, and sixteen warps read the accumulators back
 // (tcgen05.ld) at every chunk end, handing them back to the MMA thread through
 // a second pair of barriers.  A second form, 10 slices with seven exact
-// diagonals (Split<10>), serves the Cholesky factorisation's products.  Every wait on an mbarrier gives up after two
-// seconds: the kernel then raises ST_TIMEOUT, waits (bounded) for its copies and
-// MMAs in flight, frees its tensor memory and exits.
+// diagonals (Split<10>), serves the Cholesky factorisation's products.  Every
+// wait on an mbarrier gives up after two seconds: the kernel then raises
+// ST_TIMEOUT, waits (bounded) for its copies and MMAs in flight, frees its tensor
+// memory and exits.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -86,7 +88,6 @@ struct Split {
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 constexpr unsigned long long kWaitNs = 2000000000ull;
-
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
