@@ -29,7 +29,7 @@
 // ozaki.cu.  K = L L^T and Z = L^{-1} come together from a recursion on halves
 // (L21 = K21 Z11^T, K22 -= L21 L21^T, Z21 = -Z22 L21 Z11) whose large products
 // run in the same split form with 10 digit slices and seven exact diagonals (as
-// accurate as FP64 on these operands); blocks of 64 rows and products below 256
+// accurate as FP64 on these operands); blocks of 64 rows and smaller products
 // stay on the FP64 CUDA cores.  The mean uses v = Z t and g = W^T v.
 //
 // Kernels here: an FP64 tiled GEMM (64 x 64 tiles, 4 x 4 per thread) for the
@@ -486,7 +486,7 @@ struct Segment {
 
 // Products of the factorisation at least this large in every dimension run on the
 // tensor cores; smaller ones in the FP64 SIMT GEMM.
-constexpr int kMmaMin = 256;
+constexpr int kMmaMin = 64;
 // Digit slices of the factorisation's products.  The Schur complement
 // K22 - L21 L21^T cancels to the size of xi while its terms carry the capped
 // cavity variances, and the split form's error is relative to the rows' largest
