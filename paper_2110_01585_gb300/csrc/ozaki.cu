@@ -120,6 +120,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// The same wait for threads with nothing else to do (the reading warps): each
+// try asks the hardware to suspend the thread for up to 20 us until the phase
+// completes, so that they do not take issue slots from the MMA thread.
+__device__ __forceinline__ bool mbar_wait_idle(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = now_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(20000u)
+        : "memory");
+    if (done) return true;
+    if (now_ns() - t0 > kWaitNs) return false;
+  }
+}
+
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -421,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) ozaki_gemm_kernel(GemmArgs a) {
     for (int j = 0; j < kEpiCols; ++j) acc_hi[j] = acc_lo[j] = 0;
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + c_part * kEpiCols;
     for (int c = 0; c < n_chunks; ++c) {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_full, c & 1));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_idle(acc_full, c & 1));
       if (!ok) {
         *abort_flag = 1;
         break;
