@@ -239,6 +239,41 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c3, double
   __syncthreads();
 }
 
+// block_sum3 for per-thread FP32 partials of NV values (1..3): the sums within a
+// warp run in FP32 (the CG's vectors are FP32 already), the warps' sums are added
+// in FP64 in a fixed order.  GB300's FP64 pipe is narrow, and a five-level FP64
+// shuffle tree per value in every block of the CG kernels kept it busy.
+template <int NV>
+__device__ __forceinline__ void block_sumf(float a, float b, float c3, double* out_a, double* out_b,
+                                           double* out_c) {
+  __shared__ double red[3][32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    if (NV > 1) b += __shfl_down_sync(0xffffffffu, b, off);
+    if (NV > 2) c3 += __shfl_down_sync(0xffffffffu, c3, off);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = (double)a;
+    red[1][w] = (double)b;
+    red[2][w] = (double)c3;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0, sc = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      sa += red[0][i];
+      if (NV > 1) sb += red[1][i];
+      if (NV > 2) sc += red[2][i];
+    }
+    if (out_a) *out_a = sa;
+    if (NV > 1 && out_b) *out_b = sb;
+    if (NV > 2 && out_c) *out_c = sc;
+  }
+  __syncthreads();
+}
+
 // Last-block reduction.  Every block of a group has written its partial sum (by
 // thread 0, before the block barrier at the end of block_sum3); each then counts
 // itself in with an atomic, and the block that arrives last returns true and
@@ -357,6 +392,24 @@ struct ff {
 __device__ __forceinline__ ff ff_from_double(double x) {
   const float hi = (float)x;
   return {hi, (float)(x - (double)hi)};
+}
+// x as hi + lo without FP64 arithmetic (GB300's FP64 pipe retires about one
+// operation per clock per SM, and the residual stages one FP64 value per region
+// pixel): hi is x truncated to 24 significant bits, assembled from the bit fields;
+// lo is the remaining 29 mantissa bits, converted as an integer (rounded to 24
+// bits) and scaled by a power of two, so |x - hi - lo| <= 2^-47 |x|.  Zero is
+// exact; magnitudes below 2^-74 or beyond float's range take ff_from_double.
+__device__ __forceinline__ ff ff_split_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  if ((u << 1) == 0ull) return {0.f, 0.f};
+  const int ef = (int)((u >> 52) & 0x7FFull) - 1023 + 127;  // biased float exponent of hi
+  if (ef < 53 || ef > 254) return ff_from_double(x);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
+  const float scale = __uint_as_float((unsigned)(ef - 52) << 23);  // 2^(ef - 127 - 52), normal
+  const float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull)) * scale;
+  return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
 }
 __device__ __forceinline__ ff two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
@@ -488,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   for (int rr = ty; rr < RH; rr += kThreads / 32) {
     const long long rowp = (long long)wrapi(r0 - c.hr + rr, c.H) * c.W;
     for (int cc = tx; cc < RW; cc += 32) {
-      const ff t = ff_from_double(x[rowp + ctab[cc]]);
+      const ff t = ff_split_bits(x[rowp + ctab[cc]]);
       xh[rr * RW + cc] = t.hi;
       xl[rr * RW + cc] = t.lo;
     }
@@ -596,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
     bb = fmaf(b, b, bb);
   }
   const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
-  block_sum3((double)rz, (double)rr2, (double)bb, a.fft ? nullptr : a.part_rz + o,
+  block_sumf<3>(rz, rr2, bb, a.fft ? nullptr : a.part_rz + o,
              a.part_rr + o, a.part_bb + o);
 }
 
@@ -750,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 5) direction_kernel(CgArgs a, int it
     a.Qp[(long long)j * c.N + p] = q;
     pq = fmaf(pv, q, pq);
   }
-  block_sum3((double)pq, 0.0, 0.0,
+  block_sumf<1>(pq, 0.f, 0.f,
              a.part_pq + (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x, nullptr,
              nullptr);
 }
@@ -838,7 +891,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it_ar
       rr2 = fmaf(r, r, rr2);
     }
   }
-  block_sum3((double)rz2, (double)rr2, 0.0, a.fft ? nullptr : a.part_rz + (long long)j * a.nbz + blk,
+  block_sumf<2>(rz2, rr2, 0.f, a.fft ? nullptr : a.part_rz + (long long)j * a.nbz + blk,
              a.part_rr + (long long)j * a.nb + blk, nullptr);
   if (arrive_last(a.arrive + j, (unsigned)a.nb) && threadIdx.x < 32) {
     const double rr = group_sum(a.part_rr + (long long)j * a.nb, a.nb);
