@@ -85,9 +85,11 @@ struct StencilSmem {
   float* taps; // kernel taps staged in shared memory
 };
 
-// Separable H^T H with compile-time half-widths: row pass fully unrolled, column
-// pass with each thread producing four consecutive rows of one column, so the
-// 2 HR + 4 inputs it loads serve four outputs.
+// Separable H^T H with compile-time half-widths.  Row pass: each thread produces
+// two adjacent outputs of a region row from one window of 2 HC + 2 inputs read as
+// float2 (16 threads per row); column pass: each thread produces four consecutive
+// rows of one column, so the 2 HR + 4 inputs it loads serve four outputs.  Every
+// output sums its taps in the same order as a one-output loop.
 template <int HR, int HC>
 __device__ __forceinline__ void hth_tile_sep(StencilSmem& sm, float* out) {
   constexpr int RH = kTile + 2 * HR, RW = kTile + 2 * HC;
@@ -97,12 +99,24 @@ __device__ __forceinline__ void hth_tile_sep(StencilSmem& sm, float* out) {
   float wc[2 * HC + 1];
 #pragma unroll
   for (int b = 0; b <= 2 * HC; ++b) wc[b] = gc[b];
-  for (int rr = ty; rr < RH; rr += kThreads / 32) {
-    const float* row = sm.v + rr * RW + tx;
-    float acc = 0.f;
+  static_assert(RW % 2 == 0, "float2 rows");
+  const int cp = threadIdx.x & 15;  // column pair 2 cp, 2 cp + 1 of the tile
+  for (int rr = threadIdx.x >> 4; rr < RH; rr += kThreads / 16) {
+    const float2* row2 = reinterpret_cast<const float2*>(sm.v + rr * RW + 2 * cp);
+    float win[2 * HC + 2];
 #pragma unroll
-    for (int b = 0; b <= 2 * HC; ++b) acc = fmaf(wc[b], row[b], acc);
-    sm.tmp[rr * kTile + tx] = acc;
+    for (int q = 0; q <= HC; ++q) {
+      const float2 t = row2[q];
+      win[2 * q] = t.x;
+      win[2 * q + 1] = t.y;
+    }
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int b = 0; b <= 2 * HC; ++b) {
+      a0 = fmaf(wc[b], win[b], a0);
+      a1 = fmaf(wc[b], win[b + 1], a1);
+    }
+    *reinterpret_cast<float2*>(sm.tmp + rr * kTile + 2 * cp) = make_float2(a0, a1);
   }
   __syncthreads();
   float wr[2 * HR + 1];
