@@ -474,26 +474,59 @@ __device__ __forceinline__ void residual_sep_fixed(const ConvDesc& c, const floa
     vh[b] = taph[K + b];
     vl[b] = tapl[K + b];
   }
-  for (int idx = threadIdx.x; idx < RH * MW; idx += kThreads) {
-    const int rr = idx / MW, mc = idx - rr * MW;
-    const int base = rr * RW + mc + 2 * hw;
-    ff acc = {0.f, 0.f};
+  // Both float-float passes produce two adjacent outputs per thread from one
+  // window of K + 1 inputs (the row pass reads it as float2); every output sums its
+  // taps in the same order as a one-output loop.
+  static_assert(K % 2 == 1 && RW % 2 == 0 && MW % 2 == 0 && MH % 2 == 0, "paired outputs");
+  for (int idx = threadIdx.x; idx < RH * (MW / 2); idx += kThreads) {
+    const int rr = idx / (MW / 2), mp = idx - rr * (MW / 2);
+    // outputs (rr, 2 mp) and (rr, 2 mp + 1) read x[rr][2 mp .. 2 mp + K]
+    const float2* h2 = reinterpret_cast<const float2*>(xh + rr * RW + 2 * mp);
+    const float2* l2 = reinterpret_cast<const float2*>(xl + rr * RW + 2 * mp);
+    float wh[K + 1], wl[K + 1];
 #pragma unroll
-    for (int b = 0; b < K; ++b) acc = ff_fma(acc, ff{xh[base - b], xl[base - b]}, vh[b], vl[b]);
-    ph[idx] = acc.hi;
-    pl[idx] = acc.lo;
+    for (int q = 0; q < (K + 1) / 2; ++q) {
+      const float2 th = h2[q], tl = l2[q];
+      wh[2 * q] = th.x;
+      wh[2 * q + 1] = th.y;
+      wl[2 * q] = tl.x;
+      wl[2 * q + 1] = tl.y;
+    }
+    ff acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      acc0 = ff_fma(acc0, ff{wh[K - 1 - b], wl[K - 1 - b]}, vh[b], vl[b]);
+      acc1 = ff_fma(acc1, ff{wh[K - b], wl[K - b]}, vh[b], vl[b]);
+    }
+    const int o = rr * MW + 2 * mp;
+    ph[o] = acc0.hi;
+    pl[o] = acc0.lo;
+    ph[o + 1] = acc1.hi;
+    pl[o + 1] = acc1.lo;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < MH * MW; idx += kThreads) {
-    const int mr = idx / MW, mc = idx - mr * MW;
-    const int base = (mr + 2 * hh) * MW + mc;
-    ff acc = {0.f, 0.f};
+  for (int idx = threadIdx.x; idx < (MH / 2) * MW; idx += kThreads) {
+    const int mp = idx / MW, mc = idx - mp * MW, mr = 2 * mp;
+    // outputs (mr, mc) and (mr + 1, mc) read rows mr .. mr + K of column mc
+    const int gcol = wrapi(c0 - hw + mc, c.W);
+    const float y0 = yp[(long long)wrapi(r0 - hh + mr, c.H) * c.W + gcol];
+    const float y1 = yp[(long long)wrapi(r0 - hh + mr + 1, c.H) * c.W + gcol];
+    float wh[K + 1], wl[K + 1];
 #pragma unroll
-    for (int aa = 0; aa < K; ++aa)
-      acc = ff_fma(acc, ff{ph[base - aa * MW], pl[base - aa * MW]}, uh[aa], ul[aa]);
-    const int gr = wrapi(r0 - hh + mr, c.H), gcol = wrapi(c0 - hw + mc, c.W);
-    const ff v = ff_add(ff{yp[(long long)gr * c.W + gcol], 0.f}, ff_neg(acc));
-    vs[idx] = v.hi + v.lo;
+    for (int j = 0; j <= K; ++j) {
+      wh[j] = ph[(mr + j) * MW + mc];
+      wl[j] = pl[(mr + j) * MW + mc];
+    }
+    ff acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+#pragma unroll
+    for (int aa = 0; aa < K; ++aa) {
+      acc0 = ff_fma(acc0, ff{wh[K - 1 - aa], wl[K - 1 - aa]}, uh[aa], ul[aa]);
+      acc1 = ff_fma(acc1, ff{wh[K - aa], wl[K - aa]}, uh[aa], ul[aa]);
+    }
+    const ff v0 = ff_add(ff{y0, 0.f}, ff_neg(acc0));
+    const ff v1 = ff_add(ff{y1, 0.f}, ff_neg(acc1));
+    vs[mr * MW + mc] = v0.hi + v0.lo;
+    vs[(mr + 1) * MW + mc] = v1.hi + v1.lo;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < MH * kTile; idx += kThreads) {
