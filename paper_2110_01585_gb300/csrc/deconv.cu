@@ -585,12 +585,29 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   __syncthreads();
   const double* x = a.X + (long long)j * c.N;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int rr = ty; rr < RH; rr += kThreads / 32) {
-    const long long rowp = (long long)wrapi(r0 - c.hr + rr, c.H) * c.W;
-    for (int cc = tx; cc < RW; cc += 32) {
-      const ff t = ff_split_bits(x[rowp + ctab[cc]]);
-      xh[rr * RW + cc] = t.hi;
-      xl[rr * RW + cc] = t.lo;
+  {
+    // the FP64 region, kResBatch loads in flight per thread before the first split
+    constexpr int kResBatch = 8;
+    const int total = RH * RW;
+    for (int i0 = threadIdx.x; i0 < total; i0 += kResBatch * kThreads) {
+      double xv[kResBatch];
+#pragma unroll
+      for (int u = 0; u < kResBatch; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < total) {
+          const int rr = i / RW, cc = i - rr * RW;
+          xv[u] = x[(long long)wrapi(r0 - c.hr + rr, c.H) * c.W + ctab[cc]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kResBatch; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < total) {
+          const ff t = ff_split_bits(xv[u]);
+          xh[i] = t.hi;
+          xl[i] = t.lo;
+        }
+      }
     }
   }
   __syncthreads();
