@@ -689,25 +689,48 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   }
   __syncthreads();
   float rz = 0.f, rr2 = 0.f, bb = 0.f;
-  for (int tr = ty; tr < kTile; tr += kThreads / 32) {
-    const int gr = r0 + tr, gcol = c0 + tx;
+  // the thread's output rows: their d, n' inputs and right-hand sides loaded first,
+  // all in flight together
+  constexpr int kRowsPer = kTile / (kThreads / 32);
+  float dv[kRowsPer], nv[kRowsPer], ev[kRowsPer];
+  const int gcol = c0 + tx;
+#pragma unroll
+  for (int i = 0; i < kRowsPer; ++i) {
+    const int gr = r0 + ty + i * (kThreads / 32);
+    dv[i] = nv[i] = ev[i] = 0.f;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    dv[i] = a.D[p];
+    if (j == 0) {
+      nv[i] = a.Ncav[p];
+      ev[i] = a.Hty[p];
+    } else {
+      nv[i] = a.E2[(long long)(j - 1) * c.N + p];
+      ev[i] = a.E1[(long long)(j - 1) * c.N + p];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kRowsPer; ++i) {
+    const int tr = ty + i * (kThreads / 32);
+    const int gr = r0 + tr;
     if (gr >= c.H || gcol >= c.W) continue;
     const long long p = (long long)gr * c.W + gcol;
     const int xi_ = (tr + c.hr) * RW + tx + c.hc;
-    const float d = a.D[p];
+    const float d = dv[i];
     // n' - d x in float-float
     ff np;
     if (j == 0) {
-      np = {a.Ncav[p], 0.f};
+      np = {nv[i], 0.f};
     } else {
-      const float sd = sqrtf(d), e2 = a.E2[(long long)(j - 1) * c.N + p];
+      const float sd = sqrtf(d), e2 = nv[i];
       const float pr = __fmul_rn(sd, e2);
       np = {pr, fmaf(sd, e2, -pr)};
     }
     const ff t = ff_add(np, ff_neg(ff_mul_f(ff{xh[xi_], xl[xi_]}, d)));
     const float r = outb[tr * kTile + tx] * c.inv_xi + (t.hi + t.lo);
     a.Rr[(long long)j * c.N + p] = r;
-    const float b = rhs_value(a, j, p);
+    // the right-hand side as rhs_value forms it
+    const float b = j == 0 ? ev[i] + nv[i] : ev[i] + sqrtf(d) * nv[i];
     if (!a.fft) rz = fmaf(r * r, a.Minv[p], rz);
     rr2 = fmaf(r, r, rr2);
     bb = fmaf(b, b, bb);
