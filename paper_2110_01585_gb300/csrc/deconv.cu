@@ -1376,6 +1376,9 @@ __device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
   asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
   return v;
 }
+__device__ __forceinline__ void st_hint_f(float* a, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
 __device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol)
                : "memory");
@@ -1472,6 +1475,105 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
     fft512_warp(v, scratch[w], tw);
 #pragma unroll
     for (int m = 0; m < 16; ++m) st_hint(out + (long long)row * kF + 32 * m + l, v[m], keep);
+  }
+}
+
+// The CG update fused with the forward row pass (512-point rows): for each system
+// of the pair that is active when the iteration starts, alpha = r.z / p.q from the
+// direction kernel's partials, e += alpha p and r -= alpha q, exactly as update_kernel
+// forms them; the new residual rows of the pair then go through the forward row
+// transform without being read again.  A system that stopped earlier enters the
+// transform as zero (its z is not used before the next pass recomputes it).  The last
+// block of the pair sums its r.r partials in block order and sets the active flags,
+// as update_kernel's last block does, so the column and inverse passes that follow
+// skip the pairs that stopped here.
+__global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_kernel(FftDesc f,
+                                                                                CgArgs a,
+                                                                                int it_arg,
+                                                                                int rpb) {
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const bool two = j1 < f.R;
+  const bool act0 = a.scal[4 * j0] != 0.f, act1 = two && a.scal[4 * j1] != 0.f;
+  if (!act0 && !act1) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.counters) {
+    atomicAdd(&f.counters[DC_CG_PRE_UNITS], two ? 2ull : 1ull);
+    atomicAdd(&f.counters[DC_CG_UPD_UNITS], (unsigned long long)(act0 + act1));
+  }
+  const int it = a.it_dev ? *a.it_dev : it_arg;
+  const bool first = it == 0;  // the correction starts at zero: not read
+  __shared__ float2 tw[kF];
+  __shared__ float2 scratch[kF512Warps][kXs];
+  __shared__ float alpha_s[2];
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) tw[m] = f.tw512[m];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (w < 2 && (w == 0 ? act0 : act1)) {
+    const int j = j0 + w;
+    const double pqs = group_sum(a.part_pq + (long long)j * a.nb, a.nb);
+    if (l == 0) alpha_s[w] = (float)(a.rzs[j] / pqs);
+  }
+  __syncthreads();
+  const long long N = (long long)f.H * f.W;
+  float2* out = f.tmp + (long long)pair * f.H * kF;
+  const int rend = min(f.H, (blockIdx.x + 1) * rpb);
+  const uint64_t keep = l2_policy_keep();
+  float rr0 = 0.f, rr1 = 0.f;
+  for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
+    const long long p0 = (long long)row * f.W;
+    float2 v[16];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!(u ? act1 : act0)) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) (u ? v[m].y : v[m].x) = 0.f;
+        continue;
+      }
+      const long long o = (long long)(j0 + u) * N + p0;
+      const float* P = ((it & 1) ? a.P2 : a.P) + o;
+      const float* Q = a.Qp + o;
+      float* Ec = a.Ec + o;
+      float* Rr = a.Rr + o;
+      float pv[16], qv[16], rv[16], ev[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int c = 32 * m + l;
+        pv[m] = qv[m] = rv[m] = ev[m] = 0.f;
+        if (c < f.W) {
+          pv[m] = P[c];
+          qv[m] = Q[c];
+          rv[m] = Rr[c];
+          if (!first) ev[m] = Ec[c];
+        }
+      }
+      const float alpha = alpha_s[u];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int c = 32 * m + l;
+        float r = 0.f;
+        if (c < f.W) {
+          Ec[c] = fmaf(alpha, pv[m], ev[m]);
+          r = fmaf(-alpha, qv[m], rv[m]);
+          st_hint_f(Rr + c, r, keep);
+          if (u) rr1 = fmaf(r, r, rr1); else rr0 = fmaf(r, r, rr0);
+        }
+        (u ? v[m].y : v[m].x) = r;
+      }
+    }
+    fft512_warp(v, scratch[w], tw);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) st_hint(out + (long long)row * kF + 32 * m + l, v[m], keep);
+  }
+  block_sumf<2>(rr0, rr1, 0.f, act0 ? a.part_rr + (long long)j0 * a.nb + blockIdx.x : nullptr,
+                act1 ? a.part_rr + (long long)j1 * a.nb + blockIdx.x : nullptr, nullptr);
+  if (arrive_last(a.arrive + j0, gridDim.x) && threadIdx.x < 32) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!(u ? act1 : act0)) continue;
+      const int j = j0 + u;
+      const double r2 = group_sum(a.part_rr + (long long)j * a.nb, gridDim.x);
+      // the stopping rule of update_kernel
+      if (threadIdx.x == 0) a.scal[4 * j] = (r2 <= a.thr[j] || r2 > 16.0 * a.rr0[j]) ? 0.f : 1.f;
+    }
   }
 }
 
@@ -1991,8 +2093,11 @@ int ilog2(int v) {
 // pass sets beta and r.z of the active systems (first: the first application of a
 // refinement pass, beta = 0); without it every system is transformed and the CG
 // scalars are left alone (launch-shape tuning).
+// stages: 1 = the forward row pass (fused with the CG update when upd is given:
+// 512-point rows only, see fused_update), 2 = the column and inverse row passes.
 void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
-                   unsigned long long* counters, cudaStream_t s) {
+                   unsigned long long* counters, cudaStream_t s, const CgArgs* upd = nullptr,
+                   int it = 0, int stages = 3) {
   FftDesc f = L->fd;
   f.act = cg ? L->d_scal : nullptr;
   f.scal_w = cg ? L->d_scal : nullptr;
@@ -2001,12 +2106,18 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
   f.first = first;
   f.counters = counters;
   constexpr int kRows512 = kF512Warps * kRowsPerWarp512;
-  if (fft512_rows(f))
-    fft512_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs), 32 * kF512Warps, 0, s>>>(
-        f, L->Rr, kRows512);
-  else
-    fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows, s>>>(
-        f, L->Rr);
+  if (stages & 1) {
+    if (upd)
+      fft512_update_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs),
+                                      32 * kF512Warps, 0, s>>>(f, *upd, it, kRows512);
+    else if (fft512_rows(f))
+      fft512_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs), 32 * kF512Warps, 0,
+                               s>>>(f, L->Rr, kRows512);
+    else
+      fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows,
+                            s>>>(f, L->Rr);
+  }
+  if (!(stages & 2)) return;
   if (fft512_cols(f))
     fft512_cols_filter_kernel<<<dim3(f.WP / kF512Warps, f.pairs), 32 * kF512Warps, 0, s>>>(f, f.hth);
   else
@@ -2017,6 +2128,10 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
     fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z,
                                                                                 rz_buf);
 }
+
+// Whether a CG iteration runs its update inside the preconditioner's forward row
+// pass (fft512_update_rows_fwd_kernel) instead of update_kernel.
+inline bool fused_update(const LikelihoodState* L) { return L->fft && fft512_rows(L->fd); }
 
 // ---- launch-shape tuning of the FFT preconditioner
 //
@@ -2583,8 +2698,12 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
   ok = ok && capture(b_inner, [&]() {
     cond_clear_kernel<<<1, 32, 0, s>>>(h_inner);
     direction_kernel<<<grid, kThreads, L->smem, s>>>(a, 0);
-    update_kernel<<<grid, kUpdThreads, 0, s>>>(a, 0);
-    if (L->fft) precond_apply(L, a.part_rz, true, 0, counters, s);
+    if (fused_update(L)) {
+      precond_apply(L, a.part_rz, true, 0, counters, s, &a, 0);
+    } else {
+      update_kernel<<<grid, kUpdThreads, 0, s>>>(a, 0);
+      if (L->fft) precond_apply(L, a.part_rz, true, 0, counters, s);
+    }
     iter_kernel<<<1, 64, 0, s>>>(L->d_loop, L->d_scal, L->R, L->max_iter, h_inner);
     return true;
   });
@@ -2687,13 +2806,23 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
         tr->begin(EP_TV_K_CG_DIRECTION, s);
         direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
         tr->end(s, -1.0);
-        tr->begin(EP_TV_K_CG_UPDATE, s);
-        update_kernel<<<grid, kUpdThreads, 0, s>>>(a, launched);
-        tr->end(s, -1.0);
-        if (L->fft) {
-          tr->begin(EP_TV_K_CG_PRECOND, s);
-          precond_apply(L, a.part_rz, true, 0, counters, s);
+        if (fused_update(L)) {
+          // the update with the preconditioner's forward row pass, then its other passes
+          tr->begin(EP_TV_K_CG_UPDATE, s);
+          precond_apply(L, a.part_rz, true, 0, counters, s, &a, launched, 1);
           tr->end(s, -1.0);
+          tr->begin(EP_TV_K_CG_PRECOND, s);
+          precond_apply(L, a.part_rz, true, 0, counters, s, nullptr, 0, 2);
+          tr->end(s, -1.0);
+        } else {
+          tr->begin(EP_TV_K_CG_UPDATE, s);
+          update_kernel<<<grid, kUpdThreads, 0, s>>>(a, launched);
+          tr->end(s, -1.0);
+          if (L->fft) {
+            tr->begin(EP_TV_K_CG_PRECOND, s);
+            precond_apply(L, a.part_rz, true, 0, counters, s);
+            tr->end(s, -1.0);
+          }
         }
         ++launched;
       }
