@@ -895,6 +895,184 @@ __global__ void __launch_bounds__(kThreads, 5) direction_kernel(CgArgs a, int it
              nullptr);
 }
 
+// direction_kernel for the two systems 2 blockIdx.z, 2 blockIdx.z + 1 at once (FFT
+// preconditioner, separable H^T H with equal half-widths HR).  The region holds
+// (system 0, system 1) float2 pairs, so that each tap of both stencil passes is one
+// packed FP32 FMA for the two systems, and the index arithmetic, the shared-memory
+// addressing and the loads of d serve both.  Row pass: two adjacent outputs per thread
+// from one window read as float4; column pass: four consecutive rows of one column per
+// thread, whose outputs stay in registers for the epilogue.  Per system and output
+// the taps are summed in the order of hth_tile_sep.  A system that has stopped is
+// neither read nor written.
+template <int HR>
+__global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_kernel(CgArgs a, int it_arg) {
+  constexpr int RH = kTile + 2 * HR, RW = kTile + 2 * HR, NT = 2 * HR + 1;
+  extern __shared__ float4 smem4[];
+  float2* reg = reinterpret_cast<float2*>(smem4);  // RH x RW region pairs
+  float2* tmp = reg + RH * RW;                     // RH x kTile, after the row pass
+  __shared__ float2 taps2[2 * NT];                 // (g, g): row taps, then column taps
+  __shared__ int ctab[RW];
+  const ConvDesc& c = a.c;
+  const int j0 = 2 * blockIdx.z, j1 = j0 + 1;
+  const bool act0 = a.scal[4 * j0] != 0.f, act1 = j1 < a.R && a.scal[4 * j1] != 0.f;
+  if (!act0 && !act1) return;
+  const int it = a.it_dev ? *a.it_dev : it_arg;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(&a.counters[DC_CG_DIR_UNITS], (unsigned long long)(act0 + act1));
+  const float beta0 = a.scal[4 * j0 + 1], beta1 = act1 ? a.scal[4 * j1 + 1] : 0.f;
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  for (int i = threadIdx.x; i < 2 * NT; i += kThreads) {
+    const float g = i < NT ? c.gr[i] : c.gc[i - NT];
+    taps2[i] = make_float2(g, g);
+  }
+  column_table(ctab, c0 - HR, RW, c.W);
+  const long long N = c.N;
+  const long long o0 = (long long)j0 * N, o1 = (long long)j1 * N;
+  const float* Pold = (it & 1) ? a.P : a.P2;
+  __syncthreads();
+  // Region staging, all of a thread's loads issued before the first is used
+  if ((c.W & 3) == 0 && (HR & 3) == 0 && c0 >= HR && c0 + kTile + HR <= c.W) {
+    // no column wraps: float4 quads of each plane
+    constexpr int Q4 = RW / 4, NQ = RH * Q4, KQ = (NQ + kThreads - 1) / kThreads;
+    float4 zv0[KQ], zv1[KQ], pv0[KQ], pv1[KQ];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      zv0[k] = zv1[k] = pv0[k] = pv1[k] = zero4;
+      if (i < NQ) {
+        const int rr = i / Q4, q = i - rr * Q4;
+        const long long p = (long long)wrapi(r0 - HR + rr, c.H) * c.W + c0 - HR + 4 * q;
+        if (act0) {
+          zv0[k] = *reinterpret_cast<const float4*>(a.Z + o0 + p);
+          if (it > 0) pv0[k] = *reinterpret_cast<const float4*>(Pold + o0 + p);
+        }
+        if (act1) {
+          zv1[k] = *reinterpret_cast<const float4*>(a.Z + o1 + p);
+          if (it > 0) pv1[k] = *reinterpret_cast<const float4*>(Pold + o1 + p);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      if (i < NQ) {
+        const int rr = i / Q4, q = i - rr * Q4;
+        float4 v0 = zv0[k], v1 = zv1[k];
+        if (it > 0) {
+          v0.x = fmaf(beta0, pv0[k].x, v0.x);
+          v0.y = fmaf(beta0, pv0[k].y, v0.y);
+          v0.z = fmaf(beta0, pv0[k].z, v0.z);
+          v0.w = fmaf(beta0, pv0[k].w, v0.w);
+          v1.x = fmaf(beta1, pv1[k].x, v1.x);
+          v1.y = fmaf(beta1, pv1[k].y, v1.y);
+          v1.z = fmaf(beta1, pv1[k].z, v1.z);
+          v1.w = fmaf(beta1, pv1[k].w, v1.w);
+        }
+        float4* dst = reinterpret_cast<float4*>(reg + rr * RW + 4 * q);
+        dst[0] = make_float4(v0.x, v1.x, v0.y, v1.y);
+        dst[1] = make_float4(v0.z, v1.z, v0.w, v1.w);
+      }
+    }
+  } else {
+    constexpr int kBatch = 4, NE = RH * RW;
+    for (int i0 = threadIdx.x; i0 < NE; i0 += kBatch * kThreads) {
+      float zs0[kBatch], zs1[kBatch], ps0[kBatch], ps1[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + u * kThreads;
+        zs0[u] = zs1[u] = ps0[u] = ps1[u] = 0.f;
+        if (i < NE) {
+          const int rr = i / RW, cc = i - rr * RW;
+          const long long p = (long long)wrapi(r0 - HR + rr, c.H) * c.W + ctab[cc];
+          if (act0) {
+            zs0[u] = a.Z[o0 + p];
+            if (it > 0) ps0[u] = Pold[o0 + p];
+          }
+          if (act1) {
+            zs1[u] = a.Z[o1 + p];
+            if (it > 0) ps1[u] = Pold[o1 + p];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < NE)
+          reg[i] = it > 0 ? make_float2(fmaf(beta0, ps0[u], zs0[u]), fmaf(beta1, ps1[u], zs1[u]))
+                          : make_float2(zs0[u], zs1[u]);
+      }
+    }
+  }
+  __syncthreads();
+  // row pass (column taps along the rows)
+  {
+    float2 wc[NT];
+#pragma unroll
+    for (int b = 0; b < NT; ++b) wc[b] = taps2[NT + b];
+    const int cp = threadIdx.x & 15;  // column pair 2 cp, 2 cp + 1 of the tile
+    for (int rr = threadIdx.x >> 4; rr < RH; rr += kThreads / 16) {
+      const float4* row4 = reinterpret_cast<const float4*>(reg + rr * RW + 2 * cp);
+      float2 win[NT + 1];
+#pragma unroll
+      for (int q = 0; q <= HR; ++q) {
+        const float4 t = row4[q];
+        win[2 * q] = make_float2(t.x, t.y);
+        win[2 * q + 1] = make_float2(t.z, t.w);
+      }
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < NT; ++b) {
+        a0 = __ffma2_rn(wc[b], win[b], a0);
+        a1 = __ffma2_rn(wc[b], win[b + 1], a1);
+      }
+      *reinterpret_cast<float4*>(tmp + rr * kTile + 2 * cp) = make_float4(a0.x, a0.y, a1.x, a1.y);
+    }
+  }
+  __syncthreads();
+  // column pass: rows tr0 .. tr0 + 3 of column tx
+  const int tx = threadIdx.x & 31, tr0 = (threadIdx.x >> 5) * 4;
+  float2 acc[4];
+  {
+    float2 in[NT + 3];
+#pragma unroll
+    for (int i = 0; i < NT + 3; ++i) in[i] = tmp[(tr0 + i) * kTile + tx];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) acc[o] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const float2 wr = taps2[t];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) acc[o] = __ffma2_rn(wr, in[o + t], acc[o]);
+    }
+  }
+  float* P = (it & 1) ? a.P2 : a.P;
+  float pq0 = 0.f, pq1 = 0.f;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int tr = tr0 + o, gr = r0 + tr, gcol = c0 + tx;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    const float2 pv = reg[(tr + HR) * RW + tx + HR];
+    const float d = a.D[p];
+    if (act0) {
+      const float q = acc[o].x * c.inv_xi + d * pv.x;
+      P[o0 + p] = pv.x;
+      a.Qp[o0 + p] = q;
+      pq0 = fmaf(pv.x, q, pq0);
+    }
+    if (act1) {
+      const float q = acc[o].y * c.inv_xi + d * pv.y;
+      P[o1 + p] = pv.y;
+      a.Qp[o1 + p] = q;
+      pq1 = fmaf(pv.y, q, pq1);
+    }
+  }
+  const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
+  block_sumf<2>(pq0, pq1, 0.f, act0 ? a.part_pq + (long long)j0 * a.nb + blk : nullptr,
+                act1 ? a.part_pq + (long long)j1 * a.nb + blk : nullptr, nullptr);
+}
+
 // e += alpha p, r -= alpha q (e: the FP32 correction of this refinement pass,
 // added to the FP64 solution by commit_kernel when the pass ends), partials of
 // the new r.r (and r.Minv.r for Jacobi).  alpha = r.z / p.q: every block sums the
@@ -2129,6 +2307,29 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
                                                                                 rz_buf);
 }
 
+// Whether the direction step runs two systems per block (direction_pair_kernel).
+inline bool pair_direction(const LikelihoodState* L) {
+  const ConvDesc& c = L->c;
+  return L->fft && c.separable && c.hr == c.hc &&
+         (c.hr == 2 || c.hr == 4 || c.hr == 8 || c.hr == 14);
+}
+
+void launch_direction(const LikelihoodState* L, const CgArgs& a, int it, cudaStream_t s) {
+  const ConvDesc& c = L->c;
+  if (pair_direction(L)) {
+    const dim3 g(c.tiles_x, c.tiles_y, (L->R + 1) / 2);
+    // region (RH x RW) and row-pass output (RH x kTile) pairs
+    const size_t sm = sizeof(float2) * (size_t)(kTile + 2 * c.hr) * (2 * kTile + 2 * c.hr);
+    switch (c.hr) {
+      case 2: direction_pair_kernel<2><<<g, kThreads, sm, s>>>(a, it); return;
+      case 4: direction_pair_kernel<4><<<g, kThreads, sm, s>>>(a, it); return;
+      case 8: direction_pair_kernel<8><<<g, kThreads, sm, s>>>(a, it); return;
+      default: direction_pair_kernel<14><<<g, kThreads, sm, s>>>(a, it); return;
+    }
+  }
+  direction_kernel<<<dim3(c.tiles_x, c.tiles_y, L->R), kThreads, L->smem, s>>>(a, it);
+}
+
 // Whether a CG iteration runs its update inside the preconditioner's forward row
 // pass (fft512_update_rows_fwd_kernel) instead of update_kernel.
 inline bool fused_update(const LikelihoodState* L) { return L->fft && fft512_rows(L->fd); }
@@ -2697,7 +2898,7 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
   });
   ok = ok && capture(b_inner, [&]() {
     cond_clear_kernel<<<1, 32, 0, s>>>(h_inner);
-    direction_kernel<<<grid, kThreads, L->smem, s>>>(a, 0);
+    launch_direction(L, a, 0, s);
     if (fused_update(L)) {
       precond_apply(L, a.part_rz, true, 0, counters, s, &a, 0);
     } else {
@@ -2804,7 +3005,7 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
       const int n = std::min(kChunk, L->max_iter - total - launched);
       for (int t = 0; t < n; ++t) {
         tr->begin(EP_TV_K_CG_DIRECTION, s);
-        direction_kernel<<<grid, kThreads, L->smem, s>>>(a, launched);
+        launch_direction(L, a, launched, s);
         tr->end(s, -1.0);
         if (fused_update(L)) {
           // the update with the preconditioner's forward row pass, then its other passes
