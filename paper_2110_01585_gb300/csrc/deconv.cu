@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(kThreads, 5) direction_kernel(CgArgs a, int it
 // the taps are summed in the order of hth_tile_sep.  A system that has stopped is
 // neither read nor written.
 template <int HR>
-__global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_kernel(CgArgs a, int it_arg) {
+__global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 5) direction_pair_kernel(CgArgs a, int it_arg) {
   constexpr int RH = kTile + 2 * HR, RW = kTile + 2 * HR, NT = 2 * HR + 1;
   extern __shared__ float4 smem4[];
   float2* reg = reinterpret_cast<float2*>(smem4);  // RH x RW region pairs
@@ -933,12 +933,14 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_ker
   // Region staging, all of a thread's loads issued before the first is used
   if ((c.W & 3) == 0 && (HR & 3) == 0 && c0 >= HR && c0 + kTile + HR <= c.W) {
     // no column wraps: float4 quads of each plane
-    constexpr int Q4 = RW / 4, NQ = RH * Q4, KQ = (NQ + kThreads - 1) / kThreads;
-    float4 zv0[KQ], zv1[KQ], pv0[KQ], pv1[KQ];
+    // in rounds of KQ quads per thread, all loads of a round in flight together
+    constexpr int Q4 = RW / 4, NQ = RH * Q4, KQ = 2;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i0 = threadIdx.x; i0 < NQ; i0 += KQ * kThreads) {
+    float4 zv0[KQ], zv1[KQ], pv0[KQ], pv1[KQ];
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
-      const int i = threadIdx.x + k * kThreads;
+      const int i = i0 + k * kThreads;
       zv0[k] = zv1[k] = pv0[k] = pv1[k] = zero4;
       if (i < NQ) {
         const int rr = i / Q4, q = i - rr * Q4;
@@ -955,7 +957,7 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_ker
     }
 #pragma unroll
     for (int k = 0; k < KQ; ++k) {
-      const int i = threadIdx.x + k * kThreads;
+      const int i = i0 + k * kThreads;
       if (i < NQ) {
         const int rr = i / Q4, q = i - rr * Q4;
         float4 v0 = zv0[k], v1 = zv1[k];
@@ -973,6 +975,7 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_ker
         dst[0] = make_float4(v0.x, v1.x, v0.y, v1.y);
         dst[1] = make_float4(v0.z, v1.z, v0.w, v1.w);
       }
+    }
     }
   } else {
     constexpr int kBatch = 4, NE = RH * RW;
@@ -1007,25 +1010,25 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_ker
   __syncthreads();
   // row pass (column taps along the rows)
   {
-    float2 wc[NT];
-#pragma unroll
-    for (int b = 0; b < NT; ++b) wc[b] = taps2[NT + b];
     const int cp = threadIdx.x & 15;  // column pair 2 cp, 2 cp + 1 of the tile
     for (int rr = threadIdx.x >> 4; rr < RH; rr += kThreads / 16) {
       const float4* row4 = reinterpret_cast<const float4*>(reg + rr * RW + 2 * cp);
-      float2 win[NT + 1];
-#pragma unroll
-      for (int q = 0; q <= HR; ++q) {
-        const float4 t = row4[q];
-        win[2 * q] = make_float2(t.x, t.y);
-        win[2 * q + 1] = make_float2(t.z, t.w);
-      }
+      // window columns 2 q, 2 q + 1 arrive as one float4; tap b meets columns b, b + 1
       float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      float4 t = row4[0];
 #pragma unroll
-      for (int b = 0; b < NT; ++b) {
-        a0 = __ffma2_rn(wc[b], win[b], a0);
-        a1 = __ffma2_rn(wc[b], win[b + 1], a1);
+      for (int q = 0; q < HR; ++q) {
+        const float4 u = row4[q + 1];
+        const float2 w0 = taps2[NT + 2 * q], w1 = taps2[NT + 2 * q + 1];
+        a0 = __ffma2_rn(w0, make_float2(t.x, t.y), a0);
+        a1 = __ffma2_rn(w0, make_float2(t.z, t.w), a1);
+        a0 = __ffma2_rn(w1, make_float2(t.z, t.w), a0);
+        a1 = __ffma2_rn(w1, make_float2(u.x, u.y), a1);
+        t = u;
       }
+      const float2 wl = taps2[NT + 2 * HR];
+      a0 = __ffma2_rn(wl, make_float2(t.x, t.y), a0);
+      a1 = __ffma2_rn(wl, make_float2(t.z, t.w), a1);
       *reinterpret_cast<float4*>(tmp + rr * kTile + 2 * cp) = make_float4(a0.x, a0.y, a1.x, a1.y);
     }
   }
@@ -1034,16 +1037,22 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 4) direction_pair_ker
   const int tx = threadIdx.x & 31, tr0 = (threadIdx.x >> 5) * 4;
   float2 acc[4];
   {
-    float2 in[NT + 3];
-#pragma unroll
-    for (int i = 0; i < NT + 3; ++i) in[i] = tmp[(tr0 + i) * kTile + tx];
+    // a sliding window of four inputs: tap t meets rows tr0 + t .. tr0 + t + 3
+    float2 in0 = tmp[tr0 * kTile + tx], in1 = tmp[(tr0 + 1) * kTile + tx],
+           in2 = tmp[(tr0 + 2) * kTile + tx];
 #pragma unroll
     for (int o = 0; o < 4; ++o) acc[o] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
+      const float2 in3 = tmp[(tr0 + t + 3) * kTile + tx];
       const float2 wr = taps2[t];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) acc[o] = __ffma2_rn(wr, in[o + t], acc[o]);
+      acc[0] = __ffma2_rn(wr, in0, acc[0]);
+      acc[1] = __ffma2_rn(wr, in1, acc[1]);
+      acc[2] = __ffma2_rn(wr, in2, acc[2]);
+      acc[3] = __ffma2_rn(wr, in3, acc[3]);
+      in0 = in1;
+      in1 = in2;
+      in2 = in3;
     }
   }
   float* P = (it & 1) ? a.P2 : a.P;
