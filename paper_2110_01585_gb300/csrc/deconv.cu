@@ -1524,8 +1524,9 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_inv_kernel(FftDesc f,
 constexpr int kF = 512;
 constexpr int kXs = 578;        // scratch / staged-column pitch in float2
 constexpr int kF512Warps = 8;   // warps per block of the 512-point kernels
-// Rows per warp of the 512-point row passes: a warp loads its next row into
-// registers while it transforms the current one.
+// Rows per warp of the 512-point row passes, one after another; each row's loads
+// are all issued before the transform starts (prefetching the next row during the
+// transform measured slower: it raises register pressure at the 128-register limit).
 constexpr int kRowsPerWarp512 = 4;
 
 __global__ void tw512_kernel(float2* tw) {
@@ -1642,7 +1643,7 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
   float2* out = f.tmp + (long long)pair * f.H * kF;
   const int rend = min(f.H, (blockIdx.x + 1) * rpb);
   const uint64_t keep = l2_policy_keep();
-  float2 nx[16];  // the warp's next row, in flight during the current transform
+  float2 nx[16];  // the row, all loads in flight together
   auto load_row = [&](int rw) {
     const long long p0 = (long long)rw * f.W;
 #pragma unroll
@@ -1652,13 +1653,11 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
       if (c < f.W) nx[m] = make_float2(ld_hint(r0p + p0 + c, keep), two ? ld_hint(r1p + p0 + c, keep) : 0.f);
     }
   };
-  int row = blockIdx.x * rpb + w;
-  if (row < rend) load_row(row);
-  for (; row < rend; row += kF512Warps) {
+  for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
+    load_row(row);
     float2 v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = nx[m];
-    if (row + kF512Warps < rend) load_row(row + kF512Warps);
     fft512_warp(v, scratch[w], tw);
 #pragma unroll
     for (int m = 0; m < 16; ++m) st_hint(out + (long long)row * kF + 32 * m + l, v[m], keep);
@@ -1840,8 +1839,7 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_rows_inv_kernel(Fft
   const float2* tin = f.tmp + (long long)pair * f.H * kF;
   const uint64_t release = l2_policy_release();
   double acc0 = 0.0, acc1 = 0.0;
-  // the warp's next row (transform input and both residuals), in flight during
-  // the current transform
+  // the row's transform input and both residuals, all loads in flight together
   float2 nv[16], nr[16];
   auto load_row = [&](int rw) {
     const long long p0 = (long long)rw * f.W;
@@ -1857,8 +1855,8 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_rows_inv_kernel(Fft
     }
   };
   int row = blockIdx.x * rows_per + w;
-  if (row < rend) load_row(row);
   for (; row < rend; row += kF512Warps) {
+    load_row(row);
     const long long p0 = (long long)row * f.W;
     float2 v[16], rr[16];
 #pragma unroll
@@ -1866,7 +1864,6 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_rows_inv_kernel(Fft
       v[m] = nv[m];
       rr[m] = nr[m];
     }
-    if (row + kF512Warps < rend) load_row(row + kF512Warps);
     fft512_warp(v, scratch[w], tw);
     float rz0 = 0.f, rz1 = 0.f;
 #pragma unroll
