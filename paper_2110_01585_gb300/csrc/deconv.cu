@@ -454,6 +454,44 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   return fast_two_sum(p, fmaf(a.lo, b, e));
 }
 
+// Float-float on pairs: (value of system 0, value of system 1) in each float2, with
+// the packed FP32 add, multiply and FMA of sm_100-family GPUs.  Every packed
+// operation rounds each lane as the scalar one does, so a pair gives what two scalar
+// evaluations of the same expressions give.
+struct ff2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {  // a - b, one rounding
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ ff2 fast_two_sum2(float2 a, float2 b) {  // |a| >= |b|
+  const float2 s = f2add(a, b);
+  return {s, f2sub(b, f2sub(s, a))};
+}
+// ff_fma on pairs: acc + x * g with the tap g = g_hi + g_lo common to both lanes,
+// given as gh = (g_hi, g_hi), gl = (g_lo, g_lo) and gn = -gh.  The product is formed
+// negated (x.hi * -g_hi = -p exactly), so TwoSum(acc.hi, p) is written with
+// subtractions of -p; each lane's result equals ff_fma's.
+__device__ __forceinline__ ff2 ff2_fma(ff2 acc, ff2 x, float2 gh, float2 gl, float2 gn) {
+  const float2 pn = f2mul(x.hi, gn);
+  float2 e = f2fma(x.hi, gh, pn);
+  e = f2fma(x.hi, gl, f2fma(x.lo, gh, e));
+  const float2 sh = f2sub(acc.hi, pn);                                   // acc.hi + p
+  const float2 bb = f2sub(sh, acc.hi);
+  const float2 sl = f2sub(f2sub(acc.hi, f2sub(sh, bb)), f2add(pn, bb));  // + (p - bb)
+  return fast_two_sum2(sh, f2add(f2add(sl, acc.lo), e));
+}
+// y - acc for y exact in FP32 (lo = 0), as ff_add(ff{y, 0}, ff_neg(acc)) per lane
+__device__ __forceinline__ ff2 ff2_sub_from(float2 y, ff2 acc) {
+  const float2 sh = f2sub(y, acc.hi);
+  const float2 bb = f2sub(sh, y);                                        // s - a, a = y
+  const float2 sl = f2sub(f2sub(y, f2sub(sh, bb)), f2add(acc.hi, bb));   // (a - (s - bb)) + (-acc.hi - bb)
+  return fast_two_sum2(sh, f2sub(f2add(sl, make_float2(0.f, 0.f)), acc.lo));
+}
+
 // The separable part of residual_kernel with a compile-time K x K kernel: the
 // same float-float H x and FP32 H^T sums in the same order, with the region
 // sizes, index divisions and tap loops resolved at compile time.
@@ -738,6 +776,255 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
   const long long o = (long long)j * a.nb + blockIdx.y * c.tiles_x + blockIdx.x;
   block_sumf<3>(rz, rr2, bb, a.fft ? nullptr : a.part_rz + o,
              a.part_rr + o, a.part_bb + o);
+}
+
+// residual_kernel for the two systems 2 blockIdx.z, 2 blockIdx.z + 1 at once with a
+// separable K x K blur: every region value is a (system 0, system 1) pair, so each
+// float-float tap of H x and each FP32 tap of H^T is one packed operation for both
+// (ff2_fma: per lane the operations of ff_fma), and the index arithmetic, tap loads
+// and the loads of d are shared.  Per system and output the taps are summed in the
+// order of residual_sep_fixed, and the epilogue forms r, b and the partial sums as
+// residual_kernel does.  Shared memory: the x region (hi, lo) and the row-pass output
+// (hi, lo); y' - H x is written over the latter's hi half once every thread has read
+// it, and the H^T row pass over its lo half.
+template <int K>
+__global__ void __launch_bounds__(kThreads, 3) residual_pair_kernel(CgArgs a) {
+  constexpr int HR = K - 1, hh = K / 2;
+  constexpr int RH = kTile + 2 * HR, RW = RH;  // x region
+  constexpr int MH = kTile + 2 * hh, MW = MH;  // y' - H x region
+  static_assert(K % 2 == 1 && RW % 2 == 0 && MW % 2 == 0 && MH % 2 == 0, "paired outputs");
+  extern __shared__ float4 smem4[];
+  float2* xh = reinterpret_cast<float2*>(smem4);  // RH x RW
+  float2* xl = xh + RH * RW;
+  float2* ph = xl + RH * RW;                      // RH x MW
+  float2* pl = ph + RH * MW;
+  float2* vs = ph;                                // MH x MW, after the column pass
+  float2* tmpf = pl;                              // MH x kTile, H^T row pass
+  __shared__ float2 tgh[2 * K], tgl[2 * K], tgn[2 * K];  // u taps, then v taps
+  __shared__ int ctab[RW];
+  const ConvDesc& c = a.c;
+  const int j0 = 2 * blockIdx.z, j1 = j0 + 1;
+  const bool two = j1 < a.R;
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  for (int i = threadIdx.x; i < 2 * K; i += kThreads) {
+    const ff t = ff_from_double(c.hd[i]);
+    tgh[i] = make_float2(t.hi, t.hi);
+    tgl[i] = make_float2(t.lo, t.lo);
+    tgn[i] = make_float2(-t.hi, -t.hi);
+  }
+  column_table(ctab, c0 - HR, RW, c.W);
+  __syncthreads();
+  const long long N = c.N;
+  const double* x0 = a.X + (long long)j0 * N;
+  const double* x1 = a.X + (long long)j1 * N;
+  {
+    // the FP64 regions of both systems, kB positions (2 kB loads) in flight per thread
+    constexpr int kB = 4, NE = RH * RW;
+    for (int i0 = threadIdx.x; i0 < NE; i0 += kB * kThreads) {
+      double v0[kB], v1[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int i = i0 + u * kThreads;
+        v0[u] = v1[u] = 0.0;
+        if (i < NE) {
+          const int rr = i / RW, cc = i - rr * RW;
+          const long long p = (long long)wrapi(r0 - HR + rr, c.H) * c.W + ctab[cc];
+          v0[u] = x0[p];
+          if (two) v1[u] = x1[p];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < NE) {
+          const ff t0 = ff_split_bits(v0[u]), t1 = ff_split_bits(v1[u]);
+          xh[i] = make_float2(t0.hi, t1.hi);
+          xl[i] = make_float2(t0.lo, t1.lo);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // H x along the rows (v taps): outputs (rr, 2 mp), (rr, 2 mp + 1) from x[rr][2 mp .. 2 mp + K]
+  for (int idx = threadIdx.x; idx < RH * (MW / 2); idx += kThreads) {
+    const int rr = idx / (MW / 2), mp = idx - rr * (MW / 2);
+    const float4* h4 = reinterpret_cast<const float4*>(xh + rr * RW + 2 * mp);
+    const float4* l4 = reinterpret_cast<const float4*>(xl + rr * RW + 2 * mp);
+    float2 wh[K + 1], wl[K + 1];
+#pragma unroll
+    for (int q = 0; q < (K + 1) / 2; ++q) {
+      const float4 th = h4[q], tl = l4[q];
+      wh[2 * q] = make_float2(th.x, th.y);
+      wh[2 * q + 1] = make_float2(th.z, th.w);
+      wl[2 * q] = make_float2(tl.x, tl.y);
+      wl[2 * q + 1] = make_float2(tl.z, tl.w);
+    }
+    ff2 acc0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, acc1 = acc0;
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      const float2 gh = tgh[K + b], gl = tgl[K + b], gn = tgn[K + b];
+      acc0 = ff2_fma(acc0, ff2{wh[K - 1 - b], wl[K - 1 - b]}, gh, gl, gn);
+      acc1 = ff2_fma(acc1, ff2{wh[K - b], wl[K - b]}, gh, gl, gn);
+    }
+    const int o = rr * MW + 2 * mp;
+    *reinterpret_cast<float4*>(ph + o) = make_float4(acc0.hi.x, acc0.hi.y, acc1.hi.x, acc1.hi.y);
+    *reinterpret_cast<float4*>(pl + o) = make_float4(acc0.lo.x, acc0.lo.y, acc1.lo.x, acc1.lo.y);
+  }
+  __syncthreads();
+  // H x along the columns (u taps) and y' - H x: outputs (mr, mc), (mr + 1, mc); the
+  // results wait in registers until every thread has read the row-pass output
+  const float* y0p = j0 == 0 ? a.Y0 : a.Y1 + (long long)(j0 - 1) * N;
+  const float* y1p = a.Y1 + (long long)(j1 - 1) * N;
+  constexpr int kColItems = ((MH / 2) * MW + kThreads - 1) / kThreads;
+  float2 vout[kColItems][2];
+#pragma unroll
+  for (int it = 0; it < kColItems; ++it) {
+    const int idx = threadIdx.x + it * kThreads;
+    vout[it][0] = vout[it][1] = make_float2(0.f, 0.f);
+    if (idx >= (MH / 2) * MW) continue;
+    const int mp = idx / MW, mc = idx - mp * MW, mr = 2 * mp;
+    const int gcol = wrapi(c0 - hh + mc, c.W);
+    const long long q0 = (long long)wrapi(r0 - hh + mr, c.H) * c.W + gcol;
+    const long long q1 = (long long)wrapi(r0 - hh + mr + 1, c.H) * c.W + gcol;
+    const float2 ya = make_float2(y0p[q0], two ? y1p[q0] : 0.f);
+    const float2 yb = make_float2(y0p[q1], two ? y1p[q1] : 0.f);
+    float2 wh[K + 1], wl[K + 1];
+#pragma unroll
+    for (int jj = 0; jj <= K; ++jj) {
+      wh[jj] = ph[(mr + jj) * MW + mc];
+      wl[jj] = pl[(mr + jj) * MW + mc];
+    }
+    ff2 acc0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, acc1 = acc0;
+#pragma unroll
+    for (int aa = 0; aa < K; ++aa) {
+      const float2 gh = tgh[aa], gl = tgl[aa], gn = tgn[aa];
+      acc0 = ff2_fma(acc0, ff2{wh[K - 1 - aa], wl[K - 1 - aa]}, gh, gl, gn);
+      acc1 = ff2_fma(acc1, ff2{wh[K - aa], wl[K - aa]}, gh, gl, gn);
+    }
+    const ff2 v0 = ff2_sub_from(ya, acc0), v1 = ff2_sub_from(yb, acc1);
+    vout[it][0] = f2add(v0.hi, v0.lo);
+    vout[it][1] = f2add(v1.hi, v1.lo);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kColItems; ++it) {
+    const int idx = threadIdx.x + it * kThreads;
+    if (idx >= (MH / 2) * MW) continue;
+    const int mp = idx / MW, mc = idx - mp * MW, mr = 2 * mp;
+    vs[mr * MW + mc] = vout[it][0];
+    vs[(mr + 1) * MW + mc] = vout[it][1];
+  }
+  __syncthreads();
+  // H^T in FP32 along the rows (v taps, hi parts): two adjacent outputs per thread
+  for (int idx = threadIdx.x; idx < MH * (kTile / 2); idx += kThreads) {
+    const int mr = idx / (kTile / 2), tp = idx - mr * (kTile / 2);
+    const float4* r4 = reinterpret_cast<const float4*>(vs + mr * MW + 2 * tp);
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+    float4 t = r4[0];
+#pragma unroll
+    for (int q = 0; q < K / 2; ++q) {
+      const float4 u = r4[q + 1];
+      const float2 w0 = tgh[K + 2 * q], w1 = tgh[K + 2 * q + 1];
+      a0 = f2fma(w0, make_float2(t.x, t.y), a0);
+      a1 = f2fma(w0, make_float2(t.z, t.w), a1);
+      a0 = f2fma(w1, make_float2(t.z, t.w), a0);
+      a1 = f2fma(w1, make_float2(u.x, u.y), a1);
+      t = u;
+    }
+    const float2 wlast = tgh[K + K - 1];
+    a0 = f2fma(wlast, make_float2(t.x, t.y), a0);
+    a1 = f2fma(wlast, make_float2(t.z, t.w), a1);
+    *reinterpret_cast<float4*>(tmpf + mr * kTile + 2 * tp) = make_float4(a0.x, a0.y, a1.x, a1.y);
+  }
+  __syncthreads();
+  // H^T along the columns (u taps): rows tr0 .. tr0 + 3 of column tx, in registers
+  const int tx = threadIdx.x & 31, tr0 = (threadIdx.x >> 5) * 4;
+  float2 hv[4];
+  {
+    float2 in0 = tmpf[tr0 * kTile + tx], in1 = tmpf[(tr0 + 1) * kTile + tx],
+           in2 = tmpf[(tr0 + 2) * kTile + tx];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) hv[o] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      const float2 in3 = tmpf[(tr0 + t + 3) * kTile + tx];
+      const float2 wr = tgh[t];
+      hv[0] = f2fma(wr, in0, hv[0]);
+      hv[1] = f2fma(wr, in1, hv[1]);
+      hv[2] = f2fma(wr, in2, hv[2]);
+      hv[3] = f2fma(wr, in3, hv[3]);
+      in0 = in1;
+      in1 = in2;
+      in2 = in3;
+    }
+  }
+  // epilogue: the inputs of all four rows loaded first
+  const int gcol = c0 + tx;
+  float dv[4], nv0[4], ev0[4], nv1[4], ev1[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int gr = r0 + tr0 + o;
+    dv[o] = nv0[o] = ev0[o] = nv1[o] = ev1[o] = 0.f;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    dv[o] = a.D[p];
+    if (j0 == 0) {
+      nv0[o] = a.Ncav[p];
+      ev0[o] = a.Hty[p];
+    } else {
+      nv0[o] = a.E2[(long long)(j0 - 1) * N + p];
+      ev0[o] = a.E1[(long long)(j0 - 1) * N + p];
+    }
+    if (two) {
+      nv1[o] = a.E2[(long long)(j1 - 1) * N + p];
+      ev1[o] = a.E1[(long long)(j1 - 1) * N + p];
+    }
+  }
+  float rz0 = 0.f, rr0 = 0.f, bb0 = 0.f, rz1 = 0.f, rr1 = 0.f, bb1 = 0.f;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int tr = tr0 + o, gr = r0 + tr;
+    if (gr >= c.H || gcol >= c.W) continue;
+    const long long p = (long long)gr * c.W + gcol;
+    const int xi_ = (tr + HR) * RW + tx + HR;
+    const float2 xhv = xh[xi_], xlv = xl[xi_];
+    const float d = dv[o];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      const int j = u ? j1 : j0;
+      const float nvu = u ? nv1[o] : nv0[o], evu = u ? ev1[o] : ev0[o];
+      // n' - d x in float-float, as residual_kernel forms it
+      ff np;
+      if (j == 0) {
+        np = {nvu, 0.f};
+      } else {
+        const float sd = sqrtf(d);
+        const float pr = __fmul_rn(sd, nvu);
+        np = {pr, fmaf(sd, nvu, -pr)};
+      }
+      const ff xu = u ? ff{xhv.y, xlv.y} : ff{xhv.x, xlv.x};
+      const ff t = ff_add(np, ff_neg(ff_mul_f(xu, d)));
+      const float r = (u ? hv[o].y : hv[o].x) * c.inv_xi + (t.hi + t.lo);
+      a.Rr[(long long)j * N + p] = r;
+      const float b = j == 0 ? evu + nvu : evu + sqrtf(d) * nvu;
+      if (u) {
+        if (!a.fft) rz1 = fmaf(r * r, a.Minv[p], rz1);
+        rr1 = fmaf(r, r, rr1);
+        bb1 = fmaf(b, b, bb1);
+      } else {
+        if (!a.fft) rz0 = fmaf(r * r, a.Minv[p], rz0);
+        rr0 = fmaf(r, r, rr0);
+        bb0 = fmaf(b, b, bb0);
+      }
+    }
+  }
+  const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
+  const long long o0 = (long long)j0 * a.nb + blk, o1 = (long long)j1 * a.nb + blk;
+  block_sumf<3>(rz0, rr0, bb0, a.fft ? nullptr : a.part_rz + o0, a.part_rr + o0, a.part_bb + o0);
+  if (two)
+    block_sumf<3>(rz1, rr1, bb1, a.fft ? nullptr : a.part_rz + o1, a.part_rr + o1,
+                  a.part_bb + o1);
 }
 
 // Per system after a true residual: done if r.r <= rtol^2 b.b (threshold +inf),
@@ -2313,6 +2600,19 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
                                                                                 rz_buf);
 }
 
+// The true residual of every system: two systems per block for a 9 x 9 separable blur
+// (residual_pair_kernel), else one (residual_kernel).
+void launch_residual(const LikelihoodState* L, const CgArgs& a, cudaStream_t s) {
+  const ConvDesc& c = L->c;
+  if (c.separable && c.kh == 9 && c.kw == 9) {
+    constexpr int K = 9, RH = kTile + 2 * (K - 1), MW = kTile + 2 * (K / 2);
+    const size_t sm = sizeof(float2) * 2 * ((size_t)RH * RH + (size_t)RH * MW);
+    residual_pair_kernel<K><<<dim3(c.tiles_x, c.tiles_y, (L->R + 1) / 2), kThreads, sm, s>>>(a);
+    return;
+  }
+  residual_kernel<<<dim3(c.tiles_x, c.tiles_y, L->R), kThreads, L->smem_res, s>>>(a);
+}
+
 // Whether the direction step runs two systems per block (direction_pair_kernel).
 inline bool pair_direction(const LikelihoodState* L) {
   const ConvDesc& c = L->c;
@@ -2461,6 +2761,7 @@ bool raise_smem_limits() {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
   const void* fns[] = {(const void*)direction_kernel, (const void*)residual_kernel,
+                       (const void*)residual_pair_kernel<9>,
                        (const void*)fft_rows_fwd_kernel, (const void*)fft_rows_inv_kernel,
                        (const void*)fft_cols_filter_kernel};
   for (const void* f : fns) {
@@ -2887,7 +3188,7 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
   });
   ok = ok && capture(b_outer, [&]() {
     cond_clear_kernel<<<1, 32, 0, s>>>(h_outer);
-    residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
+    launch_residual(L, a, s);
     thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, a.part_rz, a.fft, L->R, L->nb,
                                          L->rtol2_true, L->rtol2_probe, kEta2, L->thr, L->d_relres,
                                          L->d_prev_rr, L->d_rr0, 0, &L->d_loop->outer, L->d_active,
@@ -2968,7 +3269,7 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
   bool converged = false;
   for (int outer = 0;; ++outer) {
     tr->begin(EP_TV_K_CG_RESIDUAL, s);
-    residual_kernel<<<grid, kThreads, L->smem_res, s>>>(a);
+    launch_residual(L, a, s);
     tr->end(s, (double)L->R * N);
     thresholds_kernel<<<1, 1024, 0, s>>>(a.part_rr, a.part_bb, a.part_rz, a.fft, L->R, L->nb,
                                          L->rtol2_true, L->rtol2_probe, eta2, L->thr, L->d_relres,
