@@ -1491,6 +1491,14 @@ __global__ void commit_kernel(double* X, const float* Ec, const int* act0, long 
 // real and even in frequency, so the real and imaginary parts of the result are
 // M^{-1} r_a and M^{-1} r_b.  Transforms are radix-2 in shared memory: rows,
 // then columns (forward, filter, inverse in one pass), then rows again.
+// Device-side state of the solver loops of a graph replay.
+struct LoopState {
+  int it;         // CG iteration within the current pass
+  int outer;      // passes started
+  int total;      // CG iterations of this update
+  int converged;  // 1 once a true residual met every system's target
+};
+
 struct FftDesc {
   int H, W;          // image
   int HP, WP;        // power-of-two transform sizes, HP >= H, WP >= W
@@ -1509,6 +1517,10 @@ struct FftDesc {
   unsigned* arrive;  // [pairs] block-arrival counters of the inverse row pass
   int first;         // 1: first application of a refinement pass (beta = 0)
   unsigned long long* counters;  // DC_CG_PRE_UNITS counts the systems transformed
+  LoopState* loop;   // graph replays: the column pass also counts the CG iteration and
+                     // sets the inner loop's condition (loop_step), else NULL
+  cudaGraphConditionalHandle h_inner;
+  int max_iter;
 };
 
 // The last block of a pair's inverse row pass sums the r.z partials of its two
@@ -1533,6 +1545,22 @@ __device__ __forceinline__ bool pair_idle(const FftDesc& f, int pair) {
   if (!f.act) return false;
   const int j0 = 2 * pair, j1 = 2 * pair + 1;
   return f.act[4 * j0] == 0.f && (j1 >= f.R || f.act[4 * j1] == 0.f);
+}
+
+// After a CG iteration's update (graph replays, by block (0, 0) of the column pass,
+// which every iteration launches): count the iteration, and go on while a system is
+// still active and the iteration budget lasts, as iter_kernel does.
+__device__ __forceinline__ void loop_step(const FftDesc& f) {
+  if (!f.loop || blockIdx.x != 0 || blockIdx.y != 0 || threadIdx.x >= 32) return;
+  int cnt = 0;
+  for (int j = threadIdx.x; j < f.R; j += 32) cnt += f.act[4 * j] != 0.f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+  if (threadIdx.x == 0) {
+    f.loop->it += 1;
+    f.loop->total += 1;
+    cudaGraphSetConditional(f.h_inner, (cnt > 0 && f.loop->total < f.max_iter) ? 1u : 0u);
+  }
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -1714,6 +1742,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_rows_fwd_kernel(FftDesc f,
 // Column transforms (rows beyond H are zero), the preconditioner filter and the
 // inverse column transforms; only rows below H are kept.
 __global__ void __launch_bounds__(kFftThreads, 4) fft_cols_filter_kernel(FftDesc f) {
+  loop_step(f);
   if (pair_idle(f, blockIdx.y)) return;
   extern __shared__ float2 sm2[];
   float2* tw = sm2;
@@ -2057,6 +2086,7 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
 // [c][i]), transforms again and leaves it in its slot for the block's store.
 __global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(FftDesc f,
                                                                             const float* __restrict__ hthT) {
+  loop_step(f);
   if (pair_idle(f, blockIdx.y)) return;
   __shared__ float2 tw[kF];
   __shared__ float2 cols[kF512Warps][kXs];
@@ -2233,13 +2263,6 @@ __global__ void check_kernel(const float* scal, int R, int* active) {
 // after the first few), so a sweep normally needs one pass; a cold start still
 // moves in steps of eta, which FP32 CG reaches before its rounding floor.
 constexpr double kEta2 = 1e-9;
-
-struct LoopState {
-  int it;         // CG iteration within the current pass
-  int outer;      // passes started
-  int total;      // CG iterations of this update
-  int converged;  // 1 once a true residual met every system's target
-};
 
 __global__ void cond_clear_kernel(cudaGraphConditionalHandle h) {
   if (threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
@@ -2514,7 +2537,7 @@ struct LikelihoodState {
 namespace {
 
 CgArgs cg_args(LikelihoodState* L) {
-  CgArgs a;
+  CgArgs a = {};
   a.c = L->c;
   a.R = L->R;
   a.S = L->S;
@@ -2566,10 +2589,16 @@ int ilog2(int v) {
 // scalars are left alone (launch-shape tuning).
 // stages: 1 = the forward row pass (fused with the CG update when upd is given:
 // 512-point rows only, see fused_update), 2 = the column and inverse row passes.
+// step: graph replays, whose column pass then advances the inner loop and its
+// condition h_step (loop_step).
 void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
                    unsigned long long* counters, cudaStream_t s, const CgArgs* upd = nullptr,
-                   int it = 0, int stages = 3) {
+                   int it = 0, int stages = 3, bool step = false,
+                   cudaGraphConditionalHandle h_step = 0) {
   FftDesc f = L->fd;
+  f.loop = step ? L->d_loop : nullptr;
+  f.h_inner = h_step;
+  f.max_iter = L->max_iter;
   f.act = cg ? L->d_scal : nullptr;
   f.scal_w = cg ? L->d_scal : nullptr;
   f.rzs = cg ? L->d_rzs : nullptr;
@@ -3203,16 +3232,19 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
     commit_kernel<<<dim3(std::min(grid1d(N), 1024), L->R), 256, 0, s>>>(L->X, L->Ec, L->d_act0, N);
     return true;
   });
+  // with the FFT preconditioner the column pass, which every iteration launches,
+  // counts the iteration and sets the condition (0 or 1, and 0 once the budget is
+  // spent); Jacobi keeps the clearing and counting kernels
   ok = ok && capture(b_inner, [&]() {
-    cond_clear_kernel<<<1, 32, 0, s>>>(h_inner);
+    if (!L->fft) cond_clear_kernel<<<1, 32, 0, s>>>(h_inner);
     launch_direction(L, a, 0, s);
     if (fused_update(L)) {
-      precond_apply(L, a.part_rz, true, 0, counters, s, &a, 0);
+      precond_apply(L, a.part_rz, true, 0, counters, s, &a, 0, 3, true, h_inner);
     } else {
       update_kernel<<<grid, kUpdThreads, 0, s>>>(a, 0);
-      if (L->fft) precond_apply(L, a.part_rz, true, 0, counters, s);
+      if (L->fft) precond_apply(L, a.part_rz, true, 0, counters, s, nullptr, 0, 3, true, h_inner);
     }
-    iter_kernel<<<1, 64, 0, s>>>(L->d_loop, L->d_scal, L->R, L->max_iter, h_inner);
+    if (!L->fft) iter_kernel<<<1, 64, 0, s>>>(L->d_loop, L->d_scal, L->R, L->max_iter, h_inner);
     return true;
   });
   cudaGraphExec_t exec = nullptr;
