@@ -1476,21 +1476,27 @@ __global__ void commit_kernel(double* X, const float* Ec, const int* act0, long 
   if (!act0[j]) return;
   double* x = X + (long long)j * N;
   const float* e = Ec + (long long)j * N;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-       p += (long long)gridDim.x * blockDim.x)
-    x[p] += (double)e[p];
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                  stride = (long long)gridDim.x * blockDim.x;
+  if ((N & 3) == 0) {
+    // four pixels per step: one float4 of e, two double2 of x (planes 32-byte aligned)
+    for (long long q = t0; q < N / 4; q += stride) {
+      const float4 ev = reinterpret_cast<const float4*>(e)[q];
+      double2* x2 = reinterpret_cast<double2*>(x) + 2 * q;
+      double2 a = x2[0], b = x2[1];
+      a.x += (double)ev.x;
+      a.y += (double)ev.y;
+      b.x += (double)ev.z;
+      b.y += (double)ev.w;
+      x2[0] = a;
+      x2[1] = b;
+    }
+    return;
+  }
+  for (long long p = t0; p < N; p += stride) x[p] += (double)e[p];
 }
 
 
-// ---------------------------------------------------------------------------
-// Circulant preconditioner for power-of-two H and W:
-//   M = H^T H / xi + dbar I,  dbar = mean(d),  M^{-1} r = F^{-1}[F r / (|h_f|^2 / xi + dbar)].
-// H^T H is circulant, so M differs from Q only by d - dbar on the diagonal; CG
-// on M^{-1} Q needs a few tens of iterations where Jacobi needs hundreds.
-// Two real systems share one complex transform (z = r_a + i r_b): the filter is
-// real and even in frequency, so the real and imaginary parts of the result are
-// M^{-1} r_a and M^{-1} r_b.  Transforms are radix-2 in shared memory: rows,
-// then columns (forward, filter, inverse in one pass), then rows again.
 // Device-side state of the solver loops of a graph replay.
 struct LoopState {
   int it;         // CG iteration within the current pass
@@ -1499,6 +1505,16 @@ struct LoopState {
   int converged;  // 1 once a true residual met every system's target
 };
 
+// ---------------------------------------------------------------------------
+// Circulant preconditioner for power-of-two H and W:
+//   M = H^T H / xi + dbar I,  dbar = mean(d),  M^{-1} r = F^{-1}[F r / (|h_f|^2 / xi + dbar)].
+// H^T H is circulant, so M differs from Q only by d - dbar on the diagonal; CG
+// on M^{-1} Q needs a few tens of iterations where Jacobi needs hundreds.
+// Two real systems share one complex transform (z = r_a + i r_b): the filter is
+// real and even in frequency, so the real and imaginary parts of the result are
+// M^{-1} r_a and M^{-1} r_b.  Rows, then columns (forward, filter, inverse in one
+// pass), then rows again; 512-point transforms are register-resident (one warp per
+// row or column), other sizes run Stockham passes in shared memory.
 struct FftDesc {
   int H, W;          // image
   int HP, WP;        // power-of-two transform sizes, HP >= H, WP >= W
@@ -2084,7 +2100,7 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
 // global memory; rows at and beyond H are zero), and each warp transforms one
 // column in registers, filters it with hthT (the filter stored column-major,
 // [c][i]), transforms again and leaves it in its slot for the block's store.
-__global__ void __launch_bounds__(32 * kF512Warps) fft512_cols_filter_kernel(FftDesc f,
+__global__ void __launch_bounds__(32 * kF512Warps, 3) fft512_cols_filter_kernel(FftDesc f,
                                                                             const float* __restrict__ hthT) {
   loop_step(f);
   if (pair_idle(f, blockIdx.y)) return;
@@ -3229,7 +3245,8 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
   ok = ok && capture(b_pass, [&]() {
     if (L->fft) precond_apply(L, a.part_rz, true, 1, counters, s);
     if (!add_cond(h_inner, cudaGraphCondTypeWhile, &b_inner)) return false;
-    commit_kernel<<<dim3(std::min(grid1d(N), 1024), L->R), 256, 0, s>>>(L->X, L->Ec, L->d_act0, N);
+    commit_kernel<<<dim3(std::min(grid1d((N + 3) / 4), 1024), L->R), 256, 0, s>>>(L->X, L->Ec,
+                                                                              L->d_act0, N);
     return true;
   });
   // with the FFT preconditioner the column pass, which every iteration launches,
@@ -3386,7 +3403,8 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     // solutions of the systems that iterated, then count the iterations up to the
     // poll that found all systems stopped
     tr->begin(EP_TV_K_CG_COMMIT, s);
-    commit_kernel<<<dim3(std::min(grid1d(N), 1024), L->R), 256, 0, s>>>(L->X, L->Ec, L->d_act0, N);
+    commit_kernel<<<dim3(std::min(grid1d((N + 3) / 4), 1024), L->R), 256, 0, s>>>(L->X, L->Ec,
+                                                                              L->d_act0, N);
     tr->end(s, (double)started * N);
     total += launched;
   }
