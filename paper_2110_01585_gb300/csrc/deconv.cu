@@ -357,11 +357,6 @@ struct CgArgs {
   unsigned long long* counters;
 };
 
-__device__ __forceinline__ float rhs_value(const CgArgs& a, int j, long long p) {
-  if (j == 0) return a.Hty[p] + a.Ncav[p];
-  return a.E1[(long long)(j - 1) * a.c.N + p] + sqrtf(a.D[p]) * a.E2[(long long)(j - 1) * a.c.N + p];
-}
-
 // d = sum tau_k, n = sum nu_k (k = 1..4), Minv = 1 / (sum k^2 / xi + d); block sums of d.
 __global__ void __launch_bounds__(kThreads) prep_kernel(const float* __restrict__ tp,
                                                         const float* __restrict__ np, long long N,
@@ -589,7 +584,8 @@ __device__ __forceinline__ void residual_sep_fixed(const ConvDesc& c, const floa
 // True residual of every system (blockIdx.z),
 //   r = H^T (y' - H x) / xi + (n' - d x),
 // y' = y, n' = n for the mean system and y' = sqrt(xi) eps1_s, n' = sqrt(d) eps2_s for
-// probe s, so that r = b - Q x with b as in rhs_value.  Near the solution H^T H x / xi
+// probe s, so that r = b - Q x with the right-hand side b = H^T y / xi + n (mean) or
+// b = H^T eps1_s / sqrt(xi) + sqrt(d) eps2_s (probe s).  Near the solution H^T H x / xi
 // and d x are several times larger than r; evaluated in FP32 they leave an error of
 // order eps |H^T y'| / xi, which the conditioning of Q (1e4..1e5) turns into
 // percent-level errors in x.  So H x and n' - d x are formed in float-float from the
@@ -767,7 +763,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
     const ff t = ff_add(np, ff_neg(ff_mul_f(ff{xh[xi_], xl[xi_]}, d)));
     const float r = outb[tr * kTile + tx] * c.inv_xi + (t.hi + t.lo);
     a.Rr[(long long)j * c.N + p] = r;
-    // the right-hand side as rhs_value forms it
+    // the right-hand side b
     const float b = j == 0 ? ev[i] + nv[i] : ev[i] + sqrtf(d) * nv[i];
     if (!a.fft) rz = fmaf(r * r, a.Minv[p], rz);
     rr2 = fmaf(r, r, rr2);
@@ -2268,9 +2264,11 @@ __global__ void check_kernel(const float* scal, int R, int* active) {
 // The refinement passes and the CG iterations of a pass run as two nested WHILE
 // nodes of a graph, with an IF node around each pass; their conditions are set
 // by the kernels below from counters in device memory, so a likelihood-site
-// update needs no host round trip.  Every loop body starts by clearing its own
-// condition (cond_clear_kernel), so a body that did not set it again ends the
-// loop; the counters bound both loops (max_outer passes, max_iter iterations).
+// update needs no host round trip.  The outer body (and the inner one with Jacobi)
+// starts by clearing its own condition (cond_clear_kernel), so a body that did not
+// set it again ends the loop; with the FFT preconditioner the column pass of every
+// iteration sets the inner condition to 0 or 1 (loop_step).  The counters bound
+// both loops (max_outer passes, max_iter iterations).
 // Iterative refinement of the likelihood-site solves: a true residual in
 // float-float, then FP32 preconditioned CG on the correction until its recurrence
 // residual has dropped below max(eta ||r||, (rtol / 2) ||b||), repeated until
