@@ -355,6 +355,8 @@ struct CgArgs {
   int nbz;               // blocks per system producing r.z partials
   int fft;               // 1: z = M^{-1} r by the circulant preconditioner, else Jacobi
   unsigned long long* counters;
+  int defer_e;           // 1: the update leaves e += alpha p to the next direction kernel
+                         // (or the commit), see fft512_update_rows_fwd_kernel
 };
 
 // d = sum tau_k, n = sum nu_k (k = 1..4), Minv = 1 / (sum k^2 / xi + d); block sums of d.
@@ -1066,6 +1068,8 @@ __global__ void thresholds_kernel(const double* part_rr, const double* part_bb,
       thr[j] = done ? INFINITY : fmax(eta2 * rr, 0.25 * rtol2 * bb);
       scal[4 * j] = done ? 0.f : 1.f;
       scal[4 * j + 1] = 0.f;
+      scal[4 * j + 2] = 0.f;   // alpha of the pending correction update
+      scal[4 * j + 3] = -1.f;  // its iteration (none yet)
       act0[j] = done ? 0 : 1;
       if (!done) atomicAdd(&cnt, 1);
     }
@@ -1363,6 +1367,38 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 5) direction_pair_ker
   const int blk = blockIdx.y * c.tiles_x + blockIdx.x;
   block_sumf<2>(pq0, pq1, 0.f, act0 ? a.part_pq + (long long)j0 * a.nb + blk : nullptr,
                 act1 ? a.part_pq + (long long)j1 * a.nb + blk : nullptr, nullptr);
+  if (a.defer_e && it > 0) {
+    // the previous iteration's correction update on this tile, e += alpha p with that
+    // iteration's alpha and direction (the update kernel left it; a system active now
+    // was active then)
+    const float al0 = a.scal[4 * j0 + 2], al1 = act1 ? a.scal[4 * j1 + 2] : 0.f;
+    const bool e_zero = it == 1;  // the correction starts at zero: not read
+    const int gr = r0 + (threadIdx.x >> 3), gc0 = c0 + (threadIdx.x & 7) * 4;
+    if (gr < c.H) {
+      const long long p = (long long)gr * c.W + gc0;
+      if ((c.W & 3) == 0 && gc0 + 4 <= c.W) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (!(u ? act1 : act0)) continue;
+          const long long q = (u ? o1 : o0) + p;
+          const float al = u ? al1 : al0;
+          const float4 pv = *reinterpret_cast<const float4*>(Pold + q);
+          float4 ev = e_zero ? make_float4(0.f, 0.f, 0.f, 0.f)
+                             : *reinterpret_cast<const float4*>(a.Ec + q);
+          ev.x = fmaf(al, pv.x, ev.x);
+          ev.y = fmaf(al, pv.y, ev.y);
+          ev.z = fmaf(al, pv.z, ev.z);
+          ev.w = fmaf(al, pv.w, ev.w);
+          *reinterpret_cast<float4*>(a.Ec + q) = ev;
+        }
+      } else {
+        for (int t = 0; t < 4 && gc0 + t < c.W; ++t) {
+          if (act0) a.Ec[o0 + p + t] = fmaf(al0, Pold[o0 + p + t], e_zero ? 0.f : a.Ec[o0 + p + t]);
+          if (act1) a.Ec[o1 + p + t] = fmaf(al1, Pold[o1 + p + t], e_zero ? 0.f : a.Ec[o1 + p + t]);
+        }
+      }
+    }
+  }
 }
 
 // e += alpha p, r -= alpha q (e: the FP32 correction of this refinement pass,
@@ -1467,17 +1503,34 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(CgArgs a, int it_ar
 }
 
 // x += e for every system that iterated in the pass that just ended.
-__global__ void commit_kernel(double* X, const float* Ec, const int* act0, long long N) {
+// With deferred correction updates (CgArgs::defer_e) the last iteration's e += alpha p
+// of each system is still pending (scal[4 j + 2] = alpha, scal[4 j + 3] = its
+// iteration, whose direction is in P or P2 by parity; e is not read if it was the
+// first): it is formed here, with the operation the update kernel would have used.
+__global__ void commit_kernel(double* X, const float* Ec, const int* act0, long long N,
+                              const float* scal, const float* P, const float* P2) {
   const int j = blockIdx.y;
   if (!act0[j]) return;
   double* x = X + (long long)j * N;
   const float* e = Ec + (long long)j * N;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x,
                   stride = (long long)gridDim.x * blockDim.x;
+  const float kp = scal ? scal[4 * j + 3] : -1.f;
+  const bool pend = kp >= 0.f;
+  const int k = pend ? (int)kp : 1;
+  const float al = pend ? scal[4 * j + 2] : 0.f;
+  const float* pk = ((k & 1) ? P2 : P) + (long long)j * N;
   if ((N & 3) == 0) {
     // four pixels per step: one float4 of e, two double2 of x (planes 32-byte aligned)
     for (long long q = t0; q < N / 4; q += stride) {
-      const float4 ev = reinterpret_cast<const float4*>(e)[q];
+      float4 ev = k > 0 ? reinterpret_cast<const float4*>(e)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (pend) {
+        const float4 pv = reinterpret_cast<const float4*>(pk)[q];
+        ev.x = fmaf(al, pv.x, ev.x);
+        ev.y = fmaf(al, pv.y, ev.y);
+        ev.z = fmaf(al, pv.z, ev.z);
+        ev.w = fmaf(al, pv.w, ev.w);
+      }
       double2* x2 = reinterpret_cast<double2*>(x) + 2 * q;
       double2 a = x2[0], b = x2[1];
       a.x += (double)ev.x;
@@ -1489,7 +1542,8 @@ __global__ void commit_kernel(double* X, const float* Ec, const int* act0, long 
     }
     return;
   }
-  for (long long p = t0; p < N; p += stride) x[p] += (double)e[p];
+  for (long long p = t0; p < N; p += stride)
+    x[p] += (double)(pend ? fmaf(al, pk[p], k > 0 ? e[p] : 0.f) : e[p]);
 }
 
 
@@ -2000,7 +2054,11 @@ __global__ void __launch_bounds__(32 * kF512Warps) fft512_rows_fwd_kernel(FftDes
 // transform as zero (its z is not used before the next pass recomputes it).  The last
 // block of the pair sums its r.r partials in block order and sets the active flags,
 // as update_kernel's last block does, so the column and inverse passes that follow
-// skip the pairs that stopped here.
+// skip the pairs that stopped here.  With a.defer_e (the paired direction kernel) only
+// r is updated here: alpha and the iteration go to the CG scalars, and e += alpha p is
+// done by the next direction kernel over its tile, where p is the direction it reads
+// anyway, or by the commit after a system's last iteration; the same operation on the
+// same values, so the results do not change.
 __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_kernel(FftDesc f,
                                                                                 CgArgs a,
                                                                                 int it_arg,
@@ -2035,6 +2093,48 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
   for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
     const long long p0 = (long long)row * f.W;
     float2 v[16];
+    if (a.defer_e) {
+      // r only, both systems' loads in flight together: e += alpha p is left to the
+      // next direction kernel or the commit
+      const float* Q0 = a.Qp + (long long)j0 * N + p0;
+      const float* Q1 = a.Qp + (long long)j1 * N + p0;
+      float* R0 = a.Rr + (long long)j0 * N + p0;
+      float* R1 = a.Rr + (long long)j1 * N + p0;
+      float qa[16], ra[16], qb[16], rb[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int c = 32 * m + l;
+        qa[m] = ra[m] = qb[m] = rb[m] = 0.f;
+        if (c < f.W) {
+          if (act0) {
+            qa[m] = Q0[c];
+            ra[m] = R0[c];
+          }
+          if (act1) {
+            qb[m] = Q1[c];
+            rb[m] = R1[c];
+          }
+        }
+      }
+      const float al0 = alpha_s[0], al1 = alpha_s[1];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int c = 32 * m + l;
+        v[m] = make_float2(0.f, 0.f);
+        if (c < f.W) {
+          if (act0) {
+            v[m].x = fmaf(-al0, qa[m], ra[m]);
+            st_hint_f(R0 + c, v[m].x, keep);
+            rr0 = fmaf(v[m].x, v[m].x, rr0);
+          }
+          if (act1) {
+            v[m].y = fmaf(-al1, qb[m], rb[m]);
+            st_hint_f(R1 + c, v[m].y, keep);
+            rr1 = fmaf(v[m].y, v[m].y, rr1);
+          }
+        }
+      }
+    } else {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (!(u ? act1 : act0)) {
@@ -2047,6 +2147,7 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
       const float* Q = a.Qp + o;
       float* Ec = a.Ec + o;
       float* Rr = a.Rr + o;
+      const float alpha = alpha_s[u];
       float pv[16], qv[16], rv[16], ev[16];
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
@@ -2059,7 +2160,6 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
           if (!first) ev[m] = Ec[c];
         }
       }
-      const float alpha = alpha_s[u];
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int c = 32 * m + l;
@@ -2072,6 +2172,7 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
         }
         (u ? v[m].y : v[m].x) = r;
       }
+    }
     }
     fft512_warp(v, scratch[w], tw);
 #pragma unroll
@@ -2086,7 +2187,13 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_update_rows_fwd_ker
       const int j = j0 + u;
       const double r2 = group_sum(a.part_rr + (long long)j * a.nb, gridDim.x);
       // the stopping rule of update_kernel
-      if (threadIdx.x == 0) a.scal[4 * j] = (r2 <= a.thr[j] || r2 > 16.0 * a.rr0[j]) ? 0.f : 1.f;
+      if (threadIdx.x == 0) {
+        a.scal[4 * j] = (r2 <= a.thr[j] || r2 > 16.0 * a.rr0[j]) ? 0.f : 1.f;
+        if (a.defer_e) {
+          a.scal[4 * j + 2] = alpha_s[u];
+          a.scal[4 * j + 3] = (float)it;
+        }
+      }
     }
   }
 }
@@ -2526,7 +2633,8 @@ struct LikelihoodState {
   size_t smem = 0;
   size_t smem_res = 0;
   int last_iters = 0;
-  float* d_scal = nullptr;      // [R][4] CG scalars: active flag, beta
+  float* d_scal = nullptr;      // [R][4] CG scalars: active flag, beta, alpha and iteration of
+                                // a deferred correction update
   double* d_rzs = nullptr;      // [R] r.z of the current iteration
   unsigned* d_arrive = nullptr; // [R + pairs] block-arrival counters (start and stay zero)
   int* d_act0 = nullptr;        // [R] systems that iterate in the current pass
@@ -2587,6 +2695,7 @@ CgArgs cg_args(LikelihoodState* L) {
   a.nbz = L->nbz;
   a.fft = L->fft ? 1 : 0;
   a.counters = nullptr;
+  a.defer_e = 0;
   return a;
 }
 
@@ -3178,6 +3287,7 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
   CgArgs a = cg_args(L);
   a.counters = counters;
   a.it_dev = &L->d_loop->it;
+  a.defer_e = fused_update(L) && pair_direction(L);
   const dim3 grid(c.tiles_x, c.tiles_y, L->R);
   const int groups = (L->S + kRbGroup - 1) / kRbGroup;
   cudaGraph_t G = nullptr;
@@ -3243,8 +3353,8 @@ bool build_update_graph(LikelihoodState* L, float* tau, float* nu, const float* 
   ok = ok && capture(b_pass, [&]() {
     if (L->fft) precond_apply(L, a.part_rz, true, 1, counters, s);
     if (!add_cond(h_inner, cudaGraphCondTypeWhile, &b_inner)) return false;
-    commit_kernel<<<dim3(std::min(grid1d((N + 3) / 4), 1024), L->R), 256, 0, s>>>(L->X, L->Ec,
-                                                                              L->d_act0, N);
+    commit_kernel<<<dim3(std::min(grid1d((N + 3) / 4), 1024), L->R), 256, 0, s>>>(
+        L->X, L->Ec, L->d_act0, N, a.defer_e ? L->d_scal : nullptr, L->P, L->P2);
     return true;
   });
   // with the FFT preconditioner the column pass, which every iteration launches,
@@ -3308,6 +3418,7 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
   mean_kernel<<<1, 1024, 0, s>>>(L->dpart, L->prep_blocks, 1.0 / (double)N, L->dbar);
   CgArgs a = cg_args(L);
   a.counters = counters;
+  a.defer_e = fused_update(L) && pair_direction(L);
   dim3 grid(c.tiles_x, c.tiles_y, L->R);
   // Iterative refinement (see kEta2): true residual (float-float), then FP32
   // preconditioned CG on the correction, repeated until ||r|| <= rtol ||b||.
@@ -3401,8 +3512,8 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
     // solutions of the systems that iterated, then count the iterations up to the
     // poll that found all systems stopped
     tr->begin(EP_TV_K_CG_COMMIT, s);
-    commit_kernel<<<dim3(std::min(grid1d((N + 3) / 4), 1024), L->R), 256, 0, s>>>(L->X, L->Ec,
-                                                                              L->d_act0, N);
+    commit_kernel<<<dim3(std::min(grid1d((N + 3) / 4), 1024), L->R), 256, 0, s>>>(
+        L->X, L->Ec, L->d_act0, N, a.defer_e ? L->d_scal : nullptr, L->P, L->P2);
     tr->end(s, (double)started * N);
     total += launched;
   }
