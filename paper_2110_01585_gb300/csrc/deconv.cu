@@ -1216,6 +1216,13 @@ __global__ void __launch_bounds__(kThreads, HR >= 14 ? 3 : 5) direction_pair_ker
   const long long N = c.N;
   const long long o0 = (long long)j0 * N, o1 = (long long)j1 * N;
   const float* Pold = (it & 1) ? a.P : a.P2;
+  if (a.defer_e && it > 1 && threadIdx.x < 64) {
+    // the tile's rows of e, read by the pending correction update at the end: fetched
+    // into L2 now, while the region is staged and the stencil runs
+    const int u = threadIdx.x >> 5, gr = r0 + (threadIdx.x & 31);
+    if ((u ? act1 : act0) && gr < c.H)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Ec + (u ? o1 : o0) + (long long)gr * c.W + c0));
+  }
   __syncthreads();
   // Region staging, all of a thread's loads issued before the first is used
   if ((c.W & 3) == 0 && (HR & 3) == 0 && c0 >= HR && c0 + kTile + HR <= c.W) {
