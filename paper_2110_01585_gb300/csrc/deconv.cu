@@ -3544,9 +3544,14 @@ ep_tv_status likelihood_update(LikelihoodState* L, float* tau, float* nu, const 
 double likelihood_bytes_per_unit(const LikelihoodState* L, int kernel) {
   if (L->cs) return kernel == EP_TV_K_CS ? cs_flops(L->cs) : kernel == EP_TV_K_CS_MMA ? 1.0 : 0.0;
   const double groups = (double)((L->S + kRbGroup - 1) / kRbGroup);
+  // with deferred correction updates the direction kernel also does e += alpha p
+  // (read and write e; p is the direction it reads anyway) and the update only r
+  const bool defer = fused_update(L) && pair_direction(L);
   switch (kernel) {
-    case EP_TV_K_CG_DIRECTION: return 16.0;  // read z, p; write p, Q p (per active system pixel)
-    case EP_TV_K_CG_UPDATE: return 24.0;     // read e, r, p, Q p; write e, r (FP32 correction)
+    case EP_TV_K_CG_DIRECTION:               // read z, p; write p, Q p (per active system
+      return defer ? 24.0 : 16.0;            // pixel); deferred: also read and write e
+    case EP_TV_K_CG_UPDATE:                  // read e, r, p, Q p; write e, r (FP32
+      return defer ? 12.0 : 24.0;            // correction); deferred: read r, Q p, write r
     case EP_TV_K_CG_RESIDUAL: return 24.0;   // read x (FP64), y', the probe planes; write r
     case EP_TV_K_CG_PRECOND: return 8.0;     // r in, z out (per transformed system pixel)
     case EP_TV_K_CG_COMMIT: return 20.0;     // read x (FP64) and e, write x (per committed
