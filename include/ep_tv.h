@@ -282,11 +282,17 @@ ep_tv_status ep_tv_solve_host(const ep_tv_operator* op, const float* y_host,
 /* Kernel classes reported by the tracer. */
 typedef enum {
   EP_TV_K_PRIOR_SWEEP = 0,   /* fused V_1..V_4 prior-site pass, unit = pixel */
-  EP_TV_K_CG_DIRECTION = 1,  /* CG direction + H^T H stencil, unit = pixel of one active system */
-  EP_TV_K_CG_UPDATE = 2,     /* CG correction / residual update, unit = pixel of one active system */
-  EP_TV_K_CG_RESIDUAL = 3,   /* initial CG residual, unit = pixel of one system */
+  EP_TV_K_CG_DIRECTION = 1,  /* CG direction + H^T H stencil (with 512-point FFT rows and a
+                                separable blur also the previous iteration's correction
+                                update), unit = pixel of one active system */
+  EP_TV_K_CG_UPDATE = 2,     /* CG correction / residual update (with 512-point FFT rows: the
+                                residual update fused with the preconditioner's forward row
+                                pass), unit = pixel of one active system */
+  EP_TV_K_CG_RESIDUAL = 3,   /* true CG residual of a refinement pass, unit = pixel of one
+                                system */
   EP_TV_K_SITE0 = 4,         /* likelihood-site update, unit = pixel */
-  EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels), unit = pixel of one
+  EP_TV_K_CG_PRECOND = 5,    /* FFT circulant preconditioner (3 kernels; 2 in CG iterations whose
+                                forward row pass runs with the update), unit = pixel of one
                                 transformed system (pairs of stopped systems are skipped) */
   EP_TV_K_CS = 6,            /* compressive-sensing likelihood site (Woodbury, FP64-accurate)
                                 except its tensor-core products, unit = pixel; its per-unit
