@@ -1583,6 +1583,7 @@ struct FftDesc {
   const float* hth;  // |h_f|^2 / xi on the HP x WP grid
   const double* dbar;
   const float2* tw512;  // exp(-2 pi i m / 512), m < 512 (the 512-point kernels)
+  const float2* tw1024; // exp(-2 pi i m / 1024), m < 512 (the 1024-point kernels)
   const float* act;  // CG scalars of the current iteration ([4 R], [4 j] = 1 if system j
                      // is active), or NULL: transform every system
   float* scal_w;     // the same array, written: beta of the active systems
@@ -1918,11 +1919,15 @@ constexpr int kF512Warps = 8;   // warps per block of the 512-point kernels
 // transform measured slower: it raises register pressure at the 128-register limit).
 constexpr int kRowsPerWarp512 = 4;
 
+// tw[m] = w512^m and tw[512 + m] = w1024^m for m < 512
 __global__ void tw512_kernel(float2* tw) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < kF) {
+  if (m < 2 * kF) {
     float sn, cs;
-    sincospif(-2.0f * (float)m / (float)kF, &sn, &cs);
+    if (m < kF)
+      sincospif(-2.0f * (float)m / (float)kF, &sn, &cs);
+    else
+      sincospif(-2.0f * (float)(m - kF) / (float)(2 * kF), &sn, &cs);
     tw[m] = make_float2(cs, sn);
   }
 }
@@ -1953,6 +1958,11 @@ __device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
   asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
   return v;
 }
+__device__ __forceinline__ void st_hint4(float2* a, float2 u, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(u.x),
+               "f"(u.y), "f"(v.x), "f"(v.y), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void st_hint_f(float* a, float v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
 }
@@ -1964,6 +1974,9 @@ __device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
 // Which passes take the 512-point kernels (the others take the Stockham ones).
 inline bool fft512_rows(const FftDesc& f) { return f.WP == kF; }
 inline bool fft512_cols(const FftDesc& f) { return f.HP == kF && f.WP >= kF512Warps; }
+// and the 1024-point ones (below)
+inline bool fft1024_rows(const FftDesc& f) { return f.WP == 2 * kF; }
+inline bool fft1024_cols(const FftDesc& f) { return f.HP == 2 * kF && f.WP >= kF512Warps; }
 
 __device__ __forceinline__ void fft512_warp(float2 (&v)[16], float2* xs, const float2* tw) {
   const int l = threadIdx.x & 31;
@@ -2332,8 +2345,233 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft512_rows_inv_kernel(Fft
   rz_tail(f, pair, part_rz);
 }
 
+// ---- register-resident 1024-point transforms
+//
+// A 1024-point transform held by one warp as lo[q] = x[32 q + l], hi[q] = x[512 + 32 q + l]
+// (q < 16) takes one decimation-in-frequency step into two 512-point transforms:
+//   a[n] = x[n] + x[n + 512],  b[n] = (x[n] - x[n + 512]) w1024^n   (n < 512),
+//   X[2 k] = A[k],  X[2 k + 1] = B[k]   (A, B the 512-point transforms of a and b),
+// which keeps the 512-point kernels' layout: afterwards lo[m] = X[64 m + 2 l] and
+// hi[m] = X[64 m + 2 l + 1] in lane l, one float4 of the transform in natural order.
+constexpr int kRowsPerWarp1024 = 2;
+constexpr int kXs2 = 2 * kF + 66;  // staged-column pitch of the 1024-point column pass
+
+__device__ __forceinline__ void fft1024_warp(float2 (&lo)[16], float2 (&hi)[16], float2* xs,
+                                             const float2* tw, const float2* tw2) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float2 x0 = lo[q], x1 = hi[q];
+    lo[q] = cadd(x0, x1);
+    hi[q] = cmul(csub(x0, x1), tw2[32 * q + l]);
+  }
+  fft512_warp(lo, xs, tw);
+  fft512_warp(hi, xs, tw);
+}
+
+// fft_rows_fwd_kernel for WP = 1024: one warp per row, rows [blockIdx.x rpb, +rpb).
+__global__ void __launch_bounds__(32 * kF512Warps, 2) fft1024_rows_fwd_kernel(FftDesc f,
+                                                                          const float* __restrict__ Rr,
+                                                                          int rpb) {
+  if (pair_idle(f, blockIdx.y)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.counters)
+    atomicAdd(&f.counters[DC_CG_PRE_UNITS], 2 * blockIdx.y + 1 < f.R ? 2ull : 1ull);
+  __shared__ float2 tw[kF], tw2[kF];
+  __shared__ float2 scratch[kF512Warps][kXs];
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) {
+    tw[m] = f.tw512[m];
+    tw2[m] = f.tw1024[m];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const bool two = j1 < f.R;
+  const long long N = (long long)f.H * f.W;
+  const float* r0p = Rr + (long long)j0 * N;
+  const float* r1p = Rr + (long long)j1 * N;
+  float2* out = f.tmp + (long long)pair * f.H * (2 * kF);
+  const int rend = min(f.H, (blockIdx.x + 1) * rpb);
+  const uint64_t keep = l2_policy_keep();
+  for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
+    const long long p0 = (long long)row * f.W;
+    float2 lo[16], hi[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int c = 32 * q + l, c2 = c + kF;
+      lo[q] = hi[q] = make_float2(0.f, 0.f);
+      if (c < f.W) lo[q] = make_float2(ld_hint(r0p + p0 + c, keep), two ? ld_hint(r1p + p0 + c, keep) : 0.f);
+      if (c2 < f.W) hi[q] = make_float2(ld_hint(r0p + p0 + c2, keep), two ? ld_hint(r1p + p0 + c2, keep) : 0.f);
+    }
+    fft1024_warp(lo, hi, scratch[w], tw, tw2);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) st_hint4(out + (long long)row * (2 * kF) + 64 * m + 2 * l, lo[m], hi[m], keep);
+  }
+}
+
+// fft_cols_filter_kernel for HP = 1024: the block stages columns c0 .. c0 + 7 of a pair
+// (rows at and beyond H are zero); each warp transforms one column, filters it with
+// hthT (column-major, [c][i]), writes it back to its slot in natural order and
+// transforms it again (the inverse as conj(F(conj(.)))); the block then stores rows
+// below H.  Shared memory: kF512Warps x kXs2 float2, dynamic.
+__global__ void __launch_bounds__(32 * kF512Warps, 2) fft1024_cols_filter_kernel(FftDesc f,
+                                                                             const float* __restrict__ hthT) {
+  loop_step(f);
+  if (pair_idle(f, blockIdx.y)) return;
+  __shared__ float2 tw[kF], tw2[kF];
+  extern __shared__ float4 colsm4[];
+  float2* cols = reinterpret_cast<float2*>(colsm4);
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) {
+    tw[m] = f.tw512[m];
+    tw2[m] = f.tw1024[m];
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int c0 = blockIdx.x * kF512Warps;
+  float2* t = f.tmp + (long long)blockIdx.y * f.H * f.WP;
+  const int cc = threadIdx.x & 7, ro = threadIdx.x >> 3;  // 32 rows x 8 columns per block step
+  const uint64_t keep = l2_policy_keep();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float2 x[16];  // half of the thread's tile loads in flight at once
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = 32 * (16 * h + u) + ro;
+      x[u] = i < f.H ? ld_hint(t + (long long)i * f.WP + c0 + cc, keep) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) cols[cc * kXs2 + 32 * (16 * h + u) + ro] = x[u];
+  }
+  __syncthreads();
+  float2* xs = cols + w * kXs2;
+  float2 lo[16], hi[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    lo[q] = xs[32 * q + l];
+    hi[q] = xs[kF + 32 * q + l];
+  }
+  __syncwarp();
+  fft1024_warp(lo, hi, xs, tw, tw2);
+  // filter (frequencies 64 m + 2 l and 64 m + 2 l + 1 of this lane), conjugated for the
+  // inverse, and back to natural order in the slot
+  const float* g = hthT + (long long)(c0 + w) * (2 * kF);
+  const float dbar = (float)(*f.dbar);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const float2 gv = *reinterpret_cast<const float2*>(g + 64 * m + 2 * l);
+    const float g0 = __frcp_rn(gv.x + dbar), g1 = __frcp_rn(gv.y + dbar);
+    lo[m] = make_float2(lo[m].x * g0, -lo[m].y * g0);
+    hi[m] = make_float2(hi[m].x * g1, -hi[m].y * g1);
+  }
+#pragma unroll
+  for (int m = 0; m < 16; ++m)
+    *reinterpret_cast<float4*>(xs + 64 * m + 2 * l) = make_float4(lo[m].x, lo[m].y, hi[m].x, hi[m].y);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    lo[q] = xs[32 * q + l];
+    hi[q] = xs[kF + 32 * q + l];
+  }
+  __syncwarp();
+  fft1024_warp(lo, hi, xs, tw, tw2);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const float2 a = cconj(lo[m]), b = cconj(hi[m]);
+    *reinterpret_cast<float4*>(xs + 64 * m + 2 * l) = make_float4(a.x, a.y, b.x, b.y);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int i = 32 * u + ro;
+    if (i < f.H) st_hint(t + (long long)i * f.WP + c0 + cc, cols[cc * kXs2 + i], keep);
+  }
+}
+
+// fft_rows_inv_kernel for WP = 1024: one warp per row of the block's range
+// [blockIdx.x rows_per, +rows_per), rows_per = ceil(H / nbz).
+__global__ void __launch_bounds__(32 * kF512Warps, 2) fft1024_rows_inv_kernel(FftDesc f,
+                                                                          const float* __restrict__ Rr,
+                                                                          float* Z, double* part_rz) {
+  if (pair_idle(f, blockIdx.y)) return;
+  __shared__ float2 tw[kF], tw2[kF];
+  __shared__ float2 scratch[kF512Warps][kXs];
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) {
+    tw[m] = f.tw512[m];
+    tw2[m] = f.tw1024[m];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const bool two = j1 < f.R;
+  const long long N = (long long)f.H * f.W;
+  const float scale = 1.0f / ((float)f.HP * (float)(2 * kF));
+  const int rows_per = (f.H + f.nbz - 1) / f.nbz;
+  const int rend = min(f.H, (blockIdx.x + 1) * rows_per);
+  const float2* tin = f.tmp + (long long)pair * f.H * (2 * kF);
+  const uint64_t release = l2_policy_release();
+  const float* r0p = Rr + (long long)j0 * N;
+  const float* r1p = Rr + (long long)j1 * N;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int row = blockIdx.x * rows_per + w; row < rend; row += kF512Warps) {
+    const long long p0 = (long long)row * f.W;
+    const float2* trow = tin + (long long)row * (2 * kF);
+    float2 lo[16], hi[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      lo[q] = cconj(ld_hint(trow + 32 * q + l, release));
+      hi[q] = cconj(ld_hint(trow + kF + 32 * q + l, release));
+    }
+    fft1024_warp(lo, hi, scratch[w], tw, tw2);
+    // lo[m], hi[m]: columns 64 m + 2 l and 64 m + 2 l + 1; the residuals there are read
+    // in two halves of eight m each
+    float rz0 = 0.f, rz1 = 0.f;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      float ra[8][2], rb[8][2];
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = 64 * (8 * hf + mm) + 2 * l + e;
+          ra[mm][e] = rb[mm][e] = 0.f;
+          if (c < f.W) {
+            ra[mm][e] = ld_hint(r0p + p0 + c, release);
+            if (two) rb[mm][e] = ld_hint(r1p + p0 + c, release);
+          }
+        }
+      }
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm) {
+        const int m = 8 * hf + mm;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int c = 64 * m + 2 * l + e;
+          if (c < f.W) {
+            const float2 v = e ? hi[m] : lo[m];
+            const long long p = p0 + c;
+            const float z0 = v.x * scale;
+            Z[(long long)j0 * N + p] = z0;
+            rz0 = fmaf(ra[mm][e], z0, rz0);
+            if (two) {
+              const float z1 = -v.y * scale;
+              Z[(long long)j1 * N + p] = z1;
+              rz1 = fmaf(rb[mm][e], z1, rz1);
+            }
+          }
+        }
+      }
+    }
+    acc0 += (double)rz0;
+    acc1 += (double)rz1;
+  }
+  block_sum3(acc0, acc1, 0.0, part_rz + (long long)j0 * f.nbz + blockIdx.x,
+             two ? part_rz + (long long)j1 * f.nbz + blockIdx.x : nullptr, nullptr);
+  rz_tail(f, pair, part_rz);
+}
+
 // |h_f|^2 / xi on the H x W frequency grid (phases reduced exactly in integers).
-// transposed: out[fc * H + fr] (column-major, the layout of the 512-point column pass).
+// transposed: out[fc * H + fr] (column-major, the layout of the 512- and 1024-point
+// column passes).
 __global__ void hth_kernel(float* out, int H, int W, const float* k, int kh, int kw, float inv_xi,
                            int transposed) {
   const long long N = (long long)H * W;
@@ -2628,7 +2866,7 @@ struct LikelihoodState {
   float2* ftmp = nullptr;
   float* Z = nullptr;
   float* hth = nullptr;
-  float2* tw512 = nullptr;
+  float2* tw512 = nullptr;      // w512^m, then w1024^m (m < 512)
   double* dpart = nullptr;
   double* dbar = nullptr;
   int prep_blocks = 0;
@@ -2736,6 +2974,7 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
   f.first = first;
   f.counters = counters;
   constexpr int kRows512 = kF512Warps * kRowsPerWarp512;
+  constexpr int kRows1024 = kF512Warps * kRowsPerWarp1024;
   if (stages & 1) {
     if (upd)
       fft512_update_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs),
@@ -2743,6 +2982,9 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
     else if (fft512_rows(f))
       fft512_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs), 32 * kF512Warps, 0,
                                s>>>(f, L->Rr, kRows512);
+    else if (fft1024_rows(f))
+      fft1024_rows_fwd_kernel<<<dim3((f.H + kRows1024 - 1) / kRows1024, f.pairs), 32 * kF512Warps,
+                                0, s>>>(f, L->Rr, kRows1024);
     else
       fft_rows_fwd_kernel<<<dim3((f.H + f.rpb - 1) / f.rpb, f.pairs), kFftThreads, L->smem_rows,
                             s>>>(f, L->Rr);
@@ -2750,10 +2992,15 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
   if (!(stages & 2)) return;
   if (fft512_cols(f))
     fft512_cols_filter_kernel<<<dim3(f.WP / kF512Warps, f.pairs), 32 * kF512Warps, 0, s>>>(f, f.hth);
+  else if (fft1024_cols(f))
+    fft1024_cols_filter_kernel<<<dim3(f.WP / kF512Warps, f.pairs), 32 * kF512Warps,
+                                 sizeof(float2) * kF512Warps * kXs2, s>>>(f, f.hth);
   else
     fft_cols_filter_kernel<<<dim3(f.WP / f.cw, f.pairs), kFftThreads, L->smem_cols, s>>>(f);
   if (fft512_rows(f))
     fft512_rows_inv_kernel<<<dim3(f.nbz, f.pairs), 32 * kF512Warps, 0, s>>>(f, L->Rr, L->Z, rz_buf);
+  else if (fft1024_rows(f))
+    fft1024_rows_inv_kernel<<<dim3(f.nbz, f.pairs), 32 * kF512Warps, 0, s>>>(f, L->Rr, L->Z, rz_buf);
   else
     fft_rows_inv_kernel<<<dim3(f.nbz, f.pairs), kFftThreads, L->smem_rows, s>>>(f, L->Rr, L->Z,
                                                                                 rz_buf);
@@ -2831,7 +3078,8 @@ void tune_fft_shape(LikelihoodState* L, cudaStream_t s) {
   const char* env = getenv("EPTV_FFT_TUNE");
   if (env && env[0] == '0') return;
   FftDesc& f = L->fd;
-  if (fft512_rows(f) && fft512_cols(f)) return;  // the tuned shapes are not used
+  if ((fft512_rows(f) || fft1024_rows(f)) && (fft512_cols(f) || fft1024_cols(f)))
+    return;  // the tuned shapes are not used
   int dev = 0;
   cudaGetDevice(&dev);
   const std::array<int, 5> key{dev, f.HP, f.WP, f.H, f.R};
@@ -2922,7 +3170,7 @@ bool raise_smem_limits() {
   const void* fns[] = {(const void*)direction_kernel, (const void*)residual_kernel,
                        (const void*)residual_pair_kernel<9>,
                        (const void*)fft_rows_fwd_kernel, (const void*)fft_rows_inv_kernel,
-                       (const void*)fft_cols_filter_kernel};
+                       (const void*)fft_cols_filter_kernel, (const void*)fft1024_cols_filter_kernel};
   for (const void* f : fns) {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return false;
@@ -3054,7 +3302,10 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     // r.z partials: one per block of the inverse row pass (kF512Warps * kRowsPerWarp512
     // rows each for 512-point rows)
     constexpr int kRowsInv512 = kF512Warps * kRowsPerWarp512;
-    f.nbz = WP == kF ? (c.H + kRowsInv512 - 1) / kRowsInv512 : std::min(c.H, 64);
+    constexpr int kRowsInv1024 = kF512Warps * kRowsPerWarp1024;
+    f.nbz = WP == kF       ? (c.H + kRowsInv512 - 1) / kRowsInv512
+            : WP == 2 * kF ? (c.H + kRowsInv1024 - 1) / kRowsInv1024
+                           : std::min(c.H, 64);
     L->nbz = f.nbz;
     L->smem_rows = sizeof(float2) * ((size_t)WP + (size_t)f.rpb * WP);
     L->smem_cols = sizeof(float2) * ((size_t)HP + (size_t)HP * f.cw);
@@ -3099,7 +3350,7 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
              (cudaMalloc(&L->ftmp, sizeof(float2) * ((L->R + 1) / 2) * c.H * L->fd.WP) == cudaSuccess &&
               cudaMalloc(&L->Z, sizeof(float) * RN) == cudaSuccess &&
               cudaMalloc(&L->hth, sizeof(float) * L->fd.HP * L->fd.WP) == cudaSuccess &&
-              cudaMalloc(&L->tw512, sizeof(float2) * kF) == cudaSuccess)) &&
+              cudaMalloc(&L->tw512, sizeof(float2) * 2 * kF) == cudaSuccess)) &&
             cudaMalloc(&L->d_active, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&L->d_relres, sizeof(double) * L->R) == cudaSuccess &&
             cudaMalloc(&L->d_prev_rr, sizeof(double) * L->R) == cudaSuccess &&
@@ -3177,10 +3428,12 @@ ep_tv_status likelihood_create(const LikelihoodConfig& cfg, cudaStream_t s, Like
     L->fd.tmp = L->ftmp;
     L->fd.hth = L->hth;
     L->fd.tw512 = L->tw512;
-    tw512_kernel<<<(kF + 255) / 256, 256, 0, s>>>(L->tw512);
+    L->fd.tw1024 = L->tw512 + kF;
+    tw512_kernel<<<(2 * kF + 255) / 256, 256, 0, s>>>(L->tw512);
     L->fd.dbar = L->dbar;
     hth_kernel<<<grid1d((long long)L->fd.HP * L->fd.WP), 256, 0, s>>>(
-        L->hth, L->fd.HP, L->fd.WP, L->d_k, kh, kw, L->inv_xi, fft512_cols(L->fd) ? 1 : 0);
+        L->hth, L->fd.HP, L->fd.WP, L->d_k, kh, kw, L->inv_xi,
+        (fft512_cols(L->fd) || fft1024_cols(L->fd)) ? 1 : 0);
   }
   // H^T y / xi
   conv_t_kernel<<<dim3(grid1d(N), 1), 256, 0, s>>>(cfg.y, L->Hty, c.H, c.W, L->d_k, kh, kw,

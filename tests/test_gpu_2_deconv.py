@@ -66,6 +66,24 @@ def test_deconv_parity_512_point_transforms(h, w):
     ep.close()
 
 
+@pytest.mark.parametrize("h,w", [(24, 520), (520, 24)])
+def test_deconv_parity_1024_point_transforms(h, w):
+    """Padded sizes whose preconditioner rows (24 x 520, padded to 32 x 1024) or
+    columns (520 x 24, padded to 1024 x 32) go through the register-resident
+    1024-point transforms (one decimation-in-frequency step into two 512-point
+    ones); the oracle does every solve by FP64 CG on the FFT operator."""
+    p = syn.deconv_problem(h, w, kernel=syn.uniform_kernel(5), bsnr_db=30.0, beta0=2.0, seed=31,
+                           grf_length=8.0)
+    S = 4
+    pr = probes(p, S, 32)
+    mu, var, ep = _gpu(p, 3, S, pr)
+    o = EPOracle("deconv", y32(p), p.xi, p.beta, h, w, kernel=p.kernel, site0="rbmc_cg", probes=pr)
+    o.run(3)
+    mu_r, var_r = o.posterior()
+    assert_parity(mu, var, mu_r, var_r, p.y)
+    ep.close()
+
+
 def test_unit_kernel_equals_denoising_path():
     """H = I through the CG/RBMC route: diagonal precision, exact RB estimate."""
     torch = cuda()
