@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(CgArgs a) {
 // (hi, lo); y' - H x is written over the latter's hi half once every thread has read
 // it, and the H^T row pass over its lo half.
 template <int K>
-__global__ void __launch_bounds__(kThreads, 3) residual_pair_kernel(CgArgs a) {
+__global__ void __launch_bounds__(kThreads, K >= 15 ? 2 : 3) residual_pair_kernel(CgArgs a) {
   constexpr int HR = K - 1, hh = K / 2;
   constexpr int RH = kTile + 2 * HR, RW = RH;  // x region
   constexpr int MH = kTile + 2 * hh, MW = MH;  // y' - H x region
@@ -3006,15 +3006,25 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
                                                                                 rz_buf);
 }
 
-// The true residual of every system: two systems per block for a 9 x 9 separable blur
-// (residual_pair_kernel), else one (residual_kernel).
+// The true residual of every system: two systems per block for a separable K x K blur,
+// K = 5, 9 or 15 (residual_pair_kernel), else one (residual_kernel).
+template <int K>
+void launch_residual_pair(const LikelihoodState* L, const CgArgs& a, cudaStream_t s) {
+  constexpr int RH = kTile + 2 * (K - 1), MW = kTile + 2 * (K / 2);
+  const size_t sm = sizeof(float2) * 2 * ((size_t)RH * RH + (size_t)RH * MW);
+  const ConvDesc& c = L->c;
+  residual_pair_kernel<K><<<dim3(c.tiles_x, c.tiles_y, (L->R + 1) / 2), kThreads, sm, s>>>(a);
+}
+
 void launch_residual(const LikelihoodState* L, const CgArgs& a, cudaStream_t s) {
   const ConvDesc& c = L->c;
-  if (c.separable && c.kh == 9 && c.kw == 9) {
-    constexpr int K = 9, RH = kTile + 2 * (K - 1), MW = kTile + 2 * (K / 2);
-    const size_t sm = sizeof(float2) * 2 * ((size_t)RH * RH + (size_t)RH * MW);
-    residual_pair_kernel<K><<<dim3(c.tiles_x, c.tiles_y, (L->R + 1) / 2), kThreads, sm, s>>>(a);
-    return;
+  if (c.separable && c.kh == c.kw) {
+    switch (c.kh) {
+      case 5: launch_residual_pair<5>(L, a, s); return;
+      case 9: launch_residual_pair<9>(L, a, s); return;
+      case 15: launch_residual_pair<15>(L, a, s); return;
+      default: break;
+    }
   }
   residual_kernel<<<dim3(c.tiles_x, c.tiles_y, L->R), kThreads, L->smem_res, s>>>(a);
 }
@@ -3168,7 +3178,8 @@ bool raise_smem_limits() {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
   const void* fns[] = {(const void*)direction_kernel, (const void*)residual_kernel,
-                       (const void*)residual_pair_kernel<9>,
+                       (const void*)residual_pair_kernel<5>, (const void*)residual_pair_kernel<9>,
+                       (const void*)residual_pair_kernel<15>,
                        (const void*)fft_rows_fwd_kernel, (const void*)fft_rows_inv_kernel,
                        (const void*)fft_cols_filter_kernel, (const void*)fft1024_cols_filter_kernel};
   for (const void* f : fns) {
