@@ -2409,6 +2409,114 @@ __global__ void __launch_bounds__(32 * kF512Warps, 2) fft1024_rows_fwd_kernel(Ff
   }
 }
 
+// fft512_update_rows_fwd_kernel for WP = 1024, deferred correction updates only
+// (a.defer_e): r -= alpha q per active system of the pair, the new residual rows
+// transformed without a re-read; the pair's last block sets the active flags, alpha
+// and the iteration.  A row's loads go in four batches of eight columns per lane.
+__global__ void __launch_bounds__(32 * kF512Warps, 2) fft1024_update_rows_fwd_kernel(FftDesc f,
+                                                                                 CgArgs a,
+                                                                                 int it_arg,
+                                                                                 int rpb) {
+  const int pair = blockIdx.y;
+  const int j0 = 2 * pair, j1 = 2 * pair + 1;
+  const bool two = j1 < f.R;
+  const bool act0 = a.scal[4 * j0] != 0.f, act1 = two && a.scal[4 * j1] != 0.f;
+  if (!act0 && !act1) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.counters) {
+    atomicAdd(&f.counters[DC_CG_PRE_UNITS], two ? 2ull : 1ull);
+    atomicAdd(&f.counters[DC_CG_UPD_UNITS], (unsigned long long)(act0 + act1));
+  }
+  const int it = a.it_dev ? *a.it_dev : it_arg;
+  __shared__ float2 tw[kF], tw2[kF];
+  __shared__ float2 scratch[kF512Warps][kXs];
+  __shared__ float alpha_s[2];
+  for (int m = threadIdx.x; m < kF; m += blockDim.x) {
+    tw[m] = f.tw512[m];
+    tw2[m] = f.tw1024[m];
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (w < 2 && (w == 0 ? act0 : act1)) {
+    const int j = j0 + w;
+    const double pqs = group_sum(a.part_pq + (long long)j * a.nb, a.nb);
+    if (l == 0) alpha_s[w] = (float)(a.rzs[j] / pqs);
+  }
+  __syncthreads();
+  const long long N = (long long)f.H * f.W;
+  float2* out = f.tmp + (long long)pair * f.H * (2 * kF);
+  const int rend = min(f.H, (blockIdx.x + 1) * rpb);
+  const uint64_t keep = l2_policy_keep();
+  const float al0 = alpha_s[0], al1 = alpha_s[1];
+  float rr0 = 0.f, rr1 = 0.f;
+  for (int row = blockIdx.x * rpb + w; row < rend; row += kF512Warps) {
+    const long long p0 = (long long)row * f.W;
+    const float* Q0 = a.Qp + (long long)j0 * N + p0;
+    const float* Q1 = a.Qp + (long long)j1 * N + p0;
+    float* R0 = a.Rr + (long long)j0 * N + p0;
+    float* R1 = a.Rr + (long long)j1 * N + p0;
+    float2 lo[16], hi[16];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      // columns 256 b + 32 qq + l, qq < 8: lo[8 b + qq] for b < 2, hi[8 (b - 2) + qq] after
+      float qa[8], ra[8], qb[8], rb[8];
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) {
+        const int c = 256 * b + 32 * qq + l;
+        qa[qq] = ra[qq] = qb[qq] = rb[qq] = 0.f;
+        if (c < f.W) {
+          if (act0) {
+            qa[qq] = Q0[c];
+            ra[qq] = R0[c];
+          }
+          if (act1) {
+            qb[qq] = Q1[c];
+            rb[qq] = R1[c];
+          }
+        }
+      }
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) {
+        const int c = 256 * b + 32 * qq + l;
+        float2 v = make_float2(0.f, 0.f);
+        if (c < f.W) {
+          if (act0) {
+            v.x = fmaf(-al0, qa[qq], ra[qq]);
+            st_hint_f(R0 + c, v.x, keep);
+            rr0 = fmaf(v.x, v.x, rr0);
+          }
+          if (act1) {
+            v.y = fmaf(-al1, qb[qq], rb[qq]);
+            st_hint_f(R1 + c, v.y, keep);
+            rr1 = fmaf(v.y, v.y, rr1);
+          }
+        }
+        if (b < 2)
+          lo[8 * b + qq] = v;
+        else
+          hi[8 * (b - 2) + qq] = v;
+      }
+    }
+    fft1024_warp(lo, hi, scratch[w], tw, tw2);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) st_hint4(out + (long long)row * (2 * kF) + 64 * m + 2 * l, lo[m], hi[m], keep);
+  }
+  block_sumf<2>(rr0, rr1, 0.f, act0 ? a.part_rr + (long long)j0 * a.nb + blockIdx.x : nullptr,
+                act1 ? a.part_rr + (long long)j1 * a.nb + blockIdx.x : nullptr, nullptr);
+  if (arrive_last(a.arrive + j0, gridDim.x) && threadIdx.x < 32) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!(u ? act1 : act0)) continue;
+      const int j = j0 + u;
+      const double r2 = group_sum(a.part_rr + (long long)j * a.nb, gridDim.x);
+      // the stopping rule of update_kernel
+      if (threadIdx.x == 0) {
+        a.scal[4 * j] = (r2 <= a.thr[j] || r2 > 16.0 * a.rr0[j]) ? 0.f : 1.f;
+        a.scal[4 * j + 2] = alpha_s[u];
+        a.scal[4 * j + 3] = (float)it;
+      }
+    }
+  }
+}
+
 // fft_cols_filter_kernel for HP = 1024: the block stages columns c0 .. c0 + 7 of a pair
 // (rows at and beyond H are zero); each warp transforms one column, filters it with
 // hthT (column-major, [c][i]), writes it back to its slot in natural order and
@@ -2976,7 +3084,10 @@ void precond_apply(LikelihoodState* L, double* rz_buf, bool cg, int first,
   constexpr int kRows512 = kF512Warps * kRowsPerWarp512;
   constexpr int kRows1024 = kF512Warps * kRowsPerWarp1024;
   if (stages & 1) {
-    if (upd)
+    if (upd && fft1024_rows(f))
+      fft1024_update_rows_fwd_kernel<<<dim3((f.H + kRows1024 - 1) / kRows1024, f.pairs),
+                                       32 * kF512Warps, 0, s>>>(f, *upd, it, kRows1024);
+    else if (upd)
       fft512_update_rows_fwd_kernel<<<dim3((f.H + kRows512 - 1) / kRows512, f.pairs),
                                       32 * kF512Warps, 0, s>>>(f, *upd, it, kRows512);
     else if (fft512_rows(f))
@@ -3053,8 +3164,11 @@ void launch_direction(const LikelihoodState* L, const CgArgs& a, int it, cudaStr
 }
 
 // Whether a CG iteration runs its update inside the preconditioner's forward row
-// pass (fft512_update_rows_fwd_kernel) instead of update_kernel.
-inline bool fused_update(const LikelihoodState* L) { return L->fft && fft512_rows(L->fd); }
+// pass (fft512_update_rows_fwd_kernel; for 1024-point rows, which take deferred
+// correction updates only, fft1024_update_rows_fwd_kernel) instead of update_kernel.
+inline bool fused_update(const LikelihoodState* L) {
+  return L->fft && (fft512_rows(L->fd) || (fft1024_rows(L->fd) && pair_direction(L)));
+}
 
 // ---- launch-shape tuning of the FFT preconditioner
 //
